@@ -1,0 +1,122 @@
+/*
+ * rts_oracle.h - FP64 CPU oracle for regional time stepping (RTS) of WCSPH and PCISPH.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, obviously correct restatement of
+ * Goswami & Batty, "Asynchronous Liquids: Regional Time Stepping for Faster SPH and
+ * PCISPH", written from the paper.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header, table or
+ * constant with the CUDA library; both receive the same seeded inputs.
+ *
+ * All arithmetic is IEEE double with round-to-nearest and no contraction
+ * (built with -ffp-contract=off).  Arrays are in the caller's (user) order:
+ * positions, velocities and accelerations are n x 3 doubles.  Discrete decisions
+ * (block index, neighbour predicate, level thresholds) are evaluated exactly on the
+ * stored values, which parity tests fill from FP32 inputs.
+ *
+ * Parity status per function is given next to each declaration:
+ *   pinned   - checked by a -m "not gpu" test against a value fixed independently
+ *              of this code (closed form, brute force, invariant, special case)
+ *   parity unpinned - no independent pin exists (the paper is silent or the figure
+ *              that defines it is missing); self-consistency checks only.
+ */
+#ifndef RTS_ORACLE_H
+#define RTS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_DOMAIN = 2, ORC_ERR_CAPACITY = 5,
+       ORC_ERR_NOT_CONVERGED = 6 };
+
+typedef struct orc_params {
+  int32_t scheme;          /* 0 WCSPH, 1 PCISPH */
+  int32_t mode;            /* 0 regional, 1 global adaptive, 2 global constant */
+  int32_t force_level;     /* -1 classify; >= 0 every filled block takes this level */
+  double s, r, edge;       /* spacing, kernel support radius (= 2h), block edge */
+  double origin[3];
+  int32_t dim[3];
+  double rho0, c_s, gamma, visc_alpha;
+  double g[3];
+  double lambda_v, lambda_f, alpha;
+  int32_t n_levels;
+  int32_t mult[8];         /* dt_L = mult[L] * dt_b */
+  double beta[8];          /* beta for level L (beta[0] = inf) */
+  double dt_b;
+  int32_t max_per_block;
+  /* PCISPH */
+  int32_t n_minor;
+  double eta, eta_T;
+  int32_t max_iters, max_global_iters, max_local_iters;
+  int32_t expand_layers, r1_rings, clean_majors, short_minor;
+  int32_t sched[4][8];     /* correction iterations per region per minor step */
+  int32_t refresh[8];      /* neighbourhood validity per region, minor steps */
+  int32_t max_neighbors;
+} orc_params;
+
+/* WCSPH state in user order. */
+typedef struct orc_wstate {
+  int32_t n, nb;
+  double *x, *v, *a;       /* 3n each; a = held acceleration of the last evaluation */
+  double *rho, *p;         /* n */
+  int32_t *klast;          /* n: substep index of the last evaluation */
+  int32_t *validity;       /* n */
+  int32_t *level;          /* n: particle level (-1 = none yet) */
+  uint8_t *compute;        /* n: output - particle evaluated in the last call */
+  int32_t *nbr;            /* n: neighbours (excluding self) at the last evaluation */
+  const double *xb;        /* 3nb static boundary positions */
+  int32_t *block_level;    /* B: output - level per block (-1 = no fluid) */
+  int64_t k;               /* completed base substeps */
+  int32_t primed;
+} orc_wstate;
+
+/* Cubic-spline (M4) kernel in 3D, support 2h [pinned: normalisation, symmetry]. */
+double orc_kernel_W(double d, double h);
+double orc_kernel_dW(double d, double h);   /* dW/dd */
+
+/* Block grid (Section 3) [pinned: brute-force key/sort check]. */
+int orc_block_key(const orc_params* P, const double* x3, int32_t* key);
+int orc_bin(const orc_params* P, int32_t n, const double* x, int32_t* key,
+            int32_t* perm, int32_t* cstart);
+
+/* Neighbour sets N(i) = { j != i : |x_i - x_j|^2 < r^2 }; fluid j as j, boundary b
+ * as n + b.  offsets has n + 1 entries; idx may be NULL to count only.
+ * [pinned: grid search equals brute force] */
+int64_t orc_neighbors_brute(int32_t n, const double* x, int32_t nb, const double* xb,
+                            double r, int32_t* offsets, int32_t* idx);
+int64_t orc_neighbors_grid(const orc_params* P, int32_t n, const double* x, int32_t nb,
+                           const double* xb, int32_t rings, int32_t* offsets, int32_t* idx);
+
+/* WCSPH density + Tait pressure, and accelerations, for particles with mask[i] != 0
+ * (mask NULL = all) [pinned: rest-lattice density, momentum, hydrostatic column]. */
+int orc_wcsph_density(const orc_params* P, int32_t n, const double* x, int32_t nb,
+                      const double* xb, const uint8_t* mask, double* rho, double* p,
+                      int32_t* nbr);
+int orc_wcsph_accel(const orc_params* P, int32_t n, const double* x, const double* v,
+                    const double* rho, const double* p, int32_t nb, const double* xb,
+                    const uint8_t* mask, double* a_out);
+
+/* Level thresholds of Eq. 1-3 per level [pinned: closed-form table]. */
+void orc_level_thresholds(const orc_params* P, double* vthr2, double* athr2, int32_t* eq1);
+
+/* Block levels: Eq. 1-3 per filled block, then the R_min smoothing (Section 4.2).
+ * raw may be NULL.  [pinned: hand-built level fields] */
+int orc_classify_wcsph(const orc_params* P, int32_t n, const double* x, const double* v,
+                       const double* a, int32_t* raw, int32_t* level);
+
+/* Regional time stepping for WCSPH (Algorithm 1 with the Serna predictor-corrector of
+ * Section 4.1).  evaluate = priming pass at the current time; substep = one dt_b.
+ * [pinned: interpolation identity, forced-finest equals global stepping] */
+int orc_wcsph_evaluate(const orc_params* P, orc_wstate* S);
+int orc_wcsph_substep(const orc_params* P, orc_wstate* S);
+/* Global stepping comparator: one step of mult * dt_b with every particle active.
+ * The multiplier is the finest level over all particles (mode 1) or 1 (mode 2),
+ * capped at max_mult.  [pinned: hydrostatic column, harmonic convergence] */
+int orc_wcsph_global_step(const orc_params* P, orc_wstate* S, int32_t max_mult,
+                          int32_t* mult_used);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,359 @@
+"""Pins of the FP64 CPU oracle (WCSPH part) against values fixed independently of it.
+
+Each test checks the oracle against a closed form, a brute-force enumeration, a
+conservation law or a special case that the paper or the mathematics fixes, chosen
+so that a plausible slip (a dropped term, a wrong sign or index, a swapped operand)
+fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2009_14514_gb300 import scenes
+
+
+def _params(scene, **over):
+    d = dict(scene.params)
+    d.update(over)
+    return O.make_params(d)
+
+
+# ------------------------------------------------------------------- kernel ---
+
+def test_kernel_normalises_to_one_on_fine_lattice():
+    # integral of W over R^3 is 1: lattice sum with h = 10 spacings
+    h, dx = 1.0, 0.1
+    m = int(2 * h / dx) + 1
+    ax = np.arange(-m, m + 1) * dx
+    X, Y, Z = np.meshgrid(ax, ax, ax, indexing="ij")
+    d = np.sqrt(X ** 2 + Y ** 2 + Z ** 2).ravel()
+    d = d[d < 2 * h]
+    total = sum(O.kernel_W(di, h) for di in d) * dx ** 3
+    assert abs(total - 1.0) < 1e-6
+
+
+def test_kernel_shape_closed_form_points():
+    h = 0.7
+    sigma = 1.0 / (math.pi * h ** 3)
+    # q = 0, 1, 2 and a point in each piece, hand-evaluated polynomials
+    assert O.kernel_W(0.0, h) == pytest.approx(sigma, rel=1e-15)
+    assert O.kernel_W(h, h) == pytest.approx(0.25 * sigma, rel=1e-14)
+    assert O.kernel_W(2 * h, h) == 0.0
+    assert O.kernel_W(0.5 * h, h) == pytest.approx(sigma * (1 - 0.375 + 0.09375), rel=1e-14)
+    assert O.kernel_W(1.5 * h, h) == pytest.approx(sigma * 0.25 * 0.125, rel=1e-14)
+    assert O.kernel_dW(0.0, h) == 0.0
+    assert O.kernel_dW(2 * h, h) == 0.0
+
+
+def test_kernel_derivative_matches_finite_difference():
+    h = 0.013
+    for q in np.linspace(0.05, 1.95, 39):
+        d = q * h
+        e = 1e-6 * h
+        fd = (O.kernel_W(d + e, h) - O.kernel_W(d - e, h)) / (2 * e)
+        assert O.kernel_dW(d, h) == pytest.approx(fd, rel=1e-6, abs=1e-9 * abs(fd) + 1e-3)
+
+
+# -------------------------------------------------------------- rest lattice ---
+
+REST_SUM = (1.0 + 1.5 + 3.0 * (2.0 - math.sqrt(2.0)) ** 3 + 2.0 * (2.0 - math.sqrt(3.0)) ** 3) / math.pi
+# Hand enumeration of a cubic lattice at h = s: the point itself (W = 1/pi s^-3),
+# 6 at distance s (q = 1), 12 at sqrt(2) s, 8 at sqrt(3) s; the 6 at 2 s are ties
+# that the predicate excludes and where W vanishes.  REST_SUM = 0.99997247...
+
+
+def _full_box(counts, s):
+    box = tuple(c * s for c in counts)
+    sc = scenes.dam_break(counts, s, box, 1e-4)
+    return sc
+
+
+def test_rest_density_closed_form_including_walls():
+    # dyadic spacing: every lattice coordinate is exact in FP32, so distances are exact
+    sc = _full_box((6, 5, 4), 1.0 / 64)        # fluid fills the box: every particle has a full lattice
+    P = _params(sc)
+    rho, p, nbr = O.density(P, sc.x, sc.xb)
+    expect = float(np.float32(1000.0)) * REST_SUM
+    assert np.max(np.abs(rho / expect - 1.0)) < 1e-12
+    assert np.all(nbr == 26)
+    assert np.all(p == 0.0)                    # rho < rho0 -> clamped Tait pressure
+
+
+def test_rest_density_value_matches_survey_lattice_sum():
+    # 0.999972 quoted for the h = s lattice sum; same enumeration as REST_SUM
+    assert REST_SUM == pytest.approx(0.999972, abs=5e-7)
+
+
+# --------------------------------------------------------------- block grid ---
+
+def test_bin_equals_sort_by_floor_index():
+    sc = scenes.wcsph_dam_break_8k()
+    P = _params(sc)
+    key, perm, cstart = O.bin_particles(P, sc.x)
+    x = sc.x.astype(np.float64)
+    c = np.floor((x - np.asarray(P.origin[:])) / P.edge).astype(np.int64)
+    lin = (c[:, 2] * P.dim[1] + c[:, 1]) * P.dim[0] + c[:, 0]
+    assert np.array_equal(key, lin)
+    assert np.array_equal(perm, np.lexsort((np.arange(len(lin)), lin)))
+    counts = np.bincount(lin, minlength=P.dim[0] * P.dim[1] * P.dim[2])
+    assert np.array_equal(np.diff(cstart), counts)
+
+
+def test_out_of_domain_is_an_error():
+    sc = scenes.wcsph_dam_break_8k()
+    P = _params(sc)
+    x = sc.x.copy()
+    x[17, 0] = -1.0
+    with pytest.raises(O.OracleError):
+        O.bin_particles(P, x)
+
+
+def _sets(off, idx):
+    return [frozenset(idx[off[i]:off[i + 1]].tolist()) for i in range(len(off) - 1)]
+
+
+@pytest.mark.parametrize("jitter", [0.0, 3e-3])
+def test_grid_neighbour_sets_equal_brute_force(jitter):
+    s = 0.02
+    sc = scenes.dam_break((10, 8, 7), s, (0.3, 0.2, 0.2), 1e-4, jitter=jitter, seed=99)
+    P = _params(sc)
+    ob, ib = O.neighbors_brute(sc.x, sc.xb, P.r)
+    og, ig = O.neighbors_grid(P, sc.x, sc.xb, rings=1)
+    assert _sets(ob, ib) == _sets(og, ig)
+
+
+def test_grid_two_ring_search_on_overpopulated_grid():
+    s = 0.01
+    sc = scenes.pool_drop((12, 12, 4), 4, 0.02, s, (0.12, 0.12, 0.12), 3.5e-4, jitter=2e-3, seed=5)
+    P = _params(sc)                             # block edge 2.2 s
+    ob, ib = O.neighbors_brute(sc.x, sc.xb, P.r)
+    for rings in (1, 2):
+        og, ig = O.neighbors_grid(P, sc.x, sc.xb, rings=rings)
+        assert _sets(ob, ib) == _sets(og, ig)
+
+
+# ---------------------------------------------------------------- momentum ---
+
+def test_pressure_and_viscous_forces_conserve_momentum():
+    s = 0.02
+    sc = scenes.dam_break((9, 8, 7), s, (0.4, 0.4, 0.4), 1e-4, jitter=4e-3, seed=3)
+    P = _params(sc, gravity=[0.0, 0.0, 0.0])
+    rng = np.random.default_rng(11)
+    v = rng.normal(0, 0.5, size=(sc.n, 3))
+    rho = 1000.0 * (1 + rng.uniform(-0.02, 0.05, sc.n))
+    prs = rng.uniform(0, 3000.0, sc.n)
+    none = np.zeros((0, 3))
+    a = O.accel(P, sc.x, v, rho, prs, none)
+    m = 1000.0 * s ** 3
+    net = np.abs((m * a).sum(axis=0))
+    scale = np.abs(m * a).sum()
+    assert scale > 0
+    assert np.all(net <= 1e-12 * scale)
+    # the viscous part alone: zero pressure
+    a_v = O.accel(P, sc.x, v, rho, np.zeros(sc.n), none)
+    assert np.all(np.abs((m * a_v).sum(axis=0)) <= 1e-12 * np.abs(m * a_v).sum())
+
+
+def test_pressure_force_pushes_apart_and_viscosity_resists_approach():
+    # two particles on the x axis, 1.5 s apart, no boundary, no gravity
+    s = 0.02
+    sc = scenes.dam_break((1, 1, 1), s, (0.4, 0.4, 0.4), 1e-4)
+    P = _params(sc, gravity=[0.0, 0.0, 0.0])
+    x = np.array([[0.2, 0.2, 0.2], [0.2 + 1.5 * s, 0.2, 0.2]])
+    v = np.zeros((2, 3))
+    a = O.accel(P, x, v, [1000.0, 1000.0], [100.0, 100.0], np.zeros((0, 3)))
+    assert a[0, 0] < 0 < a[1, 0]
+    v = np.array([[1.0, 0, 0], [-1.0, 0, 0]])          # approaching
+    a = O.accel(P, x, v, [1000.0, 1000.0], [0.0, 0.0], np.zeros((0, 3)))
+    assert a[0, 0] < 0 < a[1, 0]
+    v = np.array([[-1.0, 0, 0], [1.0, 0, 0]])          # separating: no artificial viscosity
+    a = O.accel(P, x, v, [1000.0, 1000.0], [0.0, 0.0], np.zeros((0, 3)))
+    assert np.all(a == 0.0)
+
+
+# ------------------------------------------------------------------ levels ---
+
+def test_level_thresholds_closed_form_table():
+    sc = scenes.wcsph_dam_break_1m()
+    P = _params(sc)
+    v2, a2, eq1 = O.level_thresholds(P)
+    # dt_L = 5e-5 * {1, 2, 4, 8}: V <= alpha beta r / dt, |a| <= lambda_f^2 r / dt^2
+    assert math.isinf(v2[0])
+    assert np.sqrt(v2[1:]) == pytest.approx([32.0, 3.2, 0.32], rel=1e-6)
+    assert np.sqrt(a2) == pytest.approx([5.0e5, 1.25e5, 3.125e4, 7812.5], rel=1e-6)
+    assert list(eq1) == [1, 1, 1, 1]           # 8 dt_b = 0.4 r / c_s is the coarsest level
+    # PCISPH: alpha = 1, ladder n dt_b, no sound-speed criterion
+    pc = _params(scenes.pcisph_drop_1m())
+    v2, a2, eq1 = O.level_thresholds(pc)
+    dt = 3.5e-4 * np.arange(1, 5)
+    assert np.sqrt(v2[1:]) == pytest.approx(np.array([0.4, 0.08, 0.016]) * 0.02 / dt[1:], rel=1e-6)
+    assert np.sqrt(a2) == pytest.approx(0.0625 * 0.02 / dt ** 2, rel=1e-6)
+    assert list(eq1) == [1, 1, 1, 1]
+
+
+def _block_field_scene(nb=(7, 7, 7)):
+    # one particle at the centre of each block of an nb^3 region (edge 0.04 m)
+    s = 0.02
+    sc = scenes.dam_break((2 * nb[0], 2 * nb[1], 2 * nb[2]), s,
+                          (2 * nb[0] * s, 2 * nb[1] * s, 2 * nb[2] * s), 1e-4)
+    P = _params(sc)
+    idx = np.stack(np.meshgrid(*[np.arange(k) for k in nb], indexing="ij"), -1).reshape(-1, 3)
+    centres = (idx + 0.5) * P.edge
+    return P, centres
+
+
+def _levels_by_block(P, x, lev):
+    key, _, _ = O.bin_particles(P, x)
+    return lev[key]
+
+
+def test_classify_single_fast_block_spreads_one_layer():
+    P, x = _block_field_scene()
+    n = len(x)
+    v = np.zeros((n, 3))
+    a = np.zeros((n, 3))
+    c = np.argmin(np.abs(x - 3.5 * P.edge).sum(1))          # centre block (3,3,3)
+    v[c, 0] = 20.0                                           # L1 band: 3.2 < V <= 32 at r = 0.04?
+    raw, lev = O.classify_wcsph(P, x, v, a)
+    vthr = np.sqrt(O.level_thresholds(P)[0])
+    Lc = max(L for L in range(4) if 20.0 <= vthr[L])
+    per = _levels_by_block(P, x, lev)
+    cheb = np.abs(np.floor(x / P.edge) - 3).max(axis=1)
+    assert np.all(per[cheb <= 1] == Lc)
+    assert np.all(per[cheb > 1] == 3)
+    assert _levels_by_block(P, x, raw)[c] == Lc
+    assert np.sum(_levels_by_block(P, x, raw) != 3) == 1
+
+
+def test_classify_plane_front_moves_one_layer_and_checkerboard_collapses():
+    P, x = _block_field_scene()
+    n = len(x)
+    bx = np.floor(x[:, 0] / P.edge)
+    a = np.zeros((n, 3))
+    a[bx <= 2, 2] = 1.0e9                                     # fails every level -> level 0
+    raw, lev = O.classify_wcsph(P, x, np.zeros((n, 3)), a)
+    per = _levels_by_block(P, x, lev)
+    assert np.all(per[bx <= 3] == 0) and np.all(per[bx >= 4] == 3)
+    # checkerboard of levels 1 and 3 along x: every block touches a level-1 block
+    v = np.zeros((n, 3))
+    v[(bx % 2) == 0, 1] = 20.0
+    raw, lev = O.classify_wcsph(P, x, v, np.zeros((n, 3)))
+    per = _levels_by_block(P, x, lev)
+    assert len(set(per.tolist())) == 1 and per[0] != 3
+    # forced level overrides classification on filled blocks only
+    P.force_level = 2
+    raw, lev = O.classify_wcsph(P, x, v, np.zeros((n, 3)))
+    assert np.all(_levels_by_block(P, x, lev) == 2)
+    assert np.sum(lev >= 0) == n
+
+
+def test_block_maximum_decides_not_the_mean():
+    P, x = _block_field_scene((3, 3, 3))
+    # add a second, slow particle to the fast block: the block keeps the fast level
+    x2 = np.vstack([x, x[13] + 0.1 * P.edge])
+    v = np.zeros((len(x2), 3))
+    v[13, 0] = 20.0
+    raw, _ = O.classify_wcsph(P, x2, v, np.zeros_like(v))
+    per = _levels_by_block(P, x2, raw)
+    assert per[13] == per[-1] < 3
+
+
+# ---------------------------------------------------------- time stepping ---
+
+def test_serna_substeps_are_pure_interpolation_then_correct():
+    # one isolated particle (no neighbours): held a = A, forced level 3 (8 substeps)
+    s = 0.02
+    sc = scenes.dam_break((1, 1, 1), s, (0.4, 0.4, 0.4), 1e-4)
+    P = _params(sc, force_level=3)
+    x0 = np.array([[0.2, 0.2, 0.2]])
+    v0 = np.array([[0.03, -0.02, 0.01]])
+    A = np.array([[1.5, -2.0, 0.7]])
+    S = O.WCSPH(P, x0, v0, np.zeros((0, 3)), a=A, level=[3], validity=[8], klast=[0],
+                rho=[1000.0], p=[0.0], k=0, primed=True)
+    dt = P.dt_b
+    for k in range(1, 8):
+        S.substep()
+        T = k * dt
+        assert S.compute[0] == 0
+        np.testing.assert_allclose(S.x, x0 + v0 * T + 0.5 * A * T * T, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(S.v, v0 + A * T, rtol=1e-12, atol=1e-15)
+    S.substep()                                  # validity expires: evaluate a = g, correct
+    T = 8 * dt
+    g = np.array([[0.0, 0.0, P.g[2]]])
+    assert S.compute[0] == 1
+    np.testing.assert_allclose(S.x, x0 + v0 * T + 0.5 * A * T * T + (g - A) * T * T / 6,
+                               rtol=1e-12, atol=0)
+    np.testing.assert_allclose(S.v, v0 + A * T + (g - A) * T / 2, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(S.a, g, rtol=0, atol=0)
+    assert S.klast[0] == 8
+
+
+def test_isolated_particle_falls_exactly_under_gravity():
+    # constant acceleration: the correction is a no-op and the fall is exact
+    s = 0.02
+    sc = scenes.dam_break((1, 1, 1), s, (0.4, 0.4, 0.4), 1e-4)
+    P = _params(sc)
+    x0 = np.array([[0.2, 0.2, 0.3]])
+    S = O.WCSPH(P, x0, np.zeros((1, 3)), np.zeros((0, 3)))
+    for _ in range(40):
+        S.substep()
+    T = 40 * P.dt_b
+    np.testing.assert_allclose(S.x[0, 2], 0.3 + 0.5 * P.g[2] * T * T, rtol=1e-13)
+    np.testing.assert_allclose(S.v[0, 2], P.g[2] * T, rtol=1e-12)
+
+
+def test_forced_finest_rts_reproduces_global_stepping_exactly():
+    sc = scenes.wcsph_dam_break_8k()
+    Pr = _params(sc, force_level=0)
+    Pg = _params(sc, mode=2)
+    R = O.WCSPH(Pr, sc.x, sc.v, sc.xb)
+    G = O.WCSPH(Pg, sc.x, sc.v, sc.xb)
+    for _ in range(12):
+        R.substep()
+        assert np.all(R.compute == 1)
+        assert G.global_step() == 1
+    for f in ("x", "v", "a", "rho", "p", "klast"):
+        assert np.array_equal(getattr(R, f), getattr(G, f)), f
+
+
+def test_global_adaptive_takes_finest_level_of_the_whole_fluid():
+    sc = scenes.wcsph_dam_break_8k()
+    P = _params(sc, mode=1)
+    S = O.WCSPH(P, sc.x, sc.v, sc.xb)
+    S.evaluate()
+    S.v[:] = 0.0
+    S.a[:] = 0.0
+    assert S.global_step() == 8                      # at rest: coarsest level
+    S.v[:] = 0.0
+    S.a[:] = 0.0
+    S.v[123, 0] = 5.0                                # one fast particle: V in (3.2, 32] at r = 0.04?
+    vthr = np.sqrt(O.level_thresholds(P)[0])
+    expect = max(L for L in range(4) if 5.0 <= vthr[L])
+    assert S.global_step() == [1, 2, 4, 8][expect]
+    assert S.global_step(max_mult=1) == 1
+
+
+def test_hydrostatic_column_holds_still():
+    # 10 x 10 x 20 column in a 0.2 x 0.2 x 0.6 m tank (s = 0.02), global stepping at dt_b:
+    # settle for 0.5 s with velocities scaled by 0.998 per step (a test-side choice),
+    # then 0.3 s undamped.  Bounds (ours): RMS speed < 0.05 sqrt(g H), centroid drift
+    # < 0.1 s, peak density within the Tait compression of rho0 g H.
+    s = 0.02
+    sc = scenes.dam_break((10, 10, 20), s, (0.2, 0.2, 0.6), 1e-4)
+    P = _params(sc, mode=2)
+    S = O.WCSPH(P, sc.x, sc.v, sc.xb)
+    for _ in range(5000):
+        S.global_step()
+        S.v *= 0.998
+    c0 = S.x.mean(axis=0).copy()
+    H = 20 * s
+    for _ in range(3000):
+        S.global_step()
+    speed = np.linalg.norm(S.v, axis=1)
+    assert np.sqrt(np.mean(speed ** 2)) < 0.05 * math.sqrt(9.81 * H)
+    assert np.linalg.norm(S.x.mean(axis=0) - c0) < 0.1 * s
+    rho, _, _ = O.density(P, S.x, S.xb)
+    assert rho.max() < 1000.0 * 1.05
+    assert S.x[:, 2].min() > 0.0                 # nothing leaks through the floor
