@@ -1,0 +1,188 @@
+/*
+ * rts.h - C ABI of librts: regional time stepping (RTS) for WCSPH and PCISPH on one
+ * GB300 GPU (sm_103a).
+ *
+ * Method: Goswami & Batty, "Asynchronous Liquids: Regional Time Stepping for Faster SPH
+ * and PCISPH".  The library advances fluid particles among static boundary particles.
+ * Particles are binned into a uniform block grid (Section 3); every filled block takes
+ * a time-step level from the maximum velocity and force of its particles (Section 3.1,
+ * Eq. 1-3), smoothed at region borders (R_min, Section 4.2); WCSPH evaluates density,
+ * pressure and forces only for the particles whose true step ends at the current base
+ * substep and integrates everyone with the Serna predictor-corrector (Section 4.1,
+ * Algorithm 1); PCISPH assigns density-correction iterations per region and refreshes
+ * neighbourhoods asynchronously (Section 5, Algorithms 2 and 3).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers to particle arrays may be host or device pointers (unified addressing
+ *    resolves them); they are borrowed for the duration of the call and copied.
+ *    Vectors are n x 3 floats (x, y, z), contiguous, in the caller's particle order.
+ *  - All work is enqueued on the CUDA stream given to rts_init (borrowed; 0 = legacy
+ *    default stream).  Calls that return data to the caller synchronise that stream.
+ *  - Every call returns an rts_status and never throws or aborts.  Argument errors are
+ *    returned at once.  Errors found on the device (particle outside the grid, block
+ *    over capacity, PCISPH non-convergence) are recorded in a device status word and
+ *    returned by the next call that synchronises (rts_sync, rts_advance, rts_get_*).
+ *    Such an error is sticky: later stepping calls return RTS_ERR_STATE until
+ *    rts_set_state installs a new state.  rts_last_error gives a message.
+ *  - The context owns all its device memory (allocated in rts_init, freed by
+ *    rts_destroy).  Internally particles are kept in block order; rts_get_state
+ *    returns the caller's order.
+ */
+#ifndef RTS_H
+#define RTS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rts_status {
+  RTS_OK = 0,
+  RTS_ERR_ARG = 1,            /* invalid argument (returned before any work)            */
+  RTS_ERR_DOMAIN = 2,         /* a particle left the block grid, or a NaN position       */
+  RTS_ERR_CUDA = 3,           /* a CUDA runtime call failed                              */
+  RTS_ERR_OOM = 4,            /* device allocation failed                                */
+  RTS_ERR_CAPACITY = 5,       /* a block exceeded max_per_block, or a neighbour list
+                                 exceeded max_neighbors                                  */
+  RTS_ERR_NOT_CONVERGED = 6,  /* PCISPH: a minor step hit max_iters (state is advanced)  */
+  RTS_ERR_TIMEOUT = 7,        /* a bounded device wait gave up                           */
+  RTS_ERR_STATE = 8           /* an earlier device error is pending; call rts_set_state  */
+} rts_status;
+
+enum { RTS_WCSPH = 0, RTS_PCISPH = 1 };
+
+/* mode: regional time stepping (the paper's method), or a global comparator in which
+ * every particle is active every step: adaptive (the finest level that Eq. 1-3 give for
+ * the whole fluid) or constant (dt_b). */
+enum { RTS_MODE_REGIONAL = 0, RTS_MODE_GLOBAL_ADAPTIVE = 1, RTS_MODE_GLOBAL_CONSTANT = 2 };
+
+/* Parameters (Sections 3-6).  Lengths in metres, times in seconds, SI throughout. */
+typedef struct rts_params {
+  int32_t scheme;            /* RTS_WCSPH or RTS_PCISPH                                   */
+  int32_t mode;              /* RTS_MODE_*                                                */
+  int32_t force_level;       /* -1: classify blocks; >= 0: every filled block takes this
+                                level (test hook: 0 reproduces global stepping at dt_b)   */
+  float spacing;             /* s, initial particle spacing                               */
+  float support_r;           /* r, kernel support radius (= 2h of the cubic spline)       */
+  float block_edge;          /* block edge: r for WCSPH (Section 3), 2.2 s for PCISPH
+                                (Section 5.6); must be >= support_r                       */
+  float domain_min[3];       /* grid origin                                               */
+  int32_t grid_dim[3];       /* blocks per axis; the grid spans domain_min + dim * edge   */
+  float rho0, c_s, gamma, visc_alpha;   /* rest density, sound speed, Tait exponent,
+                                           artificial viscosity alpha                    */
+  float gravity[3];
+  float lambda_v, lambda_f, alpha;      /* Eq. 1, Eq. 2, Eq. 3 coefficients               */
+  int32_t n_levels;          /* number of levels (<= 8)                                    */
+  int32_t level_mult[8];     /* dt of level L = level_mult[L] * dt_b (increasing)          */
+  float beta[8];             /* beta of level L in Eq. 3 (beta[0] = +inf)                  */
+  float dt_b;                /* base (smallest) step                                       */
+  int32_t max_per_block;     /* block capacity (fluid particles per block), <= 1024        */
+  /* PCISPH (Section 5) */
+  int32_t n_minor;           /* minor steps per major step (N = 4)                         */
+  float eta;                 /* allowed density error (relative), 0.01                     */
+  float eta_T;               /* average-error threshold for global extra iterations        */
+  int32_t max_iters;         /* iteration cap per minor step                               */
+  int32_t max_global_iters;  /* global iterations after which major steps are shortened    */
+  int32_t max_local_iters;   /* local iterations before reverting to global                */
+  int32_t expand_layers;     /* dilation of regions 1 and 2 (4 blocks)                     */
+  int32_t r1_search_rings;   /* neighbour search rings for region 1 (2)                    */
+  int32_t clean_majors;      /* clean major steps before the major step is restored (10)   */
+  int32_t short_minor;       /* minor steps of a shortened major step (2)                  */
+  int32_t sched[4][8];       /* correction iterations of region n in minor step j          */
+  int32_t refresh[8];        /* neighbourhood validity of region n, in minor steps         */
+  int32_t max_neighbors;     /* PCISPH neighbour list capacity per particle                */
+} rts_params;
+
+/* Counters accumulated over one rts_advance call. */
+typedef struct rts_stats {
+  int64_t substeps;          /* base substeps (dt_b) advanced                              */
+  int64_t steps;             /* calls of the step kernel sequence (global steps may span
+                                several substeps)                                          */
+  int64_t particle_evals;    /* particles whose density and acceleration were evaluated   */
+  int64_t pair_interactions; /* neighbour pairs (d < r) of those evaluations               */
+  int64_t active_blocks;     /* sum over steps of blocks with an evaluated particle        */
+  int64_t level_count[8];    /* fluid particles per level at the end of the call           */
+  int64_t pcisph_iterations; /* density-correction iterations                              */
+  int64_t pcisph_local_iterations;
+  int64_t pcisph_global_restarts;
+  double t_sim;              /* simulated time at the end of the call                      */
+} rts_stats;
+
+typedef struct rts_ctx rts_ctx;
+
+/* Create a context.  x, v: n_fluid x 3 positions and velocities; xb: n_boundary x 3
+ * static boundary positions.  The state starts unprimed: accelerations, validity and
+ * levels are zero, and the first stepping call first evaluates every particle at the
+ * current time (Section 4.1 needs an acceleration to predict with).
+ * Errors: RTS_ERR_ARG (bad sizes or parameters), RTS_ERR_OOM, RTS_ERR_CUDA,
+ * RTS_ERR_DOMAIN (a boundary particle outside the grid). */
+rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, const float* v,
+                    int32_t n_boundary, const float* xb, void* cuda_stream, rts_ctx** out);
+
+/* Section 3: bin the fluid particles at their current positions into the block grid
+ * (sorted by block, then by the caller's particle index). */
+rts_status rts_bin(rts_ctx* ctx);
+
+/* Section 3.1 and 4.2: block maxima of |v| and |a|, level per filled block from
+ * Eq. 1-3, then the R_min smoothing (or force_level).  Uses the current bins. */
+rts_status rts_classify_blocks(rts_ctx* ctx);
+
+/* Evaluate density, pressure and acceleration of every fluid particle at the current
+ * state, without advancing time (the priming evaluation of the Serna scheme): bins,
+ * classifies, sets every particle's level and validity from its block, the held
+ * acceleration to the new one and the last-evaluation substep to the current one. */
+rts_status rts_evaluate(rts_ctx* ctx);
+
+/* One WCSPH base substep dt_b (Algorithm 1, Section 4.1): predict all particles, bin,
+ * classify, decrement validity and pre-empt on a level change, evaluate the active
+ * particles against every particle's predicted state, correct the active particles.
+ * In a global mode, one global step of mult * dt_b instead (see rts_advance). */
+rts_status rts_wcsph_substep(rts_ctx* ctx);
+
+/* One PCISPH minor step dt_b (Algorithm 2 with Algorithm 3 for density correction).
+ * Region assignment, grid and neighbourhood refresh happen at major-step starts. */
+rts_status rts_pcisph_step(rts_ctx* ctx);
+
+/* Advance to simulated time t_sim (rounded to whole base substeps) with the context's
+ * scheme and mode; synchronises.  out may be NULL. */
+rts_status rts_advance(rts_ctx* ctx, double t_sim, rts_stats* out);
+
+/* Copy the state out in the caller's order.  Any pointer may be NULL.  x, v, a are
+ * n x 3; level, validity, klast, nbr are n int32; compute is n bytes (1 = evaluated by
+ * the last step).  a is the held acceleration; nbr the neighbour count (excluding the
+ * particle itself) at the last evaluation.  Synchronises. */
+rts_status rts_get_state(rts_ctx* ctx, float* x, float* v, float* a, float* rho, float* p,
+                         int32_t* level, int32_t* validity, int32_t* klast, int32_t* nbr,
+                         uint8_t* compute);
+
+/* Install a state (caller's order).  x, v required; the others may be NULL (then zero,
+ * rho0 for rho).  k: completed base substeps; primed: 0 = evaluate before the next
+ * step.  Clears a pending device error. */
+rts_status rts_set_state(rts_ctx* ctx, const float* x, const float* v, const float* a,
+                         const float* rho, const float* p, const int32_t* level,
+                         const int32_t* validity, const int32_t* klast, int64_t k,
+                         int32_t primed);
+
+/* Bins of the last rts_bin / step: key (block id of each particle, caller's order),
+ * perm (caller's index of the particle at each sorted position), cstart (n_blocks + 1
+ * exclusive prefix of the block counts).  Any pointer may be NULL.  Synchronises. */
+rts_status rts_get_bins(rts_ctx* ctx, int32_t* key, int32_t* perm, int32_t* cstart);
+
+/* Block levels of the last classification (n_blocks int32, -1 = no fluid): raw from
+ * Eq. 1-3, level after R_min smoothing (and, for PCISPH, region expansion).
+ * Any pointer may be NULL.  Synchronises. */
+rts_status rts_get_blocks(rts_ctx* ctx, int32_t* raw, int32_t* level);
+
+/* Wait for the stream; return a pending device error, if any. */
+rts_status rts_sync(rts_ctx* ctx);
+
+int64_t rts_num_blocks(const rts_ctx* ctx);
+int64_t rts_substep_index(const rts_ctx* ctx);   /* completed base substeps */
+const char* rts_last_error(const rts_ctx* ctx);  /* never NULL; ctx may be NULL */
+rts_status rts_destroy(rts_ctx* ctx);            /* NULL is a no-op */
+
+#ifdef __cplusplus
+}
+#endif
+#endif

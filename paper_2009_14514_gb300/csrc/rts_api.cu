@@ -1,0 +1,629 @@
+// rts_api.cu - the C ABI of librts (declared in rts.h): context set-up, parameter
+// validation, caller-order I/O and the step sequences of Algorithm 1 (WCSPH) and of
+// the global comparators.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rts_internal.cuh"
+
+using namespace rts;
+
+static char g_noctx_err[512] = "";
+
+const char* rts::cuda_err(rts_ctx* c, cudaError_t e, const char* what) {
+  char* dst = c ? c->err : g_noctx_err;
+  snprintf(dst, 512, "%s: %s", what, cudaGetErrorString(e));
+  return dst;
+}
+
+static rts_status fail(rts_ctx* c, rts_status st, const char* msg) {
+  snprintf(c ? c->err : g_noctx_err, 512, "%s", msg);
+  return st;
+}
+
+#define CK(expr)                                       \
+  do {                                                 \
+    cudaError_t _e = (expr);                           \
+    if (_e != cudaSuccess) {                           \
+      rts::cuda_err(c, _e, #expr);                     \
+      return _e == cudaErrorMemoryAllocation ? RTS_ERR_OOM : RTS_ERR_CUDA; \
+    }                                                  \
+  } while (0)
+
+namespace rts {
+int neighbor_grid_size();
+}
+
+// ------------------------------------------------------------- parameters ---
+
+static void level_thresholds(const rts_params& p, double* vthr2, double* athr2, int* eq1) {
+  // Eq. 1: dt <= lambda_v r / c_s (WCSPH only).  Eq. 2 with F = m |a|, squared twice:
+  // |a|^2 <= (lambda_f^2 r / dt^2)^2.  Eq. 3: |v|^2 <= (alpha beta r / dt)^2.
+  for (int L = 0; L < p.n_levels; ++L) {
+    double dt = (double)p.level_mult[L] * (double)p.dt_b;
+    double vt = (double)p.alpha * (double)p.beta[L] * (double)p.support_r / dt;
+    vthr2[L] = vt * vt;
+    double at = (double)p.lambda_f * (double)p.lambda_f * (double)p.support_r / (dt * dt);
+    athr2[L] = at * at;
+    eq1[L] = p.scheme == RTS_WCSPH
+                 ? (dt <= (double)p.lambda_v * (double)p.support_r / (double)p.c_s)
+                 : 1;
+  }
+}
+
+static const char* validate(const rts_params* p, int32_t n, int32_t nb) {
+  if (!p) return "params is NULL";
+  if (p->scheme != RTS_WCSPH && p->scheme != RTS_PCISPH) return "scheme must be RTS_WCSPH or RTS_PCISPH";
+  if (p->mode < 0 || p->mode > 2) return "mode must be 0, 1 or 2";
+  if (n < 0 || nb < 0) return "negative particle count";
+  if (!(p->spacing > 0.f) || !(p->support_r > 0.f) || !(p->block_edge > 0.f))
+    return "spacing, support_r and block_edge must be positive";
+  if (p->block_edge < p->support_r) return "block_edge must be >= support_r";
+  for (int d = 0; d < 3; ++d) {
+    if (p->grid_dim[d] < 1 || p->grid_dim[d] > 4096) return "grid_dim must be in [1, 4096]";
+    if (!std::isfinite(p->domain_min[d]) || !std::isfinite(p->gravity[d])) return "non-finite domain_min or gravity";
+  }
+  if ((double)p->grid_dim[0] * p->grid_dim[1] * p->grid_dim[2] > 2.0e9) return "too many blocks";
+  if (p->n_levels < 1 || p->n_levels > kMaxLevels) return "n_levels must be in [1, 8]";
+  for (int L = 0; L < p->n_levels; ++L) {
+    if (p->level_mult[L] < 1) return "level_mult must be >= 1";
+    if (L > 0 && p->level_mult[L] <= p->level_mult[L - 1]) return "level_mult must increase";
+    if (!(p->beta[L] > 0.f)) return "beta must be positive";
+  }
+  if (p->force_level >= p->n_levels) return "force_level must be < n_levels";
+  if (!(p->dt_b > 0.f)) return "dt_b must be positive";
+  if (p->max_per_block < 1 || p->max_per_block > 1024) return "max_per_block must be in [1, 1024]";
+  if (!(p->rho0 > 0.f) || !(p->c_s > 0.f) || !(p->gamma > 0.f) || !(p->visc_alpha >= 0.f))
+    return "rho0, c_s, gamma must be positive and visc_alpha non-negative";
+  if (!(p->lambda_f > 0.f) || !(p->alpha > 0.f) || !(p->lambda_v > 0.f)) return "lambda_v, lambda_f, alpha must be positive";
+  if (p->scheme == RTS_PCISPH) {
+    if (p->n_minor < 1 || p->n_minor > 8) return "n_minor must be in [1, 8]";
+    if (p->n_levels > 4) return "PCISPH uses at most 4 regions";
+    if (p->max_iters < 1 || p->max_neighbors < 8 || p->max_neighbors > 1024) return "bad PCISPH iteration or neighbour limits";
+  }
+  return nullptr;
+}
+
+static void make_dev_params(const rts_params& p, DevParams& d) {
+  memset(&d, 0, sizeof(d));
+  d.ox = p.domain_min[0];
+  d.oy = p.domain_min[1];
+  d.oz = p.domain_min[2];
+  d.edge = p.block_edge;
+  d.inv_edge = 1.0f / p.block_edge;
+  d.oxd = d.ox;
+  d.oyd = d.oy;
+  d.ozd = d.oz;
+  d.edged = d.edge;
+  d.nx = p.grid_dim[0];
+  d.ny = p.grid_dim[1];
+  d.nz = p.grid_dim[2];
+  d.nblocks = d.nx * d.ny * d.nz;
+  d.max_per_block = p.max_per_block;
+  d.r = p.support_r;
+  d.r2 = p.support_r * p.support_r;
+  d.r2d = (double)p.support_r * (double)p.support_r;
+  d.r2_lo = (float)(d.r2d * (1.0 - 1e-5));
+  d.r2_hi = (float)(d.r2d * (1.0 + 1e-5));
+  double h = 0.5 * (double)p.support_r;
+  double sigma = 1.0 / (M_PI * h * h * h);
+  d.h = (float)h;
+  d.inv_h = (float)(1.0 / h);
+  d.sigma = (float)sigma;
+  d.sigma_h = (float)(sigma / h);
+  double s = p.spacing;
+  d.m = (float)((double)p.rho0 * s * s * s);
+  d.rho0 = p.rho0;
+  d.inv_rho0 = (float)(1.0 / (double)p.rho0);
+  d.tait_B = (float)((double)p.c_s * p.c_s * p.rho0 / p.gamma);
+  d.gamma = p.gamma;
+  d.gamma_is_7 = p.gamma == 7.0f;
+  d.visc_coef = (float)(2.0 * p.visc_alpha * h * p.c_s);
+  d.eps_h2 = (float)(0.01 * h * h);
+  d.gx = p.gravity[0];
+  d.gy = p.gravity[1];
+  d.gz = p.gravity[2];
+  d.n_levels = p.n_levels;
+  for (int L = 0; L < p.n_levels; ++L) d.mult[L] = p.level_mult[L];
+  level_thresholds(p, d.vthr2, d.athr2, d.eq1);
+  d.force_level = p.force_level;
+  d.dt_b = p.dt_b;
+}
+
+// ------------------------------------------------------------ caller I/O ---
+
+__global__ void k_pack3(int n, const float* __restrict__ in, float4* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float4(in[3 * i], in[3 * i + 1], in[3 * i + 2], 0.f);
+}
+
+__global__ void k_in_vec(int n, const float* __restrict__ in, float4* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    float4 o = out[i];
+    out[i] = in ? make_float4(in[3 * i], in[3 * i + 1], in[3 * i + 2], o.w)
+                : make_float4(0.f, 0.f, 0.f, o.w);
+  }
+}
+
+template <class T>
+__global__ void k_in_scalar(int n, const T* __restrict__ in, T* __restrict__ out, T dflt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in ? in[i] : dflt;
+}
+
+// Identity order after an upload; x.w = p / rho^2, v.w = rho.
+__global__ void k_finish_in(int n, PState s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    float rho = s.rho[i];
+    s.x[i].w = s.prs[i] / (rho * rho);
+    s.v[i].w = rho;
+    s.uid[i] = (uint32_t)i;
+    s.nbr[i] = 0;
+  }
+}
+
+__global__ void k_out_vec(int n, const uint32_t* __restrict__ uid, const float4* __restrict__ in,
+                          float* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    uint32_t u = uid[i];
+    float4 q = in[i];
+    out[3 * u] = q.x;
+    out[3 * u + 1] = q.y;
+    out[3 * u + 2] = q.z;
+  }
+}
+
+template <class T>
+__global__ void k_out_scalar(int n, const uint32_t* __restrict__ uid, const T* __restrict__ in,
+                             T* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[uid[i]] = in[i];
+}
+
+static inline int nblk(int n) { return (n + 255) / 256; }
+
+static rts_status upload_state(rts_ctx* c, const float* x, const float* v, const float* a,
+                               const float* rho, const float* p, const int32_t* level,
+                               const int32_t* validity, const int32_t* klast) {
+  int n = c->n;
+  if (n == 0) return RTS_OK;
+  size_t v3 = sizeof(float) * 3 * (size_t)n, s1 = sizeof(float) * (size_t)n;
+  float* io = c->io;
+  int g = nblk(n);
+  // scalars first: x.w and v.w are derived from rho and p
+  if (rho) CK(cudaMemcpyAsync(io, rho, s1, cudaMemcpyDefault, c->stream));
+  k_in_scalar<float><<<g, 256, 0, c->stream>>>(n, rho ? io : nullptr, c->s.rho, c->p.rho0);
+  if (p) CK(cudaMemcpyAsync(io, p, s1, cudaMemcpyDefault, c->stream));
+  k_in_scalar<float><<<g, 256, 0, c->stream>>>(n, p ? io : nullptr, c->s.prs, 0.0f);
+  int32_t* ii = c->io_i;
+  if (level) CK(cudaMemcpyAsync(ii, level, s1, cudaMemcpyDefault, c->stream));
+  k_in_scalar<int32_t><<<g, 256, 0, c->stream>>>(n, level ? ii : nullptr, c->s.level, -1);
+  if (validity) CK(cudaMemcpyAsync(ii, validity, s1, cudaMemcpyDefault, c->stream));
+  k_in_scalar<int32_t><<<g, 256, 0, c->stream>>>(n, validity ? ii : nullptr, c->s.valid, 0);
+  if (klast) CK(cudaMemcpyAsync(ii, klast, s1, cudaMemcpyDefault, c->stream));
+  k_in_scalar<int32_t><<<g, 256, 0, c->stream>>>(n, klast ? ii : nullptr, c->s.klast, 0);
+  CK(cudaMemcpyAsync(io, x, v3, cudaMemcpyDefault, c->stream));
+  k_in_vec<<<g, 256, 0, c->stream>>>(n, io, c->s.x);
+  CK(cudaMemcpyAsync(io, v, v3, cudaMemcpyDefault, c->stream));
+  k_in_vec<<<g, 256, 0, c->stream>>>(n, io, c->s.v);
+  if (a) CK(cudaMemcpyAsync(io, a, v3, cudaMemcpyDefault, c->stream));
+  k_in_vec<<<g, 256, 0, c->stream>>>(n, a ? io : nullptr, c->s.a);
+  k_finish_in<<<g, 256, 0, c->stream>>>(n, c->s);
+  CK(cudaGetLastError());
+  // the staging buffers are reused by the next call: finish before returning
+  CK(cudaStreamSynchronize(c->stream));
+  return RTS_OK;
+}
+
+// --------------------------------------------------------------- status ---
+
+static rts_status sync_status(rts_ctx* c) {
+  CK(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  int st = c->h_ctl->status;
+  if (st != 0 && st != RTS_ERR_NOT_CONVERGED) {
+    c->sticky = st;
+    const char* what = st == RTS_ERR_DOMAIN     ? "a particle left the block grid (or is NaN)"
+                       : st == RTS_ERR_CAPACITY ? "a block or neighbour list exceeded its capacity"
+                       : st == RTS_ERR_TIMEOUT  ? "a bounded device wait gave up"
+                                                : "device error";
+    snprintf(c->err, sizeof c->err, "device status %d: %s", st, what);
+    return (rts_status)st;
+  }
+  return (rts_status)st;
+}
+
+// --------------------------------------------------------- WCSPH stepping ---
+
+static rts_status wcsph_evaluate(rts_ctx* c) {
+  launch_bin(c, 0.0f);
+  launch_classify(c);
+  launch_activity(c, kActAll, 0, 0);
+  launch_density_force(c);
+  launch_correct(c, c->k, 1);
+  c->primed = 1;
+  c->bins_valid = 1;
+  CK(cudaGetLastError());
+  return RTS_OK;
+}
+
+static rts_status wcsph_regional(rts_ctx* c) {
+  int64_t k1 = c->k + 1;
+  launch_bin(c, c->p.dt_b);
+  launch_classify(c);
+  launch_activity(c, kActRegional, 0, 0);
+  launch_density_force(c);
+  launch_correct(c, k1, 0);
+  c->k = k1;
+  c->bins_valid = 1;
+  CK(cudaGetLastError());
+  return RTS_OK;
+}
+
+static int host_pick_level(const rts_ctx* c, double v2, double a2) {
+  int L = 0;
+  for (int l = 0; l < c->dp.n_levels; ++l)
+    if (c->dp.eq1[l] && v2 <= c->dp.vthr2[l] && a2 <= c->dp.athr2[l]) L = l;
+  return L;
+}
+
+static rts_status wcsph_global(rts_ctx* c, int64_t max_mult) {
+  int L = 0;
+  if (c->p.mode == RTS_MODE_GLOBAL_ADAPTIVE) {
+    launch_global_max(c);
+    CK(cudaMemcpyAsync(&c->h_ctl->vmax2_bits, &c->ctl->vmax2_bits, 2 * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double v2, a2;
+    memcpy(&v2, &c->h_ctl->vmax2_bits, sizeof v2);
+    memcpy(&a2, &c->h_ctl->amax2_bits, sizeof a2);
+    L = host_pick_level(c, v2, a2);
+  }
+  int64_t m = c->p.level_mult[L];
+  if (m > max_mult) m = max_mult;
+  if (m < 1) m = 1;
+  int64_t k1 = c->k + m;
+  launch_bin(c, (float)m * c->p.dt_b);
+  launch_activity(c, kActGlobal, L, (int)m);
+  launch_density_force(c);
+  launch_correct(c, k1, 0);
+  c->k = k1;
+  c->bins_valid = 1;
+  CK(cudaGetLastError());
+  return RTS_OK;
+}
+
+static rts_status wcsph_step(rts_ctx* c, int64_t max_mult) {
+  rts_status st;
+  if (!c->primed && (st = wcsph_evaluate(c)) != RTS_OK) return st;
+  if (c->p.mode == RTS_MODE_REGIONAL) return wcsph_regional(c);
+  return wcsph_global(c, max_mult);
+}
+
+// ================================================================ C ABI ===
+
+extern "C" {
+
+rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, const float* v,
+                    int32_t n_boundary, const float* xb, void* cuda_stream, rts_ctx** out) {
+  if (!out) return fail(nullptr, RTS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (const char* why = validate(params, n_fluid, n_boundary)) return fail(nullptr, RTS_ERR_ARG, why);
+  if (n_fluid > 0 && (!x || !v)) return fail(nullptr, RTS_ERR_ARG, "x and v are required");
+  if (n_boundary > 0 && !xb) return fail(nullptr, RTS_ERR_ARG, "xb is required");
+  rts_ctx* c = new (std::nothrow) rts_ctx;
+  if (!c) return fail(nullptr, RTS_ERR_OOM, "host allocation failed");
+  memset(c, 0, sizeof(*c));
+  c->p = *params;
+  make_dev_params(c->p, c->dp);
+  c->stream = (cudaStream_t)cuda_stream;
+  c->n = n_fluid;
+  c->nb = n_boundary;
+  int n1 = n_fluid > 0 ? n_fluid : 1;
+  size_t nbk = (size_t)c->dp.nblocks;
+  c->ntiles = (int)((nbk + 2047) / 2048);
+  rts_status st = RTS_OK;
+#define ALLOC(ptr, bytes)                                                    \
+  do {                                                                       \
+    cudaError_t _e = cudaMalloc((void**)&(ptr), (bytes));                    \
+    if (_e != cudaSuccess) {                                                 \
+      rts::cuda_err(c, _e, "cudaMalloc " #ptr);                              \
+      st = RTS_ERR_OOM;                                                      \
+      goto fail_alloc;                                                       \
+    }                                                                        \
+  } while (0)
+  {
+    size_t f4 = sizeof(float4) * n1, f1 = sizeof(float) * n1, u1 = sizeof(uint32_t) * n1;
+    PState* ss[2] = {&c->s, &c->s2};
+    for (PState* s : ss) {
+      ALLOC(s->x, f4);
+      ALLOC(s->v, f4);
+      ALLOC(s->a, f4);
+      ALLOC(s->rho, f1);
+      ALLOC(s->prs, f1);
+      ALLOC(s->uid, u1);
+      ALLOC(s->klast, u1);
+      ALLOC(s->valid, u1);
+      ALLOC(s->level, u1);
+      ALLOC(s->nbr, u1);
+    }
+    ALLOC(c->anew, f4);
+    ALLOC(c->cflag, (size_t)n1);
+    ALLOC(c->key, u1);
+    ALLOC(c->key_tmp, u1);
+    ALLOC(c->slot, u1);
+    ALLOC(c->tmp_uid, u1);
+    ALLOC(c->tmp_src, u1);
+    ALLOC(c->io, sizeof(float) * 4 * (size_t)n1);
+    ALLOC(c->io_i, u1);
+    ALLOC(c->count, sizeof(uint32_t) * nbk);
+    ALLOC(c->cstart, sizeof(uint32_t) * (nbk + 1));
+    ALLOC(c->bcstart, sizeof(uint32_t) * (nbk + 1));
+    ALLOC(c->tile_sums, sizeof(uint32_t) * (size_t)c->ntiles);
+    ALLOC(c->raw, nbk);
+    ALLOC(c->blevel, nbk);
+    ALLOC(c->act, sizeof(uint32_t) * nbk);
+    ALLOC(c->ctl, sizeof(Ctl));
+    ALLOC(c->xb, sizeof(float4) * (size_t)(n_boundary > 0 ? n_boundary : 1));
+    if (cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl)) != cudaSuccess) {
+      st = fail(c, RTS_ERR_OOM, "pinned host allocation failed");
+      goto fail_alloc;
+    }
+  }
+#undef ALLOC
+  {
+    cudaError_t e = cudaMemsetAsync(c->count, 0, sizeof(uint32_t) * nbk, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->raw, 0xff, nbk, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->blevel, 0xff, nbk, c->stream);
+    if (e != cudaSuccess) {
+      rts::cuda_err(c, e, "initial memset");
+      st = RTS_ERR_CUDA;
+      goto fail_alloc;
+    }
+  }
+  c->grid_persistent = neighbor_grid_size();
+  if (n_boundary > 0) {
+    float *tmp3 = nullptr;
+    float4* tmp4 = nullptr;
+    size_t b3 = sizeof(float) * 3 * (size_t)n_boundary;
+    cudaError_t e = cudaMalloc((void**)&tmp3, b3);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&tmp4, sizeof(float4) * (size_t)n_boundary);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp3, xb, b3, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) {
+      k_pack3<<<nblk(n_boundary), 256, 0, c->stream>>>(n_boundary, tmp3, tmp4);
+      st = launch_bin_boundary(c, tmp4, n_boundary);
+    }
+    cudaFree(tmp3);
+    cudaFree(tmp4);
+    if (e != cudaSuccess) {
+      rts::cuda_err(c, e, "boundary upload");
+      st = RTS_ERR_CUDA;
+    }
+    if (st != RTS_OK) goto fail_alloc;
+    st = sync_status(c);
+    if (st != RTS_OK) goto fail_alloc;
+  } else {
+    cudaMemsetAsync(c->bcstart, 0, sizeof(uint32_t) * (nbk + 1), c->stream);
+  }
+  if (n_fluid > 0) {
+    st = upload_state(c, x, v, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (st != RTS_OK) goto fail_alloc;
+  }
+  c->k = 0;
+  c->primed = 0;
+  c->bins_valid = 0;
+  *out = c;
+  return RTS_OK;
+fail_alloc:
+  if (c->err[0]) snprintf(g_noctx_err, sizeof g_noctx_err, "%s", c->err);
+  rts_destroy(c);
+  return st;
+}
+
+rts_status rts_destroy(rts_ctx* c) {
+  if (!c) return RTS_OK;
+  cudaStreamSynchronize(c->stream);
+  PState* ss[2] = {&c->s, &c->s2};
+  for (PState* s : ss) {
+    cudaFree(s->x); cudaFree(s->v); cudaFree(s->a); cudaFree(s->rho); cudaFree(s->prs);
+    cudaFree(s->uid); cudaFree(s->klast); cudaFree(s->valid); cudaFree(s->level); cudaFree(s->nbr);
+  }
+  cudaFree(c->anew); cudaFree(c->cflag); cudaFree(c->key); cudaFree(c->key_tmp); cudaFree(c->slot);
+  cudaFree(c->tmp_uid); cudaFree(c->tmp_src); cudaFree(c->io); cudaFree(c->io_i);
+  cudaFree(c->count); cudaFree(c->cstart); cudaFree(c->bcstart); cudaFree(c->tile_sums);
+  cudaFree(c->raw); cudaFree(c->blevel); cudaFree(c->act); cudaFree(c->ctl); cudaFree(c->xb);
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  delete c;
+  return RTS_OK;
+}
+
+const char* rts_last_error(const rts_ctx* c) { return c ? c->err : g_noctx_err; }
+
+int64_t rts_num_blocks(const rts_ctx* c) { return c ? (int64_t)c->dp.nblocks : 0; }
+
+int64_t rts_substep_index(const rts_ctx* c) { return c ? c->k : 0; }
+
+rts_status rts_sync(rts_ctx* c) {
+  if (!c) return fail(nullptr, RTS_ERR_ARG, "ctx is NULL");
+  return sync_status(c);
+}
+
+#define GUARD()                                                                  \
+  do {                                                                           \
+    if (!c) return fail(nullptr, RTS_ERR_ARG, "ctx is NULL");                    \
+    if (c->sticky) return fail(c, RTS_ERR_STATE, "a device error is pending; call rts_set_state"); \
+  } while (0)
+
+rts_status rts_bin(rts_ctx* c) {
+  GUARD();
+  launch_bin(c, 0.0f);
+  c->bins_valid = 1;
+  CK(cudaGetLastError());
+  return RTS_OK;
+}
+
+rts_status rts_classify_blocks(rts_ctx* c) {
+  GUARD();
+  if (!c->bins_valid) launch_bin(c, 0.0f);
+  c->bins_valid = 1;
+  launch_classify(c);
+  CK(cudaGetLastError());
+  return RTS_OK;
+}
+
+rts_status rts_evaluate(rts_ctx* c) {
+  GUARD();
+  if (c->p.scheme != RTS_WCSPH) return fail(c, RTS_ERR_ARG, "rts_evaluate is the WCSPH evaluation");
+  return wcsph_evaluate(c);
+}
+
+rts_status rts_wcsph_substep(rts_ctx* c) {
+  GUARD();
+  if (c->p.scheme != RTS_WCSPH) return fail(c, RTS_ERR_ARG, "context was created for PCISPH");
+  return wcsph_step(c, (int64_t)1 << 40);
+}
+
+rts_status rts_advance(rts_ctx* c, double t_sim, rts_stats* out) {
+  GUARD();
+  if (!std::isfinite(t_sim)) return fail(c, RTS_ERR_ARG, "t_sim must be finite");
+  int64_t K = llround(t_sim / (double)c->p.dt_b);
+  CK(cudaMemsetAsync(&c->ctl->evals, 0, 3 * sizeof(unsigned long long), c->stream));
+  int64_t k0 = c->k, steps = 0;
+  rts_status st = RTS_OK;
+  while (c->k < K) {
+    if (c->p.scheme == RTS_WCSPH) {
+      st = wcsph_step(c, K - c->k);
+    } else {
+      st = rts_pcisph_step(c);
+    }
+    if (st != RTS_OK && st != RTS_ERR_NOT_CONVERGED) return st;
+    ++steps;
+  }
+  launch_level_hist(c);
+  rts_status ds = sync_status(c);
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->substeps = c->k - k0;
+    out->steps = steps;
+    out->particle_evals = (int64_t)c->h_ctl->evals;
+    out->pair_interactions = (int64_t)c->h_ctl->pairs;
+    out->active_blocks = (int64_t)c->h_ctl->act_blocks;
+    for (int L = 0; L < kMaxLevels; ++L) out->level_count[L] = (int64_t)c->h_ctl->level_count[L];
+    out->t_sim = (double)c->k * (double)c->p.dt_b;
+  }
+  return ds;
+}
+
+rts_status rts_get_state(rts_ctx* c, float* x, float* v, float* a, float* rho, float* p,
+                         int32_t* level, int32_t* validity, int32_t* klast, int32_t* nbr,
+                         uint8_t* compute) {
+  if (!c) return fail(nullptr, RTS_ERR_ARG, "ctx is NULL");
+  int n = c->n;
+  if (n == 0) return sync_status(c);
+  int g = nblk(n);
+  size_t v3 = sizeof(float) * 3 * (size_t)n, s1 = sizeof(float) * (size_t)n;
+  const float4* vecs[3] = {c->s.x, c->s.v, c->s.a};
+  float* vdst[3] = {x, v, a};
+  for (int k = 0; k < 3; ++k) {
+    if (!vdst[k]) continue;
+    k_out_vec<<<g, 256, 0, c->stream>>>(n, c->s.uid, vecs[k], c->io);
+    CK(cudaMemcpyAsync(vdst[k], c->io, v3, cudaMemcpyDefault, c->stream));
+  }
+  const float* fs[2] = {c->s.rho, c->s.prs};
+  float* fdst[2] = {rho, p};
+  for (int k = 0; k < 2; ++k) {
+    if (!fdst[k]) continue;
+    k_out_scalar<float><<<g, 256, 0, c->stream>>>(n, c->s.uid, fs[k], c->io);
+    CK(cudaMemcpyAsync(fdst[k], c->io, s1, cudaMemcpyDefault, c->stream));
+  }
+  const int32_t* is[4] = {c->s.level, c->s.valid, c->s.klast, c->s.nbr};
+  int32_t* idst[4] = {level, validity, klast, nbr};
+  for (int k = 0; k < 4; ++k) {
+    if (!idst[k]) continue;
+    k_out_scalar<int32_t><<<g, 256, 0, c->stream>>>(n, c->s.uid, is[k], c->io_i);
+    CK(cudaMemcpyAsync(idst[k], c->io_i, s1, cudaMemcpyDefault, c->stream));
+  }
+  if (compute) {
+    k_out_scalar<uint8_t><<<g, 256, 0, c->stream>>>(n, c->s.uid, c->cflag, (uint8_t*)c->io_i);
+    CK(cudaMemcpyAsync(compute, c->io_i, (size_t)n, cudaMemcpyDefault, c->stream));
+  }
+  CK(cudaGetLastError());
+  return sync_status(c);
+}
+
+rts_status rts_set_state(rts_ctx* c, const float* x, const float* v, const float* a,
+                         const float* rho, const float* p, const int32_t* level,
+                         const int32_t* validity, const int32_t* klast, int64_t k,
+                         int32_t primed) {
+  if (!c) return fail(nullptr, RTS_ERR_ARG, "ctx is NULL");
+  if (c->n > 0 && (!x || !v)) return fail(c, RTS_ERR_ARG, "x and v are required");
+  if (k < 0) return fail(c, RTS_ERR_ARG, "k must be >= 0");
+  rts_status st = upload_state(c, x, v, a, rho, p, level, validity, klast);
+  if (st != RTS_OK) return st;
+  CK(cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream));
+  CK(cudaMemsetAsync(c->cflag, 0, (size_t)(c->n > 0 ? c->n : 1), c->stream));
+  c->sticky = 0;
+  c->k = k;
+  c->primed = primed ? 1 : 0;
+  c->err[0] = 0;
+  launch_bin(c, 0.0f);
+  c->bins_valid = 1;
+  return sync_status(c);
+}
+
+rts_status rts_get_bins(rts_ctx* c, int32_t* key, int32_t* perm, int32_t* cstart) {
+  if (!c) return fail(nullptr, RTS_ERR_ARG, "ctx is NULL");
+  rts_status st = sync_status(c);
+  if (st != RTS_OK) return st;
+  int n = c->n;
+  size_t nbk = (size_t)c->dp.nblocks;
+  std::vector<uint32_t> hk(n), hu(n);
+  if (n > 0) {
+    CK(cudaMemcpy(hk.data(), c->key, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hu.data(), c->s.uid, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+  }
+  if (key) {
+    std::vector<int32_t> ku(n);
+    for (int f = 0; f < n; ++f) ku[hu[f]] = (int32_t)hk[f];
+    CK(cudaMemcpy(key, ku.data(), sizeof(int32_t) * n, cudaMemcpyDefault));
+  }
+  if (perm) CK(cudaMemcpy(perm, hu.data(), sizeof(int32_t) * n, cudaMemcpyDefault));
+  if (cstart) CK(cudaMemcpy(cstart, c->cstart, sizeof(uint32_t) * (nbk + 1), cudaMemcpyDefault));
+  return RTS_OK;
+}
+
+rts_status rts_get_blocks(rts_ctx* c, int32_t* raw, int32_t* level) {
+  if (!c) return fail(nullptr, RTS_ERR_ARG, "ctx is NULL");
+  rts_status st = sync_status(c);
+  if (st != RTS_OK) return st;
+  size_t nbk = (size_t)c->dp.nblocks;
+  std::vector<int8_t> h(nbk);
+  std::vector<int32_t> w(nbk);
+  const int8_t* src[2] = {c->raw, c->blevel};
+  int32_t* dst[2] = {raw, level};
+  for (int k = 0; k < 2; ++k) {
+    if (!dst[k]) continue;
+    CK(cudaMemcpy(h.data(), src[k], nbk, cudaMemcpyDeviceToHost));
+    for (size_t b = 0; b < nbk; ++b) w[b] = h[b];
+    CK(cudaMemcpy(dst[k], w.data(), sizeof(int32_t) * nbk, cudaMemcpyDefault));
+  }
+  return RTS_OK;
+}
+
+rts_status rts_pcisph_step(rts_ctx* c) {
+  GUARD();
+  if (c->p.scheme != RTS_PCISPH) return fail(c, RTS_ERR_ARG, "context was created for WCSPH");
+  return fail(c, RTS_ERR_ARG, "PCISPH stepping is not available in this build");
+}
+
+}  // extern "C"

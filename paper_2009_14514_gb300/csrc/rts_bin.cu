@@ -1,0 +1,275 @@
+// rts_bin.cu - block grid binning (Section 3): every particle lies in exactly one block
+// of a uniform grid; particles are kept sorted by block so that a block and its x
+// neighbours are one contiguous range.
+//
+// Sort: counting sort on the block id.  An atomic per-block counter gives each
+// particle a slot, an exclusive scan of the counts gives the block starts, and a
+// rank pass orders each block's particles by the caller's index, so the sorted order
+// is canonical (block, caller index) and independent of atomic arrival order.  The
+// WCSPH predictor (Section 4.1) is fused into the key pass.
+#include <cuda_runtime.h>
+
+#include "rts_internal.cuh"
+
+namespace rts {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Block coordinate floor((x - o) / edge).  The FP32 value is within 1e-3 block of the
+// exact one for grids up to 4096 blocks per axis; within 2e-3 of an integer the FP64
+// quotient decides, so the result is that of the double-precision definition.
+__device__ __forceinline__ int block_coord(float x, float o, double od, float inv_e, double ed,
+                                           int n, int* bad) {
+  float t = (x - o) * inv_e;
+  float f = floorf(t);
+  float fr = t - f;
+  double fd;
+  if (fr < 2e-3f || fr > 0.998f)
+    fd = floor(__ddiv_rn(__dsub_rn((double)x, od), ed));
+  else
+    fd = (double)f;
+  if (!(fd >= 0.0 && fd < (double)n)) {
+    *bad = 1;
+    return 0;
+  }
+  return (int)fd;
+}
+
+__device__ __forceinline__ uint32_t block_key(const DevParams& P, float4 p, int* bad) {
+  int cx = block_coord(p.x, P.ox, P.oxd, P.inv_edge, P.edged, P.nx, bad);
+  int cy = block_coord(p.y, P.oy, P.oyd, P.inv_edge, P.edged, P.ny, bad);
+  int cz = block_coord(p.z, P.oz, P.ozd, P.inv_edge, P.edged, P.nz, bad);
+  return ((uint32_t)cz * P.ny + cy) * P.nx + cx;
+}
+
+// Predict (dt != 0: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt), then key and slot.
+__global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4* __restrict__ v,
+                              const float4* __restrict__ a, float dt, uint32_t* __restrict__ key,
+                              uint32_t* __restrict__ slot, uint32_t* __restrict__ count, Ctl* ctl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 xi = x[i];
+  if (dt != 0.0f) {
+    float4 vi = v[i];
+    float4 ai = a[i];
+    float hdt2 = 0.5f * dt * dt;
+    xi.x = xi.x + vi.x * dt + ai.x * hdt2;
+    xi.y = xi.y + vi.y * dt + ai.y * hdt2;
+    xi.z = xi.z + vi.z * dt + ai.z * hdt2;
+    vi.x = vi.x + ai.x * dt;
+    vi.y = vi.y + ai.y * dt;
+    vi.z = vi.z + ai.z * dt;
+    x[i] = xi;
+    v[i] = vi;
+  }
+  int bad = 0;
+  uint32_t b = block_key(P, xi, &bad);
+  if (bad) {
+    set_status(ctl, RTS_ERR_DOMAIN);
+    b = 0;
+  }
+  key[i] = b;
+  slot[i] = atomicAdd(&count[b], 1u);
+}
+
+// ---- exclusive scan of the per-block counts (reduce, scan tile sums, apply) ----
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan of one value per thread across the CTA; returns the CTA total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_tot[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = warp_incl_scan(v);
+  if (lane == 31) warp_tot[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < nw ? warp_tot[lane] : 0u;
+    uint32_t ti = warp_incl_scan(t);
+    if (lane < nw) warp_tot[lane] = ti - t;
+    if (lane == nw - 1) warp_tot[31] = ti;
+  }
+  __syncthreads();
+  uint32_t res = inc - v + warp_tot[w];
+  *total = warp_tot[31];
+  __syncthreads();
+  return res;
+}
+
+__global__ void k_scan_reduce(const uint32_t* __restrict__ count, int nb, uint32_t* tile_sums) {
+  int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < nb) s += count[base + k];
+  uint32_t tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_tiles(uint32_t* tile_sums, int ntiles) {
+  uint32_t carry = 0;
+  for (int base = 0; base < ntiles; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    uint32_t v = i < ntiles ? tile_sums[i] : 0u;
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(v, &tot);
+    if (i < ntiles) tile_sums[i] = ex + carry;
+    carry += tot;
+  }
+}
+
+// cstart[i] = exclusive prefix of count; count is reset to zero for the next binning.
+__global__ void k_scan_apply(uint32_t* __restrict__ count, int nb, const uint32_t* __restrict__ tile_sums,
+                             uint32_t* __restrict__ cstart) {
+  int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  uint32_t c[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    c[k] = (base + k < nb) ? count[base + k] : 0u;
+    s += c[k];
+  }
+  uint32_t tot;
+  uint32_t ex = block_excl_scan(s, &tot) + tile_sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < nb) {
+      cstart[base + k] = ex;
+      count[base + k] = 0u;
+    }
+    ex += c[k];
+  }
+  // the thread holding the last element writes the grand total
+  if (base <= nb - 1 && nb - 1 < base + kScanItems) cstart[nb] = ex;
+}
+
+__global__ void k_scatter(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ slot,
+                          const uint32_t* __restrict__ uid, const uint32_t* __restrict__ cstart,
+                          uint32_t* __restrict__ tkey, uint32_t* __restrict__ tuid,
+                          uint32_t* __restrict__ tsrc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t b = key[i];
+  uint32_t q = cstart[b] + slot[i];
+  tkey[q] = b;
+  tuid[q] = uid[i];
+  tsrc[q] = (uint32_t)i;
+}
+
+// Order each block's particles by caller index and move every field to its place.
+__global__ void k_canon_gather(int n, int max_per_block, const uint32_t* __restrict__ cstart,
+                               const uint32_t* __restrict__ tkey, const uint32_t* __restrict__ tuid,
+                               const uint32_t* __restrict__ tsrc, PState src, PState dst,
+                               uint32_t* __restrict__ key_out, Ctl* ctl) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  uint32_t b = tkey[q];
+  uint32_t beg = cstart[b], end = cstart[b + 1];
+  if (q == (int)beg && (int)(end - beg) > max_per_block) set_status(ctl, RTS_ERR_CAPACITY);
+  uint32_t u = tuid[q];
+  uint32_t rank = 0;
+  for (uint32_t r = beg; r < end; ++r) rank += (tuid[r] < u) ? 1u : 0u;
+  uint32_t f = beg + rank;
+  uint32_t s = tsrc[q];
+  key_out[f] = b;
+  dst.uid[f] = u;
+  dst.x[f] = src.x[s];
+  if (src.v) {
+    dst.v[f] = src.v[s];
+    dst.a[f] = src.a[s];
+    dst.rho[f] = src.rho[s];
+    dst.prs[f] = src.prs[s];
+    dst.klast[f] = src.klast[s];
+    dst.valid[f] = src.valid[s];
+    dst.level[f] = src.level[s];
+    dst.nbr[f] = src.nbr[s];
+  }
+}
+
+static rts_status scan_counts(rts_ctx* c) {
+  int nb = c->dp.nblocks;
+  int ntiles = (nb + kScanTile - 1) / kScanTile;
+  k_scan_reduce<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums);
+  k_scan_tiles<<<1, 1024, 0, c->stream>>>(c->tile_sums, ntiles);
+  k_scan_apply<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums, c->cstart);
+  return RTS_OK;
+}
+
+rts_status launch_bin(rts_ctx* c, float dt) {
+  int n = c->n;
+  if (n == 0) {
+    cudaMemsetAsync(c->cstart, 0, sizeof(uint32_t) * ((size_t)c->dp.nblocks + 1), c->stream);
+    return RTS_OK;
+  }
+  int tb = 256, g = (n + tb - 1) / tb;
+  k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, n, c->s.x, c->s.v, c->s.a, dt, c->key, c->slot,
+                                          c->count, c->ctl);
+  scan_counts(c);
+  k_scatter<<<g, tb, 0, c->stream>>>(n, c->key, c->slot, c->s.uid, c->cstart, c->key_tmp,
+                                      c->tmp_uid, c->tmp_src);
+  k_canon_gather<<<g, tb, 0, c->stream>>>(n, c->dp.max_per_block, c->cstart, c->key_tmp,
+                                           c->tmp_uid, c->tmp_src, c->s, c->s2, c->key, c->ctl);
+  PState t = c->s;
+  c->s = c->s2;
+  c->s2 = t;
+  return RTS_OK;
+}
+
+// Boundary particles are static: sort them once by (block, index) into xb / bcstart.
+__global__ void k_iota(int n, uint32_t* u) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) u[i] = (uint32_t)i;
+}
+
+rts_status launch_bin_boundary(rts_ctx* c, const float4* xb_unsorted, int nb) {
+  if (nb == 0) {
+    cudaMemsetAsync(c->bcstart, 0, sizeof(uint32_t) * ((size_t)c->dp.nblocks + 1), c->stream);
+    return RTS_OK;
+  }
+  uint32_t *key, *slot, *tkey, *tuid, *tsrc, *uid, *uid2;
+  size_t sz = sizeof(uint32_t) * (size_t)nb;
+  cudaError_t e = cudaSuccess;
+  uint32_t** bufs[] = {&key, &slot, &tkey, &tuid, &tsrc, &uid, &uid2};
+  for (auto b : bufs)
+    if (e == cudaSuccess) e = cudaMalloc((void**)b, sz);
+  if (e != cudaSuccess) {
+    cuda_err(c, e, "boundary binning buffers");
+    return RTS_ERR_OOM;
+  }
+  int tb = 256, g = (nb + tb - 1) / tb;
+  k_iota<<<g, tb, 0, c->stream>>>(nb, uid);
+  k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, nb, const_cast<float4*>(xb_unsorted), nullptr,
+                                          nullptr, 0.0f, key, slot, c->count, c->ctl);
+  uint32_t* save = c->cstart;
+  c->cstart = c->bcstart;
+  scan_counts(c);
+  c->cstart = save;
+  k_scatter<<<g, tb, 0, c->stream>>>(nb, key, slot, uid, c->bcstart, tkey, tuid, tsrc);
+  PState src{}, dst{};
+  src.x = const_cast<float4*>(xb_unsorted);
+  src.uid = uid;
+  dst.x = c->xb;
+  dst.uid = uid2;
+  k_canon_gather<<<g, tb, 0, c->stream>>>(nb, 1 << 30, c->bcstart, tkey, tuid, tsrc, src, dst, key,
+                                           c->ctl);
+  e = cudaStreamSynchronize(c->stream);
+  for (auto b : bufs) cudaFree(*b);
+  if (e != cudaSuccess) {
+    cuda_err(c, e, "boundary binning");
+    return RTS_ERR_CUDA;
+  }
+  return RTS_OK;
+}
+
+}  // namespace rts

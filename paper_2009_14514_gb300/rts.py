@@ -1,0 +1,340 @@
+"""Thin ctypes binding of librts (the C ABI in include/rts.h), same names as the ABI.
+
+Argument marshalling only: every step of the method runs in the CUDA library.  Arrays
+may be numpy arrays (host) or torch tensors (host or CUDA); vectors are (n, 3) float32
+in the caller's particle order.  The stream defaults to torch's current CUDA stream.
+If the library cannot be loaded, every call raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RTS_OK = 0
+STATUS_NAMES = {
+    0: "RTS_OK", 1: "RTS_ERR_ARG", 2: "RTS_ERR_DOMAIN", 3: "RTS_ERR_CUDA", 4: "RTS_ERR_OOM",
+    5: "RTS_ERR_CAPACITY", 6: "RTS_ERR_NOT_CONVERGED", 7: "RTS_ERR_TIMEOUT", 8: "RTS_ERR_STATE",
+}
+EXPORTED = [
+    "rts_init", "rts_bin", "rts_classify_blocks", "rts_evaluate", "rts_wcsph_substep",
+    "rts_pcisph_step", "rts_advance", "rts_get_state", "rts_set_state", "rts_get_bins",
+    "rts_get_blocks", "rts_sync", "rts_num_blocks", "rts_substep_index", "rts_last_error",
+    "rts_destroy",
+]
+
+
+class RtsError(RuntimeError):
+    def __init__(self, status, what, msg):
+        self.status = status
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+class RtsParams(C.Structure):
+    _fields_ = [
+        ("scheme", C.c_int32), ("mode", C.c_int32), ("force_level", C.c_int32),
+        ("spacing", C.c_float), ("support_r", C.c_float), ("block_edge", C.c_float),
+        ("domain_min", C.c_float * 3), ("grid_dim", C.c_int32 * 3),
+        ("rho0", C.c_float), ("c_s", C.c_float), ("gamma", C.c_float), ("visc_alpha", C.c_float),
+        ("gravity", C.c_float * 3),
+        ("lambda_v", C.c_float), ("lambda_f", C.c_float), ("alpha", C.c_float),
+        ("n_levels", C.c_int32), ("level_mult", C.c_int32 * 8), ("beta", C.c_float * 8),
+        ("dt_b", C.c_float), ("max_per_block", C.c_int32),
+        ("n_minor", C.c_int32), ("eta", C.c_float), ("eta_T", C.c_float),
+        ("max_iters", C.c_int32), ("max_global_iters", C.c_int32), ("max_local_iters", C.c_int32),
+        ("expand_layers", C.c_int32), ("r1_search_rings", C.c_int32),
+        ("clean_majors", C.c_int32), ("short_minor", C.c_int32),
+        ("sched", (C.c_int32 * 8) * 4), ("refresh", C.c_int32 * 8),
+        ("max_neighbors", C.c_int32),
+    ]
+
+
+class RtsStats(C.Structure):
+    _fields_ = [
+        ("substeps", C.c_int64), ("steps", C.c_int64), ("particle_evals", C.c_int64),
+        ("pair_interactions", C.c_int64), ("active_blocks", C.c_int64),
+        ("level_count", C.c_int64 * 8), ("pcisph_iterations", C.c_int64),
+        ("pcisph_local_iterations", C.c_int64), ("pcisph_global_restarts", C.c_int64),
+        ("t_sim", C.c_double),
+    ]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "level_count"}
+        d["level_count"] = list(self.level_count)
+        return d
+
+
+def make_params(d: dict) -> RtsParams:
+    P = RtsParams()
+    P.scheme = int(d["scheme"])
+    P.mode = int(d.get("mode", 0))
+    P.force_level = int(d.get("force_level", -1))
+    P.spacing = d["spacing"]
+    P.support_r = d["support_r"]
+    P.block_edge = d["block_edge"]
+    for k in range(3):
+        P.domain_min[k] = d["domain_min"][k]
+        P.grid_dim[k] = int(d["grid_dim"][k])
+        P.gravity[k] = d["gravity"][k]
+    for f in ("rho0", "c_s", "gamma", "visc_alpha", "lambda_v", "lambda_f", "alpha", "dt_b",
+              "eta", "eta_T"):
+        setattr(P, f, float(d[f]))
+    P.n_levels = int(d["n_levels"])
+    for L in range(min(8, len(d["level_mult"]))):
+        P.level_mult[L] = int(d["level_mult"][L])
+        P.beta[L] = float(d["beta"][L])
+    for f in ("max_per_block", "n_minor", "max_iters", "max_global_iters", "max_local_iters",
+              "expand_layers", "r1_search_rings", "clean_majors", "short_minor", "max_neighbors"):
+        setattr(P, f, int(d[f]))
+    for n in range(4):
+        for j in range(len(d["sched"][n])):
+            P.sched[n][j] = int(d["sched"][n][j])
+    for L in range(len(d["refresh"])):
+        P.refresh[L] = int(d["refresh"][L])
+    return P
+
+
+_LIB = None
+
+
+def lib():
+    """Load librts (building it in-tree if needed).  Raises if that fails."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build() if not os.environ.get("RTS_NO_BUILD") else _build.LIB
+        L = C.CDLL(path)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        sig = {
+            "rts_init": [vp, i32, vp, vp, i32, vp, vp, vp],
+            "rts_bin": [vp], "rts_classify_blocks": [vp], "rts_evaluate": [vp],
+            "rts_wcsph_substep": [vp], "rts_pcisph_step": [vp],
+            "rts_advance": [vp, C.c_double, vp],
+            "rts_get_state": [vp] * 11,
+            "rts_set_state": [vp] * 9 + [i64, i32],
+            "rts_get_bins": [vp] * 4, "rts_get_blocks": [vp] * 3, "rts_sync": [vp],
+            "rts_destroy": [vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.rts_last_error.argtypes = [vp]
+        L.rts_last_error.restype = C.c_char_p
+        L.rts_num_blocks.argtypes = [vp]
+        L.rts_num_blocks.restype = i64
+        L.rts_substep_index.argtypes = [vp]
+        L.rts_substep_index.restype = i64
+        _LIB = L
+    return _LIB
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+# ------------------------------------------------------------- marshalling ---
+
+def _ptr(a):
+    """Pointer of a numpy array or torch tensor (contiguous), or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _f32(a, n, width=3):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, np.float32)
+    elif hasattr(a, "dtype"):
+        import torch
+        if a.dtype != torch.float32:
+            raise TypeError("tensors must be float32")
+    shape = tuple(a.shape)
+    want = (n, width) if width > 1 else (n,)
+    if shape != want and not (width > 1 and n == 0):
+        raise ValueError(f"expected shape {want}, got {shape}")
+    return a
+
+
+def _i32(a, n):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, np.int32)
+    if tuple(a.shape) != (n,):
+        raise ValueError(f"expected shape ({n},), got {tuple(a.shape)}")
+    return a
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return C.c_void_p(0)
+
+
+class Ctx:
+    """Owner of an rts_ctx handle (destroyed on close / garbage collection)."""
+
+    def __init__(self, handle, params, n, nb):
+        self.handle = handle
+        self.params = params
+        self.n = n
+        self.nb = nb
+
+    def close(self):
+        if self.handle:
+            lib().rts_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_blocks(self):
+        return lib().rts_num_blocks(self.handle)
+
+    @property
+    def substep_index(self):
+        return lib().rts_substep_index(self.handle)
+
+
+def _check(st, what, ctx=None):
+    if st != RTS_OK:
+        h = ctx.handle if isinstance(ctx, Ctx) else None
+        msg = lib().rts_last_error(h)
+        raise RtsError(st, what, msg.decode() if msg else "")
+    return st
+
+
+# ------------------------------------------------------------------- calls ---
+
+def rts_init(params, x, v, xb, stream=None) -> Ctx:
+    P = params if isinstance(params, RtsParams) else make_params(params)
+    n = int(x.shape[0])
+    nb = int(xb.shape[0])
+    x, v, xb = _f32(x, n), _f32(v, n), _f32(xb, nb)
+    h = C.c_void_p()
+    st = lib().rts_init(C.byref(P), n, _ptr(x), _ptr(v), nb, _ptr(xb), _stream(stream), C.byref(h))
+    _check(st, "rts_init")
+    return Ctx(h, P, n, nb)
+
+
+def rts_bin(ctx):
+    return _check(lib().rts_bin(ctx.handle), "rts_bin", ctx)
+
+
+def rts_classify_blocks(ctx):
+    return _check(lib().rts_classify_blocks(ctx.handle), "rts_classify_blocks", ctx)
+
+
+def rts_evaluate(ctx):
+    return _check(lib().rts_evaluate(ctx.handle), "rts_evaluate", ctx)
+
+
+def rts_wcsph_substep(ctx):
+    return _check(lib().rts_wcsph_substep(ctx.handle), "rts_wcsph_substep", ctx)
+
+
+def rts_pcisph_step(ctx, allow_not_converged=True):
+    st = lib().rts_pcisph_step(ctx.handle)
+    if allow_not_converged and st == 6:
+        return st
+    return _check(st, "rts_pcisph_step", ctx)
+
+
+def rts_advance(ctx, t_sim, allow_not_converged=True) -> dict:
+    s = RtsStats()
+    st = lib().rts_advance(ctx.handle, float(t_sim), C.byref(s))
+    if not (allow_not_converged and st == 6):
+        _check(st, "rts_advance", ctx)
+    return s.as_dict()
+
+
+def rts_sync(ctx, allow_not_converged=True):
+    st = lib().rts_sync(ctx.handle)
+    if allow_not_converged and st == 6:
+        return st
+    return _check(st, "rts_sync", ctx)
+
+
+def rts_get_state(ctx, fields=("x", "v", "a", "rho", "p", "level", "validity", "klast", "nbr",
+                               "compute")) -> dict:
+    """State in the caller's order as numpy arrays (host)."""
+    n = ctx.n
+    out = {}
+    spec = {"x": (np.float32, 3), "v": (np.float32, 3), "a": (np.float32, 3),
+            "rho": (np.float32, 1), "p": (np.float32, 1), "level": (np.int32, 1),
+            "validity": (np.int32, 1), "klast": (np.int32, 1), "nbr": (np.int32, 1),
+            "compute": (np.uint8, 1)}
+    for f in fields:
+        dt, w = spec[f]
+        out[f] = np.zeros((n, 3) if w == 3 else (n,), dt)
+    args = [_ptr(out.get(f)) for f in ("x", "v", "a", "rho", "p", "level", "validity", "klast",
+                                      "nbr", "compute")]
+    _check(lib().rts_get_state(ctx.handle, *args), "rts_get_state", ctx)
+    return out
+
+
+def rts_get_state_into(ctx, x=None, v=None, a=None, rho=None, p=None):
+    """Copy state into caller-provided buffers (numpy or torch, host or device)."""
+    _check(lib().rts_get_state(ctx.handle, _ptr(x), _ptr(v), _ptr(a), _ptr(rho), _ptr(p),
+                               None, None, None, None, None), "rts_get_state", ctx)
+
+
+def rts_set_state(ctx, x, v, a=None, rho=None, p=None, level=None, validity=None, klast=None,
+                  k=0, primed=False):
+    n = ctx.n
+    x, v, a = _f32(x, n), _f32(v, n), _f32(a, n)
+    rho, p = _f32(rho, n, 1), _f32(p, n, 1)
+    level, validity, klast = _i32(level, n), _i32(validity, n), _i32(klast, n)
+    st = lib().rts_set_state(ctx.handle, _ptr(x), _ptr(v), _ptr(a), _ptr(rho), _ptr(p),
+                             _ptr(level), _ptr(validity), _ptr(klast), int(k), 1 if primed else 0)
+    return _check(st, "rts_set_state", ctx)
+
+
+def rts_get_bins(ctx):
+    n = ctx.n
+    B = ctx.num_blocks
+    key = np.zeros(n, np.int32)
+    perm = np.zeros(n, np.int32)
+    cstart = np.zeros(B + 1, np.int32)
+    _check(lib().rts_get_bins(ctx.handle, _ptr(key), _ptr(perm), _ptr(cstart)), "rts_get_bins", ctx)
+    return key, perm, cstart
+
+
+def rts_get_blocks(ctx):
+    B = ctx.num_blocks
+    raw = np.zeros(B, np.int32)
+    lev = np.zeros(B, np.int32)
+    _check(lib().rts_get_blocks(ctx.handle, _ptr(raw), _ptr(lev)), "rts_get_blocks", ctx)
+    return raw, lev
+
+
+def rts_destroy(ctx):
+    ctx.close()
+
+
+def rts_last_error(ctx=None) -> str:
+    h = ctx.handle if isinstance(ctx, Ctx) else None
+    return lib().rts_last_error(h).decode()

@@ -1,0 +1,294 @@
+"""GPU parity of the WCSPH regional-time-stepping path against the FP64 oracle.
+
+Every test drives the CUDA library through its C ABI and the oracle with the same seeded
+input state.  Bins, neighbour counts, block levels, activity flags: bit-exact.  Density:
+1e-4 relative.  Accelerations: 1e-3 of the max-norm.  Positions and velocities after a
+substep: the consequences of those bounds (plus FP32 rounding of the predictor).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from common import ACC_FRAC, RHO_RTOL, dynamic_state, gpu_ctx, max_norm, oracle_state, params, ulp32
+from paper_2009_14514_gb300 import rts, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _levels_by_particle(P, x, block_levels):
+    key, _, _ = O.bin_particles(P, x)
+    return block_levels[key]
+
+
+# ------------------------------------------------------------------- binning ---
+
+@pytest.mark.parametrize("which", ["jittered", "dyadic_on_block_faces", "ragged_37"])
+def test_bins_are_bit_exact(which):
+    if which == "jittered":
+        sc = scenes.wcsph_dam_break_8k()
+        x = sc.x
+    elif which == "dyadic_on_block_faces":
+        # spacing 1/64, edge 1/32: half the particles sit exactly on block faces
+        sc = scenes.dam_break((12, 10, 9), 1.0 / 64, (0.5, 0.25, 0.25), 1e-4)
+        x = (sc.x - np.float32(0.5 / 64)).astype(np.float32)
+    else:
+        sc = scenes.dam_break((37, 1, 1), 0.02, (0.8, 0.4, 0.4), 1e-4, jitter=3e-3, seed=4)
+        x = sc.x
+    P = O.make_params(sc.params)
+    ctx = gpu_ctx(sc, x=x)
+    rts.rts_bin(ctx)
+    key, perm, cstart = rts.rts_get_bins(ctx)
+    okey, operm, ocstart = O.bin_particles(P, x)
+    assert np.array_equal(key, okey)
+    assert np.array_equal(perm, operm)
+    assert np.array_equal(cstart, ocstart)
+
+
+# ------------------------------------------------------------ classification ---
+
+@pytest.mark.parametrize("force_level", [-1, 2])
+def test_block_levels_are_bit_exact(force_level):
+    sc = scenes.wcsph_dam_break_8k()
+    st = dynamic_state(sc, seed=21)
+    d = params(sc, force_level=force_level)
+    P = O.make_params(d)
+    ctx = gpu_ctx(sc, d)
+    rts.rts_set_state(ctx, st["x"], st["v"], a=st["a"])
+    rts.rts_classify_blocks(ctx)
+    raw, lev = rts.rts_get_blocks(ctx)
+    oraw, olev = O.classify_wcsph(P, st["x"], st["v"], st["a"])
+    assert np.array_equal(raw, oraw)
+    assert np.array_equal(lev, olev)
+    if force_level < 0:
+        assert len(set(oraw[oraw >= 0].tolist())) == 4        # every level occurs
+
+
+# ----------------------------------------------------------------- evaluation ---
+
+def _check_eval(g, o, mask=None):
+    m = np.ones(len(o.rho), bool) if mask is None else mask
+    assert np.array_equal(g["nbr"][m], o.nbr[m])
+    np.testing.assert_allclose(g["rho"][m], o.rho[m], rtol=RHO_RTOL, atol=0)
+    tol = ACC_FRAC * max_norm(o.a[m])
+    err = np.linalg.norm(g["a"][m].astype(np.float64) - o.a[m], axis=1)
+    assert err.max() <= tol, (err.max(), tol)
+
+
+def test_evaluate_density_neighbours_forces_match_oracle():
+    sc = scenes.wcsph_dam_break_8k()
+    st = dynamic_state(sc, seed=5)
+    ctx = gpu_ctx(sc)
+    rts.rts_set_state(ctx, st["x"], st["v"], a=st["a"], rho=st["rho"], p=st["p"])
+    rts.rts_evaluate(ctx)
+    g = rts.rts_get_state(ctx)
+    o = oracle_state(sc, sc.params, st)
+    o.evaluate()
+    _check_eval(g, o)
+    assert np.array_equal(g["level"], o.level)
+    assert np.array_equal(g["validity"], o.validity)
+    assert np.all(g["compute"] == 1) and np.all(g["klast"] == 0)
+    # positions and velocities are untouched by the priming evaluation
+    assert np.array_equal(g["x"], st["x"]) and np.array_equal(g["v"], st["v"])
+
+
+def test_rest_lattice_density_on_gpu():
+    # fluid filling the tank: every particle has a complete lattice (dyadic spacing)
+    s = 1.0 / 64
+    sc = scenes.dam_break((8, 6, 5), s, (8 * s, 6 * s, 5 * s), 1e-4)
+    ctx = gpu_ctx(sc)
+    rts.rts_evaluate(ctx)
+    g = rts.rts_get_state(ctx, ("rho", "nbr"))
+    o = oracle_state(sc, sc.params, {"x": sc.x, "v": sc.v})
+    o.evaluate()
+    assert np.all(g["nbr"] == 26)
+    np.testing.assert_allclose(g["rho"], o.rho, rtol=RHO_RTOL)
+
+
+# -------------------------------------------------------------------- substep ---
+
+def _predicted(st, dt):
+    x = st["x"].astype(np.float64)
+    v = st["v"].astype(np.float64)
+    a = st["a"].astype(np.float64)
+    return x + v * dt + a * dt * dt / 2, v + a * dt
+
+
+def _near_threshold(P, xt, vt, a, blocks, rel=1e-5):
+    """Blocks whose FP64 maxima lie within rel of a level threshold (don't-care band)."""
+    key, _, _ = O.bin_particles(P, xt)
+    v2 = (vt ** 2).sum(1)
+    a2 = (a ** 2).sum(1)
+    vthr2, athr2, _ = O.level_thresholds(P)
+    near = set()
+    for b in blocks:
+        sel = key == b
+        for val, thr in ((v2[sel].max(), vthr2), (a2[sel].max(), athr2)):
+            if np.any(np.abs(val / thr - 1.0) < rel):
+                near.add(int(b))
+    return near
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_one_regional_substep_matches_oracle(seed):
+    sc = scenes.wcsph_dam_break_8k()
+    st = dynamic_state(sc, seed=seed)
+    k0 = 8
+    ctx = gpu_ctx(sc)
+    rts.rts_set_state(ctx, st["x"], st["v"], a=st["a"], rho=st["rho"], p=st["p"],
+                      level=st["level"], validity=st["validity"], klast=st["klast"], k=k0,
+                      primed=True)
+    rts.rts_wcsph_substep(ctx)
+    g = rts.rts_get_state(ctx)
+    o = oracle_state(sc, sc.params, st, k=k0, primed=True)
+    o.substep()
+    P = o.P
+    mism = np.nonzero(g["compute"] != o.compute)[0]
+    if len(mism):
+        xt, vt = _predicted(st, P.dt_b)
+        key, _, _ = O.bin_particles(P, xt)
+        near = _near_threshold(P, xt, vt, st["a"].astype(np.float64), np.unique(key[mism]))
+        assert all(int(key[i]) in near for i in mism), f"{len(mism)} activity mismatches"
+    same = g["compute"] == o.compute
+    assert same.mean() > 0.999
+    comp = (o.compute == 1) & same
+    assert comp.sum() > 100 and (~comp).sum() > 100   # both kinds present
+    assert np.array_equal(g["level"][same], o.level[same])
+    assert np.array_equal(g["validity"][same], o.validity[same])
+    assert np.array_equal(g["klast"][same], o.klast[same])
+    _check_eval(g, o, comp)
+    # positions / velocities: FP32 predictor rounding plus the force tolerance
+    tol_a = ACC_FRAC * max_norm(o.a[comp])
+    dt = (k0 + 1 - st["klast"].astype(np.float64)) * P.dt_b
+    dx = np.abs(g["x"] - o.x).max(axis=1)
+    dv = np.abs(g["v"] - o.v).max(axis=1)
+    x_tol = 8 * ulp32(o.x).max(axis=1) + np.where(comp, tol_a * dt * dt / 6, 0)
+    v_tol = 8 * ulp32(o.v).max(axis=1) + 1e-6 * np.abs(st["a"]).max() * P.dt_b + np.where(comp, tol_a * dt / 2, 0)
+    assert np.all(dx[same] <= x_tol[same])
+    assert np.all(dv[same] <= v_tol[same])
+
+
+def test_forced_finest_level_reproduces_global_stepping_bit_for_bit():
+    sc = scenes.wcsph_dam_break_8k()
+    a = gpu_ctx(sc, params(sc, force_level=0))
+    b = gpu_ctx(sc, params(sc, mode=2))
+    for _ in range(10):
+        rts.rts_wcsph_substep(a)
+        rts.rts_wcsph_substep(b)
+    ga, gb = rts.rts_get_state(a), rts.rts_get_state(b)
+    for f in ("x", "v", "a", "rho", "p", "klast", "nbr"):
+        assert np.array_equal(ga[f], gb[f]), f
+    assert np.all(ga["compute"] == 1)
+
+
+def test_global_adaptive_step_size_matches_oracle():
+    sc = scenes.wcsph_dam_break_8k()
+    d = params(sc, mode=1)
+    ctx = gpu_ctx(sc, d)
+    o = oracle_state(sc, d, {"x": sc.x, "v": sc.v})
+    for _ in range(4):
+        rts.rts_wcsph_substep(ctx)                 # one global step of the finest level
+        o.global_step()
+        assert ctx.substep_index == o.k
+    g = rts.rts_get_state(ctx)
+    np.testing.assert_allclose(g["x"], o.x, atol=2e-5)
+
+
+# ------------------------------------------------------------------ rollouts ---
+
+def test_rollout_statistics_match_oracle():
+    # 0.05 s of the 8k dam break with regional stepping: trajectories diverge, so compare
+    # mass (particle count), kinetic energy and density-error statistics.
+    sc = scenes.wcsph_dam_break_8k()
+    T = 0.05
+    ctx = gpu_ctx(sc)
+    stats = rts.rts_advance(ctx, T)
+    g = rts.rts_get_state(ctx)
+    o = oracle_state(sc, sc.params, {"x": sc.x, "v": sc.v})
+    evals = 0
+    while o.k < stats["substeps"]:
+        o.substep()
+        evals += int(o.compute.sum())
+    assert stats["substeps"] == round(T / sc.params["dt_b"])
+    ke_g = 0.5 * (g["v"].astype(np.float64) ** 2).sum()
+    ke_o = 0.5 * (o.v ** 2).sum()
+    assert abs(ke_g / ke_o - 1) < 0.05
+    err_g = np.abs(g["rho"] / 1000.0 - 1)
+    err_o = np.abs(o.rho / 1000.0 - 1)
+    assert abs(err_g.mean() - err_o.mean()) < 0.1 * err_o.mean() + 1e-4
+    assert abs(np.percentile(err_g, 99) - np.percentile(err_o, 99)) < 0.1 * np.percentile(err_o, 99) + 1e-3
+    assert abs(stats["particle_evals"] / evals - 1) < 0.05
+    assert sum(stats["level_count"]) == sc.n
+
+
+# ------------------------------------------------------------- full size ---
+
+def test_full_size_evaluation_sampled():
+    # 1M-particle dam break, evaluated in the launch configuration of the benchmark;
+    # the oracle computes a seeded sample of particles one by one.
+    sc = scenes.wcsph_dam_break_1m()
+    ctx = gpu_ctx(sc)
+    rts.rts_evaluate(ctx)
+    g = rts.rts_get_state(ctx, ("rho", "nbr", "a", "level"))
+    rng = np.random.default_rng(9)
+    sample = rng.choice(sc.n, 3000, replace=False)
+    P = O.make_params(sc.params)
+    mask = np.zeros(sc.n, np.uint8)
+    mask[sample] = 1
+    rho, prs, nbr = O.density(P, sc.x, sc.xb)          # all: forces need every neighbour's rho
+    a = O.accel(P, sc.x, sc.v, rho, prs, sc.xb, mask)
+    assert np.array_equal(g["nbr"][sample], nbr[sample])
+    np.testing.assert_allclose(g["rho"][sample], rho[sample], rtol=RHO_RTOL)
+    tol = ACC_FRAC * max_norm(a[sample])
+    assert np.linalg.norm(g["a"][sample] - a[sample], axis=1).max() <= tol
+    raw, lev = O.classify_wcsph(P, sc.x, sc.v, np.zeros_like(sc.x))
+    assert np.array_equal(g["level"], _levels_by_particle(P, sc.x, lev))
+
+
+def test_full_size_substeps_run_and_conserve_particles():
+    sc = scenes.wcsph_dam_break_1m()
+    ctx = gpu_ctx(sc)
+    s = rts.rts_advance(ctx, 40 * sc.params["dt_b"])
+    assert s["substeps"] == 40
+    assert sum(s["level_count"]) == sc.n
+    g = rts.rts_get_state(ctx, ("x", "rho"))
+    assert np.isfinite(g["x"]).all()
+    assert np.all(g["x"].min(0) > -0.02) and np.all(g["x"].max(0) < np.array([4.02, 2.02, 2.02]))
+
+
+# ---------------------------------------------------------------- edge cases ---
+
+def test_empty_fluid_and_no_boundary():
+    sc = scenes.wcsph_dam_break_8k()
+    ctx = rts.rts_init(sc.params, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), sc.xb)
+    s = rts.rts_advance(ctx, 5 * sc.params["dt_b"])
+    assert s["substeps"] == 5 and s["particle_evals"] == 0
+    ctx2 = rts.rts_init(sc.params, sc.x, sc.v, np.zeros((0, 3), np.float32))
+    rts.rts_advance(ctx2, 3 * sc.params["dt_b"])
+    g = rts.rts_get_state(ctx2, ("nbr",))
+    assert g["nbr"].max() <= 40
+
+
+def test_out_of_domain_particle_is_a_sticky_error_until_set_state():
+    sc = scenes.wcsph_dam_break_8k()
+    x = sc.x.copy()
+    x[123] = [50.0, 0.1, 0.1]
+    ctx = gpu_ctx(sc, x=x)
+    with pytest.raises(rts.RtsError) as e:
+        rts.rts_advance(ctx, 2 * sc.params["dt_b"])
+    assert e.value.status == 2
+    with pytest.raises(rts.RtsError) as e:
+        rts.rts_wcsph_substep(ctx)
+    assert e.value.status == 8
+    rts.rts_set_state(ctx, sc.x, sc.v)
+    rts.rts_advance(ctx, 2 * sc.params["dt_b"])
+
+
+def test_block_over_capacity_is_reported():
+    sc = scenes.wcsph_dam_break_8k()
+    x = sc.x.copy()
+    x[:100] = x[0] + np.linspace(0, 1e-3, 100, dtype=np.float32)[:, None]   # 100 in one block
+    ctx = gpu_ctx(sc, params(sc, max_per_block=64), x=x)
+    with pytest.raises(rts.RtsError) as e:
+        rts.rts_sync(ctx)
+        rts.rts_advance(ctx, sc.params["dt_b"])
+    assert e.value.status == 5
