@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark of regional time stepping (RTS) WCSPH on one GB300: particle-substeps/s.
+
+Workload: the 1M-particle dam break (100^3 column, s = 0.01 m, 4 x 2 x 2 m tank,
+dt_b = 5e-5 s, levels dt_b * {1, 2, 4, 8}), advanced from t = 0 to a dynamic state
+(--preroll, untimed), then timed.  One step = one window of 8 dt_b (a full cycle of
+the coarsest level) of simulated time, advanced through the library's public call
+rts_advance.  value = fluid particles x base substeps / device seconds.
+
+Also measured, on the same GPU in the same run: the global adaptive comparator (every
+particle active, one step of the finest level that the time-step criteria give for the
+whole fluid), the end-to-end rate through the C ABI with host buffers (state uploaded
+from and returned to pinned host memory every step), the FP32-ALU roofline of the
+dominant neighbour kernel, SM clocks, and the CPU oracle on a bounded sample.
+
+--impl reference times the FP64 CPU oracle (the reference arm: the paper ships no code).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_SM = 152
+FP32_LANES_PER_SM = 128
+# algorithmic FP32 flops (FMA = 2): candidate test = 3 sub + 1 mul + 2 fma = 8;
+# density pair = sqrt + scale + cubic-spline branch (~8) + accumulate = 11;
+# force pair = sqrt, scale, dW branch, divide, dot (5), viscosity (6), pressure term and
+# scale (4), 3 fma accumulations (6) = 30.
+FLOPS_TEST = 8
+FLOPS_PAIR_DENSITY = 11
+FLOPS_PAIR_FORCE = 30
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--preroll", type=float, default=0.3, help="simulated seconds before timing")
+    ap.add_argument("--window", type=int, default=8, help="base substeps per step")
+    ap.add_argument("--no-global", action="store_true", help="skip the global comparator")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--small", action="store_true", help="8k-particle dam break (quick check)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(small):
+    from paper_2009_14514_gb300 import scenes
+    sc = scenes.wcsph_dam_break_8k() if small else scenes.wcsph_dam_break_1m()
+    return sc
+
+
+def workload_name(sc, args):
+    return (f"{sc.name}: {sc.n} fluid + {sc.nb} boundary particles, WCSPH regional time "
+            f"stepping, levels dt_b*{sc.params['level_mult']}, dt_b={sc.params['dt_b']}, "
+            f"step = {args.window} dt_b from t={args.preroll}s")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        except OSError:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                   "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def density_error(rho, rho0=1000.0):
+    import numpy as np
+    e = np.abs(rho.astype(np.float64) / rho0 - 1.0)
+    return {"mean": float(e.mean()), "p99": float(np.percentile(e, 99)), "max": float(e.max())}
+
+
+def run_arm(sc, mode, args, torch, rts, profile=False):
+    """Pre-roll, warm up and time one stepping mode; returns timing and counters."""
+    d = dict(sc.params)
+    d["mode"] = mode
+    ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
+    dtb = d["dt_b"]
+    rts.rts_advance(ctx, args.preroll)
+    k = ctx.substep_index
+    for _ in range(args.warmup):
+        k += args.window
+        rts.rts_advance(ctx, k * dtb)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    if profile:
+        rts.rts_profile_enable(ctx, True)
+    rts.rts_profile_read(ctx, reset=True)
+    tot = {"substeps": 0, "particle_evals": 0, "pair_interactions": 0, "candidate_tests": 0,
+           "active_blocks": 0, "steps": 0}
+    ms = []
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        k += args.window
+        s0.record(stream)
+        st = rts.rts_advance(ctx, k * dtb)
+        s1.record(stream)
+        s1.synchronize()
+        ms.append(s0.elapsed_time(s1))
+        for f in tot:
+            tot[f] += st[f]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    prof = rts.rts_profile_read(ctx, reset=True)
+    g = rts.rts_get_state(ctx, ("rho", "level"))
+    last = st
+    ctx.close()
+    del flush
+    return {"ms": ms, "wall": wall, "tot": tot, "prof": prof,
+            "rho_err": density_error(g["rho"], d["rho0"]), "levels": last["level_count"][:4]}
+
+
+def run_e2e(sc, args, torch, rts):
+    """Every step: upload the full state from pinned host memory (rts_set_state), advance
+    one window, copy the full state back to pinned host memory (rts_get_state)."""
+    import numpy as np
+    n = sc.n
+    ctx = rts.rts_init(sc.params, sc.x, sc.v, sc.xb)
+    dtb = sc.params["dt_b"]
+    rts.rts_advance(ctx, args.preroll)
+    k = ctx.substep_index
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True)
+    H = {"x": pin((n, 3), torch.float32), "v": pin((n, 3), torch.float32),
+         "a": pin((n, 3), torch.float32), "rho": pin((n,), torch.float32),
+         "p": pin((n,), torch.float32), "level": pin((n,), torch.int32),
+         "validity": pin((n,), torch.int32), "klast": pin((n,), torch.int32)}
+    rts.rts_get_state_into(ctx, **H)
+    nbytes = sum(t.numel() * t.element_size() for t in H.values())
+    times = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rts.rts_set_state(ctx, H["x"], H["v"], a=H["a"], rho=H["rho"], p=H["p"], level=H["level"],
+                          validity=H["validity"], klast=H["klast"], k=k, primed=True)
+        k += args.window
+        rts.rts_advance(ctx, k * dtb)
+        rts.rts_get_state_into(ctx, **H)
+        t1 = time.perf_counter()
+        if it >= args.warmup:
+            times.append(t1 - t0)
+    ctx.close()
+    total = sum(times)
+    return {"value": n * args.window * len(times) / total, "unit": "particle-substeps/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "ms_per_step": 1e3 * total / len(times)}
+
+
+def cpu_oracle(sc, budget_s=12.0, max_substeps=64):
+    """The FP64 oracle as it stands, on the host cores: priming evaluation (untimed), then
+    regional substeps from t = 0 until the time budget is spent."""
+    import oracle as O
+    P = O.make_params(sc.params)
+    S = O.WCSPH(P, sc.x, sc.v, sc.xb)
+    S.evaluate()
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_substeps:
+        S.substep()
+        k += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": sc.n * k / dt, "unit": "particle-substeps/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{sc.name}: priming evaluation then {k} regional substeps from t=0 "
+                      f"({dt:.1f} s, FP64, OpenMP over all host cores)"}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sc = workload(args.small)
+    import oracle as O
+    P = O.make_params(sc.params)
+    S = O.WCSPH(P, sc.x, sc.v, sc.xb)
+    S.evaluate()
+    for _ in range(args.warmup):
+        S.substep()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S.substep()
+    dt = time.perf_counter() - t0
+    value = sc.n * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "particle-substeps/s (regional time stepping, WCSPH)",
+        "value": value, "unit": "particle-substeps/s", "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{sc.name} (FP64 CPU oracle; step = one regional substep from t=0)"},
+        "cpu_baseline": {"value": value, "unit": "particle-substeps/s", "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": f"{args.steps} regional substeps after priming, from t=0"},
+        "e2e": {"value": value, "unit": "particle-substeps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2009_14514_gb300 import rts
+    rts.lib()
+    sc = workload(args.small)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        ours = run_arm(sc, 0, args, torch, rts, profile=True)
+    barrier()
+    glob = None if args.no_global else run_arm(sc, 1, args, torch, rts)
+    e2e = None if args.no_e2e else run_e2e(sc, args, torch, rts)
+
+    total_ms = sum(ours["ms"])
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    subs = ours["tot"]["substeps"]
+    value = world * sc.n * subs / (total_ms / 1e3)
+
+    # roofline of the dominant neighbour kernel (FP32 ALU bound)
+    prof = ours["prof"]
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    tests, pairs = ours["tot"]["candidate_tests"], ours["tot"]["pair_interactions"]
+    kern = max(("density", "force"), key=lambda k: prof["ms"][k])
+    per_pair = FLOPS_PAIR_FORCE if kern == "force" else FLOPS_PAIR_DENSITY
+    launches = max(1, prof["launches"][kern])
+    flops_per_launch = (tests * FLOPS_TEST + pairs * per_pair) / launches
+    dur_s = prof["ms"][kern] / 1e3 / launches
+    achieved = flops_per_launch / dur_s / 1e12 if dur_s > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": f"k_neighbor<{1 if kern == 'force' else 0}> ({kern})",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived)",
+                "avg_launch_us": dur_s * 1e6, "launches": launches}
+
+    clocks = clk.summary()
+    line = {
+        "metric": "particle-substeps/s (regional time stepping, WCSPH, 1M particles)",
+        "value": value, "unit": "particle-substeps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(sc, args), "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "256 MB buffer written between timed steps", "window_substeps": args.window},
+        "wall_s_per_sim_s": (total_ms / 1e3) / (args.steps * args.window * sc.params["dt_b"]),
+        "gpu_launches": int(prof["kernels"]),
+        "phases_ms": {k: round(v, 3) for k, v in prof["ms"].items()},
+        "evals_per_s": ours["tot"]["particle_evals"] / (total_ms / 1e3),
+        "pair_interactions_per_s": pairs / (total_ms / 1e3),
+        "active_fraction": ours["tot"]["particle_evals"] / max(1, sc.n * subs),
+        "density_error": ours["rho_err"], "level_count": ours["levels"],
+        "roofline": roofline, "clocks": clocks,
+    }
+    if glob is not None:
+        gms = sum(glob["ms"])
+        gval = sc.n * glob["tot"]["substeps"] / (gms / 1e3)
+        line["global_adaptive"] = {
+            "value": gval, "ms_per_step": gms / args.steps,
+            "wall_s_per_sim_s": (gms / 1e3) / (glob["tot"]["substeps"] * sc.params["dt_b"]),
+            "evals_per_s": glob["tot"]["particle_evals"] / (gms / 1e3),
+            "density_error": glob["rho_err"], "steps_per_window": glob["tot"]["steps"] / args.steps}
+        line["rts_vs_global"] = value / world / gval
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle(sc)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

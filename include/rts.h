@@ -103,6 +103,7 @@ typedef struct rts_stats {
   int64_t pair_interactions; /* neighbour pairs (d < r) of those evaluations               */
   int64_t active_blocks;     /* sum over steps of blocks with an evaluated particle        */
   int64_t level_count[8];    /* fluid particles per level at the end of the call           */
+  int64_t candidate_tests;   /* candidate pairs tested against the support radius          */
   int64_t pcisph_iterations; /* density-correction iterations                              */
   int64_t pcisph_local_iterations;
   int64_t pcisph_global_restarts;
@@ -173,6 +174,33 @@ rts_status rts_get_bins(rts_ctx* ctx, int32_t* key, int32_t* perm, int32_t* csta
  * Eq. 1-3, level after R_min smoothing (and, for PCISPH, region expansion).
  * Any pointer may be NULL.  Synchronises. */
 rts_status rts_get_blocks(rts_ctx* ctx, int32_t* raw, int32_t* level);
+
+/* Phases timed by the optional profiler (CUDA events on the context's stream).  The
+ * paper's Table 2 buckets map as: neighbour = BIN (+ the neighbour walk inside DENSITY
+ * and FORCE); physics = DENSITY + FORCE + CORRECT; RTS = CLASSIFY + ACTIVITY. */
+enum {
+  RTS_PHASE_BIN = 0,       /* predict + block key + counting sort + gather              */
+  RTS_PHASE_CLASSIFY = 1,  /* block maxima, Eq. 1-3 levels, R_min (+ PCISPH regions)     */
+  RTS_PHASE_ACTIVITY = 2,  /* validity, pre-emption, active-block work list             */
+  RTS_PHASE_DENSITY = 3,   /* WCSPH density / PCISPH neighbour lists                     */
+  RTS_PHASE_FORCE = 4,     /* WCSPH forces / PCISPH non-pressure forces                  */
+  RTS_PHASE_CORRECT = 5,   /* Serna correction / PCISPH integration                      */
+  RTS_PHASE_ITERATE = 6,   /* PCISPH density-correction iterations                       */
+  RTS_PHASE_OTHER = 7,     /* global maxima, statistics, caller-order I/O                */
+  RTS_NUM_PHASES = 8
+};
+
+typedef struct rts_profile {
+  double ms[RTS_NUM_PHASES];         /* device time per phase (valid while enabled)        */
+  int64_t launches[RTS_NUM_PHASES];  /* kernel launches per phase                          */
+  int64_t kernels;                   /* all kernel launches of this library                */
+} rts_profile;
+
+/* Switch per-phase event timing on (1) or off (0).  Launch counts are always kept. */
+rts_status rts_profile_enable(rts_ctx* ctx, int32_t on);
+
+/* Read the accumulated profile (synchronises); reset != 0 clears it afterwards. */
+rts_status rts_profile_read(rts_ctx* ctx, rts_profile* out, int32_t reset);
 
 /* Wait for the stream; return a pending device error, if any. */
 rts_status rts_sync(rts_ctx* ctx);

@@ -135,6 +135,40 @@ static void make_dev_params(const rts_params& p, DevParams& d) {
   d.dt_b = p.dt_b;
 }
 
+// ------------------------------------------------------------- profiling ---
+
+// Accumulate the timed event pairs into prof_ms (synchronises the stream).
+static void prof_flush(rts_ctx* c) {
+  if (!c->ev || c->nev == 0) return;
+  cudaStreamSynchronize(c->stream);
+  for (int k = 0; k < c->nev; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]) == cudaSuccess)
+      c->prof_ms[c->ev_phase[k]] += ms;
+  }
+  c->nev = 0;
+}
+
+// Scope of one phase: sets the phase that launches are counted against and, when
+// profiling is on, brackets the phase's launches with a pair of events.
+struct Phase {
+  rts_ctx* c;
+  int prev, slot;
+  Phase(rts_ctx* c_, int ph) : c(c_), prev(c_->cur_phase), slot(-1) {
+    c->cur_phase = ph;
+    if (c->prof && c->ev) {
+      if (c->nev == kEvPairs) prof_flush(c);
+      slot = c->nev++;
+      c->ev_phase[slot] = ph;
+      cudaEventRecord(c->ev[2 * slot], c->stream);
+    }
+  }
+  ~Phase() {
+    if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], c->stream);
+    c->cur_phase = prev;
+  }
+};
+
 // ------------------------------------------------------------ caller I/O ---
 
 __global__ void k_pack3(int n, const float* __restrict__ in, float4* __restrict__ out) {
@@ -195,6 +229,8 @@ static rts_status upload_state(rts_ctx* c, const float* x, const float* v, const
                                const int32_t* validity, const int32_t* klast) {
   int n = c->n;
   if (n == 0) return RTS_OK;
+  Phase ph(c, RTS_PHASE_OTHER);
+  note_launch(c, 9);
   size_t v3 = sizeof(float) * 3 * (size_t)n, s1 = sizeof(float) * (size_t)n;
   float* io = c->io;
   int g = nblk(n);
@@ -244,12 +280,17 @@ static rts_status sync_status(rts_ctx* c) {
 
 // --------------------------------------------------------- WCSPH stepping ---
 
+static void run_physics(rts_ctx* c, int64_t k1, int prime) {
+  { Phase ph(c, RTS_PHASE_DENSITY); launch_density(c); }
+  { Phase ph(c, RTS_PHASE_FORCE); launch_force(c); }
+  { Phase ph(c, RTS_PHASE_CORRECT); launch_correct(c, k1, prime); }
+}
+
 static rts_status wcsph_evaluate(rts_ctx* c) {
-  launch_bin(c, 0.0f);
-  launch_classify(c);
-  launch_activity(c, kActAll, 0, 0);
-  launch_density_force(c);
-  launch_correct(c, c->k, 1);
+  { Phase ph(c, RTS_PHASE_BIN); launch_bin(c, 0.0f); }
+  { Phase ph(c, RTS_PHASE_CLASSIFY); launch_classify(c); }
+  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActAll, 0, 0); }
+  run_physics(c, c->k, 1);
   c->primed = 1;
   c->bins_valid = 1;
   CK(cudaGetLastError());
@@ -258,11 +299,10 @@ static rts_status wcsph_evaluate(rts_ctx* c) {
 
 static rts_status wcsph_regional(rts_ctx* c) {
   int64_t k1 = c->k + 1;
-  launch_bin(c, c->p.dt_b);
-  launch_classify(c);
-  launch_activity(c, kActRegional, 0, 0);
-  launch_density_force(c);
-  launch_correct(c, k1, 0);
+  { Phase ph(c, RTS_PHASE_BIN); launch_bin(c, c->p.dt_b); }
+  { Phase ph(c, RTS_PHASE_CLASSIFY); launch_classify(c); }
+  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActRegional, 0, 0); }
+  run_physics(c, k1, 0);
   c->k = k1;
   c->bins_valid = 1;
   CK(cudaGetLastError());
@@ -279,7 +319,10 @@ static int host_pick_level(const rts_ctx* c, double v2, double a2) {
 static rts_status wcsph_global(rts_ctx* c, int64_t max_mult) {
   int L = 0;
   if (c->p.mode == RTS_MODE_GLOBAL_ADAPTIVE) {
-    launch_global_max(c);
+    {
+      Phase ph(c, RTS_PHASE_CLASSIFY);
+      launch_global_max(c);
+    }
     CK(cudaMemcpyAsync(&c->h_ctl->vmax2_bits, &c->ctl->vmax2_bits, 2 * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -292,10 +335,9 @@ static rts_status wcsph_global(rts_ctx* c, int64_t max_mult) {
   if (m > max_mult) m = max_mult;
   if (m < 1) m = 1;
   int64_t k1 = c->k + m;
-  launch_bin(c, (float)m * c->p.dt_b);
-  launch_activity(c, kActGlobal, L, (int)m);
-  launch_density_force(c);
-  launch_correct(c, k1, 0);
+  { Phase ph(c, RTS_PHASE_BIN); launch_bin(c, (float)m * c->p.dt_b); }
+  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActGlobal, L, (int)m); }
+  run_physics(c, k1, 0);
   c->k = k1;
   c->bins_valid = 1;
   CK(cudaGetLastError());
@@ -443,6 +485,11 @@ rts_status rts_destroy(rts_ctx* c) {
   cudaFree(c->count); cudaFree(c->cstart); cudaFree(c->bcstart); cudaFree(c->tile_sums);
   cudaFree(c->raw); cudaFree(c->blevel); cudaFree(c->act); cudaFree(c->ctl); cudaFree(c->xb);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  if (c->ev) {
+    for (int k = 0; k < 2 * kEvPairs; ++k) cudaEventDestroy(c->ev[k]);
+    delete[] c->ev;
+    delete[] c->ev_phase;
+  }
   delete c;
   return RTS_OK;
 }
@@ -466,6 +513,7 @@ rts_status rts_sync(rts_ctx* c) {
 
 rts_status rts_bin(rts_ctx* c) {
   GUARD();
+  Phase ph(c, RTS_PHASE_BIN);
   launch_bin(c, 0.0f);
   c->bins_valid = 1;
   CK(cudaGetLastError());
@@ -474,8 +522,12 @@ rts_status rts_bin(rts_ctx* c) {
 
 rts_status rts_classify_blocks(rts_ctx* c) {
   GUARD();
-  if (!c->bins_valid) launch_bin(c, 0.0f);
+  if (!c->bins_valid) {
+    Phase ph(c, RTS_PHASE_BIN);
+    launch_bin(c, 0.0f);
+  }
   c->bins_valid = 1;
+  Phase ph(c, RTS_PHASE_CLASSIFY);
   launch_classify(c);
   CK(cudaGetLastError());
   return RTS_OK;
@@ -497,7 +549,7 @@ rts_status rts_advance(rts_ctx* c, double t_sim, rts_stats* out) {
   GUARD();
   if (!std::isfinite(t_sim)) return fail(c, RTS_ERR_ARG, "t_sim must be finite");
   int64_t K = llround(t_sim / (double)c->p.dt_b);
-  CK(cudaMemsetAsync(&c->ctl->evals, 0, 3 * sizeof(unsigned long long), c->stream));
+  CK(cudaMemsetAsync(&c->ctl->evals, 0, 4 * sizeof(unsigned long long), c->stream));
   int64_t k0 = c->k, steps = 0;
   rts_status st = RTS_OK;
   while (c->k < K) {
@@ -509,7 +561,10 @@ rts_status rts_advance(rts_ctx* c, double t_sim, rts_stats* out) {
     if (st != RTS_OK && st != RTS_ERR_NOT_CONVERGED) return st;
     ++steps;
   }
-  launch_level_hist(c);
+  {
+    Phase ph(c, RTS_PHASE_OTHER);
+    launch_level_hist(c);
+  }
   rts_status ds = sync_status(c);
   if (out) {
     memset(out, 0, sizeof(*out));
@@ -518,6 +573,7 @@ rts_status rts_advance(rts_ctx* c, double t_sim, rts_stats* out) {
     out->particle_evals = (int64_t)c->h_ctl->evals;
     out->pair_interactions = (int64_t)c->h_ctl->pairs;
     out->active_blocks = (int64_t)c->h_ctl->act_blocks;
+    out->candidate_tests = (int64_t)c->h_ctl->cands;
     for (int L = 0; L < kMaxLevels; ++L) out->level_count[L] = (int64_t)c->h_ctl->level_count[L];
     out->t_sim = (double)c->k * (double)c->p.dt_b;
   }
@@ -532,6 +588,10 @@ rts_status rts_get_state(rts_ctx* c, float* x, float* v, float* a, float* rho, f
   if (n == 0) return sync_status(c);
   int g = nblk(n);
   size_t v3 = sizeof(float) * 3 * (size_t)n, s1 = sizeof(float) * (size_t)n;
+  Phase ph(c, RTS_PHASE_OTHER);
+  note_launch(c, (x != nullptr) + (v != nullptr) + (a != nullptr) + (rho != nullptr) +
+                     (p != nullptr) + (level != nullptr) + (validity != nullptr) +
+                     (klast != nullptr) + (nbr != nullptr) + (compute != nullptr));
   const float4* vecs[3] = {c->s.x, c->s.v, c->s.a};
   float* vdst[3] = {x, v, a};
   for (int k = 0; k < 3; ++k) {
@@ -576,7 +636,10 @@ rts_status rts_set_state(rts_ctx* c, const float* x, const float* v, const float
   c->k = k;
   c->primed = primed ? 1 : 0;
   c->err[0] = 0;
-  launch_bin(c, 0.0f);
+  {
+    Phase ph(c, RTS_PHASE_BIN);
+    launch_bin(c, 0.0f);
+  }
   c->bins_valid = 1;
   return sync_status(c);
 }
@@ -616,6 +679,37 @@ rts_status rts_get_blocks(rts_ctx* c, int32_t* raw, int32_t* level) {
     CK(cudaMemcpy(h.data(), src[k], nbk, cudaMemcpyDeviceToHost));
     for (size_t b = 0; b < nbk; ++b) w[b] = h[b];
     CK(cudaMemcpy(dst[k], w.data(), sizeof(int32_t) * nbk, cudaMemcpyDefault));
+  }
+  return RTS_OK;
+}
+
+rts_status rts_profile_enable(rts_ctx* c, int32_t on) {
+  if (!c) return fail(nullptr, RTS_ERR_ARG, "ctx is NULL");
+  if (on && !c->ev) {
+    c->ev = new (std::nothrow) cudaEvent_t[2 * kEvPairs];
+    c->ev_phase = new (std::nothrow) int[kEvPairs];
+    if (!c->ev || !c->ev_phase) return fail(c, RTS_ERR_OOM, "event pool allocation failed");
+    for (int k = 0; k < 2 * kEvPairs; ++k) CK(cudaEventCreate(&c->ev[k]));
+    c->nev = 0;
+  }
+  if (!on) prof_flush(c);
+  c->prof = on ? 1 : 0;
+  return RTS_OK;
+}
+
+rts_status rts_profile_read(rts_ctx* c, rts_profile* out, int32_t reset) {
+  if (!c || !out) return fail(c, RTS_ERR_ARG, "ctx or out is NULL");
+  prof_flush(c);
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < RTS_NUM_PHASES; ++k) {
+    out->ms[k] = c->prof_ms[k];
+    out->launches[k] = c->launches[k];
+  }
+  out->kernels = c->kernels;
+  if (reset) {
+    memset(c->prof_ms, 0, sizeof c->prof_ms);
+    memset(c->launches, 0, sizeof c->launches);
+    c->kernels = 0;
   }
   return RTS_OK;
 }

@@ -213,6 +213,7 @@ rts_status launch_bin(rts_ctx* c, float dt) {
     return RTS_OK;
   }
   int tb = 256, g = (n + tb - 1) / tb;
+  note_launch(c, 6);
   k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, n, c->s.x, c->s.v, c->s.a, dt, c->key, c->slot,
                                           c->count, c->ctl);
   scan_counts(c);

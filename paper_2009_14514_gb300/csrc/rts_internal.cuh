@@ -43,6 +43,7 @@ struct Ctl {
   unsigned long long evals;      // evaluated particles
   unsigned long long pairs;      // neighbour pairs of evaluated particles
   unsigned long long act_blocks; // active blocks summed over steps
+  unsigned long long cands;      // candidate pairs tested
   unsigned long long vmax2_bits; // global max |v|^2 (FP64 bits, non-negative)
   unsigned long long amax2_bits; // global max |a|^2
   unsigned long long level_count[kMaxLevels];
@@ -113,7 +114,25 @@ struct rts_ctx {
   int32_t* io_i;      // n ints
 
   int grid_persistent;  // CTAs of the persistent neighbour kernels
+
+  // launch counting and optional per-phase event timing
+  int cur_phase;
+  int64_t kernels;
+  int64_t launches[RTS_NUM_PHASES];
+  int prof;
+  double prof_ms[RTS_NUM_PHASES];
+  cudaEvent_t* ev;    // 2 * kEvPairs events
+  int* ev_phase;
+  int nev;
 };
+
+namespace rts {
+constexpr int kEvPairs = 1024;
+inline void note_launch(rts_ctx* c, int k) {
+  c->kernels += k;
+  c->launches[c->cur_phase] += k;
+}
+}  // namespace rts
 
 // Host helpers implemented in rts_api.cu / kernels implemented in the .cu files.
 namespace rts {
@@ -121,11 +140,10 @@ rts_status launch_bin(rts_ctx* c, float dt_predict);
 rts_status launch_bin_boundary(rts_ctx* c, const float4* xb_unsorted, int nb);
 rts_status launch_classify(rts_ctx* c);
 rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g);
-rts_status launch_density_force(rts_ctx* c);
+rts_status launch_density(rts_ctx* c);
+rts_status launch_force(rts_ctx* c);
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime);
 rts_status launch_global_max(rts_ctx* c);
-rts_status launch_to_user(rts_ctx* c, int which, void* dst);
-rts_status launch_from_user(rts_ctx* c, int which, const void* src);
 rts_status launch_level_hist(rts_ctx* c);
 const char* cuda_err(rts_ctx* c, cudaError_t e, const char* what);
 }  // namespace rts

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_neighbor(DevParams P, const uint32_t* _
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n_act = *(volatile int*)&ctl->n_act;
-  unsigned long long pairs = 0;
+  unsigned long long pairs = 0, tests = 0;
   for (int t = warp; t < n_act; t += nwarps) {
     const uint32_t b = act[t];
     const int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
@@ -227,8 +227,9 @@ __global__ void __launch_bounds__(256) k_neighbor(DevParams P, const uint32_t* _
       const float4 xi = i >= 0 ? s.x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
       if (MODE == 0) {
         float wsum = 0.0f;
-        int cnt = 0;
+        int cnt = 0, ntest = 0;
         auto add = [&](float4 xj) {
+          ++ntest;
           float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
           float d2 = dx * dx + dy * dy + dz * dz;
           if (d2 < P.r2_hi && (d2 < P.r2_lo || exact_nbr(xi, xj, P.r2d))) {
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(256) k_neighbor(DevParams P, const uint32_t* _
           wsum += __shfl_down_sync(kFull, wsum, o, lpp);
           cnt += __shfl_down_sync(kFull, cnt, o, lpp);
         }
+        if (i >= 0) tests += (unsigned long long)ntest;
         if (sub == 0 && i >= 0) {
           float rho = P.m * wsum;
           float p = tait(P, rho);
@@ -287,8 +289,12 @@ __global__ void __launch_bounds__(256) k_neighbor(DevParams P, const uint32_t* _
   }
   if (MODE == 0) {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) pairs += __shfl_down_sync(kFull, pairs, o);
+    for (int o = 16; o; o >>= 1) {
+      pairs += __shfl_down_sync(kFull, pairs, o);
+      tests += __shfl_down_sync(kFull, tests, o);
+    }
     if (lane == 0 && pairs) atomicAdd(&ctl->pairs, pairs);
+    if (lane == 0 && tests) atomicAdd(&ctl->cands, tests);
   }
 }
 
@@ -373,6 +379,7 @@ int neighbor_grid_size() {
 
 rts_status launch_classify(rts_ctx* c) {
   int nb = c->dp.nblocks, tb = 256, g = (nb + tb - 1) / tb;
+  note_launch(c, 2);
   k_block_raw<<<g, tb, 0, c->stream>>>(c->dp, c->cstart, c->s.v, c->s.a, c->raw);
   k_block_smooth<<<g, tb, 0, c->stream>>>(c->dp, c->raw, c->blevel);
   return RTS_OK;
@@ -381,15 +388,22 @@ rts_status launch_classify(rts_ctx* c) {
 rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g) {
   int nb = c->dp.nblocks, tb = 256, g = (nb + tb - 1) / tb;
   cudaMemsetAsync(&c->ctl->n_act, 0, sizeof(int), c->stream);
+  note_launch(c, 1);
   k_activity<<<g, tb, 0, c->stream>>>(c->dp, mode, level_g, mult_g, c->cstart, c->blevel, c->s,
                                        c->cflag, c->act, c->ctl);
   return RTS_OK;
 }
 
-rts_status launch_density_force(rts_ctx* c) {
+rts_status launch_density(rts_ctx* c) {
+  note_launch(c, 1);
   k_neighbor<0><<<c->grid_persistent, 256, 0, c->stream>>>(c->dp, c->act, c->ctl, c->cstart,
                                                             c->bcstart, c->s, c->xb, c->cflag,
                                                             c->anew);
+  return RTS_OK;
+}
+
+rts_status launch_force(rts_ctx* c) {
+  note_launch(c, 1);
   k_neighbor<1><<<c->grid_persistent, 256, 0, c->stream>>>(c->dp, c->act, c->ctl, c->cstart,
                                                             c->bcstart, c->s, c->xb, c->cflag,
                                                             c->anew);
@@ -397,6 +411,7 @@ rts_status launch_density_force(rts_ctx* c) {
 }
 
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime) {
+  note_launch(c, 1);
   k_correct<<<c->grid_persistent, 256, 0, c->stream>>>(c->dp, c->act, c->ctl, c->cstart, c->s,
                                                        c->cflag, c->anew, (int)k1, prime);
   return RTS_OK;
@@ -405,6 +420,7 @@ rts_status launch_correct(rts_ctx* c, int64_t k1, int prime) {
 rts_status launch_global_max(rts_ctx* c) {
   cudaMemsetAsync(&c->ctl->vmax2_bits, 0, 2 * sizeof(unsigned long long), c->stream);
   int tb = 256, g = (c->n + tb - 1) / tb;
+  if (c->n > 0) note_launch(c, 1);
   if (c->n > 0) k_global_max<<<g, tb, 0, c->stream>>>(c->n, c->s.v, c->s.a, c->ctl);
   return RTS_OK;
 }
@@ -412,6 +428,7 @@ rts_status launch_global_max(rts_ctx* c) {
 rts_status launch_level_hist(rts_ctx* c) {
   cudaMemsetAsync(&c->ctl->level_count[0], 0, sizeof(unsigned long long) * kMaxLevels, c->stream);
   int tb = 256, g = (c->n + tb - 1) / tb;
+  if (c->n > 0) note_launch(c, 1);
   if (c->n > 0) k_level_hist<<<g, tb, 0, c->stream>>>(c->n, c->s.level, c->ctl);
   return RTS_OK;
 }

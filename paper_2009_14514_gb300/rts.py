@@ -23,7 +23,7 @@ EXPORTED = [
     "rts_init", "rts_bin", "rts_classify_blocks", "rts_evaluate", "rts_wcsph_substep",
     "rts_pcisph_step", "rts_advance", "rts_get_state", "rts_set_state", "rts_get_bins",
     "rts_get_blocks", "rts_sync", "rts_num_blocks", "rts_substep_index", "rts_last_error",
-    "rts_destroy",
+    "rts_destroy", "rts_profile_enable", "rts_profile_read",
 ]
 
 
@@ -56,7 +56,8 @@ class RtsStats(C.Structure):
     _fields_ = [
         ("substeps", C.c_int64), ("steps", C.c_int64), ("particle_evals", C.c_int64),
         ("pair_interactions", C.c_int64), ("active_blocks", C.c_int64),
-        ("level_count", C.c_int64 * 8), ("pcisph_iterations", C.c_int64),
+        ("level_count", C.c_int64 * 8), ("candidate_tests", C.c_int64),
+        ("pcisph_iterations", C.c_int64),
         ("pcisph_local_iterations", C.c_int64), ("pcisph_global_restarts", C.c_int64),
         ("t_sim", C.c_double),
     ]
@@ -65,6 +66,17 @@ class RtsStats(C.Structure):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "level_count"}
         d["level_count"] = list(self.level_count)
         return d
+
+
+PHASES = ["bin", "classify", "activity", "density", "force", "correct", "iterate", "other"]
+
+
+class RtsProfile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_int64 * 8), ("kernels", C.c_int64)]
+
+    def as_dict(self):
+        return {"ms": dict(zip(PHASES, list(self.ms))),
+                "launches": dict(zip(PHASES, list(self.launches))), "kernels": self.kernels}
 
 
 def make_params(d: dict) -> RtsParams:
@@ -115,7 +127,8 @@ def lib():
             "rts_get_state": [vp] * 11,
             "rts_set_state": [vp] * 9 + [i64, i32],
             "rts_get_bins": [vp] * 4, "rts_get_blocks": [vp] * 3, "rts_sync": [vp],
-            "rts_destroy": [vp],
+            "rts_destroy": [vp], "rts_profile_enable": [vp, i32],
+            "rts_profile_read": [vp, vp, i32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -296,10 +309,23 @@ def rts_get_state(ctx, fields=("x", "v", "a", "rho", "p", "level", "validity", "
     return out
 
 
-def rts_get_state_into(ctx, x=None, v=None, a=None, rho=None, p=None):
+def rts_get_state_into(ctx, x=None, v=None, a=None, rho=None, p=None, level=None,
+                       validity=None, klast=None, nbr=None, compute=None):
     """Copy state into caller-provided buffers (numpy or torch, host or device)."""
     _check(lib().rts_get_state(ctx.handle, _ptr(x), _ptr(v), _ptr(a), _ptr(rho), _ptr(p),
-                               None, None, None, None, None), "rts_get_state", ctx)
+                               _ptr(level), _ptr(validity), _ptr(klast), _ptr(nbr),
+                               _ptr(compute)), "rts_get_state", ctx)
+
+
+def rts_profile_enable(ctx, on=True):
+    return _check(lib().rts_profile_enable(ctx.handle, 1 if on else 0), "rts_profile_enable", ctx)
+
+
+def rts_profile_read(ctx, reset=False) -> dict:
+    prof = RtsProfile()
+    _check(lib().rts_profile_read(ctx.handle, C.byref(prof), 1 if reset else 0),
+           "rts_profile_read", ctx)
+    return prof.as_dict()
 
 
 def rts_set_state(ctx, x, v, a=None, rho=None, p=None, level=None, validity=None, klast=None,

@@ -65,9 +65,23 @@ def test_block_levels_are_bit_exact(force_level):
 
 # ----------------------------------------------------------------- evaluation ---
 
-def _check_eval(g, o, mask=None):
+def _near_tie(i, xp, xb, r, rel=1e-5):
+    """Particle i has a pair within rel of the support radius in the FP64 state xp."""
+    d2 = np.concatenate([((xp - xp[i]) ** 2).sum(1), ((xb - xp[i]) ** 2).sum(1)])
+    return bool(np.any(np.abs(d2 / (r * r) - 1.0) < rel))
+
+
+def _check_eval(g, o, mask=None, xpred=None):
     m = np.ones(len(o.rho), bool) if mask is None else mask
-    assert np.array_equal(g["nbr"][m], o.nbr[m])
+    if xpred is None:
+        assert np.array_equal(g["nbr"][m], o.nbr[m])
+    else:
+        # counts on predicted positions: FP32 and FP64 predictors round differently, so a
+        # pair within rounding of r may flip; every other count must agree exactly
+        bad = np.nonzero(m & (g["nbr"] != o.nbr))[0]
+        xb = o.xb
+        assert all(_near_tie(i, xpred, xb, o.P.r) for i in bad), f"{len(bad)} count mismatches"
+        assert len(bad) <= 1e-3 * m.sum() + 2
     np.testing.assert_allclose(g["rho"][m], o.rho[m], rtol=RHO_RTOL, atol=0)
     tol = ACC_FRAC * max_norm(o.a[m])
     err = np.linalg.norm(g["a"][m].astype(np.float64) - o.a[m], axis=1)
@@ -155,7 +169,8 @@ def test_one_regional_substep_matches_oracle(seed):
     assert np.array_equal(g["level"][same], o.level[same])
     assert np.array_equal(g["validity"][same], o.validity[same])
     assert np.array_equal(g["klast"][same], o.klast[same])
-    _check_eval(g, o, comp)
+    xt, _ = _predicted(st, P.dt_b)
+    _check_eval(g, o, comp, xpred=xt)
     # positions / velocities: FP32 predictor rounding plus the force tolerance
     tol_a = ACC_FRAC * max_norm(o.a[comp])
     dt = (k0 + 1 - st["klast"].astype(np.float64)) * P.dt_b
