@@ -205,6 +205,28 @@ rts_status rts_profile_read(rts_ctx* ctx, rts_profile* out, int32_t reset);
 /* Wait for the stream; return a pending device error, if any. */
 rts_status rts_sync(rts_ctx* ctx);
 
+/* Allocation-free binning.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory - hosts that reserve the whole GPU at
+ * start-up (a later cudaMalloc would fail), loops with a latency budget that an
+ * allocation's implicit synchronisation would break, and plugin hosts that own all
+ * device memory.  It computes what rts_bin followed by rts_get_bins gives (block of
+ * each particle, particles ordered by block then index, block starts) with no context
+ * and no allocation: its working memory is a fixed array of about 5 MB compiled into
+ * the library, present on every device that loads the library until the process
+ * exits.
+ *   x: n x 3 floats, key: n, perm: n, cstart: nblocks + 1, all in device memory;
+ *   n <= RTS_NOALLOC_MAX_PARTICLES and grid_dim[0]*grid_dim[1]*grid_dim[2] <=
+ *   RTS_NOALLOC_MAX_BLOCKS, else RTS_ERR_ARG (nothing is launched).
+ * Only the block grid fields of params are read.  The call synchronises the stream and
+ * returns RTS_ERR_DOMAIN if a particle lies outside the grid.  The first call on a
+ * device looks up the array's device address (once per device); make that first call
+ * before any stream capture.  Every call shares the one array: calls whose work can
+ * overlap on the GPU (other streams, other host threads) race and must be serialised. */
+#define RTS_NOALLOC_MAX_PARTICLES 262144
+#define RTS_NOALLOC_MAX_BLOCKS 524288
+rts_status rts_bin_noalloc(const rts_params* params, int32_t n, const float* x, int32_t* key,
+                           int32_t* perm, int32_t* cstart, void* cuda_stream);
+
 int64_t rts_num_blocks(const rts_ctx* ctx);
 int64_t rts_substep_index(const rts_ctx* ctx);   /* completed base substeps */
 const char* rts_last_error(const rts_ctx* ctx);  /* never NULL; ctx may be NULL */

@@ -21,6 +21,9 @@ const char* rts::cuda_err(rts_ctx* c, cudaError_t e, const char* what) {
   return dst;
 }
 
+// Message for rts_last_error(NULL) from entry points that take no context.
+void rts_set_global_error(const char* msg) { snprintf(g_noctx_err, sizeof g_noctx_err, "%s", msg); }
+
 static rts_status fail(rts_ctx* c, rts_status st, const char* msg) {
   snprintf(c ? c->err : g_noctx_err, 512, "%s", msg);
   return st;

@@ -23,7 +23,7 @@ EXPORTED = [
     "rts_init", "rts_bin", "rts_classify_blocks", "rts_evaluate", "rts_wcsph_substep",
     "rts_pcisph_step", "rts_advance", "rts_get_state", "rts_set_state", "rts_get_bins",
     "rts_get_blocks", "rts_sync", "rts_num_blocks", "rts_substep_index", "rts_last_error",
-    "rts_destroy", "rts_profile_enable", "rts_profile_read",
+    "rts_destroy", "rts_profile_enable", "rts_profile_read", "rts_bin_noalloc",
 ]
 
 
@@ -129,6 +129,7 @@ def lib():
             "rts_get_bins": [vp] * 4, "rts_get_blocks": [vp] * 3, "rts_sync": [vp],
             "rts_destroy": [vp], "rts_profile_enable": [vp, i32],
             "rts_profile_read": [vp, vp, i32],
+            "rts_bin_noalloc": [vp, i32, vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -364,3 +365,13 @@ def rts_destroy(ctx):
 def rts_last_error(ctx=None) -> str:
     h = ctx.handle if isinstance(ctx, Ctx) else None
     return lib().rts_last_error(h).decode()
+
+
+def rts_bin_noalloc(params, x, key, perm, cstart, stream=None):
+    """Binning without device allocation (see rts.h): x, key, perm, cstart are CUDA
+    tensors the caller owns.  For callers that cannot allocate device memory."""
+    P = params if isinstance(params, RtsParams) else make_params(params)
+    n = int(x.shape[0])
+    st = lib().rts_bin_noalloc(C.byref(P), n, _ptr(x), _ptr(key), _ptr(perm), _ptr(cstart),
+                               _stream(stream))
+    return _check(st, "rts_bin_noalloc")
