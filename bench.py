@@ -51,7 +51,25 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="8k-particle dam break (quick check)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="short run for ncu: 1M jittered lattice with a seeded dynamic state, "
+                         "primed, then --steps windows (few launches, nothing printed but a line)")
     return ap.parse_args()
+
+
+def profile_case(args):
+    """A bounded case for ncu captures: the 1M dam-break lattice jittered by +-1 mm with a
+    seeded state whose velocities and accelerations span levels 1-3; the first call primes
+    (every particle evaluated), then --steps windows of regional substeps."""
+    from paper_2009_14514_gb300 import rts, scenes
+    sc = scenes.dam_break((100, 100, 100), 0.01, (4.0, 2.0, 2.0), 5e-5, jitter=1e-3, seed=1234)
+    st = scenes.perturbed_state(sc, seed=777, vmax=3.0, amax=3.0e3)
+    ctx = rts.rts_init(sc.params, sc.x, st["v"], sc.xb)
+    rts.rts_set_state(ctx, sc.x, st["v"], a=st["a"])
+    dtb = sc.params["dt_b"]
+    st_all = rts.rts_advance(ctx, args.steps * args.window * dtb)
+    print(json.dumps({"profile_case": sc.name, "substeps": st_all["substeps"],
+                      "particle_evals": st_all["particle_evals"]}), flush=True)
 
 
 def dist_env():
@@ -277,6 +295,9 @@ def reference_arm(args):
 
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -322,7 +343,7 @@ def main():
     flops_per_launch = (tests * FLOPS_TEST + pairs * per_pair) / launches
     dur_s = prof["ms"][kern] / 1e3 / launches
     achieved = flops_per_launch / dur_s / 1e12 if dur_s > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": f"k_neighbor<{1 if kern == 'force' else 0}> ({kern})",
+    roofline = {"bound": "alu", "kernel": "k_force" if kern == "force" else "k_density",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived)",

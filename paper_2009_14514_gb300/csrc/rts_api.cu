@@ -81,6 +81,7 @@ static const char* validate(const rts_params* p, int32_t n, int32_t nb) {
   if (p->force_level >= p->n_levels) return "force_level must be < n_levels";
   if (!(p->dt_b > 0.f)) return "dt_b must be positive";
   if (p->max_per_block < 1 || p->max_per_block > 1024) return "max_per_block must be in [1, 1024]";
+  if (p->max_neighbors < 8 || p->max_neighbors > 1024) return "max_neighbors must be in [8, 1024]";
   if (!(p->rho0 > 0.f) || !(p->c_s > 0.f) || !(p->gamma > 0.f) || !(p->visc_alpha >= 0.f))
     return "rho0, c_s, gamma must be positive and visc_alpha non-negative";
   if (!(p->lambda_f > 0.f) || !(p->alpha > 0.f) || !(p->lambda_v > 0.f)) return "lambda_v, lambda_f, alpha must be positive";
@@ -136,6 +137,7 @@ static void make_dev_params(const rts_params& p, DevParams& d) {
   level_thresholds(p, d.vthr2, d.athr2, d.eq1);
   d.force_level = p.force_level;
   d.dt_b = p.dt_b;
+  d.nbl_cap = p.max_neighbors > 0 ? p.max_neighbors : 96;
 }
 
 // ------------------------------------------------------------- profiling ---
@@ -340,6 +342,7 @@ static rts_status wcsph_global(rts_ctx* c, int64_t max_mult) {
   int64_t k1 = c->k + m;
   { Phase ph(c, RTS_PHASE_BIN); launch_bin(c, (float)m * c->p.dt_b); }
   { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActGlobal, L, (int)m); }
+  c->last_global_level = L;
   run_physics(c, k1, 0);
   c->k = k1;
   c->bins_valid = 1;
@@ -414,8 +417,13 @@ rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, c
     ALLOC(c->cstart, sizeof(uint32_t) * (nbk + 1));
     ALLOC(c->bcstart, sizeof(uint32_t) * (nbk + 1));
     ALLOC(c->tile_sums, sizeof(uint32_t) * (size_t)c->ntiles);
-    ALLOC(c->raw, nbk);
-    ALLOC(c->blevel, nbk);
+    ALLOC(c->raw, sizeof(uint32_t) * nbk);
+    ALLOC(c->blevel, sizeof(uint32_t) * nbk);
+    ALLOC(c->bmax_v, sizeof(unsigned long long) * nbk);
+    ALLOC(c->bmax_a, sizeof(unsigned long long) * nbk);
+    ALLOC(c->filled, sizeof(uint32_t) * nbk);
+    c->nbl_cap = c->dp.nbl_cap;
+    ALLOC(c->nbl, sizeof(uint32_t) * (size_t)n1 * (size_t)c->nbl_cap);
     ALLOC(c->act, sizeof(uint32_t) * nbk);
     ALLOC(c->ctl, sizeof(Ctl));
     ALLOC(c->xb, sizeof(float4) * (size_t)(n_boundary > 0 ? n_boundary : 1));
@@ -428,8 +436,11 @@ rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, c
   {
     cudaError_t e = cudaMemsetAsync(c->count, 0, sizeof(uint32_t) * nbk, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->raw, 0xff, nbk, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->blevel, 0xff, nbk, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->raw, 0, sizeof(uint32_t) * nbk, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->blevel, 0, sizeof(uint32_t) * nbk, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->bmax_v, 0, sizeof(unsigned long long) * nbk, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->bmax_a, 0, sizeof(unsigned long long) * nbk, c->stream);
+    c->stamp = 0;
     if (e != cudaSuccess) {
       rts::cuda_err(c, e, "initial memset");
       st = RTS_ERR_CUDA;
@@ -487,6 +498,7 @@ rts_status rts_destroy(rts_ctx* c) {
   cudaFree(c->tmp_uid); cudaFree(c->tmp_src); cudaFree(c->io); cudaFree(c->io_i);
   cudaFree(c->count); cudaFree(c->cstart); cudaFree(c->bcstart); cudaFree(c->tile_sums);
   cudaFree(c->raw); cudaFree(c->blevel); cudaFree(c->act); cudaFree(c->ctl); cudaFree(c->xb);
+  cudaFree(c->bmax_v); cudaFree(c->bmax_a); cudaFree(c->filled); cudaFree(c->nbl);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   if (c->ev) {
     for (int k = 0; k < 2 * kEvPairs; ++k) cudaEventDestroy(c->ev[k]);
@@ -530,8 +542,14 @@ rts_status rts_classify_blocks(rts_ctx* c) {
     launch_bin(c, 0.0f);
   }
   c->bins_valid = 1;
-  Phase ph(c, RTS_PHASE_CLASSIFY);
-  launch_classify(c);
+  {
+    Phase ph(c, RTS_PHASE_CLASSIFY);
+    launch_classify(c);
+  }
+  {
+    Phase ph(c, RTS_PHASE_ACTIVITY);
+    launch_activity(c, -1, 0, 0);
+  }
   CK(cudaGetLastError());
   return RTS_OK;
 }
@@ -673,14 +691,15 @@ rts_status rts_get_blocks(rts_ctx* c, int32_t* raw, int32_t* level) {
   rts_status st = sync_status(c);
   if (st != RTS_OK) return st;
   size_t nbk = (size_t)c->dp.nblocks;
-  std::vector<int8_t> h(nbk);
+  std::vector<uint32_t> h(nbk);
   std::vector<int32_t> w(nbk);
-  const int8_t* src[2] = {c->raw, c->blevel};
+  const uint32_t* src[2] = {c->raw, c->blevel};
   int32_t* dst[2] = {raw, level};
   for (int k = 0; k < 2; ++k) {
     if (!dst[k]) continue;
-    CK(cudaMemcpy(h.data(), src[k], nbk, cudaMemcpyDeviceToHost));
-    for (size_t b = 0; b < nbk; ++b) w[b] = h[b];
+    CK(cudaMemcpy(h.data(), src[k], sizeof(uint32_t) * nbk, cudaMemcpyDeviceToHost));
+    // records of this binning pass hold a level; every other block has no fluid
+    for (size_t b = 0; b < nbk; ++b) w[b] = (h[b] >> 8) == c->stamp ? (int32_t)(h[b] & 0xffu) : -1;
     CK(cudaMemcpy(dst[k], w.data(), sizeof(int32_t) * nbk, cudaMemcpyDefault));
   }
   return RTS_OK;

@@ -106,12 +106,27 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
   return res;
 }
 
+// Eight consecutive counts of one thread (two 16-byte loads when the tile is full).
+__device__ __forceinline__ void load8(const uint32_t* __restrict__ count, int nb, int base,
+                                      uint32_t c[kScanItems]) {
+  if (base + kScanItems <= nb) {
+    uint4 a = *reinterpret_cast<const uint4*>(count + base);
+    uint4 b = *reinterpret_cast<const uint4*>(count + base + 4);
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) c[k] = base + k < nb ? count[base + k] : 0u;
+  }
+}
+
 __global__ void k_scan_reduce(const uint32_t* __restrict__ count, int nb, uint32_t* tile_sums) {
   int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  uint32_t c[kScanItems];
+  load8(count, nb, base, c);
   uint32_t s = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k)
-    if (base + k < nb) s += count[base + k];
+  for (int k = 0; k < kScanItems; ++k) s += c[k];
   uint32_t tot;
   block_excl_scan(s, &tot);
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
@@ -130,28 +145,61 @@ __global__ void k_scan_tiles(uint32_t* tile_sums, int ntiles) {
 }
 
 // cstart[i] = exclusive prefix of count; count is reset to zero for the next binning.
+// Filled blocks (count > 0) are appended to the filled list (warp-aggregated; the
+// list's order is irrelevant to every consumer).
 __global__ void k_scan_apply(uint32_t* __restrict__ count, int nb, const uint32_t* __restrict__ tile_sums,
-                             uint32_t* __restrict__ cstart) {
+                             uint32_t* __restrict__ cstart, uint32_t* __restrict__ filled,
+                             Ctl* ctl) {
   int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
   uint32_t c[kScanItems];
+  load8(count, nb, base, c);
   uint32_t s = 0;
+  int nf = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    c[k] = (base + k < nb) ? count[base + k] : 0u;
     s += c[k];
+    nf += c[k] ? 1 : 0;
   }
   uint32_t tot;
   uint32_t ex = block_excl_scan(s, &tot) + tile_sums[blockIdx.x];
+  uint32_t o[kScanItems];
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    if (base + k < nb) {
-      cstart[base + k] = ex;
-      count[base + k] = 0u;
-    }
+    o[k] = ex;
     ex += c[k];
+  }
+  if (base + kScanItems <= nb) {
+    *reinterpret_cast<uint4*>(cstart + base) = make_uint4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<uint4*>(cstart + base + 4) = make_uint4(o[4], o[5], o[6], o[7]);
+    *reinterpret_cast<uint4*>(count + base) = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(count + base + 4) = make_uint4(0u, 0u, 0u, 0u);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+      if (base + k < nb) {
+        cstart[base + k] = o[k];
+        count[base + k] = 0u;
+      }
   }
   // the thread holding the last element writes the grand total
   if (base <= nb - 1 && nb - 1 < base + kScanItems) cstart[nb] = ex;
+  if (filled) {
+    int lane = threadIdx.x & 31;
+    int inc = nf;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += t;
+    }
+    int wtot = __shfl_sync(0xffffffffu, inc, 31);
+    int wbase = 0;
+    if (lane == 31 && wtot) wbase = atomicAdd(&ctl->n_filled, wtot);
+    wbase = __shfl_sync(0xffffffffu, wbase, 31);
+    int pos = wbase + inc - nf;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+      if (c[k]) filled[pos++] = (uint32_t)(base + k);
+  }
 }
 
 __global__ void k_scatter(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ slot,
@@ -167,13 +215,46 @@ __global__ void k_scatter(int n, const uint32_t* __restrict__ key, const uint32_
   tsrc[q] = (uint32_t)i;
 }
 
-// Order each block's particles by caller index and move every field to its place.
+// Warp-segmented maximum over lanes holding the same block (lanes of one block are
+// consecutive); the first lane of each segment merges it into the block's stamped record.
+__device__ __forceinline__ void block_max_merge(uint32_t b, bool valid, float val, uint32_t stamp,
+                                                unsigned long long* rec) {
+  const unsigned full = 0xffffffffu;
+  int lane = threadIdx.x & 31;
+  unsigned long long tagged = valid ? (((unsigned long long)stamp << 32) | __float_as_uint(val)) : 0ull;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    unsigned long long o = __shfl_down_sync(full, tagged, d);
+    uint32_t ob = __shfl_down_sync(full, b, d);
+    if (lane + d < 32 && ob == b && o > tagged) tagged = o;
+  }
+  uint32_t prev = __shfl_up_sync(full, b, 1);
+  bool head = valid && (lane == 0 || prev != b);
+  if (head) atomicMax(rec + b, tagged);
+}
+
+// Order each block's particles by caller index and move every field to its place; the
+// fluid pass also merges |v|^2 and |a|^2 into the block maxima (Section 3.1 step 2).
 __global__ void k_canon_gather(int n, int max_per_block, const uint32_t* __restrict__ cstart,
                                const uint32_t* __restrict__ tkey, const uint32_t* __restrict__ tuid,
                                const uint32_t* __restrict__ tsrc, PState src, PState dst,
-                               uint32_t* __restrict__ key_out, Ctl* ctl) {
+                               uint32_t* __restrict__ key_out, Ctl* ctl, uint32_t stamp,
+                               unsigned long long* bmax_v, unsigned long long* bmax_a) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
+  bool valid = q < n;
+  if (bmax_v) {
+    // every lane reaches the shuffles of block_max_merge
+    uint32_t b = valid ? tkey[q] : 0xffffffffu;
+    float v2 = 0.f, a2 = 0.f;
+    if (valid) {
+      float4 vi = src.v[tsrc[q]], ai = src.a[tsrc[q]];
+      v2 = vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+      a2 = ai.x * ai.x + ai.y * ai.y + ai.z * ai.z;
+    }
+    block_max_merge(b, valid, v2, stamp, bmax_v);
+    block_max_merge(b, valid, a2, stamp, bmax_a);
+  }
+  if (!valid) return;
   uint32_t b = tkey[q];
   uint32_t beg = cstart[b], end = cstart[b + 1];
   if (q == (int)beg && (int)(end - beg) > max_per_block) set_status(ctl, RTS_ERR_CAPACITY);
@@ -197,30 +278,48 @@ __global__ void k_canon_gather(int n, int max_per_block, const uint32_t* __restr
   }
 }
 
-static rts_status scan_counts(rts_ctx* c) {
+static rts_status scan_counts(rts_ctx* c, uint32_t* filled) {
   int nb = c->dp.nblocks;
   int ntiles = (nb + kScanTile - 1) / kScanTile;
+  if (filled) cudaMemsetAsync(&c->ctl->n_filled, 0, sizeof(int), c->stream);
   k_scan_reduce<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums);
   k_scan_tiles<<<1, 1024, 0, c->stream>>>(c->tile_sums, ntiles);
-  k_scan_apply<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums, c->cstart);
+  k_scan_apply<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums, c->cstart,
+                                                        filled, c->ctl);
   return RTS_OK;
+}
+
+// Next stamp; on wrap-around every stamped record is cleared once.
+static void next_stamp(rts_ctx* c) {
+  if (++c->stamp >= (1u << 24)) {
+    size_t nb = (size_t)c->dp.nblocks;
+    cudaMemsetAsync(c->bmax_v, 0, sizeof(unsigned long long) * nb, c->stream);
+    cudaMemsetAsync(c->bmax_a, 0, sizeof(unsigned long long) * nb, c->stream);
+    cudaMemsetAsync(c->raw, 0, sizeof(uint32_t) * nb, c->stream);
+    cudaMemsetAsync(c->blevel, 0, sizeof(uint32_t) * nb, c->stream);
+    c->stamp = 1;
+  }
 }
 
 rts_status launch_bin(rts_ctx* c, float dt) {
   int n = c->n;
   if (n == 0) {
+    next_stamp(c);
     cudaMemsetAsync(c->cstart, 0, sizeof(uint32_t) * ((size_t)c->dp.nblocks + 1), c->stream);
+    cudaMemsetAsync(&c->ctl->n_filled, 0, sizeof(int), c->stream);
     return RTS_OK;
   }
   int tb = 256, g = (n + tb - 1) / tb;
   note_launch(c, 6);
+  next_stamp(c);
   k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, n, c->s.x, c->s.v, c->s.a, dt, c->key, c->slot,
                                           c->count, c->ctl);
-  scan_counts(c);
+  scan_counts(c, c->filled);
   k_scatter<<<g, tb, 0, c->stream>>>(n, c->key, c->slot, c->s.uid, c->cstart, c->key_tmp,
                                       c->tmp_uid, c->tmp_src);
   k_canon_gather<<<g, tb, 0, c->stream>>>(n, c->dp.max_per_block, c->cstart, c->key_tmp,
-                                           c->tmp_uid, c->tmp_src, c->s, c->s2, c->key, c->ctl);
+                                           c->tmp_uid, c->tmp_src, c->s, c->s2, c->key, c->ctl,
+                                           c->stamp, c->bmax_v, c->bmax_a);
   PState t = c->s;
   c->s = c->s2;
   c->s2 = t;
@@ -254,7 +353,7 @@ rts_status launch_bin_boundary(rts_ctx* c, const float4* xb_unsorted, int nb) {
                                           nullptr, 0.0f, key, slot, c->count, c->ctl);
   uint32_t* save = c->cstart;
   c->cstart = c->bcstart;
-  scan_counts(c);
+  scan_counts(c, nullptr);
   c->cstart = save;
   k_scatter<<<g, tb, 0, c->stream>>>(nb, key, slot, uid, c->bcstart, tkey, tuid, tsrc);
   PState src{}, dst{};
@@ -263,7 +362,7 @@ rts_status launch_bin_boundary(rts_ctx* c, const float4* xb_unsorted, int nb) {
   dst.x = c->xb;
   dst.uid = uid2;
   k_canon_gather<<<g, tb, 0, c->stream>>>(nb, 1 << 30, c->bcstart, tkey, tuid, tsrc, src, dst, key,
-                                           c->ctl);
+                                           c->ctl, 0u, nullptr, nullptr);
   e = cudaStreamSynchronize(c->stream);
   for (auto b : bufs) cudaFree(*b);
   if (e != cudaSuccess) {

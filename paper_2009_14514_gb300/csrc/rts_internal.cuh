@@ -27,6 +27,7 @@ struct DevParams {
   float visc_coef;   // 2 alpha h c_s
   float eps_h2;      // 0.01 h^2
   float gx, gy, gz;
+  int nbl_cap;       // neighbour list capacity per particle
   // levels (Section 3.1)
   int n_levels;
   int mult[kMaxLevels];
@@ -44,6 +45,7 @@ struct Ctl {
   unsigned long long pairs;      // neighbour pairs of evaluated particles
   unsigned long long act_blocks; // active blocks summed over steps
   unsigned long long cands;      // candidate pairs tested
+  int n_filled;                  // blocks holding a fluid particle (filled list length)
   unsigned long long vmax2_bits; // global max |v|^2 (FP64 bits, non-negative)
   unsigned long long amax2_bits; // global max |a|^2
   unsigned long long level_count[kMaxLevels];
@@ -99,8 +101,14 @@ struct rts_ctx {
   uint32_t* cstart;   // nblocks + 1
   uint32_t* tile_sums;
   int ntiles;
-  int8_t* raw;        // per block level from Eq. 1-3, -1 = empty
-  int8_t* blevel;     // per block level after smoothing
+  // Per-block records stamped with the binning pass that wrote them, so nothing has to
+  // be cleared between passes: a record is current iff its stamp equals c->stamp.
+  uint32_t stamp;                 // binning pass counter (1 .. 2^24 - 1)
+  unsigned long long* bmax_v;     // (stamp << 32) | FP32 bits of the block max |v|^2
+  unsigned long long* bmax_a;     // (stamp << 32) | FP32 bits of the block max |a|^2
+  uint32_t* raw;                  // (stamp << 8) | level from Eq. 1-3
+  uint32_t* blevel;               // (stamp << 8) | level after smoothing
+  uint32_t* filled;               // list of filled blocks of the current pass
   uint32_t* act;      // active block list
   rts::Ctl* ctl;
   rts::Ctl* h_ctl;    // pinned host mirror
@@ -114,6 +122,9 @@ struct rts_ctx {
   int32_t* io_i;      // n ints
 
   int grid_persistent;  // CTAs of the persistent neighbour kernels
+  uint32_t* nbl;        // neighbour lists of evaluated particles, nbl_cap per particle
+  int nbl_cap;
+  int last_global_level;
 
   // launch counting and optional per-phase event timing
   int cur_phase;

@@ -29,107 +29,131 @@ __device__ __forceinline__ int pick_level(const DevParams& P, double v2, double 
   return L;
 }
 
-// Raw block level from the block maxima of |v|^2 and |a|^2 (FP64, order independent).
-__global__ void k_block_raw(DevParams P, const uint32_t* __restrict__ cstart,
-                            const float4* __restrict__ v, const float4* __restrict__ a,
-                            int8_t* __restrict__ raw) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= P.nblocks) return;
-  uint32_t beg = cstart[b], end = cstart[b + 1];
-  if (beg == end) {
-    raw[b] = -1;
-    return;
+// Section 3.1 in FP32: thresholds rounded to FP32; a maximum within 1e-5 of a finite
+// threshold is undecided in FP32 (its error is below 3e-7 relative).
+__device__ __forceinline__ int pick_level_f(const DevParams& P, float v2, float a2, bool* undecided) {
+  int L = 0;
+  for (int l = 0; l < P.n_levels; ++l) {
+    float tv = (float)P.vthr2[l], ta = (float)P.athr2[l];
+    if (isfinite(tv) && fabsf(v2 - tv) <= 1e-5f * tv) *undecided = true;
+    if (isfinite(ta) && fabsf(a2 - ta) <= 1e-5f * ta) *undecided = true;
+    if (P.eq1[l] && v2 <= tv && a2 <= ta) L = l;
   }
-  double vm = 0.0, am = 0.0;
-  for (uint32_t i = beg; i < end; ++i) {
-    float4 vi = v[i], ai = a[i];
-    vm = fmax(vm, norm2d(vi.x, vi.y, vi.z));
-    am = fmax(am, norm2d(ai.x, ai.y, ai.z));
-  }
-  raw[b] = (int8_t)pick_level(P, vm, am);
+  return L;
 }
 
-// R_min (Section 4.2): a filled block takes the smallest level among itself and its
-// filled 26 neighbours (Jacobi: reads raw, writes lev), or the forced level.
-__global__ void k_block_smooth(DevParams P, const int8_t* __restrict__ raw, int8_t* __restrict__ lev) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= P.nblocks) return;
-  int L = raw[b];
-  if (L < 0) {
-    lev[b] = -1;
-    return;
-  }
-  if (P.force_level >= 0) {
-    lev[b] = (int8_t)P.force_level;
-    return;
-  }
-  int bx = b % P.nx, r = b / P.nx, by = r % P.ny, bz = r / P.ny;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int cz = bz + dz;
-    if (cz < 0 || cz >= P.nz) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int cy = by + dy;
-      if (cy < 0 || cy >= P.ny) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        int cx = bx + dx;
-        if (cx < 0 || cx >= P.nx) continue;
-        int Lc = raw[(cz * P.ny + cy) * P.nx + cx];
-        if (Lc >= 0 && Lc < L) L = Lc;
+// Raw level of every filled block (Section 3.1 steps 1-2) from the stamped FP32 block
+// maxima written by the sort; in the rare undecided case the exact FP64 maxima of the
+// block's particles decide, as the double-precision definition does.
+__global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled, const Ctl* ctl,
+                              const uint32_t* __restrict__ cstart, const float4* __restrict__ v,
+                              const float4* __restrict__ a,
+                              const unsigned long long* __restrict__ bmax_v,
+                              const unsigned long long* __restrict__ bmax_a, uint32_t stamp,
+                              uint32_t* __restrict__ raw) {
+  const int nf = ctl->n_filled;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    uint32_t b = filled[t];
+    float vm = __uint_as_float((uint32_t)bmax_v[b]);
+    float am = __uint_as_float((uint32_t)bmax_a[b]);
+    bool undecided = false;
+    int L = pick_level_f(P, vm, am, &undecided);
+    if (undecided) {
+      double vmd = 0.0, amd = 0.0;
+      for (uint32_t i = cstart[b]; i < cstart[b + 1]; ++i) {
+        float4 vi = v[i], ai = a[i];
+        vmd = fmax(vmd, norm2d(vi.x, vi.y, vi.z));
+        amd = fmax(amd, norm2d(ai.x, ai.y, ai.z));
       }
+      L = pick_level(P, vmd, amd);
     }
+    raw[b] = (stamp << 8) | (uint32_t)L;
   }
-  lev[b] = (int8_t)L;
 }
 
-// Algorithm 1 region bookkeeping per particle; blocks with an evaluated particle are
-// appended to the work list (warp-aggregated).
-__global__ void k_activity(DevParams P, int mode, int level_g, int mult_g,
-                           const uint32_t* __restrict__ cstart, const int8_t* __restrict__ lev,
-                           PState s, uint8_t* __restrict__ cflag, uint32_t* __restrict__ act,
-                           Ctl* ctl) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  int ncomp = 0;
-  if (b < P.nblocks) {
-    uint32_t beg = cstart[b], end = cstart[b + 1];
-    if (beg != end) {
-      int Lb = mode == kActGlobal ? level_g : (int)lev[b];
-      int mb = mode == kActGlobal ? mult_g : P.mult[Lb];
-      for (uint32_t i = beg; i < end; ++i) {
-        int c;
-        if (mode == kActRegional) {
-          int val = s.valid[i] - 1;
-          int li = s.level[i];
-          if (val <= 0 || li < 0 || P.mult[li] != mb) {
-            c = 1;
-            s.level[i] = Lb;
-            val = mb;
-          } else {
-            c = 0;
+// R_min (Section 4.2: a filled block takes the smallest level among itself and its
+// filled 26 neighbours, one Jacobi pass), or the forced / global level; then, with
+// mode >= 0, Algorithm 1's per-particle bookkeeping (validity, pre-emption on a level
+// change) and the work list of blocks holding an evaluated particle.
+__global__ void k_block_activity(DevParams P, int mode, int level_g, int mult_g,
+                                 const uint32_t* __restrict__ filled, Ctl* ctl,
+                                 const uint32_t* __restrict__ cstart,
+                                 const uint32_t* __restrict__ raw, uint32_t* __restrict__ blevel,
+                                 uint32_t stamp, PState s, uint8_t* __restrict__ cflag,
+                                 uint32_t* __restrict__ act) {
+  const int nf = ctl->n_filled;
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < nf; base += stride) {
+    const int t = base + threadIdx.x;
+    int ncomp = 0;
+    uint32_t b = 0;
+    if (t < nf) {
+      b = filled[t];
+      int L;
+      if (mode == kActGlobal) {
+        L = level_g;
+      } else if (P.force_level >= 0) {
+        L = P.force_level;
+      } else {
+        L = (int)(raw[b] & 0xffu);
+        int bx = b % P.nx, r = b / P.nx, by = r % P.ny, bz = r / P.ny;
+        for (int dz = -1; dz <= 1; ++dz) {
+          int cz = bz + dz;
+          if (cz < 0 || cz >= P.nz) continue;
+          for (int dy = -1; dy <= 1; ++dy) {
+            int cy = by + dy;
+            if (cy < 0 || cy >= P.ny) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+              int cx = bx + dx;
+              if (cx < 0 || cx >= P.nx) continue;
+              uint32_t rc = raw[((uint32_t)cz * P.ny + cy) * P.nx + cx];
+              if ((rc >> 8) == stamp && (int)(rc & 0xffu) < L) L = (int)(rc & 0xffu);
+            }
           }
-          s.valid[i] = val;
-        } else {
-          c = 1;
-          s.level[i] = Lb;
-          s.valid[i] = mb;
         }
-        cflag[i] = (uint8_t)c;
-        ncomp += c;
+      }
+      blevel[b] = (stamp << 8) | (uint32_t)L;
+      if (mode >= 0) {
+        const int mb = mode == kActGlobal ? mult_g : P.mult[L];
+        for (uint32_t i = cstart[b]; i < cstart[b + 1]; ++i) {
+          int c;
+          if (mode == kActRegional) {
+            int val = s.valid[i] - 1;
+            int li = s.level[i];
+            if (val <= 0 || li < 0 || P.mult[li] != mb) {
+              c = 1;
+              s.level[i] = L;
+              val = mb;
+            } else {
+              c = 0;
+            }
+            s.valid[i] = val;
+          } else {
+            c = 1;
+            s.level[i] = L;
+            s.valid[i] = mb;
+          }
+          cflag[i] = (uint8_t)c;
+          ncomp += c;
+        }
       }
     }
-  }
-  unsigned m = __ballot_sync(kFull, ncomp > 0);
-  int lane = threadIdx.x & 31;
-  unsigned long long tot = ncomp;
+    if (mode >= 0) {
+      unsigned m = __ballot_sync(kFull, ncomp > 0);
+      unsigned long long tot = ncomp;
 #pragma unroll
-  for (int o = 16; o; o >>= 1) tot += __shfl_down_sync(kFull, tot, o);
-  int base = 0;
-  if (lane == 0 && m) {
-    base = atomicAdd(&ctl->n_act, __popc(m));
-    atomicAdd(&ctl->evals, tot);
-    atomicAdd(&ctl->act_blocks, (unsigned long long)__popc(m));
+      for (int o = 16; o; o >>= 1) tot += __shfl_down_sync(kFull, tot, o);
+      int wb = 0;
+      if (lane == 0 && m) {
+        wb = atomicAdd(&ctl->n_act, __popc(m));
+        atomicAdd(&ctl->evals, tot);
+        atomicAdd(&ctl->act_blocks, (unsigned long long)__popc(m));
+      }
+      wb = __shfl_sync(kFull, wb, 0);
+      if (ncomp > 0) act[wb + __popc(m & ((1u << lane) - 1u))] = b;
+    }
   }
-  base = __shfl_sync(kFull, base, 0);
-  if (ncomp > 0) act[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)b;
 }
 
 // ---------------------------------------------------------------- kernel W ---
@@ -168,133 +192,259 @@ __device__ __forceinline__ float tait(const DevParams& P, float rho) {
   return fmaxf(0.0f, P.tait_B * (rg - 1.0f));
 }
 
-// Candidate rows of block b: for each (dz, dy) the x range [bx - 1, bx + 1] is one
-// contiguous run of the fluid (cstart) and of the boundary (bcstart) arrays.
-template <class FluidFn, class BndFn>
-__device__ __forceinline__ void for_candidates(const DevParams& P, int bx, int by, int bz,
-                                               const uint32_t* __restrict__ cstart,
-                                               const uint32_t* __restrict__ bcstart, int sub,
-                                               int lpp, FluidFn&& ff, BndFn&& bf) {
-  int xlo = bx > 0 ? bx - 1 : 0;
-  int xhi = bx + 1 < P.nx ? bx + 1 : P.nx - 1;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int cz = bz + dz;
-    if (cz < 0 || cz >= P.nz) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int cy = by + dy;
-      if (cy < 0 || cy >= P.ny) continue;
-      uint32_t rb = ((uint32_t)cz * P.ny + cy) * P.nx;
-      uint32_t fs = __ldg(&cstart[rb + xlo]), fe = __ldg(&cstart[rb + xhi + 1]);
-      for (uint32_t j = fs + sub; j < fe; j += lpp) ff(j);
-      uint32_t bs = __ldg(&bcstart[rb + xlo]), be = __ldg(&bcstart[rb + xhi + 1]);
-      for (uint32_t j = bs + sub; j < be; j += lpp) bf(j);
-    }
-  }
+// ------------------------------------------------------ neighbour passes ---
+
+constexpr int kNbThreads = 128;            // 4 warps per CTA, one active block per warp
+constexpr int kCap = 320;                  // candidates staged per warp and chunk
+constexpr uint32_t kBoundaryBit = 0x80000000u;  // neighbour index refers to a boundary particle
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// MODE 0: density, Tait pressure, neighbour count.  MODE 1: acceleration.
-template <int MODE>
-__global__ void __launch_bounds__(256) k_neighbor(DevParams P, const uint32_t* __restrict__ act,
-                                                  Ctl* ctl, const uint32_t* __restrict__ cstart,
-                                                  const uint32_t* __restrict__ bcstart, PState s,
-                                                  const float4* __restrict__ xb,
-                                                  const uint8_t* __restrict__ cflag,
-                                                  float4* __restrict__ anew) {
+__device__ __forceinline__ uint32_t warp_incl_sum(uint32_t v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t t = __shfl_up_sync(kFull, v, d);
+    if (lane >= d) v += t;
+  }
+  return v;
+}
+
+// The candidates of block b are 18 contiguous runs: for each of the 9 (dz, dy) rows the
+// x range [bx - 1, bx + 1] of the fluid array (runs 0-8) and of the boundary array
+// (runs 9-17).  Lane r < 18 holds run r's start and length; off is the run's offset in
+// the concatenation (fluid first).
+struct Runs {
+  uint32_t start, len, off, total, nfluid;
+};
+
+__device__ __forceinline__ Runs block_runs(const DevParams& P, int bx, int by, int bz,
+                                           const uint32_t* __restrict__ cstart,
+                                           const uint32_t* __restrict__ bcstart, int lane) {
+  Runs R;
+  R.start = 0;
+  R.len = 0;
+  if (lane < 18) {
+    int row = lane < 9 ? lane : lane - 9;
+    int cz = bz + row / 3 - 1, cy = by + row % 3 - 1;
+    if (cz >= 0 && cz < P.nz && cy >= 0 && cy < P.ny) {
+      int xlo = bx > 0 ? bx - 1 : 0;
+      int xhi = bx + 1 < P.nx ? bx + 1 : P.nx - 1;
+      uint32_t rb = ((uint32_t)cz * P.ny + cy) * P.nx;
+      const uint32_t* cs = lane < 9 ? cstart : bcstart;
+      R.start = __ldg(&cs[rb + xlo]);
+      R.len = __ldg(&cs[rb + xhi + 1]) - R.start;
+    }
+  }
+  uint32_t inc = warp_incl_sum(R.len, lane);
+  R.off = inc - R.len;
+  R.total = __shfl_sync(kFull, inc, 17);
+  R.nfluid = __shfl_sync(kFull, inc, 8);
+  return R;
+}
+
+// Stage candidates [c0, c0 + cnt) of the concatenated runs into shared memory with
+// asynchronous 16-byte copies, with each candidate's index (boundary: top bit set).
+__device__ __forceinline__ void stage_chunk(const Runs& R, uint32_t c0, uint32_t cnt,
+                                            const float4* __restrict__ xf,
+                                            const float4* __restrict__ xbnd, float4* sx,
+                                            uint32_t* sidx, int lane) {
+#pragma unroll 1
+  for (int r = 0; r < 18; ++r) {
+    uint32_t st = __shfl_sync(kFull, R.start, r);
+    uint32_t ln = __shfl_sync(kFull, R.len, r);
+    uint32_t of = __shfl_sync(kFull, R.off, r);
+    uint32_t lo = of > c0 ? of : c0;
+    uint32_t hi = of + ln < c0 + cnt ? of + ln : c0 + cnt;
+    if (lo >= hi) continue;
+    const float4* src = r < 9 ? xf : xbnd;
+    const uint32_t tag = r < 9 ? 0u : kBoundaryBit;
+    for (uint32_t k = lo + lane; k < hi; k += 32) {
+      uint32_t g = st + (k - of);
+      cp_async16(&sx[k - c0], &src[g]);
+      sidx[k - c0] = g | tag;
+    }
+  }
+  cp_async_wait_all();
+  __syncwarp();
+}
+
+// The evaluated particles of one active block, split over the warp's lanes: lpp lanes
+// per particle (a power of two), particle pid of the group, lane sub within it.
+struct Group {
+  int i, lpp, pid, sub;
+  unsigned gmask;
+};
+
+__device__ __forceinline__ bool next_group(uint32_t base, uint32_t end,
+                                           const uint8_t* __restrict__ cflag, int lane, Group& G) {
+  const uint32_t ii = base + lane;
+  const bool c = ii < end && cflag[ii];
+  const unsigned m = __ballot_sync(kFull, c);
+  if (!m) return false;
+  const int nc = __popc(m);
+  const int np2 = nc <= 1 ? 1 : 1 << (32 - __clz(nc - 1));
+  G.lpp = 32 / np2;
+  G.pid = lane / G.lpp;
+  G.sub = lane - G.pid * G.lpp;
+  G.gmask = (G.lpp == 32 ? kFull : ((1u << G.lpp) - 1u)) << (G.pid * G.lpp);
+  G.i = -1;
+  if (G.pid < nc) {  // position of the pid-th set bit of m
+    unsigned mm = m;
+    for (int q = 0; q < G.pid; ++q) mm &= mm - 1u;
+    G.i = (int)(base + (uint32_t)(__ffs(mm) - 1));
+  }
+  return true;
+}
+
+// Density pass (Algorithm 1, "find neighborhoods" and "update rho, p"): every evaluated
+// particle tests the staged candidates of its block's 27-block stencil with the exact
+// predicate, sums m W over its neighbours (itself included), applies the Tait equation
+// and records its neighbour list for the force pass.
+__global__ void __launch_bounds__(kNbThreads) k_density(DevParams P, const uint32_t* __restrict__ act,
+                                                        Ctl* ctl, const uint32_t* __restrict__ cstart,
+                                                        const uint32_t* __restrict__ bcstart, PState s,
+                                                        const float4* __restrict__ xb,
+                                                        const uint8_t* __restrict__ cflag,
+                                                        uint32_t* __restrict__ nbl) {
+  extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float4* sx = smem + wib * kCap;
+  uint32_t* sidx = reinterpret_cast<uint32_t*>(smem + (kNbThreads / 32) * kCap) + wib * kCap;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n_act = *(volatile int*)&ctl->n_act;
+  const unsigned below = (1u << lane) - 1u;
   unsigned long long pairs = 0, tests = 0;
   for (int t = warp; t < n_act; t += nwarps) {
     const uint32_t b = act[t];
     const int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
     const uint32_t beg = cstart[b], end = cstart[b + 1];
+    const Runs R = block_runs(P, bx, by, bz, cstart, bcstart, lane);
     for (uint32_t base = beg; base < end; base += 32) {
-      const uint32_t ii = base + lane;
-      const bool c = ii < end && cflag[ii];
-      const unsigned m = __ballot_sync(kFull, c);
-      if (!m) continue;
-      const int nc = __popc(m);
-      const int np2 = nc <= 1 ? 1 : 1 << (32 - __clz(nc - 1));
-      const int lpp = 32 / np2;
-      const int pid = lane / lpp, sub = lane - pid * lpp;
-      int i = -1;
-      if (pid < nc) {  // position of the pid-th set bit of m
-        unsigned mm = m;
-        for (int q = 0; q < pid; ++q) mm &= mm - 1u;
-        i = (int)(base + (uint32_t)(__ffs(mm) - 1));
-      }
+      Group G;
+      if (!next_group(base, end, cflag, lane, G)) continue;
+      const int i = G.i;
       const float4 xi = i >= 0 ? s.x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-      if (MODE == 0) {
-        float wsum = 0.0f;
-        int cnt = 0, ntest = 0;
-        auto add = [&](float4 xj) {
-          ++ntest;
-          float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-          float d2 = dx * dx + dy * dy + dz * dz;
-          if (d2 < P.r2_hi && (d2 < P.r2_lo || exact_nbr(xi, xj, P.r2d))) {
-            ++cnt;
-            wsum += spline_W(P, sqrtf(d2) * P.inv_h);
+      uint32_t* list = nbl + (size_t)(i >= 0 ? i : 0) * P.nbl_cap;
+      float wsum = 0.f;
+      int nn = 0, ntest = 0;
+      for (uint32_t c0 = 0; c0 < R.total; c0 += kCap) {
+        const uint32_t cn = R.total - c0 < (uint32_t)kCap ? R.total - c0 : (uint32_t)kCap;
+        __syncwarp();
+        stage_chunk(R, c0, cn, s.x, xb, sx, sidx, lane);
+        for (uint32_t kb = 0; kb < cn; kb += G.lpp) {
+          const uint32_t k = kb + G.sub;
+          const bool valid = i >= 0 && k < cn;
+          const float4 xj = valid ? sx[k] : xi;
+          const uint32_t jg = valid ? sidx[k] : (uint32_t)i;
+          const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+          const float d2 = dx * dx + dy * dy + dz * dz;
+          const bool in = valid && d2 < P.r2_hi && (d2 < P.r2_lo || exact_nbr(xi, xj, P.r2d));
+          const float d = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
+          wsum += in ? spline_W(P, d * P.inv_h) : 0.f;
+          const bool put = in && jg != (uint32_t)i;
+          const unsigned hit = __ballot_sync(kFull, put) & G.gmask;
+          const int pos = nn + __popc(hit & below);
+          if (put && pos < P.nbl_cap) list[pos] = jg;
+          nn += __popc(hit);
+          ntest += valid ? 1 : 0;
+        }
+      }
+      for (int o = G.lpp >> 1; o; o >>= 1) wsum += __shfl_down_sync(kFull, wsum, o, G.lpp);
+      if (i >= 0) tests += (unsigned long long)ntest;
+      if (G.sub == 0 && i >= 0) {
+        if (nn > P.nbl_cap) set_status(ctl, RTS_ERR_CAPACITY);
+        float rho = P.m * wsum;
+        float p = tait(P, rho);
+        s.rho[i] = rho;
+        s.prs[i] = p;
+        s.nbr[i] = nn;
+        s.x[i].w = p / (rho * rho);
+        s.v[i].w = rho;
+        pairs += (unsigned long long)nn;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    pairs += __shfl_down_sync(kFull, pairs, o);
+    tests += __shfl_down_sync(kFull, tests, o);
+  }
+  if (lane == 0 && pairs) atomicAdd(&ctl->pairs, pairs);
+  if (lane == 0 && tests) atomicAdd(&ctl->cands, tests);
+}
+
+// Force pass (Algorithm 1, "update F^{p,v,g}"): every evaluated particle walks the
+// neighbour list of the density pass.  Pressure: -m (p_i/rho_i^2 + p_j/rho_j^2) grad W;
+// boundary neighbours: -m p_i/rho_i^2 grad W.  Artificial viscosity for approaching
+// pairs with nu = 2 alpha h c / (rho_i + rho_j) (boundary: rho_j = rho_i, v_j = 0).
+__global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_t* __restrict__ act,
+                                                      Ctl* ctl, const uint32_t* __restrict__ cstart,
+                                                      PState s, const float4* __restrict__ xb,
+                                                      const uint8_t* __restrict__ cflag,
+                                                      const uint32_t* __restrict__ nbl,
+                                                      float4* __restrict__ anew) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int n_act = *(volatile int*)&ctl->n_act;
+  const float4* __restrict__ xf = s.x;
+  const float4* __restrict__ vf = s.v;
+  for (int t = warp; t < n_act; t += nwarps) {
+    const uint32_t b = act[t];
+    const uint32_t beg = cstart[b], end = cstart[b + 1];
+    for (uint32_t base = beg; base < end; base += 32) {
+      Group G;
+      if (!next_group(base, end, cflag, lane, G)) continue;
+      const int i = G.i;
+      float ax = 0.f, ay = 0.f, az = 0.f;
+      if (i >= 0) {
+        const float4 xi = xf[i], vi = vf[i];
+        int nn = s.nbr[i];
+        if (nn > P.nbl_cap) nn = P.nbl_cap;
+        const uint32_t* list = nbl + (size_t)i * P.nbl_cap;
+        for (int e = G.sub; e < nn; e += G.lpp) {
+          const uint32_t jg = __ldg(&list[e]);
+          float4 xj, vj;
+          float pcj;
+          if (jg & kBoundaryBit) {
+            xj = __ldg(&xb[jg & ~kBoundaryBit]);
+            vj = make_float4(0.f, 0.f, 0.f, vi.w);
+            pcj = 0.f;
+          } else {
+            xj = xf[jg];
+            vj = vf[jg];
+            pcj = xj.w;
           }
-        };
-        for_candidates(P, bx, by, bz, cstart, bcstart, sub, lpp,
-                       [&](uint32_t j) { add(s.x[j]); }, [&](uint32_t j) { add(xb[j]); });
-        for (int o = lpp >> 1; o; o >>= 1) {
-          wsum += __shfl_down_sync(kFull, wsum, o, lpp);
-          cnt += __shfl_down_sync(kFull, cnt, o, lpp);
-        }
-        if (i >= 0) tests += (unsigned long long)ntest;
-        if (sub == 0 && i >= 0) {
-          float rho = P.m * wsum;
-          float p = tait(P, rho);
-          s.rho[i] = rho;
-          s.prs[i] = p;
-          s.nbr[i] = cnt - 1;  // the particle itself passed the predicate
-          s.x[i].w = p / (rho * rho);
-          s.v[i].w = rho;
-          pairs += (unsigned long long)(cnt - 1);
-        }
-      } else {
-        const float4 vi = i >= 0 ? s.v[i] : make_float4(0.f, 0.f, 0.f, 1.f);
-        float ax = 0.f, ay = 0.f, az = 0.f;
-        auto add = [&](float4 xj, float vjx, float vjy, float vjz, float pcj, float rhoj) {
-          float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-          float d2 = dx * dx + dy * dy + dz * dz;
-          if (d2 < P.r2 && d2 > 0.0f) {
-            float d = sqrtf(d2);
-            float f = spline_dW(P, d * P.inv_h) / d;
-            float vx = (vi.x - vjx) * dx + (vi.y - vjy) * dy + (vi.z - vjz) * dz;
-            float visc = vx < 0.0f ? -P.visc_coef * vx / ((vi.w + rhoj) * (d2 + P.eps_h2)) : 0.0f;
-            float sc = -P.m * (xi.w + pcj + visc) * f;
+          const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+          const float d2 = dx * dx + dy * dy + dz * dz;
+          if (d2 > 0.f) {
+            const float inv_d = rsqrtf(d2);
+            const float f = spline_dW(P, d2 * inv_d * P.inv_h) * inv_d;
+            const float vx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+            const float visc =
+                vx < 0.0f ? -P.visc_coef * __fdividef(vx, (vi.w + vj.w) * (d2 + P.eps_h2)) : 0.0f;
+            const float sc = -P.m * (xi.w + pcj + visc) * f;
             ax += sc * dx;
             ay += sc * dy;
             az += sc * dz;
           }
-        };
-        for_candidates(
-            P, bx, by, bz, cstart, bcstart, sub, lpp,
-            [&](uint32_t j) {
-              float4 xj = s.x[j], vj = s.v[j];
-              add(xj, vj.x, vj.y, vj.z, xj.w, vj.w);
-            },
-            [&](uint32_t j) { add(xb[j], 0.f, 0.f, 0.f, 0.f, vi.w); });
-        for (int o = lpp >> 1; o; o >>= 1) {
-          ax += __shfl_down_sync(kFull, ax, o, lpp);
-          ay += __shfl_down_sync(kFull, ay, o, lpp);
-          az += __shfl_down_sync(kFull, az, o, lpp);
         }
-        if (sub == 0 && i >= 0) anew[i] = make_float4(P.gx + ax, P.gy + ay, P.gz + az, 0.f);
       }
+      for (int o = G.lpp >> 1; o; o >>= 1) {
+        ax += __shfl_down_sync(kFull, ax, o, G.lpp);
+        ay += __shfl_down_sync(kFull, ay, o, G.lpp);
+        az += __shfl_down_sync(kFull, az, o, G.lpp);
+      }
+      if (G.sub == 0 && i >= 0) anew[i] = make_float4(P.gx + ax, P.gy + ay, P.gz + az, 0.f);
     }
-  }
-  if (MODE == 0) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      pairs += __shfl_down_sync(kFull, pairs, o);
-      tests += __shfl_down_sync(kFull, tests, o);
-    }
-    if (lane == 0 && pairs) atomicAdd(&ctl->pairs, pairs);
-    if (lane == 0 && tests) atomicAdd(&ctl->cands, tests);
   }
 }
 
@@ -358,62 +508,82 @@ __global__ void k_global_max(int n, const float4* __restrict__ v, const float4* 
 }
 
 __global__ void k_level_hist(int n, const int32_t* __restrict__ level, Ctl* ctl) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
+  __shared__ unsigned int h[kMaxLevels];
+  if (threadIdx.x < kMaxLevels) h[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int L = level[i];
-    if (L >= 0 && L < kMaxLevels) atomicAdd(&ctl->level_count[L], 1ull);
+    if (L >= 0 && L < kMaxLevels) atomicAdd(&h[L], 1u);
   }
+  __syncthreads();
+  if (threadIdx.x < kMaxLevels && h[threadIdx.x])
+    atomicAdd(&ctl->level_count[threadIdx.x], (unsigned long long)h[threadIdx.x]);
 }
 
 // ------------------------------------------------------------------ launch ---
 
 // CTAs of the persistent neighbour kernels: every resident slot of every SM.
-int neighbor_grid_size() {
-  int dev = 0, sms = 1, occ = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_neighbor<1>, 256, 0);
-  if (occ < 1) occ = 1;
-  return sms * occ;
+static int g_sms = 0;
+static int sm_count() {
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms < 1) g_sms = 1;
+  }
+  return g_sms;
 }
 
+static size_t density_smem() { return (size_t)(kNbThreads / 32) * kCap * (sizeof(float4) + sizeof(uint32_t)); }
+
+int neighbor_grid_size() {
+  int occ0 = 1, occ1 = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_density, kNbThreads, density_smem());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_force, kNbThreads, 0);
+  int occ = occ0 < occ1 ? occ0 : occ1;
+  if (occ < 1) occ = 1;
+  return sm_count() * occ;
+}
+
+static int filled_grid() { return sm_count() * 8; }
+
 rts_status launch_classify(rts_ctx* c) {
-  int nb = c->dp.nblocks, tb = 256, g = (nb + tb - 1) / tb;
-  note_launch(c, 2);
-  k_block_raw<<<g, tb, 0, c->stream>>>(c->dp, c->cstart, c->s.v, c->s.a, c->raw);
-  k_block_smooth<<<g, tb, 0, c->stream>>>(c->dp, c->raw, c->blevel);
+  note_launch(c, 1);
+  k_block_level<<<filled_grid(), 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->cstart, c->s.v,
+                                                      c->s.a, c->bmax_v, c->bmax_a, c->stamp,
+                                                      c->raw);
   return RTS_OK;
 }
 
+// mode < 0: smoothing only (public classification); otherwise smoothing + activity.
 rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g) {
-  int nb = c->dp.nblocks, tb = 256, g = (nb + tb - 1) / tb;
   cudaMemsetAsync(&c->ctl->n_act, 0, sizeof(int), c->stream);
   note_launch(c, 1);
-  k_activity<<<g, tb, 0, c->stream>>>(c->dp, mode, level_g, mult_g, c->cstart, c->blevel, c->s,
-                                       c->cflag, c->act, c->ctl);
+  k_block_activity<<<filled_grid(), 256, 0, c->stream>>>(c->dp, mode, level_g, mult_g, c->filled,
+                                                         c->ctl, c->cstart, c->raw, c->blevel,
+                                                         c->stamp, c->s, c->cflag, c->act);
   return RTS_OK;
 }
 
 rts_status launch_density(rts_ctx* c) {
   note_launch(c, 1);
-  k_neighbor<0><<<c->grid_persistent, 256, 0, c->stream>>>(c->dp, c->act, c->ctl, c->cstart,
-                                                            c->bcstart, c->s, c->xb, c->cflag,
-                                                            c->anew);
+  k_density<<<c->grid_persistent, kNbThreads, density_smem(), c->stream>>>(
+      c->dp, c->act, c->ctl, c->cstart, c->bcstart, c->s, c->xb, c->cflag, c->nbl);
   return RTS_OK;
 }
 
 rts_status launch_force(rts_ctx* c) {
   note_launch(c, 1);
-  k_neighbor<1><<<c->grid_persistent, 256, 0, c->stream>>>(c->dp, c->act, c->ctl, c->cstart,
-                                                            c->bcstart, c->s, c->xb, c->cflag,
-                                                            c->anew);
+  k_force<<<c->grid_persistent, kNbThreads, 0, c->stream>>>(
+      c->dp, c->act, c->ctl, c->cstart, c->s, c->xb, c->cflag, c->nbl, c->anew);
   return RTS_OK;
 }
 
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime) {
   note_launch(c, 1);
-  k_correct<<<c->grid_persistent, 256, 0, c->stream>>>(c->dp, c->act, c->ctl, c->cstart, c->s,
-                                                       c->cflag, c->anew, (int)k1, prime);
+  k_correct<<<c->grid_persistent, kNbThreads, 0, c->stream>>>(c->dp, c->act, c->ctl, c->cstart,
+                                                              c->s, c->cflag, c->anew, (int)k1,
+                                                              prime);
   return RTS_OK;
 }
 
@@ -427,9 +597,8 @@ rts_status launch_global_max(rts_ctx* c) {
 
 rts_status launch_level_hist(rts_ctx* c) {
   cudaMemsetAsync(&c->ctl->level_count[0], 0, sizeof(unsigned long long) * kMaxLevels, c->stream);
-  int tb = 256, g = (c->n + tb - 1) / tb;
   if (c->n > 0) note_launch(c, 1);
-  if (c->n > 0) k_level_hist<<<g, tb, 0, c->stream>>>(c->n, c->s.level, c->ctl);
+  if (c->n > 0) k_level_hist<<<sm_count() * 4, 256, 0, c->stream>>>(c->n, c->s.level, c->ctl);
   return RTS_OK;
 }
 
