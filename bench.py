@@ -363,6 +363,7 @@ def main():
         "evals_per_s": ours["tot"]["particle_evals"] / (total_ms / 1e3),
         "pair_interactions_per_s": pairs / (total_ms / 1e3),
         "active_fraction": ours["tot"]["particle_evals"] / max(1, sc.n * subs),
+        "evals_per_active_block": ours["tot"]["particle_evals"] / max(1, ours["tot"]["active_blocks"]),
         "density_error": ours["rho_err"], "level_count": ours["levels"],
         "roofline": roofline, "clocks": clocks,
     }

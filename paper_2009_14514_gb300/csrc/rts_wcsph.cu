@@ -305,7 +305,9 @@ __device__ __forceinline__ bool next_group(uint32_t base, uint32_t end,
 // Density pass (Algorithm 1, "find neighborhoods" and "update rho, p"): every evaluated
 // particle tests the staged candidates of its block's 27-block stencil with the exact
 // predicate, sums m W over its neighbours (itself included), applies the Tait equation
-// and records its neighbour list for the force pass.
+// and records its neighbour list for the force pass.  Each lane keeps a bit per tested
+// candidate and appends its hits every 32 iterations (segmented prefix over the lpp
+// lanes of its particle), so the list order is fixed by the group layout.
 __global__ void __launch_bounds__(kNbThreads) k_density(DevParams P, const uint32_t* __restrict__ act,
                                                         Ctl* ctl, const uint32_t* __restrict__ cstart,
                                                         const uint32_t* __restrict__ bcstart, PState s,
@@ -320,7 +322,6 @@ __global__ void __launch_bounds__(kNbThreads) k_density(DevParams P, const uint3
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n_act = *(volatile int*)&ctl->n_act;
-  const unsigned below = (1u << lane) - 1u;
   unsigned long long pairs = 0, tests = 0;
   for (int t = warp; t < n_act; t += nwarps) {
     const uint32_t b = act[t];
@@ -331,35 +332,58 @@ __global__ void __launch_bounds__(kNbThreads) k_density(DevParams P, const uint3
       Group G;
       if (!next_group(base, end, cflag, lane, G)) continue;
       const int i = G.i;
-      const float4 xi = i >= 0 ? s.x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-      uint32_t* list = nbl + (size_t)(i >= 0 ? i : 0) * P.nbl_cap;
+      const bool gvalid = i >= 0;
+      const uint32_t lpp = (uint32_t)G.lpp, sub = (uint32_t)G.sub;
+      const float4 xi = gvalid ? s.x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      uint32_t* list = nbl + (size_t)(gvalid ? i : 0) * P.nbl_cap;
       float wsum = 0.f;
-      int nn = 0, ntest = 0;
+      int nn = 0;
       for (uint32_t c0 = 0; c0 < R.total; c0 += kCap) {
         const uint32_t cn = R.total - c0 < (uint32_t)kCap ? R.total - c0 : (uint32_t)kCap;
         __syncwarp();
         stage_chunk(R, c0, cn, s.x, xb, sx, sidx, lane);
-        for (uint32_t kb = 0; kb < cn; kb += G.lpp) {
-          const uint32_t k = kb + G.sub;
-          const bool valid = i >= 0 && k < cn;
-          const float4 xj = valid ? sx[k] : xi;
-          const uint32_t jg = valid ? sidx[k] : (uint32_t)i;
-          const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-          const float d2 = dx * dx + dy * dy + dz * dz;
-          const bool in = valid && d2 < P.r2_hi && (d2 < P.r2_lo || exact_nbr(xi, xj, P.r2d));
-          const float d = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
-          wsum += in ? spline_W(P, d * P.inv_h) : 0.f;
-          const bool put = in && jg != (uint32_t)i;
-          const unsigned hit = __ballot_sync(kFull, put) & G.gmask;
-          const int pos = nn + __popc(hit & below);
-          if (put && pos < P.nbl_cap) list[pos] = jg;
-          nn += __popc(hit);
-          ntest += valid ? 1 : 0;
+        const uint32_t iters = (cn + lpp - 1) / lpp;  // uniform over the warp
+        for (uint32_t r0 = 0; r0 < iters; r0 += 32) {
+          const uint32_t rn = iters - r0 < 32u ? iters - r0 : 32u;
+          uint32_t bits = 0;
+#pragma unroll 2
+          for (uint32_t j = 0; j < rn; ++j) {
+            const uint32_t k = (r0 + j) * lpp + sub;
+            const bool valid = gvalid && k < cn;
+            const float4 xj = sx[valid ? k : 0u];
+            const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            bool in = valid && d2 < P.r2_lo;
+            if (valid && d2 >= P.r2_lo && d2 < P.r2_hi) in = exact_nbr(xi, xj, P.r2d);
+            const float d = d2 * rsqrtf(d2);
+            const float w = spline_W(P, d * P.inv_h);
+            if (in) wsum += d2 > 0.f ? w : P.sigma;
+            // a neighbour is any candidate passing the predicate except the particle itself
+            bool put = in && d2 > 0.f;
+            if (in && d2 == 0.f) put = sidx[k] != (uint32_t)i;
+            bits |= put ? (1u << j) : 0u;
+          }
+          // append this round's hits: segmented exclusive prefix over the group's lanes
+          const int c = __popc(bits);
+          int inc = c;
+          for (uint32_t o = 1; o < lpp; o <<= 1) {
+            int tv = __shfl_up_sync(kFull, inc, o, lpp);
+            if (sub >= o) inc += tv;
+          }
+          const int tot = __shfl_sync(kFull, inc, lpp - 1, lpp);
+          int pos = nn + inc - c;
+          while (bits) {
+            const uint32_t bj = (uint32_t)(__ffs(bits) - 1);
+            bits &= bits - 1u;
+            if (pos < P.nbl_cap) list[pos] = sidx[(r0 + bj) * lpp + sub];
+            ++pos;
+          }
+          nn += tot;
         }
+        if (gvalid && sub == 0) tests += cn;
       }
-      for (int o = G.lpp >> 1; o; o >>= 1) wsum += __shfl_down_sync(kFull, wsum, o, G.lpp);
-      if (i >= 0) tests += (unsigned long long)ntest;
-      if (G.sub == 0 && i >= 0) {
+      for (uint32_t o = lpp >> 1; o; o >>= 1) wsum += __shfl_down_sync(kFull, wsum, o, lpp);
+      if (sub == 0 && gvalid) {
         if (nn > P.nbl_cap) set_status(ctl, RTS_ERR_CAPACITY);
         float rho = P.m * wsum;
         float p = tait(P, rho);
