@@ -129,10 +129,13 @@ def _declare(L):
     L.orc_wcsph_evaluate.argtypes = [vp, vp]
     L.orc_wcsph_substep.argtypes = [vp, vp]
     L.orc_wcsph_global_step.argtypes = [vp, vp, i32, vp]
-    for name in ("orc_pcisph_init", "orc_pcisph_step", "orc_pcisph_delta",
-                 "orc_classify_pcisph"):
-        if hasattr(L, name):
-            pass
+    L.orc_pcisph_delta.restype = dbl
+    L.orc_pcisph_delta.argtypes = [vp]
+    L.orc_classify_pcisph.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    L.orc_observed_blocks.restype = None
+    L.orc_observed_blocks.argtypes = [vp, vp, vp, vp]
+    L.orc_pcisph_step.argtypes = [vp, vp]
+    L.orc_pcisph_plain_step.argtypes = [vp, vp]
 
 
 class OracleError(RuntimeError):
@@ -288,3 +291,114 @@ class WCSPH:
         _check(lib().orc_wcsph_global_step(C.byref(self.P), C.byref(self.S), int(max_mult),
                                            C.byref(used)), "orc_wcsph_global_step")
         return used.value
+
+
+# ------------------------------------------------------------------ PCISPH ---
+
+class PState(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32), ("nb", C.c_int32),
+        ("x", C.c_void_p), ("v", C.c_void_p), ("anp", C.c_void_p), ("ap", C.c_void_p),
+        ("p", C.c_void_p), ("rho", C.c_void_p), ("err", C.c_void_p),
+        ("level", C.c_void_p), ("validity", C.c_void_p), ("compute", C.c_void_p),
+        ("nbr_cnt", C.c_void_p), ("nbr_idx", C.c_void_p), ("cap", C.c_int32),
+        ("xb", C.c_void_p), ("pblock", C.c_void_p), ("cs", C.c_void_p), ("pm", C.c_void_p),
+        ("bcs", C.c_void_p), ("bpm", C.c_void_p), ("block_level", C.c_void_p),
+        ("block_raw", C.c_void_p), ("block_ob", C.c_void_p), ("p_backup", C.c_void_p),
+        ("in_se", C.c_void_p), ("minor", C.c_int32), ("n_minor_cur", C.c_int32),
+        ("clean", C.c_int32), ("shorten_now", C.c_int32), ("k", C.c_int64),
+        ("iters", C.c_int32), ("global_iters", C.c_int32), ("local_iters", C.c_int32),
+        ("reverts", C.c_int32), ("not_converged", C.c_int32),
+        ("err_max", C.c_double), ("err_avg", C.c_double),
+        ("total_iters", C.c_int64), ("total_local", C.c_int64), ("total_restarts", C.c_int64),
+    ]
+
+
+def pcisph_delta(P):
+    return lib().orc_pcisph_delta(C.byref(P))
+
+
+def classify_pcisph(P, x, v, a):
+    x, v, a = d3(x), d3(v), d3(a)
+    B = n_blocks(P)
+    raw = np.zeros(B, np.int32)
+    lev = np.zeros(B, np.int32)
+    _check(lib().orc_classify_pcisph(C.byref(P), x.shape[0], _p(x), _p(v), _p(a), _p(raw),
+                                     _p(lev)), "orc_classify_pcisph")
+    return raw, lev
+
+
+def observed_blocks(P, block_level, in_re=None):
+    lev = np.ascontiguousarray(block_level, np.int32)
+    re_ = None if in_re is None else np.ascontiguousarray(in_re, np.uint8)
+    ob = np.zeros(len(lev), np.uint8)
+    lib().orc_observed_blocks(C.byref(P), _p(lev), _p(re_), _p(ob))
+    return ob
+
+
+class PCISPH:
+    """RTS-PCISPH state (user order, FP64) advanced by the oracle."""
+
+    def __init__(self, P, x, v, xb, cap=None):
+        self.P = P
+        n = len(x)
+        B = n_blocks(P)
+        self.cap = int(cap or P.max_neighbors)
+        self.x = d3(x).copy()
+        self.v = d3(v).copy()
+        self.anp = np.zeros((n, 3))
+        self.ap = np.zeros((n, 3))
+        self.p = np.zeros(n)
+        self.rho = np.full(n, P.rho0)
+        self.err = np.zeros(n)
+        self.level = np.zeros(n, np.int32)
+        self.validity = np.zeros(n, np.int32)
+        self.compute = np.ones(n, np.uint8)
+        self.nbr_cnt = np.zeros(n, np.int32)
+        self.nbr_idx = np.zeros(max(n, 1) * self.cap, np.int32)
+        self.xb = d3(xb).copy()
+        self.pblock = np.zeros(max(n, 1), np.int32)
+        self.cs = np.zeros(B + 1, np.int32)
+        self.pm = np.zeros(max(n, 1), np.int32)
+        _, self.bpm, self.bcs = bin_particles(P, self.xb) if len(self.xb) else (
+            None, np.zeros(1, np.int32), np.zeros(B + 1, np.int32))
+        self.bpm = np.ascontiguousarray(self.bpm, np.int32)
+        self.bcs = np.ascontiguousarray(self.bcs, np.int32)
+        self.block_level = np.full(B, -1, np.int32)
+        self.block_raw = np.full(B, -1, np.int32)
+        self.block_ob = np.zeros(B, np.uint8)
+        self.p_backup = np.zeros(max(n, 1))
+        self.in_se = np.zeros(max(n, 1), np.uint8)
+        self.S = PState()
+        self.S.n = n
+        self.S.nb = self.xb.shape[0]
+        self.S.cap = self.cap
+        for f in ("x", "v", "anp", "ap", "p", "rho", "err", "level", "validity", "compute",
+                  "nbr_cnt", "nbr_idx", "xb", "pblock", "cs", "pm", "bcs", "bpm",
+                  "block_level", "block_raw", "block_ob", "p_backup", "in_se"):
+            setattr(self.S, f, getattr(self, f).ctypes.data)
+        self.S.n_minor_cur = P.n_minor
+
+    def step(self, allow_not_converged=True):
+        st = lib().orc_pcisph_step(C.byref(self.P), C.byref(self.S))
+        if st == 6 and allow_not_converged:
+            return st
+        _check(st, "orc_pcisph_step")
+        return st
+
+    def plain_step(self, allow_not_converged=True):
+        st = lib().orc_pcisph_plain_step(C.byref(self.P), C.byref(self.S))
+        if st == 6 and allow_not_converged:
+            return st
+        _check(st, "orc_pcisph_plain_step")
+        return st
+
+    def neighbors(self, i):
+        return self.nbr_idx[i * self.cap: i * self.cap + self.nbr_cnt[i]]
+
+    @property
+    def stats(self):
+        S = self.S
+        return dict(iters=S.iters, global_iters=S.global_iters, local_iters=S.local_iters,
+                    reverts=S.reverts, not_converged=S.not_converged, err_max=S.err_max,
+                    err_avg=S.err_avg, minor=S.minor, n_minor_cur=S.n_minor_cur, k=S.k)

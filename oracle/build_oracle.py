@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "_lib", "liboracle.so")
 
 def build(force: bool = False) -> str:
     srcs = [os.path.join(HERE, s) for s in SOURCES if os.path.exists(os.path.join(HERE, s))]
-    deps = srcs + [os.path.join(HERE, "rts_oracle.h")]
+    deps = srcs + [os.path.join(HERE, "rts_oracle.h"), os.path.join(HERE, "oracle_internal.h")]
     if not force and os.path.exists(OUT):
         t = os.path.getmtime(OUT)
         if all(os.path.getmtime(d) <= t for d in deps):

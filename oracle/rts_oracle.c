@@ -21,6 +21,7 @@
  * No blocking, fusion or reordering beyond the paper's own block grid.
  */
 #include "rts_oracle.h"
+#include "oracle_internal.h"
 
 #include <math.h>
 #ifndef M_PI
@@ -29,7 +30,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define NBR_CAP 8192
+
 
 /* ---------------------------------------------------------------- kernel --- */
 
@@ -60,7 +61,7 @@ double orc_kernel_dW(double d, double h) {
 
 /* ------------------------------------------------------------ block grid --- */
 
-static int block_coords(const orc_params* P, const double* x, int c[3]) {
+int orci_block_coords(const orc_params* P, const double* x, int c[3]) {
   for (int d = 0; d < 3; ++d) {
     double t = (x[d] - P->origin[d]) / P->edge;
     double f = floor(t);
@@ -70,27 +71,27 @@ static int block_coords(const orc_params* P, const double* x, int c[3]) {
   return ORC_OK;
 }
 
-static int32_t block_lin(const orc_params* P, int bx, int by, int bz) {
+int32_t orci_block_lin(const orc_params* P, int bx, int by, int bz) {
   return ((int32_t)bz * P->dim[1] + by) * P->dim[0] + bx;
 }
 
-static int32_t n_blocks(const orc_params* P) {
+int32_t orci_n_blocks(const orc_params* P) {
   return P->dim[0] * P->dim[1] * P->dim[2];
 }
 
 /* Section 3: each particle lies in exactly one block of a uniform virtual grid. */
 int orc_block_key(const orc_params* P, const double* x3, int32_t* key) {
   int c[3];
-  int st = block_coords(P, x3, c);
+  int st = orci_block_coords(P, x3, c);
   if (st) return st;
-  *key = block_lin(P, c[0], c[1], c[2]);
+  *key = orci_block_lin(P, c[0], c[1], c[2]);
   return ORC_OK;
 }
 
 /* Particles ordered by block, ties by index; cstart[b]..cstart[b+1] lists block b. */
 int orc_bin(const orc_params* P, int32_t n, const double* x, int32_t* key, int32_t* perm,
             int32_t* cstart) {
-  int32_t B = n_blocks(P);
+  int32_t B = orci_n_blocks(P);
   for (int32_t i = 0; i < n; ++i) {
     int st = orc_block_key(P, x + 3 * (int64_t)i, &key[i]);
     if (st) return st;
@@ -105,22 +106,16 @@ int orc_bin(const orc_params* P, int32_t n, const double* x, int32_t* key, int32
   return ORC_OK;
 }
 
-typedef struct {
-  int32_t B;
-  int32_t *key, *cs, *pm;    /* fluid */
-  int32_t *bkey, *bcs, *bpm; /* boundary */
-} ogrid;
-
-static void grid_free(ogrid* G) {
+void orci_grid_free(ogrid* G) {
   free(G->key); free(G->cs); free(G->pm);
   free(G->bkey); free(G->bcs); free(G->bpm);
   memset(G, 0, sizeof(*G));
 }
 
-static int grid_build(const orc_params* P, int32_t n, const double* x, int32_t nb,
+int orci_grid_build(const orc_params* P, int32_t n, const double* x, int32_t nb,
                       const double* xb, ogrid* G) {
   memset(G, 0, sizeof(*G));
-  G->B = n_blocks(P);
+  G->B = orci_n_blocks(P);
   G->key = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
   G->pm = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
   G->cs = (int32_t*)malloc(sizeof(int32_t) * ((size_t)G->B + 1));
@@ -129,14 +124,14 @@ static int grid_build(const orc_params* P, int32_t n, const double* x, int32_t n
   G->bcs = (int32_t*)malloc(sizeof(int32_t) * ((size_t)G->B + 1));
   int st = orc_bin(P, n, x, G->key, G->pm, G->cs);
   if (!st) st = orc_bin(P, nb, xb, G->bkey, G->bpm, G->bcs);
-  if (st) grid_free(G);
+  if (st) orci_grid_free(G);
   return st;
 }
 
 /* ------------------------------------------------------------ neighbours --- */
 
 /* Neighbour predicate: d^2 = ((dx dx + dy dy) + dz dz) < r^2, evaluated in double. */
-static int is_nbr(const double* a, const double* b, double r2) {
+int orci_is_nbr(const double* a, const double* b, double r2) {
   double dx = a[0] - b[0];
   double dy = a[1] - b[1];
   double dz = a[2] - b[2];
@@ -148,7 +143,7 @@ static int is_nbr(const double* a, const double* b, double r2) {
 
 /* N(i) searched over the (2 rings + 1)^3 blocks around block c (Section 3: neighbours
  * of particles in a block are found in the neighbouring blocks). */
-static int nbr_list(const orc_params* P, const ogrid* G, int32_t n, const double* x,
+int orci_nbr_list(const orc_params* P, const ogrid* G, int32_t n, const double* x,
                     const double* xb, int32_t i, const int c[3], int rings, double r2,
                     int32_t* out, int cap) {
   const double* xi = x + 3 * (int64_t)i;
@@ -162,18 +157,18 @@ static int nbr_list(const orc_params* P, const ogrid* G, int32_t n, const double
       for (int dx = -rings; dx <= rings; ++dx) {
         int bx = c[0] + dx;
         if (bx < 0 || bx >= P->dim[0]) continue;
-        int32_t b = block_lin(P, bx, by, bz);
+        int32_t b = orci_block_lin(P, bx, by, bz);
         for (int32_t q = G->cs[b]; q < G->cs[b + 1]; ++q) {
           int32_t j = G->pm[q];
           if (j == i) continue;
-          if (is_nbr(xi, x + 3 * (int64_t)j, r2)) {
+          if (orci_is_nbr(xi, x + 3 * (int64_t)j, r2)) {
             if (cnt >= cap) return -1;
             out[cnt++] = j;
           }
         }
         for (int32_t q = G->bcs[b]; q < G->bcs[b + 1]; ++q) {
           int32_t j = G->bpm[q];
-          if (is_nbr(xi, xb + 3 * (int64_t)j, r2)) {
+          if (orci_is_nbr(xi, xb + 3 * (int64_t)j, r2)) {
             if (cnt >= cap) return -1;
             out[cnt++] = n + j;
           }
@@ -191,12 +186,12 @@ int64_t orc_neighbors_brute(int32_t n, const double* x, int32_t nb, const double
   for (int32_t i = 0; i < n; ++i) {
     offsets[i] = (int32_t)total;
     for (int32_t j = 0; j < n; ++j) {
-      if (j == i || !is_nbr(x + 3 * (int64_t)i, x + 3 * (int64_t)j, r2)) continue;
+      if (j == i || !orci_is_nbr(x + 3 * (int64_t)i, x + 3 * (int64_t)j, r2)) continue;
       if (idx) idx[total] = j;
       ++total;
     }
     for (int32_t j = 0; j < nb; ++j) {
-      if (!is_nbr(x + 3 * (int64_t)i, xb + 3 * (int64_t)j, r2)) continue;
+      if (!orci_is_nbr(x + 3 * (int64_t)i, xb + 3 * (int64_t)j, r2)) continue;
       if (idx) idx[total] = n + j;
       ++total;
     }
@@ -208,14 +203,14 @@ int64_t orc_neighbors_brute(int32_t n, const double* x, int32_t nb, const double
 int64_t orc_neighbors_grid(const orc_params* P, int32_t n, const double* x, int32_t nb,
                            const double* xb, int32_t rings, int32_t* offsets, int32_t* idx) {
   ogrid G;
-  if (grid_build(P, n, x, nb, xb, &G)) return -ORC_ERR_DOMAIN;
+  if (orci_grid_build(P, n, x, nb, xb, &G)) return -ORC_ERR_DOMAIN;
   double r2 = P->r * P->r;
   int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * NBR_CAP);
   int64_t total = 0;
   for (int32_t i = 0; i < n; ++i) {
     int c[3];
-    block_coords(P, x + 3 * (int64_t)i, c);
-    int cnt = nbr_list(P, &G, n, x, xb, i, c, rings, r2, buf, NBR_CAP);
+    orci_block_coords(P, x + 3 * (int64_t)i, c);
+    int cnt = orci_nbr_list(P, &G, n, x, xb, i, c, rings, r2, buf, NBR_CAP);
     if (cnt < 0) { total = -ORC_ERR_CAPACITY; break; }
     offsets[i] = (int32_t)total;
     if (idx) memcpy(idx + total, buf, sizeof(int32_t) * (size_t)cnt);
@@ -223,13 +218,13 @@ int64_t orc_neighbors_grid(const orc_params* P, int32_t n, const double* x, int3
   }
   if (total >= 0) offsets[n] = (int32_t)total;
   free(buf);
-  grid_free(&G);
+  orci_grid_free(&G);
   return total;
 }
 
 /* ------------------------------------------------------------ WCSPH physics --- */
 
-static double particle_mass(const orc_params* P) { return P->rho0 * P->s * P->s * P->s; }
+double orci_particle_mass(const orc_params* P) { return P->rho0 * P->s * P->s * P->s; }
 
 /* Tait equation of state, p = B ((rho / rho0)^gamma - 1), B = c^2 rho0 / gamma,
  * clamped at zero. */
@@ -243,10 +238,10 @@ static double tait(const orc_params* P, double rho) {
 static int density_one(const orc_params* P, const ogrid* G, int32_t n, const double* x,
                        const double* xb, int32_t i, int32_t* buf, double* rho, int32_t* nbr) {
   int c[3];
-  if (block_coords(P, x + 3 * (int64_t)i, c)) return ORC_ERR_DOMAIN;
-  int cnt = nbr_list(P, G, n, x, xb, i, c, 1, P->r * P->r, buf, NBR_CAP);
+  if (orci_block_coords(P, x + 3 * (int64_t)i, c)) return ORC_ERR_DOMAIN;
+  int cnt = orci_nbr_list(P, G, n, x, xb, i, c, 1, P->r * P->r, buf, NBR_CAP);
   if (cnt < 0) return ORC_ERR_CAPACITY;
-  double h = 0.5 * P->r, m = particle_mass(P);
+  double h = 0.5 * P->r, m = orci_particle_mass(P);
   const double* xi = x + 3 * (int64_t)i;
   double sum = m * orc_kernel_W(0.0, h);
   for (int q = 0; q < cnt; ++q) {
@@ -266,10 +261,10 @@ static int accel_one(const orc_params* P, const ogrid* G, int32_t n, const doubl
                      const double* v, const double* rho, const double* p, const double* xb,
                      int32_t i, int32_t* buf, double* out) {
   int c[3];
-  if (block_coords(P, x + 3 * (int64_t)i, c)) return ORC_ERR_DOMAIN;
-  int cnt = nbr_list(P, G, n, x, xb, i, c, 1, P->r * P->r, buf, NBR_CAP);
+  if (orci_block_coords(P, x + 3 * (int64_t)i, c)) return ORC_ERR_DOMAIN;
+  int cnt = orci_nbr_list(P, G, n, x, xb, i, c, 1, P->r * P->r, buf, NBR_CAP);
   if (cnt < 0) return ORC_ERR_CAPACITY;
-  double h = 0.5 * P->r, m = particle_mass(P);
+  double h = 0.5 * P->r, m = orci_particle_mass(P);
   const double* xi = x + 3 * (int64_t)i;
   const double* vi = v + 3 * (int64_t)i;
   double ri = rho[i], pi = p[i];
@@ -359,10 +354,10 @@ int orc_wcsph_density(const orc_params* P, int32_t n, const double* x, int32_t n
                       const double* xb, const uint8_t* mask, double* rho, double* p,
                       int32_t* nbr) {
   ogrid G;
-  int st = grid_build(P, n, x, nb, xb, &G);
+  int st = orci_grid_build(P, n, x, nb, xb, &G);
   if (st) return st;
   st = density_masked(P, &G, n, x, xb, mask, rho, p, nbr);
-  grid_free(&G);
+  orci_grid_free(&G);
   return st;
 }
 
@@ -370,10 +365,10 @@ int orc_wcsph_accel(const orc_params* P, int32_t n, const double* x, const doubl
                     const double* rho, const double* p, int32_t nb, const double* xb,
                     const uint8_t* mask, double* a_out) {
   ogrid G;
-  int st = grid_build(P, n, x, nb, xb, &G);
+  int st = orci_grid_build(P, n, x, nb, xb, &G);
   if (st) return st;
   st = accel_masked(P, &G, n, x, v, rho, p, xb, mask, a_out);
-  grid_free(&G);
+  orci_grid_free(&G);
   return st;
 }
 
@@ -392,7 +387,7 @@ void orc_level_thresholds(const orc_params* P, double* vthr2, double* athr2, int
   }
 }
 
-static double norm2(const double* u) {
+double orci_norm2(const double* u) {
   double s = u[0] * u[0];
   s = s + u[1] * u[1];
   s = s + u[2] * u[2];
@@ -401,7 +396,7 @@ static double norm2(const double* u) {
 
 /* Section 3.1: a block takes the largest level whose criteria hold for the maximum
  * velocity and force of its particles; level 0 if none holds. */
-static int32_t pick_level(const orc_params* P, const double* vthr2, const double* athr2,
+int32_t orci_pick_level(const orc_params* P, const double* vthr2, const double* athr2,
                           const int32_t* eq1, double vmax2, double amax2) {
   int32_t L = 0;
   for (int l = 0; l < P->n_levels; ++l)
@@ -410,9 +405,9 @@ static int32_t pick_level(const orc_params* P, const double* vthr2, const double
 }
 
 /* Raw block levels from the block maxima (Section 3.1 steps 1-2). */
-static int raw_levels(const orc_params* P, int32_t n, const double* x, const double* v,
+int orci_raw_levels(const orc_params* P, int32_t n, const double* x, const double* v,
                       const double* a, int32_t* raw) {
-  int32_t B = n_blocks(P);
+  int32_t B = orci_n_blocks(P);
   double* vmax = (double*)malloc(sizeof(double) * (size_t)B);
   double* amax = (double*)malloc(sizeof(double) * (size_t)B);
   for (int32_t b = 0; b < B; ++b) { vmax[b] = -1.0; amax[b] = -1.0; }
@@ -421,7 +416,7 @@ static int raw_levels(const orc_params* P, int32_t n, const double* x, const dou
     int32_t key;
     st = orc_block_key(P, x + 3 * (int64_t)i, &key);
     if (st) break;
-    double v2 = norm2(v + 3 * (int64_t)i), a2 = norm2(a + 3 * (int64_t)i);
+    double v2 = orci_norm2(v + 3 * (int64_t)i), a2 = orci_norm2(a + 3 * (int64_t)i);
     if (v2 > vmax[key]) vmax[key] = v2;
     if (a2 > amax[key]) amax[key] = a2;
   }
@@ -430,7 +425,7 @@ static int raw_levels(const orc_params* P, int32_t n, const double* x, const dou
     int32_t eq1[8];
     orc_level_thresholds(P, vthr2, athr2, eq1);
     for (int32_t b = 0; b < B; ++b)
-      raw[b] = vmax[b] < 0.0 ? -1 : pick_level(P, vthr2, athr2, eq1, vmax[b], amax[b]);
+      raw[b] = vmax[b] < 0.0 ? -1 : orci_pick_level(P, vthr2, athr2, eq1, vmax[b], amax[b]);
   }
   free(vmax);
   free(amax);
@@ -439,11 +434,11 @@ static int raw_levels(const orc_params* P, int32_t n, const double* x, const dou
 
 /* Section 4.2 R_min: a filled block takes the smallest level among itself and its
  * filled 26 neighbours (one pass, reading the unsmoothed levels). */
-static void rmin_smooth(const orc_params* P, const int32_t* raw, int32_t* out) {
+void orci_rmin_smooth(const orc_params* P, const int32_t* raw, int32_t* out) {
   for (int bz = 0; bz < P->dim[2]; ++bz)
     for (int by = 0; by < P->dim[1]; ++by)
       for (int bx = 0; bx < P->dim[0]; ++bx) {
-        int32_t b = block_lin(P, bx, by, bz);
+        int32_t b = orci_block_lin(P, bx, by, bz);
         int32_t L = raw[b];
         if (L >= 0) {
           for (int dz = -1; dz <= 1; ++dz)
@@ -453,7 +448,7 @@ static void rmin_smooth(const orc_params* P, const int32_t* raw, int32_t* out) {
                 if (cx < 0 || cy < 0 || cz < 0 || cx >= P->dim[0] || cy >= P->dim[1] ||
                     cz >= P->dim[2])
                   continue;
-                int32_t Lc = raw[block_lin(P, cx, cy, cz)];
+                int32_t Lc = raw[orci_block_lin(P, cx, cy, cz)];
                 if (Lc >= 0 && Lc < L) L = Lc;
               }
         }
@@ -463,14 +458,14 @@ static void rmin_smooth(const orc_params* P, const int32_t* raw, int32_t* out) {
 
 int orc_classify_wcsph(const orc_params* P, int32_t n, const double* x, const double* v,
                        const double* a, int32_t* raw, int32_t* level) {
-  int32_t B = n_blocks(P);
+  int32_t B = orci_n_blocks(P);
   int32_t* r = raw ? raw : (int32_t*)malloc(sizeof(int32_t) * (size_t)B);
-  int st = raw_levels(P, n, x, v, a, r);
+  int st = orci_raw_levels(P, n, x, v, a, r);
   if (!st) {
     if (P->force_level >= 0) {
       for (int32_t b = 0; b < B; ++b) level[b] = r[b] < 0 ? -1 : P->force_level;
     } else {
-      rmin_smooth(P, r, level);
+      orci_rmin_smooth(P, r, level);
     }
   }
   if (!raw) free(r);
@@ -484,11 +479,11 @@ int orc_classify_wcsph(const orc_params* P, int32_t n, const double* x, const do
 static int evaluate_masked(const orc_params* P, orc_wstate* S, const uint8_t* mask,
                            double* anew) {
   ogrid G;
-  int st = grid_build(P, S->n, S->x, S->nb, S->xb, &G);
+  int st = orci_grid_build(P, S->n, S->x, S->nb, S->xb, &G);
   if (st) return st;
   st = density_masked(P, &G, S->n, S->x, S->xb, mask, S->rho, S->p, S->nbr);
   if (!st) st = accel_masked(P, &G, S->n, S->x, S->v, S->rho, S->p, S->xb, mask, anew);
-  grid_free(&G);
+  orci_grid_free(&G);
   return st;
 }
 
@@ -592,14 +587,14 @@ int orc_wcsph_global_step(const orc_params* P, orc_wstate* S, int32_t max_mult,
   if (P->mode != 2) {
     double vmax2 = 0.0, amax2 = 0.0;
     for (int32_t i = 0; i < n; ++i) {
-      double v2 = norm2(S->v + 3 * (int64_t)i), a2 = norm2(S->a + 3 * (int64_t)i);
+      double v2 = orci_norm2(S->v + 3 * (int64_t)i), a2 = orci_norm2(S->a + 3 * (int64_t)i);
       if (v2 > vmax2) vmax2 = v2;
       if (a2 > amax2) amax2 = a2;
     }
     double vthr2[8], athr2[8];
     int32_t eq1[8];
     orc_level_thresholds(P, vthr2, athr2, eq1);
-    L = pick_level(P, vthr2, athr2, eq1, vmax2, amax2);
+    L = orci_pick_level(P, vthr2, athr2, eq1, vmax2, amax2);
   }
   int32_t m = P->mult[L];
   if (m > max_mult) m = max_mult;

@@ -116,6 +116,67 @@ int orc_wcsph_substep(const orc_params* P, orc_wstate* S);
 int orc_wcsph_global_step(const orc_params* P, orc_wstate* S, int32_t max_mult,
                           int32_t* mult_used);
 
+/* ------------------------------------------------------------------ PCISPH --- */
+
+/* PCISPH state in user order (Sections 5.2-5.6, Algorithms 2 and 3). */
+typedef struct orc_pstate {
+  int32_t n, nb;
+  double *x, *v;           /* 3n */
+  double *anp;             /* 3n: non-pressure acceleration (viscosity + gravity), held */
+  double *ap;              /* 3n: pressure acceleration of the current minor step */
+  double *p, *rho, *err;   /* n: pressure, latest predicted density, latest relative error */
+  int32_t *level;          /* n: region index (0 = R_1 ... 3 = R_4) */
+  int32_t *validity;       /* n: minor steps until the neighbourhood expires */
+  uint8_t *compute;        /* n: neighbourhood / non-pressure forces refreshed this step */
+  int32_t *nbr_cnt;        /* n */
+  int32_t *nbr_idx;        /* n * cap: fluid j as j, boundary b as n + b */
+  int32_t cap;
+  const double *xb;        /* 3nb */
+  int32_t *pblock;         /* n: block of each particle at the major-step start */
+  int32_t *cs, *pm;        /* grid of the major-step start: B + 1, n */
+  int32_t *bcs, *bpm;      /* static boundary grid: B + 1, nb */
+  int32_t *block_level;    /* B: region of each block (-1 = no fluid) */
+  int32_t *block_raw;      /* B: region from Eq. 2-3 before smoothing and expansion */
+  uint8_t *block_ob;       /* B: observed blocks (R_ob) of the last iteration */
+  double *p_backup;        /* n: pressures before local iterations began */
+  uint8_t *in_se;          /* n: particle in S_e */
+  int32_t minor;           /* minor step within the major step */
+  int32_t n_minor_cur;     /* minor steps of the current major step (N or shortened) */
+  int32_t clean;           /* consecutive major steps without > max_global_iters */
+  int32_t shorten_now;     /* this major step exceeded max_global_iters */
+  int64_t k;               /* minor steps done */
+  /* statistics of the last minor step */
+  int32_t iters, global_iters, local_iters, reverts, not_converged;
+  double err_max, err_avg;
+  int64_t total_iters, total_local, total_restarts;
+} orc_pstate;
+
+/* Solenthaler-Pajarola pressure scaling: delta = 1 / (beta sum |grad W|^2) on a prototype
+ * particle with a full cubic lattice of spacing s, beta = 2 (dt_b m / rho0)^2.
+ * [pinned: closed-form lattice sum] */
+double orc_pcisph_delta(const orc_params* P);
+
+/* Regions: Eq. 2-3 (alpha = 1, no Eq. 1), R_min smoothing, expansion of R_1 then R_2 by
+ * expand_layers blocks (Section 5.5).  [pinned: hand-built fields] */
+int orc_classify_pcisph(const orc_params* P, int32_t n, const double* x, const double* v,
+                        const double* a, int32_t* raw, int32_t* level);
+
+/* Observed blocks: filled blocks not in R_e bordering R_e or a smaller region
+ * (Section 5.4, Figure 4 c-d).  in_re: B flags.  [pinned: hand-built fields] */
+void orc_observed_blocks(const orc_params* P, const int32_t* block_level, const uint8_t* in_re,
+                         uint8_t* ob);
+
+/* One minor step of Algorithm 2 with Algorithm 3 (major-step start included).
+ * Returns ORC_ERR_NOT_CONVERGED (state advanced) when a minor step hits max_iters.
+ * [parity unpinned for the correction schedule, which is reconstructed; pinned: rest
+ * lattice at rest, forced-R_1 equals plain PCISPH, delta] */
+int orc_pcisph_step(const orc_params* P, orc_pstate* S);
+
+/* Plain PCISPH (Solenthaler & Pajarola) for comparison: every particle refreshes its
+ * neighbourhood from a fresh grid, >= 3 global iterations until max error <= eta.
+ * Shares the state layout; uses dt_b. */
+int orc_pcisph_plain_step(const orc_params* P, orc_pstate* S);
+
 #ifdef __cplusplus
 }
 #endif
