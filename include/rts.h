@@ -171,7 +171,8 @@ rts_status rts_set_state(rts_ctx* ctx, const float* x, const float* v, const flo
 rts_status rts_get_bins(rts_ctx* ctx, int32_t* key, int32_t* perm, int32_t* cstart);
 
 /* Block levels of the last classification (n_blocks int32, -1 = no fluid): raw from
- * Eq. 1-3, level after R_min smoothing (and, for PCISPH, region expansion).
+ * Eq. 1-3, level after R_min smoothing.  For a PCISPH context, level is the region
+ * field of the current major step (R_min, region expansion, pre-emption).
  * Any pointer may be NULL.  Synchronises. */
 rts_status rts_get_blocks(rts_ctx* ctx, int32_t* raw, int32_t* level);
 
@@ -201,6 +202,32 @@ rts_status rts_profile_enable(rts_ctx* ctx, int32_t on);
 
 /* Read the accumulated profile (synchronises); reset != 0 clears it afterwards. */
 rts_status rts_profile_read(rts_ctx* ctx, rts_profile* out, int32_t reset);
+
+/* Statistics of the last PCISPH minor step (Algorithm 3). */
+typedef struct rts_pcisph_info {
+  int32_t iterations;        /* density-correction iterations                         */
+  int32_t global_iterations; /* iterations in which every region had a turn          */
+  int32_t local_iterations;  /* iterations on S_e only (Section 5.5)                  */
+  int32_t reverts;           /* local runs that failed and restored the pressures    */
+  int32_t not_converged;     /* 1 if max_iters was reached                           */
+  int32_t minor;             /* minor step the next call will take                   */
+  int32_t n_minor_current;   /* minor steps of the current major step (N or short)   */
+  int32_t clean_majors;      /* shortened major steps without an overrun so far      */
+  double err_max, err_avg;   /* maximum and average relative compression error       */
+} rts_pcisph_info;
+
+rts_status rts_pcisph_last(rts_ctx* ctx, rts_pcisph_info* out);
+
+/* PCISPH state in the caller's order: ap (n x 3) pressure acceleration of the last minor
+ * step, err (n) latest relative compression error max(0, rho* - rho0) / rho0, in_se (n)
+ * membership of S_e.  Any pointer may be NULL.  Synchronises. */
+rts_status rts_get_pcisph_state(rts_ctx* ctx, float* ap, float* err, uint8_t* in_se);
+
+/* Neighbour lists of the last evaluation, caller's order: counts (n); idx (n x cap,
+ * may be NULL) with fluid j as j and boundary particle b as n + b (caller indices).
+ * WCSPH: valid for the particles the last step evaluated; PCISPH: the lists in use.
+ * RTS_ERR_CAPACITY if a list is longer than cap.  Synchronises. */
+rts_status rts_get_neighbors(rts_ctx* ctx, int32_t* counts, int32_t* idx, int32_t cap);
 
 /* Wait for the stream; return a pending device error, if any. */
 rts_status rts_sync(rts_ctx* ctx);

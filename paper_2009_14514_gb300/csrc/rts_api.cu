@@ -138,6 +138,41 @@ static void make_dev_params(const rts_params& p, DevParams& d) {
   d.force_level = p.force_level;
   d.dt_b = p.dt_b;
   d.nbl_cap = p.max_neighbors > 0 ? p.max_neighbors : 96;
+  // PCISPH (Section 5): Solenthaler-Pajarola scaling on a prototype particle with a full
+  // cubic lattice of spacing s inside the support: delta = -1 / (beta (-|sum g|^2 -
+  // sum |g|^2)), beta = 2 (dt_b m / rho0)^2, g = grad W.
+  d.eta = p.eta;
+  d.visc_nu = (float)((double)p.visc_alpha * h * p.c_s / p.rho0);
+  d.r1_rings = p.r1_search_rings > 0 ? p.r1_search_rings : 1;
+  d.expand_layers = p.expand_layers;
+  d.n_minor = p.n_minor;
+  for (int r = 0; r < 4; ++r)
+    for (int j = 0; j < 8; ++j) d.sched[r][j] = p.sched[r][j];
+  for (int L = 0; L < 8; ++L) d.refresh[L] = p.refresh[L] > 0 ? p.refresh[L] : 1;
+  {
+    double m = (double)p.rho0 * s * s * s, rr = (double)p.support_r;
+    double g[3] = {0, 0, 0}, gg = 0.0;
+    int R = (int)std::ceil(rr / s) + 1;
+    for (int a = -R; a <= R; ++a)
+      for (int b = -R; b <= R; ++b)
+        for (int e = -R; e <= R; ++e) {
+          if (!a && !b && !e) continue;
+          double x[3] = {-a * s, -b * s, -e * s};
+          double d2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+          if (!(d2 < rr * rr)) continue;
+          double dd = std::sqrt(d2), q = dd / h;
+          double dW = q < 1.0 ? sigma * (-3.0 * q + 2.25 * q * q) / h
+                              : (q < 2.0 ? -0.75 * sigma * (2.0 - q) * (2.0 - q) / h : 0.0);
+          for (int k = 0; k < 3; ++k) {
+            double gk = dW / dd * x[k];
+            g[k] += gk;
+            gg += gk * gk;
+          }
+        }
+    double beta = 2.0 * ((double)p.dt_b * m / p.rho0) * ((double)p.dt_b * m / p.rho0);
+    double denom = -(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) - gg;
+    d.delta = (float)(-1.0 / (beta * denom));
+  }
 }
 
 // ------------------------------------------------------------- profiling ---
@@ -258,6 +293,14 @@ static rts_status upload_state(rts_ctx* c, const float* x, const float* v, const
   if (a) CK(cudaMemcpyAsync(io, a, v3, cudaMemcpyDefault, c->stream));
   k_in_vec<<<g, 256, 0, c->stream>>>(n, a ? io : nullptr, c->s.a);
   k_finish_in<<<g, 256, 0, c->stream>>>(n, c->s);
+  if (c->s.ap) {
+    CK(cudaMemsetAsync(c->s.ap, 0, sizeof(float4) * (size_t)n, c->stream));
+    CK(cudaMemsetAsync(c->s.err, 0, sizeof(float) * (size_t)n, c->stream));
+    c->minor = 0;
+    c->n_minor_cur = c->p.n_minor;
+    c->clean = 0;
+    c->shorten_now = 0;
+  }
   CK(cudaGetLastError());
   // the staging buffers are reused by the next call: finish before returning
   CK(cudaStreamSynchronize(c->stream));
@@ -424,6 +467,20 @@ rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, c
     ALLOC(c->filled, sizeof(uint32_t) * nbk);
     c->nbl_cap = c->dp.nbl_cap;
     ALLOC(c->nbl, sizeof(uint32_t) * (size_t)n1 * (size_t)c->nbl_cap);
+    ALLOC(c->buid, sizeof(uint32_t) * (size_t)(n_boundary > 0 ? n_boundary : 1));
+    if (params->scheme == RTS_PCISPH) {
+      for (PState* s : ss) {
+        ALLOC(s->ap, f4);
+        ALLOC(s->err, f1);
+      }
+      ALLOC(c->xs, f4);
+      ALLOC(c->pbak, f1);
+      ALLOC(c->in_se, (size_t)n1);
+      ALLOC(c->in_re, nbk);
+      ALLOC(c->ob, nbk);
+      ALLOC(c->preg, sizeof(int32_t) * nbk);
+      ALLOC(c->pnew, sizeof(int32_t) * nbk);
+    }
     ALLOC(c->act, sizeof(uint32_t) * nbk);
     ALLOC(c->ctl, sizeof(Ctl));
     ALLOC(c->xb, sizeof(float4) * (size_t)(n_boundary > 0 ? n_boundary : 1));
@@ -440,7 +497,10 @@ rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, c
     if (e == cudaSuccess) e = cudaMemsetAsync(c->blevel, 0, sizeof(uint32_t) * nbk, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bmax_v, 0, sizeof(unsigned long long) * nbk, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bmax_a, 0, sizeof(unsigned long long) * nbk, c->stream);
+    if (e == cudaSuccess && c->preg) e = cudaMemsetAsync(c->preg, 0xff, sizeof(int32_t) * nbk, c->stream);
+    if (e == cudaSuccess && c->ob) e = cudaMemsetAsync(c->ob, 0, nbk, c->stream);
     c->stamp = 0;
+    c->n_minor_cur = params->n_minor;
     if (e != cudaSuccess) {
       rts::cuda_err(c, e, "initial memset");
       st = RTS_ERR_CUDA;
@@ -499,6 +559,9 @@ rts_status rts_destroy(rts_ctx* c) {
   cudaFree(c->count); cudaFree(c->cstart); cudaFree(c->bcstart); cudaFree(c->tile_sums);
   cudaFree(c->raw); cudaFree(c->blevel); cudaFree(c->act); cudaFree(c->ctl); cudaFree(c->xb);
   cudaFree(c->bmax_v); cudaFree(c->bmax_a); cudaFree(c->filled); cudaFree(c->nbl);
+  cudaFree(c->buid); cudaFree(c->s.ap); cudaFree(c->s2.ap); cudaFree(c->s.err); cudaFree(c->s2.err);
+  cudaFree(c->xs); cudaFree(c->pbak); cudaFree(c->in_se); cudaFree(c->in_re); cudaFree(c->ob);
+  cudaFree(c->preg); cudaFree(c->pnew);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   if (c->ev) {
     for (int k = 0; k < 2 * kEvPairs; ++k) cudaEventDestroy(c->ev[k]);
@@ -572,6 +635,8 @@ rts_status rts_advance(rts_ctx* c, double t_sim, rts_stats* out) {
   int64_t K = llround(t_sim / (double)c->p.dt_b);
   CK(cudaMemsetAsync(&c->ctl->evals, 0, 4 * sizeof(unsigned long long), c->stream));
   int64_t k0 = c->k, steps = 0;
+  int64_t it0 = c->tot_iters, lo0 = c->tot_local, rv0 = c->tot_reverts;
+  rts_status nconv = RTS_OK;
   rts_status st = RTS_OK;
   while (c->k < K) {
     if (c->p.scheme == RTS_WCSPH) {
@@ -580,6 +645,7 @@ rts_status rts_advance(rts_ctx* c, double t_sim, rts_stats* out) {
       st = rts_pcisph_step(c);
     }
     if (st != RTS_OK && st != RTS_ERR_NOT_CONVERGED) return st;
+    if (st == RTS_ERR_NOT_CONVERGED) nconv = st;
     ++steps;
   }
   {
@@ -595,10 +661,13 @@ rts_status rts_advance(rts_ctx* c, double t_sim, rts_stats* out) {
     out->pair_interactions = (int64_t)c->h_ctl->pairs;
     out->active_blocks = (int64_t)c->h_ctl->act_blocks;
     out->candidate_tests = (int64_t)c->h_ctl->cands;
+    out->pcisph_iterations = c->tot_iters - it0;
+    out->pcisph_local_iterations = c->tot_local - lo0;
+    out->pcisph_global_restarts = c->tot_reverts - rv0;
     for (int L = 0; L < kMaxLevels; ++L) out->level_count[L] = (int64_t)c->h_ctl->level_count[L];
     out->t_sim = (double)c->k * (double)c->p.dt_b;
   }
-  return ds;
+  return ds != RTS_OK ? ds : nconv;
 }
 
 rts_status rts_get_state(rts_ctx* c, float* x, float* v, float* a, float* rho, float* p,
@@ -697,6 +766,12 @@ rts_status rts_get_blocks(rts_ctx* c, int32_t* raw, int32_t* level) {
   int32_t* dst[2] = {raw, level};
   for (int k = 0; k < 2; ++k) {
     if (!dst[k]) continue;
+    if (k == 1 && c->preg) {
+      // PCISPH: the region field of the current major step (after expansion and
+      // pre-emption), -1 for blocks without fluid
+      CK(cudaMemcpy(dst[k], c->preg, sizeof(int32_t) * nbk, cudaMemcpyDefault));
+      continue;
+    }
     CK(cudaMemcpy(h.data(), src[k], sizeof(uint32_t) * nbk, cudaMemcpyDeviceToHost));
     // records of this binning pass hold a level; every other block has no fluid
     for (size_t b = 0; b < nbk; ++b) w[b] = (h[b] >> 8) == c->stamp ? (int32_t)(h[b] & 0xffu) : -1;
@@ -739,7 +814,78 @@ rts_status rts_profile_read(rts_ctx* c, rts_profile* out, int32_t reset) {
 rts_status rts_pcisph_step(rts_ctx* c) {
   GUARD();
   if (c->p.scheme != RTS_PCISPH) return fail(c, RTS_ERR_ARG, "context was created for WCSPH");
-  return fail(c, RTS_ERR_ARG, "PCISPH stepping is not available in this build");
+  return pcisph_step(c);
+}
+
+rts_status rts_pcisph_last(rts_ctx* c, rts_pcisph_info* out) {
+  if (!c || !out) return fail(c, RTS_ERR_ARG, "ctx or out is NULL");
+  out->iterations = c->it_iters;
+  out->global_iterations = c->it_global;
+  out->local_iterations = c->it_local;
+  out->reverts = c->it_reverts;
+  out->not_converged = c->it_notconv;
+  out->minor = c->minor;
+  out->n_minor_current = c->n_minor_cur;
+  out->clean_majors = c->clean;
+  out->err_max = c->it_errmax;
+  out->err_avg = c->it_erravg;
+  return RTS_OK;
+}
+
+rts_status rts_get_pcisph_state(rts_ctx* c, float* ap, float* err, uint8_t* in_se) {
+  if (!c) return fail(nullptr, RTS_ERR_ARG, "ctx is NULL");
+  if (c->p.scheme != RTS_PCISPH) return fail(c, RTS_ERR_ARG, "context was created for WCSPH");
+  int n = c->n;
+  if (n == 0) return sync_status(c);
+  int g = nblk(n);
+  Phase ph(c, RTS_PHASE_OTHER);
+  if (ap) {
+    note_launch(c, 1);
+    k_out_vec<<<g, 256, 0, c->stream>>>(n, c->s.uid, c->s.ap, c->io);
+    CK(cudaMemcpyAsync(ap, c->io, sizeof(float) * 3 * (size_t)n, cudaMemcpyDefault, c->stream));
+  }
+  if (err) {
+    note_launch(c, 1);
+    k_out_scalar<float><<<g, 256, 0, c->stream>>>(n, c->s.uid, c->s.err, c->io);
+    CK(cudaMemcpyAsync(err, c->io, sizeof(float) * (size_t)n, cudaMemcpyDefault, c->stream));
+  }
+  if (in_se) {
+    note_launch(c, 1);
+    k_out_scalar<uint8_t><<<g, 256, 0, c->stream>>>(n, c->s.uid, c->in_se, (uint8_t*)c->io_i);
+    CK(cudaMemcpyAsync(in_se, c->io_i, (size_t)n, cudaMemcpyDefault, c->stream));
+  }
+  CK(cudaGetLastError());
+  return sync_status(c);
+}
+
+rts_status rts_get_neighbors(rts_ctx* c, int32_t* counts, int32_t* idx, int32_t cap) {
+  if (!c || !counts || (idx && cap < 1)) return fail(c, RTS_ERR_ARG, "bad arguments");
+  rts_status st = sync_status(c);
+  if (st != RTS_OK && st != RTS_ERR_NOT_CONVERGED) return st;
+  int n = c->n, nb = c->nb;
+  if (n == 0) return RTS_OK;
+  std::vector<uint32_t> uid(n), buid(nb > 0 ? nb : 1), lists((size_t)n * c->nbl_cap);
+  std::vector<int32_t> cnt(n), ocnt(n);
+  CK(cudaMemcpy(uid.data(), c->s.uid, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+  if (nb > 0) CK(cudaMemcpy(buid.data(), c->buid, sizeof(uint32_t) * nb, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(cnt.data(), c->s.nbr, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(lists.data(), c->nbl, sizeof(uint32_t) * lists.size(), cudaMemcpyDeviceToHost));
+  std::vector<int32_t> out(idx ? (size_t)n * cap : 0, -1);
+  for (int f = 0; f < n; ++f) {
+    int u = (int)uid[f];
+    int k = cnt[f] < c->nbl_cap ? cnt[f] : c->nbl_cap;
+    ocnt[u] = k;
+    if (!idx) continue;
+    if (k > cap) return fail(c, RTS_ERR_CAPACITY, "rts_get_neighbors: cap smaller than a list");
+    for (int e = 0; e < k; ++e) {
+      uint32_t j = lists[(size_t)f * c->nbl_cap + e];
+      out[(size_t)u * cap + e] = (j & 0x80000000u) ? n + (int32_t)buid[j & 0x7fffffffu]
+                                                   : (int32_t)uid[j];
+    }
+  }
+  CK(cudaMemcpy(counts, ocnt.data(), sizeof(int32_t) * n, cudaMemcpyDefault));
+  if (idx) CK(cudaMemcpy(idx, out.data(), sizeof(int32_t) * out.size(), cudaMemcpyDefault));
+  return RTS_OK;
 }
 
 }  // extern "C"

@@ -248,6 +248,12 @@ __global__ void k_canon_gather(int n, int max_per_block, const uint32_t* __restr
     float v2 = 0.f, a2 = 0.f;
     if (valid) {
       float4 vi = src.v[tsrc[q]], ai = src.a[tsrc[q]];
+      if (src.ap) {  // PCISPH: total acceleration = non-pressure + pressure
+        float4 pa = src.ap[tsrc[q]];
+        ai.x += pa.x;
+        ai.y += pa.y;
+        ai.z += pa.z;
+      }
       v2 = vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
       a2 = ai.x * ai.x + ai.y * ai.y + ai.z * ai.z;
     }
@@ -275,6 +281,10 @@ __global__ void k_canon_gather(int n, int max_per_block, const uint32_t* __restr
     dst.valid[f] = src.valid[s];
     dst.level[f] = src.level[s];
     dst.nbr[f] = src.nbr[s];
+    if (src.ap) {
+      dst.ap[f] = src.ap[s];
+      dst.err[f] = src.err[s];
+    }
   }
 }
 
@@ -363,6 +373,7 @@ rts_status launch_bin_boundary(rts_ctx* c, const float4* xb_unsorted, int nb) {
   dst.uid = uid2;
   k_canon_gather<<<g, tb, 0, c->stream>>>(nb, 1 << 30, c->bcstart, tkey, tuid, tsrc, src, dst, key,
                                            c->ctl, 0u, nullptr, nullptr);
+  cudaMemcpyAsync(c->buid, uid2, sz, cudaMemcpyDeviceToDevice, c->stream);
   e = cudaStreamSynchronize(c->stream);
   for (auto b : bufs) cudaFree(*b);
   if (e != cudaSuccess) {

@@ -28,6 +28,11 @@ struct DevParams {
   float eps_h2;      // 0.01 h^2
   float gx, gy, gz;
   int nbl_cap;       // neighbour list capacity per particle
+  // PCISPH (Section 5)
+  float eta, delta, visc_nu;   // tolerance, pressure scaling, alpha h c / rho0
+  int r1_rings, expand_layers, n_minor;
+  int sched[4][8];
+  int refresh[8];
   // levels (Section 3.1)
   int n_levels;
   int mult[kMaxLevels];
@@ -49,6 +54,8 @@ struct Ctl {
   unsigned long long vmax2_bits; // global max |v|^2 (FP64 bits, non-negative)
   unsigned long long amax2_bits; // global max |a|^2
   unsigned long long level_count[kMaxLevels];
+  unsigned int err_max_bits;      // PCISPH: max relative error (FP32 bits)
+  unsigned long long err_sum_fx;  // PCISPH: sum of relative errors, fixed point 2^-32
 };
 
 // Particle state in block-sorted order.  x.w = p / rho^2 and v.w = rho of the last
@@ -64,6 +71,8 @@ struct PState {
   int32_t* valid;   // validity counter (base substeps)
   int32_t* level;   // particle level, -1 = none
   int32_t* nbr;     // neighbour count at the last evaluation
+  float4* ap;       // PCISPH: pressure acceleration of the current minor step (else null)
+  float* err;       // PCISPH: latest relative compression error (else null)
 };
 
 __device__ __forceinline__ void set_status(Ctl* ctl, int code) {
@@ -124,6 +133,20 @@ struct rts_ctx {
   int grid_persistent;  // CTAs of the persistent neighbour kernels
   uint32_t* nbl;        // neighbour lists of evaluated particles, nbl_cap per particle
   int nbl_cap;
+  uint32_t* buid;       // boundary: caller index of each sorted boundary particle
+
+  // PCISPH (Algorithms 2 and 3)
+  float4* xs;           // predicted positions x*
+  float* pbak;          // pressures before a run of local iterations
+  uint8_t* in_se;       // particle in S_e
+  uint8_t* in_re;       // block in R_e
+  uint8_t* ob;          // block observed (R_ob)
+  int32_t* preg;        // region of each block in the current major step (-1 = empty)
+  int32_t* pnew;        // scratch region field (dilation, pre-emption)
+  int minor, n_minor_cur, clean, shorten_now;
+  int it_iters, it_global, it_local, it_reverts, it_notconv;
+  double it_errmax, it_erravg;
+  int64_t tot_iters, tot_local, tot_reverts, tot_steps;
   int last_global_level;
 
   // launch counting and optional per-phase event timing
@@ -157,4 +180,5 @@ rts_status launch_correct(rts_ctx* c, int64_t k1, int prime);
 rts_status launch_global_max(rts_ctx* c);
 rts_status launch_level_hist(rts_ctx* c);
 const char* cuda_err(rts_ctx* c, cudaError_t e, const char* what);
+rts_status pcisph_step(rts_ctx* c);
 }  // namespace rts

@@ -1,0 +1,604 @@
+// rts_pcisph.cu - regional time stepping for PCISPH (Algorithms 2 and 3).
+//
+// A major step of n_minor minor steps of dt_b keeps the block grid (edge 2.2 s) built at
+// its start (Section 5.6).  At the start: bin, regions from Eq. 2-3 (alpha = 1, no
+// Eq. 1), R_min, expansion of R_1 and R_2 by expand_layers blocks (Section 5.5).  Each
+// minor step refreshes the neighbour lists and non-pressure forces of the particles
+// whose validity expired (1-ring search, 2 rings for R_1), then runs the density
+// correction of Algorithm 3 with the per-region schedule, S_e and the observed blocks
+// R_ob (Section 5.4), extra local / global iterations (Section 5.5), integrates every
+// particle, and lowers the region of blocks around particles that need a smaller step.
+//
+// The correction loop is controlled from the host: after every iteration the maximum
+// and the average relative error are read back (exact max, fixed-point sum) and the
+// host decides the next iteration, as Algorithm 3 does.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "rts_internal.cuh"
+
+namespace rts {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr uint32_t kBnd = 0x80000000u;
+constexpr int kModeSched = 0, kModeGlobal = 1, kModeLocal = 2;
+
+__device__ __forceinline__ float pW(const DevParams& P, float q) {
+  if (q < 1.0f) return P.sigma * (1.0f + q * q * (-1.5f + 0.75f * q));
+  float t = 2.0f - q;
+  return q < 2.0f ? 0.25f * P.sigma * t * t * t : 0.0f;
+}
+
+__device__ __forceinline__ float pdW(const DevParams& P, float q) {
+  if (q < 1.0f) return P.sigma_h * q * (-3.0f + 2.25f * q);
+  float t = 2.0f - q;
+  return q < 2.0f ? -0.75f * P.sigma_h * t * t : 0.0f;
+}
+
+__device__ __forceinline__ bool pexact(float4 a, float4 b, double r2d) {
+  double dx = __dsub_rn((double)a.x, (double)b.x);
+  double dy = __dsub_rn((double)a.y, (double)b.y);
+  double dz = __dsub_rn((double)a.z, (double)b.z);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) < r2d;
+}
+
+__device__ __forceinline__ double pnorm2(float x, float y, float z) {
+  double dx = x, dy = y, dz = z;
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ bool has_turn(const DevParams& P, int mode, int row, int j, int L) {
+  return mode == kModeGlobal || (mode == kModeSched && row <= P.sched[L][j]);
+}
+
+// ------------------------------------------------------------- regions ---
+
+__global__ void k_preg_from_blevel(const uint32_t* __restrict__ filled, const Ctl* ctl,
+                                   const uint32_t* __restrict__ blevel, int32_t* __restrict__ preg) {
+  const int nf = ctl->n_filled;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    uint32_t b = filled[t];
+    preg[b] = (int32_t)(blevel[b] & 0xffu);
+  }
+}
+
+// Section 5.5: blocks within Chebyshev distance <= layers of a filled block of region
+// <= target take min(region, target) (Jacobi: reads in, writes out; filled blocks only).
+__global__ void k_dilate(DevParams P, const uint32_t* __restrict__ filled, const Ctl* ctl,
+                         const int32_t* __restrict__ in, int32_t* __restrict__ out, int target,
+                         int layers) {
+  const int nf = ctl->n_filled;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    uint32_t b = filled[t];
+    int L = in[b];
+    if (L > target) {
+      int bx = b % P.nx, r = b / P.nx, by = r % P.ny, bz = r / P.ny;
+      bool hit = false;
+      for (int dz = -layers; dz <= layers && !hit; ++dz) {
+        int cz = bz + dz;
+        if (cz < 0 || cz >= P.nz) continue;
+        for (int dy = -layers; dy <= layers && !hit; ++dy) {
+          int cy = by + dy;
+          if (cy < 0 || cy >= P.ny) continue;
+          int x0 = bx - layers < 0 ? 0 : bx - layers;
+          int x1 = bx + layers >= P.nx ? P.nx - 1 : bx + layers;
+          const int32_t* row = in + ((size_t)cz * P.ny + cy) * P.nx;
+          for (int cx = x0; cx <= x1; ++cx) {
+            int Lc = row[cx];
+            if (Lc >= 0 && Lc <= target) {
+              hit = true;
+              break;
+            }
+          }
+        }
+      }
+      if (hit) L = target;
+    }
+    out[b] = L;
+  }
+}
+
+// Every particle takes its block's region; neighbourhoods are refreshed at the start.
+__global__ void k_assign_regions(DevParams P, int n, const uint32_t* __restrict__ key,
+                                 const int32_t* __restrict__ preg, PState s,
+                                 uint8_t* __restrict__ cflag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int L = preg[key[i]];
+  s.level[i] = L;
+  s.valid[i] = P.refresh[L];
+  cflag[i] = 1;
+}
+
+// R_ob (Section 5.4): filled blocks outside R_e bordering R_e or a smaller region.
+__global__ void k_observed(DevParams P, const uint32_t* __restrict__ filled, const Ctl* ctl,
+                           const int32_t* __restrict__ preg, const uint8_t* __restrict__ in_re,
+                           uint8_t* __restrict__ ob) {
+  const int nf = ctl->n_filled;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    uint32_t b = filled[t];
+    uint8_t o = 0;
+    if (!in_re[b]) {
+      int L = preg[b];
+      int bx = b % P.nx, r = b / P.nx, by = r % P.ny, bz = r / P.ny;
+      for (int dz = -1; dz <= 1 && !o; ++dz) {
+        int cz = bz + dz;
+        if (cz < 0 || cz >= P.nz) continue;
+        for (int dy = -1; dy <= 1 && !o; ++dy) {
+          int cy = by + dy;
+          if (cy < 0 || cy >= P.ny) continue;
+          for (int dx = -1; dx <= 1 && !o; ++dx) {
+            int cx = bx + dx;
+            if (cx < 0 || cx >= P.nx || (!dx && !dy && !dz)) continue;
+            size_t c = ((size_t)cz * P.ny + cy) * P.nx + cx;
+            int Lc = preg[c];
+            if (Lc < 0) continue;
+            if (in_re[c] || Lc < L) o = 1;
+          }
+        }
+      }
+    }
+    ob[b] = o;
+  }
+}
+
+// ---------------------------------------------------------- neighbours ---
+
+// Section 5.6: the neighbourhood of a refreshing particle is searched in the blocks
+// around its block of the major-step start (2 rings for R_1) with current positions.
+__global__ void k_lists(DevParams P, int n, const uint32_t* __restrict__ key,
+                        const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ bcstart,
+                        PState s, const float4* __restrict__ xb, const uint8_t* __restrict__ cflag,
+                        uint32_t* __restrict__ nbl, Ctl* ctl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !cflag[i]) return;
+  uint32_t b = key[i];
+  int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
+  int R = s.level[i] == 0 ? P.r1_rings : 1;
+  float4 xi = s.x[i];
+  uint32_t* list = nbl + (size_t)i * P.nbl_cap;
+  int cnt = 0;
+  int x0 = bx - R < 0 ? 0 : bx - R;
+  int x1 = bx + R >= P.nx ? P.nx - 1 : bx + R;
+  for (int dz = -R; dz <= R; ++dz) {
+    int cz = bz + dz;
+    if (cz < 0 || cz >= P.nz) continue;
+    for (int dy = -R; dy <= R; ++dy) {
+      int cy = by + dy;
+      if (cy < 0 || cy >= P.ny) continue;
+      uint32_t rb = ((uint32_t)cz * P.ny + cy) * P.nx;
+      for (int pass = 0; pass < 2; ++pass) {
+        const uint32_t* cs = pass ? bcstart : cstart;
+        const float4* src = pass ? xb : s.x;
+        uint32_t j0 = cs[rb + x0], j1 = cs[rb + x1 + 1];
+        for (uint32_t j = j0; j < j1; ++j) {
+          if (!pass && j == (uint32_t)i) continue;
+          float4 xj = src[j];
+          float dx = xi.x - xj.x, dy2 = xi.y - xj.y, dz2 = xi.z - xj.z;
+          float d2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+          bool in = d2 < P.r2_lo;
+          if (d2 >= P.r2_lo && d2 < P.r2_hi) in = pexact(xi, xj, P.r2d);
+          if (in) {
+            if (cnt < P.nbl_cap) list[cnt] = pass ? (j | kBnd) : j;
+            ++cnt;
+          }
+        }
+      }
+    }
+  }
+  if (cnt > P.nbl_cap) {
+    set_status(ctl, RTS_ERR_CAPACITY);
+    cnt = P.nbl_cap;
+  }
+  s.nbr[i] = cnt;
+}
+
+// Non-pressure acceleration of refreshing particles: gravity + artificial viscosity
+// (nu = alpha h c / rho0) over the neighbourhood; boundary particles are at rest.
+__global__ void k_nonpressure(DevParams P, int n, PState s, const float4* __restrict__ xb,
+                              const uint8_t* __restrict__ cflag, const uint32_t* __restrict__ nbl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !cflag[i]) return;
+  float4 xi = s.x[i], vi = s.v[i];
+  float ax = P.gx, ay = P.gy, az = P.gz;
+  const uint32_t* list = nbl + (size_t)i * P.nbl_cap;
+  int cnt = s.nbr[i];
+  for (int e = 0; e < cnt; ++e) {
+    uint32_t j = list[e];
+    float4 xj, vj = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j & kBnd) {
+      xj = xb[j & ~kBnd];
+    } else {
+      xj = s.x[j];
+      vj = s.v[j];
+    }
+    float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+    float d2 = dx * dx + dy * dy + dz * dz;
+    if (!(d2 > 0.f)) continue;
+    float vx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+    if (vx >= 0.f) continue;
+    float d = sqrtf(d2);
+    float Pi = -P.visc_nu * vx / (d2 + P.eps_h2);
+    float f = pdW(P, d * P.inv_h) / d;
+    float sc = -P.m * Pi * f;
+    ax += sc * dx;
+    ay += sc * dy;
+    az += sc * dz;
+  }
+  s.a[i] = make_float4(ax, ay, az, 0.f);
+}
+
+// ------------------------------------------------------- Algorithm 3 ---
+
+// Predict v* = v + dt (a_np + a_p), x* = x + dt v* (every particle).
+__global__ void k_predict(DevParams P, int n, PState s, float4* __restrict__ xs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 x = s.x[i], v = s.v[i], a = s.a[i], pa = s.ap[i];
+  float dt = P.dt_b;
+  float vx = v.x + dt * (a.x + pa.x), vy = v.y + dt * (a.y + pa.y), vz = v.z + dt * (a.z + pa.z);
+  xs[i] = make_float4(x.x + dt * vx, x.y + dt * vy, x.z + dt * vz, 0.f);
+}
+
+// Predicted density, relative error and pressure of the participants (turn, S_e, S_ob):
+// rho* = m W(0) + sum m W(|x*_i - x*_j|), p += delta max(0, rho* - rho0).
+__global__ void k_pdensity(DevParams P, int n, int j_minor, int row, int mode,
+                           const uint32_t* __restrict__ key, PState s,
+                           const uint8_t* __restrict__ in_se, const uint8_t* __restrict__ ob,
+                           const float4* __restrict__ xs, const float4* __restrict__ xb,
+                           const uint32_t* __restrict__ nbl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (!(has_turn(P, mode, row, j_minor, s.level[i]) || in_se[i] || ob[key[i]])) return;
+  float4 xi = xs[i];
+  float w = P.sigma;  // W(0): the particle itself
+  const uint32_t* list = nbl + (size_t)i * P.nbl_cap;
+  int cnt = s.nbr[i];
+  for (int e = 0; e < cnt; ++e) {
+    uint32_t j = list[e];
+    float4 xj = (j & kBnd) ? xb[j & ~kBnd] : xs[j];
+    float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+    float d2 = dx * dx + dy * dy + dz * dz;
+    w += pW(P, sqrtf(d2) * P.inv_h);
+  }
+  float rho = P.m * w;
+  float comp = fmaxf(0.f, rho - P.rho0);
+  float p = s.prs[i] + P.delta * comp;
+  s.rho[i] = rho;
+  s.err[i] = comp * P.inv_rho0;
+  s.prs[i] = p;
+}
+
+// S_e = {err > eta / 2}; R_e = blocks holding an S_e particle; max and sum of the latest
+// errors of all particles (exact max on FP32 bits, fixed-point sum).
+__global__ void k_se_reduce(DevParams P, int n, const uint32_t* __restrict__ key, PState s,
+                            uint8_t* __restrict__ in_se, uint8_t* __restrict__ in_re, Ctl* ctl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float e = 0.f;
+  if (i < n) {
+    e = s.err[i];
+    bool se = e > 0.5f * P.eta;
+    in_se[i] = se ? 1 : 0;
+    if (se) in_re[key[i]] = 1;
+  }
+  unsigned mx = __float_as_uint(e);
+  unsigned long long fx = (unsigned long long)((double)e * 4294967296.0 + 0.5);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    mx = max(mx, __shfl_down_sync(kFullMask, mx, o));
+    fx += __shfl_down_sync(kFullMask, fx, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&ctl->err_max_bits, mx);
+    atomicAdd(&ctl->err_sum_fx, fx);
+  }
+}
+
+// Pressure acceleration of turn and S_e: -m sum (p_i/rho_i*^2 + p_j/rho_j*^2) grad W(x*_ij);
+// boundary neighbours contribute the p_i/rho_i*^2 term only.
+__global__ void k_ppressure(DevParams P, int n, int j_minor, int row, int mode, PState s,
+                            const uint8_t* __restrict__ in_se, const float4* __restrict__ xs,
+                            const float4* __restrict__ xb, const uint32_t* __restrict__ nbl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (!(has_turn(P, mode, row, j_minor, s.level[i]) || in_se[i])) return;
+  float4 xi = xs[i];
+  const float ri = s.rho[i];
+  float ci = s.prs[i] / (ri * ri);
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  const uint32_t* list = nbl + (size_t)i * P.nbl_cap;
+  int cnt = s.nbr[i];
+  for (int e = 0; e < cnt; ++e) {
+    uint32_t j = list[e];
+    float4 xj;
+    float cj;
+    if (j & kBnd) {
+      xj = xb[j & ~kBnd];
+      cj = 0.f;
+    } else {
+      xj = xs[j];
+      const float rj = s.rho[j];
+      cj = s.prs[j] / (rj * rj);
+    }
+    float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+    float d2 = dx * dx + dy * dy + dz * dz;
+    if (!(d2 > 0.f)) continue;
+    float d = sqrtf(d2);
+    float f = pdW(P, d * P.inv_h) / d;
+    float sc = -P.m * (ci + cj) * f;
+    ax += sc * dx;
+    ay += sc * dy;
+    az += sc * dz;
+  }
+  s.ap[i] = make_float4(ax, ay, az, 0.f);
+}
+
+// ------------------------------------------------------- Algorithm 2 ---
+
+__global__ void k_integrate(DevParams P, int n, PState s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 x = s.x[i], v = s.v[i], a = s.a[i], pa = s.ap[i];
+  float dt = P.dt_b;
+  v.x += dt * (a.x + pa.x);
+  v.y += dt * (a.y + pa.y);
+  v.z += dt * (a.z + pa.z);
+  x.x += dt * v.x;
+  x.y += dt * v.y;
+  x.z += dt * v.z;
+  s.x[i] = x;
+  s.v[i] = v;
+}
+
+__global__ void k_validity(DevParams P, int n, PState s, uint8_t* __restrict__ cflag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int val = s.valid[i] - 1;
+  if (val <= 0) {
+    cflag[i] = 1;
+    val = P.refresh[s.level[i]];
+  } else {
+    cflag[i] = 0;
+  }
+  s.valid[i] = val;
+}
+
+__device__ __forceinline__ int ppick(const DevParams& P, double v2, double a2) {
+  int L = 0;
+  for (int l = 0; l < P.n_levels; ++l)
+    if (P.eq1[l] && v2 <= P.vthr2[l] && a2 <= P.athr2[l]) L = l;
+  return L;
+}
+
+// Section 5.6: a particle needing a smaller region lowers its block and the 26 around.
+__global__ void k_preempt_mark(DevParams P, int n, const uint32_t* __restrict__ key, PState s,
+                               int32_t* __restrict__ pnew) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 v = s.v[i], a = s.a[i], pa = s.ap[i];
+  int L = ppick(P, pnorm2(v.x, v.y, v.z), pnorm2(a.x + pa.x, a.y + pa.y, a.z + pa.z));
+  if (P.force_level >= 0) L = P.force_level;
+  if (L >= s.level[i]) return;
+  uint32_t b = key[i];
+  int bx = b % P.nx, r = b / P.nx, by = r % P.ny, bz = r / P.ny;
+  for (int dz = -1; dz <= 1; ++dz) {
+    int cz = bz + dz;
+    if (cz < 0 || cz >= P.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      int cy = by + dy;
+      if (cy < 0 || cy >= P.ny) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        int cx = bx + dx;
+        if (cx < 0 || cx >= P.nx) continue;
+        size_t c = ((size_t)cz * P.ny + cy) * P.nx + cx;
+        if (pnew[c] >= 0) atomicMin(&pnew[c], L);
+      }
+    }
+  }
+}
+
+__global__ void k_preempt_apply(DevParams P, int n, const uint32_t* __restrict__ key,
+                                const int32_t* __restrict__ pnew, PState s,
+                                uint8_t* __restrict__ cflag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int L = pnew[key[i]];
+  if (L < s.level[i]) {
+    s.level[i] = L;
+    s.valid[i] = P.refresh[L];
+    cflag[i] = 1;
+  }
+}
+
+// ------------------------------------------------------------- host ---
+
+static inline int grid_of(int n) { return (n + 255) / 256; }
+
+int filled_grid_size();
+
+// Scope that counts launches against a phase (no event timing for PCISPH phases).
+struct PPhase {
+  rts_ctx* c;
+  int prev;
+  PPhase(rts_ctx* c_, int ph) : c(c_), prev(c_->cur_phase) { c->cur_phase = ph; }
+  ~PPhase() { c->cur_phase = prev; }
+};
+
+static rts_status major_start(rts_ctx* c) {
+  int n = c->n;
+  size_t nbk = (size_t)c->dp.nblocks;
+  {
+    PPhase ph(c, RTS_PHASE_BIN);
+    launch_bin(c, 0.0f);
+  }
+  PPhase ph(c, RTS_PHASE_CLASSIFY);
+  launch_classify(c);             // Eq. 2-3 from the block maxima (thresholds for PCISPH)
+  launch_activity(c, -1, 0, 0);   // R_min (or the forced region)
+  cudaMemsetAsync(c->preg, 0xff, sizeof(int32_t) * nbk, c->stream);
+  int fg = filled_grid_size();
+  note_launch(c, 1);
+  k_preg_from_blevel<<<fg, 256, 0, c->stream>>>(c->filled, c->ctl, c->blevel, c->preg);
+  if (c->p.force_level < 0 && c->p.expand_layers > 0) {
+    for (int target = 0; target <= 1; ++target) {
+      cudaMemsetAsync(c->pnew, 0xff, sizeof(int32_t) * nbk, c->stream);
+      note_launch(c, 1);
+      k_dilate<<<fg, 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->preg, c->pnew, target,
+                                          c->p.expand_layers);
+      int32_t* t = c->preg;
+      c->preg = c->pnew;
+      c->pnew = t;
+    }
+  }
+  if (n > 0) {
+    note_launch(c, 1);
+    k_assign_regions<<<grid_of(n), 256, 0, c->stream>>>(c->dp, n, c->key, c->preg, c->s, c->cflag);
+  }
+  c->shorten_now = 0;
+  return RTS_OK;
+}
+
+rts_status pcisph_step(rts_ctx* c) {
+  const int n = c->n;
+  const int g = grid_of(n > 0 ? n : 1);
+  const int fg = filled_grid_size();
+  const size_t nbk = (size_t)c->dp.nblocks;
+  if (c->n_minor_cur <= 0) c->n_minor_cur = c->p.n_minor;
+  if (c->minor == 0) major_start(c);
+  const int j = c->minor;
+  if (n > 0) {
+    PPhase ph(c, RTS_PHASE_DENSITY);
+    note_launch(c, 1);
+    k_lists<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->cstart, c->bcstart, c->s, c->xb,
+                                      c->cflag, c->nbl, c->ctl);
+  }
+  if (n > 0) {
+    PPhase ph(c, RTS_PHASE_FORCE);
+    note_launch(c, 1);
+    k_nonpressure<<<g, 256, 0, c->stream>>>(c->dp, n, c->s, c->xb, c->cflag, c->nbl);
+  }
+  cudaMemsetAsync(c->s.prs, 0, sizeof(float) * (size_t)(n > 0 ? n : 1), c->stream);
+  cudaMemsetAsync(c->s.ap, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c->stream);
+  cudaMemsetAsync(c->in_se, 0, (size_t)(n > 0 ? n : 1), c->stream);
+  cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
+  note_launch(c, 1);
+  k_observed<<<fg, 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->preg, c->in_re, c->ob);
+
+  int min_sched = 1 << 30;
+  for (int r = 0; r < c->p.n_levels && r < 4; ++r)
+    if (c->p.sched[r][j] < min_sched) min_sched = c->p.sched[r][j];
+  int min_iter = 3, done = 0, row = 1, mode = kModeSched, local_run = 0, stay_global = 0;
+  rts_status status = RTS_OK;
+  c->it_global = c->it_local = c->it_reverts = c->it_notconv = 0;
+  for (;;) {
+    const int all_turn = mode == kModeGlobal || (mode == kModeSched && row <= min_sched);
+    {
+      PPhase ph(c, RTS_PHASE_ITERATE);
+      note_launch(c, 5);
+      k_predict<<<g, 256, 0, c->stream>>>(c->dp, n, c->s, c->xs);
+      k_pdensity<<<g, 256, 0, c->stream>>>(c->dp, n, j, row, mode, c->key, c->s, c->in_se, c->ob,
+                                           c->xs, c->xb, c->nbl);
+      cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
+      cudaMemsetAsync(&c->ctl->err_max_bits, 0, sizeof(unsigned int), c->stream);
+      cudaMemsetAsync(&c->ctl->err_sum_fx, 0, sizeof(unsigned long long), c->stream);
+      k_se_reduce<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->s, c->in_se, c->in_re, c->ctl);
+      k_observed<<<fg, 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->preg, c->in_re, c->ob);
+      k_ppressure<<<g, 256, 0, c->stream>>>(c->dp, n, j, row, mode, c->s, c->in_se, c->xs, c->xb,
+                                            c->nbl);
+    }
+    cudaMemcpyAsync(&c->h_ctl->err_max_bits, &c->ctl->err_max_bits, sizeof(unsigned int),
+                    cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(&c->h_ctl->err_sum_fx, &c->ctl->err_sum_fx, sizeof(unsigned long long),
+                    cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      cuda_err(c, e, "PCISPH iteration");
+      return RTS_ERR_CUDA;
+    }
+    ++done;
+    if (all_turn) ++c->it_global;
+    if (mode == kModeLocal) ++c->it_local;
+    float emax;
+    unsigned bits = c->h_ctl->err_max_bits;
+    memcpy(&emax, &bits, sizeof emax);
+    c->it_errmax = emax;
+    c->it_erravg = n > 0 ? (double)c->h_ctl->err_sum_fx / 4294967296.0 / n : 0.0;
+    const bool converged = emax <= c->p.eta;
+    if (done >= min_iter && converged) break;
+    if (done >= c->p.max_iters) {
+      status = RTS_ERR_NOT_CONVERGED;
+      c->it_notconv = 1;
+      break;
+    }
+    if (done < 3) {
+      ++row;
+      continue;
+    }
+    min_iter = done + 1;
+    if (stay_global || c->it_erravg >= (double)c->p.eta_T) {
+      mode = kModeGlobal;
+      local_run = 0;
+    } else {
+      if (mode != kModeLocal) {
+        cudaMemcpyAsync(c->pbak, c->s.prs, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice,
+                        c->stream);
+        local_run = 0;
+      }
+      mode = kModeLocal;
+      if (++local_run > c->p.max_local_iters) {
+        cudaMemcpyAsync(c->s.prs, c->pbak, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice,
+                        c->stream);
+        ++c->it_reverts;
+        mode = kModeGlobal;
+        stay_global = 1;
+        local_run = 0;
+      }
+    }
+  }
+  c->it_iters = done;
+  c->tot_iters += done;
+  c->tot_local += c->it_local;
+  c->tot_reverts += c->it_reverts;
+  c->tot_steps += 1;
+  {
+    PPhase ph(c, RTS_PHASE_CORRECT);
+    note_launch(c, 2);
+    k_integrate<<<g, 256, 0, c->stream>>>(c->dp, n, c->s);
+    if (c->it_global > c->p.max_global_iters) c->shorten_now = 1;
+    const int last = (j + 1 >= c->n_minor_cur) || c->shorten_now;
+    k_validity<<<g, 256, 0, c->stream>>>(c->dp, n, c->s, c->cflag);
+    if (!last && n > 0) {
+      note_launch(c, 2);
+      cudaMemcpyAsync(c->pnew, c->preg, sizeof(int32_t) * nbk, cudaMemcpyDeviceToDevice, c->stream);
+      k_preempt_mark<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->s, c->pnew);
+      k_preempt_apply<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->pnew, c->s, c->cflag);
+      int32_t* t = c->preg;
+      c->preg = c->pnew;
+      c->pnew = t;
+    }
+    c->k += 1;
+    if (last) {
+      if (c->shorten_now) {
+        c->n_minor_cur = c->p.short_minor;
+        c->clean = 0;
+      } else if (c->n_minor_cur != c->p.n_minor) {
+        if (++c->clean >= c->p.clean_majors) {
+          c->n_minor_cur = c->p.n_minor;
+          c->clean = 0;
+        }
+      }
+      c->minor = 0;
+    } else {
+      c->minor = j + 1;
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cuda_err(c, e, "PCISPH step");
+    return RTS_ERR_CUDA;
+  }
+  return status;
+}
+
+}  // namespace rts

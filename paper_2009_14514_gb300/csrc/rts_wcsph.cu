@@ -47,7 +47,7 @@ __device__ __forceinline__ int pick_level_f(const DevParams& P, float v2, float 
 // block's particles decide, as the double-precision definition does.
 __global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled, const Ctl* ctl,
                               const uint32_t* __restrict__ cstart, const float4* __restrict__ v,
-                              const float4* __restrict__ a,
+                              const float4* __restrict__ a, const float4* __restrict__ ap,
                               const unsigned long long* __restrict__ bmax_v,
                               const unsigned long long* __restrict__ bmax_a, uint32_t stamp,
                               uint32_t* __restrict__ raw) {
@@ -62,6 +62,12 @@ __global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled, 
       double vmd = 0.0, amd = 0.0;
       for (uint32_t i = cstart[b]; i < cstart[b + 1]; ++i) {
         float4 vi = v[i], ai = a[i];
+        if (ap) {  // PCISPH: total acceleration
+          float4 pa = ap[i];
+          ai.x += pa.x;
+          ai.y += pa.y;
+          ai.z += pa.z;
+        }
         vmd = fmax(vmd, norm2d(vi.x, vi.y, vi.z));
         amd = fmax(amd, norm2d(ai.x, ai.y, ai.z));
       }
@@ -570,12 +576,13 @@ int neighbor_grid_size() {
 }
 
 static int filled_grid() { return sm_count() * 8; }
+int filled_grid_size() { return filled_grid(); }
 
 rts_status launch_classify(rts_ctx* c) {
   note_launch(c, 1);
   k_block_level<<<filled_grid(), 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->cstart, c->s.v,
-                                                      c->s.a, c->bmax_v, c->bmax_a, c->stamp,
-                                                      c->raw);
+                                                      c->s.a, c->s.ap, c->bmax_v, c->bmax_a,
+                                                      c->stamp, c->raw);
   return RTS_OK;
 }
 

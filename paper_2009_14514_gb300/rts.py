@@ -24,6 +24,7 @@ EXPORTED = [
     "rts_pcisph_step", "rts_advance", "rts_get_state", "rts_set_state", "rts_get_bins",
     "rts_get_blocks", "rts_sync", "rts_num_blocks", "rts_substep_index", "rts_last_error",
     "rts_destroy", "rts_profile_enable", "rts_profile_read", "rts_bin_noalloc",
+    "rts_pcisph_last", "rts_get_pcisph_state", "rts_get_neighbors",
 ]
 
 
@@ -69,6 +70,17 @@ class RtsStats(C.Structure):
 
 
 PHASES = ["bin", "classify", "activity", "density", "force", "correct", "iterate", "other"]
+
+
+class RtsPcisphInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("global_iterations", C.c_int32),
+                ("local_iterations", C.c_int32), ("reverts", C.c_int32),
+                ("not_converged", C.c_int32), ("minor", C.c_int32),
+                ("n_minor_current", C.c_int32), ("clean_majors", C.c_int32),
+                ("err_max", C.c_double), ("err_avg", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class RtsProfile(C.Structure):
@@ -130,6 +142,8 @@ def lib():
             "rts_destroy": [vp], "rts_profile_enable": [vp, i32],
             "rts_profile_read": [vp, vp, i32],
             "rts_bin_noalloc": [vp, i32, vp, vp, vp, vp, vp],
+            "rts_pcisph_last": [vp, vp], "rts_get_pcisph_state": [vp, vp, vp, vp],
+            "rts_get_neighbors": [vp, vp, vp, i32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -375,3 +389,28 @@ def rts_bin_noalloc(params, x, key, perm, cstart, stream=None):
     st = lib().rts_bin_noalloc(C.byref(P), n, _ptr(x), _ptr(key), _ptr(perm), _ptr(cstart),
                                _stream(stream))
     return _check(st, "rts_bin_noalloc")
+
+
+def rts_pcisph_last(ctx) -> dict:
+    info = RtsPcisphInfo()
+    _check(lib().rts_pcisph_last(ctx.handle, C.byref(info)), "rts_pcisph_last", ctx)
+    return info.as_dict()
+
+
+def rts_get_pcisph_state(ctx) -> dict:
+    n = ctx.n
+    out = {"ap": np.zeros((n, 3), np.float32), "err": np.zeros(n, np.float32),
+           "in_se": np.zeros(n, np.uint8)}
+    _check(lib().rts_get_pcisph_state(ctx.handle, _ptr(out["ap"]), _ptr(out["err"]),
+                                      _ptr(out["in_se"])), "rts_get_pcisph_state", ctx)
+    return out
+
+
+def rts_get_neighbors(ctx, cap=None):
+    """Neighbour lists (caller indices; boundary b as n + b) as a list of arrays."""
+    n = ctx.n
+    cap = int(cap or ctx.params.max_neighbors)
+    counts = np.zeros(n, np.int32)
+    idx = np.zeros(max(n, 1) * cap, np.int32)
+    _check(lib().rts_get_neighbors(ctx.handle, _ptr(counts), _ptr(idx), cap), "rts_get_neighbors", ctx)
+    return [idx[i * cap: i * cap + counts[i]] for i in range(n)]
