@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="8k-particle dam break (quick check)")
+    ap.add_argument("--no-pcisph", action="store_true", help="skip the PCISPH pool-drop section")
+    ap.add_argument("--pcisph-preroll", type=float, default=0.2)
     ap.add_argument("--profile-case", action="store_true",
                     help="short run for ncu: 1M jittered lattice with a seeded dynamic state, "
                          "primed, then --steps windows (few launches, nothing printed but a line)")
@@ -183,6 +185,7 @@ def run_arm(sc, mode, args, torch, rts, profile=False):
     ms = []
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
+    torch.cuda.nvtx.range_push(f"timed_mode{mode}")   # ncu --nvtx-include timed_mode0/
     for _ in range(args.steps):
         flush.zero_()
         s0 = torch.cuda.Event(enable_timing=True)
@@ -195,6 +198,7 @@ def run_arm(sc, mode, args, torch, rts, profile=False):
         ms.append(s0.elapsed_time(s1))
         for f in tot:
             tot[f] += st[f]
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     prof = rts.rts_profile_read(ctx, reset=True)
@@ -204,6 +208,48 @@ def run_arm(sc, mode, args, torch, rts, profile=False):
     del flush
     return {"ms": ms, "wall": wall, "tot": tot, "prof": prof,
             "rho_err": density_error(g["rho"], d["rho0"]), "levels": last["level_count"][:4]}
+
+
+def run_pcisph(args, torch, rts):
+    """The 1M pool + cube drop (PCISPH): regional time stepping against the global
+    adaptive comparator and the paper's constant 1.66e-4 s step, each advanced from t = 0
+    to --pcisph-preroll and then timed over the same simulated time (args.steps major
+    steps of 4 dt_b).  Values are fluid particles x (simulated time / dt_b) per second
+    with the regional dt_b = 3.5e-4 s for every arm."""
+    from paper_2009_14514_gb300 import scenes
+    sc = scenes.pcisph_drop_1m()
+    dtb = sc.params["dt_b"]
+    window = 4 * dtb * args.steps
+    out = {"workload": f"{sc.name}: {sc.n} fluid + {sc.nb} boundary, window {window:.4f} s "
+                       f"from t={args.pcisph_preroll}s"}
+    stream = torch.cuda.current_stream()
+    for arm, over in (("rts", {}), ("global_adaptive", {"mode": 1}),
+                      ("constant_dt", {"mode": 2, "dt_b": 1.66e-4})):
+        d = dict(sc.params)
+        d.update(over)
+        ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
+        rts.rts_advance(ctx, args.pcisph_preroll)
+        t0 = ctx.substep_index * d["dt_b"]
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = rts.rts_advance(ctx, t0 + window)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        sim = st["substeps"] * d["dt_b"]
+        err = rts.rts_get_pcisph_state(ctx)["err"]
+        out[arm] = {"value": sc.n * (sim / dtb) / (ms / 1e3), "ms": ms, "sim_s": sim,
+                    "wall_s_per_sim_s": (ms / 1e3) / sim, "steps": st["steps"],
+                    "iterations": st["pcisph_iterations"],
+                    "local_iterations": st["pcisph_local_iterations"],
+                    "err_mean": float(err.mean()), "err_max": float(err.max()),
+                    "level_count": st["level_count"][:4]}
+        ctx.close()
+    out["rts_vs_global"] = out["rts"]["value"] / out["global_adaptive"]["value"]
+    out["rts_vs_constant"] = out["rts"]["value"] / out["constant_dt"]["value"]
+    return out
 
 
 def run_e2e(sc, args, torch, rts):
@@ -322,6 +368,7 @@ def main():
     barrier()
     glob = None if args.no_global else run_arm(sc, 1, args, torch, rts)
     e2e = None if args.no_e2e else run_e2e(sc, args, torch, rts)
+    pcisph = None if (args.no_pcisph or args.small) else run_pcisph(args, torch, rts)
 
     total_ms = sum(ours["ms"])
     if world > 1:
@@ -378,6 +425,8 @@ def main():
         line["rts_vs_global"] = value / world / gval
     if e2e is not None:
         line["e2e"] = e2e
+    if pcisph is not None:
+        line["pcisph"] = pcisph
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle(sc)
     if rank == 0:

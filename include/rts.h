@@ -142,7 +142,9 @@ rts_status rts_evaluate(rts_ctx* ctx);
 rts_status rts_wcsph_substep(rts_ctx* ctx);
 
 /* One PCISPH minor step dt_b (Algorithm 2 with Algorithm 3 for density correction).
- * Region assignment, grid and neighbourhood refresh happen at major-step starts. */
+ * Region assignment, grid and neighbourhood refresh happen at major-step starts.  In a
+ * global mode, one plain PCISPH step of mult * dt_b for every particle instead (mult from
+ * the whole fluid's maxima, or 1), with a fresh grid and fresh neighbourhoods. */
 rts_status rts_pcisph_step(rts_ctx* ctx);
 
 /* Advance to simulated time t_sim (rounded to whole base substeps) with the context's

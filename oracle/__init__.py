@@ -136,6 +136,7 @@ def _declare(L):
     L.orc_observed_blocks.argtypes = [vp, vp, vp, vp]
     L.orc_pcisph_step.argtypes = [vp, vp]
     L.orc_pcisph_plain_step.argtypes = [vp, vp]
+    L.orc_pcisph_global_step.argtypes = [vp, vp, i32, vp]
 
 
 class OracleError(RuntimeError):
@@ -392,6 +393,14 @@ class PCISPH:
             return st
         _check(st, "orc_pcisph_plain_step")
         return st
+
+    def global_step(self, max_mult=1 << 30, allow_not_converged=True):
+        used = C.c_int32(0)
+        st = lib().orc_pcisph_global_step(C.byref(self.P), C.byref(self.S), int(max_mult),
+                                          C.byref(used))
+        if not (st == 6 and allow_not_converged):
+            _check(st, "orc_pcisph_global_step")
+        return used.value
 
     def neighbors(self, i):
         return self.nbr_idx[i * self.cap: i * self.cap + self.nbr_cnt[i]]

@@ -177,6 +177,13 @@ int orc_pcisph_step(const orc_params* P, orc_pstate* S);
  * Shares the state layout; uses dt_b. */
 int orc_pcisph_plain_step(const orc_params* P, orc_pstate* S);
 
+/* Global comparators for PCISPH: plain PCISPH with one step of mult * dt_b, mult from the
+ * finest region Eq. 2-3 give for the whole fluid (mode 1) or 1 (mode 2), capped at
+ * max_mult; delta follows the step.  Mode 1 rejects a step whose correction reaches
+ * max_iters and retries it with half the multiplier.  [pinned: mode 2 is plain PCISPH] */
+int orc_pcisph_global_step(const orc_params* P, orc_pstate* S, int32_t max_mult,
+                           int32_t* mult_used);
+
 #ifdef __cplusplus
 }
 #endif

@@ -520,3 +520,50 @@ int orc_pcisph_plain_step(const orc_params* P, orc_pstate* S) {
   S->k += 1;
   return status;
 }
+
+int orc_pcisph_global_step(const orc_params* P, orc_pstate* S, int32_t max_mult,
+                           int32_t* mult_used) {
+  int32_t L = 0;
+  if (P->mode != 2) {
+    double vthr2[8], athr2[8];
+    int32_t eq1[8];
+    orc_level_thresholds(P, vthr2, athr2, eq1);
+    double vmax2 = 0.0, amax2 = 0.0;
+    for (int32_t i = 0; i < S->n; ++i) {
+      double a[3] = {S->anp[3 * i] + S->ap[3 * i], S->anp[3 * i + 1] + S->ap[3 * i + 1],
+                     S->anp[3 * i + 2] + S->ap[3 * i + 2]};
+      double v2 = orci_norm2(S->v + 3 * (int64_t)i), a2 = orci_norm2(a);
+      if (v2 > vmax2) vmax2 = v2;
+      if (a2 > amax2) amax2 = a2;
+    }
+    L = orci_pick_level(P, vthr2, athr2, eq1, vmax2, amax2);
+  }
+  int32_t m = P->mult[L];
+  if (m > max_mult) m = max_mult;
+  if (m < 1) m = 1;
+  /* a step whose correction does not converge is rejected and retried with half the
+   * multiplier (density-error feedback of an adaptive global step) */
+  int32_t n = S->n;
+  size_t v3 = sizeof(double) * 3 * (size_t)(n > 0 ? n : 1);
+  double* x0 = (double*)malloc(v3);
+  double* v0 = (double*)malloc(v3);
+  memcpy(x0, S->x, v3);
+  memcpy(v0, S->v, v3);
+  int64_t k0 = S->k;
+  int st;
+  for (;;) {
+    orc_params Q = *P;
+    Q.dt_b = (double)m * P->dt_b;
+    st = orc_pcisph_plain_step(&Q, S);
+    if (st != ORC_ERR_NOT_CONVERGED || m == 1 || P->mode == 2) break;
+    memcpy(S->x, x0, v3);
+    memcpy(S->v, v0, v3);
+    m = m / 2 > 1 ? m / 2 : 1;
+  }
+  free(x0);
+  free(v0);
+  S->k = k0 + m;
+  for (int32_t i = 0; i < S->n; ++i) S->level[i] = L;
+  if (mult_used) *mult_used = m;
+  return st;
+}

@@ -642,7 +642,7 @@ rts_status rts_advance(rts_ctx* c, double t_sim, rts_stats* out) {
     if (c->p.scheme == RTS_WCSPH) {
       st = wcsph_step(c, K - c->k);
     } else {
-      st = rts_pcisph_step(c);
+      st = pcisph_step(c, K - c->k);
     }
     if (st != RTS_OK && st != RTS_ERR_NOT_CONVERGED) return st;
     if (st == RTS_ERR_NOT_CONVERGED) nconv = st;
@@ -814,7 +814,7 @@ rts_status rts_profile_read(rts_ctx* c, rts_profile* out, int32_t reset) {
 rts_status rts_pcisph_step(rts_ctx* c) {
   GUARD();
   if (c->p.scheme != RTS_PCISPH) return fail(c, RTS_ERR_ARG, "context was created for WCSPH");
-  return pcisph_step(c);
+  return pcisph_step(c, (int64_t)1 << 40);
 }
 
 rts_status rts_pcisph_last(rts_ctx* c, rts_pcisph_info* out) {

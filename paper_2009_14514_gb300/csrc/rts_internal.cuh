@@ -180,5 +180,5 @@ rts_status launch_correct(rts_ctx* c, int64_t k1, int prime);
 rts_status launch_global_max(rts_ctx* c);
 rts_status launch_level_hist(rts_ctx* c);
 const char* cuda_err(rts_ctx* c, cudaError_t e, const char* what);
-rts_status pcisph_step(rts_ctx* c);
+rts_status pcisph_step(rts_ctx* c, int64_t max_mult);
 }  // namespace rts

@@ -459,52 +459,37 @@ static rts_status major_start(rts_ctx* c) {
   return RTS_OK;
 }
 
-rts_status pcisph_step(rts_ctx* c) {
+// Algorithm 3 for minor step j with parameters Q.  plain: every particle in every
+// iteration and only global extra iterations (the comparators' plain PCISPH).
+static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool plain) {
   const int n = c->n;
   const int g = grid_of(n > 0 ? n : 1);
   const int fg = filled_grid_size();
   const size_t nbk = (size_t)c->dp.nblocks;
-  if (c->n_minor_cur <= 0) c->n_minor_cur = c->p.n_minor;
-  if (c->minor == 0) major_start(c);
-  const int j = c->minor;
-  if (n > 0) {
-    PPhase ph(c, RTS_PHASE_DENSITY);
-    note_launch(c, 1);
-    k_lists<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->cstart, c->bcstart, c->s, c->xb,
-                                      c->cflag, c->nbl, c->ctl);
-  }
-  if (n > 0) {
-    PPhase ph(c, RTS_PHASE_FORCE);
-    note_launch(c, 1);
-    k_nonpressure<<<g, 256, 0, c->stream>>>(c->dp, n, c->s, c->xb, c->cflag, c->nbl);
-  }
-  cudaMemsetAsync(c->s.prs, 0, sizeof(float) * (size_t)(n > 0 ? n : 1), c->stream);
-  cudaMemsetAsync(c->s.ap, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c->stream);
-  cudaMemsetAsync(c->in_se, 0, (size_t)(n > 0 ? n : 1), c->stream);
-  cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
-  note_launch(c, 1);
-  k_observed<<<fg, 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->preg, c->in_re, c->ob);
-
   int min_sched = 1 << 30;
   for (int r = 0; r < c->p.n_levels && r < 4; ++r)
     if (c->p.sched[r][j] < min_sched) min_sched = c->p.sched[r][j];
   int min_iter = 3, done = 0, row = 1, mode = kModeSched, local_run = 0, stay_global = 0;
   rts_status status = RTS_OK;
+  if (plain) {
+    mode = kModeGlobal;
+    stay_global = 1;
+  }
   c->it_global = c->it_local = c->it_reverts = c->it_notconv = 0;
   for (;;) {
     const int all_turn = mode == kModeGlobal || (mode == kModeSched && row <= min_sched);
     {
       PPhase ph(c, RTS_PHASE_ITERATE);
       note_launch(c, 5);
-      k_predict<<<g, 256, 0, c->stream>>>(c->dp, n, c->s, c->xs);
-      k_pdensity<<<g, 256, 0, c->stream>>>(c->dp, n, j, row, mode, c->key, c->s, c->in_se, c->ob,
+      k_predict<<<g, 256, 0, c->stream>>>(Q, n, c->s, c->xs);
+      k_pdensity<<<g, 256, 0, c->stream>>>(Q, n, j, row, mode, c->key, c->s, c->in_se, c->ob,
                                            c->xs, c->xb, c->nbl);
       cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
       cudaMemsetAsync(&c->ctl->err_max_bits, 0, sizeof(unsigned int), c->stream);
       cudaMemsetAsync(&c->ctl->err_sum_fx, 0, sizeof(unsigned long long), c->stream);
-      k_se_reduce<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->s, c->in_se, c->in_re, c->ctl);
-      k_observed<<<fg, 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->preg, c->in_re, c->ob);
-      k_ppressure<<<g, 256, 0, c->stream>>>(c->dp, n, j, row, mode, c->s, c->in_se, c->xs, c->xb,
+      k_se_reduce<<<g, 256, 0, c->stream>>>(Q, n, c->key, c->s, c->in_se, c->in_re, c->ctl);
+      k_observed<<<fg, 256, 0, c->stream>>>(Q, c->filled, c->ctl, c->preg, c->in_re, c->ob);
+      k_ppressure<<<g, 256, 0, c->stream>>>(Q, n, j, row, mode, c->s, c->in_se, c->xs, c->xb,
                                             c->nbl);
     }
     cudaMemcpyAsync(&c->h_ctl->err_max_bits, &c->ctl->err_max_bits, sizeof(unsigned int),
@@ -561,6 +546,146 @@ rts_status pcisph_step(rts_ctx* c) {
   c->tot_local += c->it_local;
   c->tot_reverts += c->it_reverts;
   c->tot_steps += 1;
+  return status;
+}
+
+// Maxima of |v|^2 and |a_np + a_p|^2 over the fluid (FP64, order independent).
+__global__ void k_pglobal_max(int n, PState s, Ctl* ctl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double vm = 0.0, am = 0.0;
+  if (i < n) {
+    float4 v = s.v[i], a = s.a[i], pa = s.ap[i];
+    vm = pnorm2(v.x, v.y, v.z);
+    am = pnorm2(a.x + pa.x, a.y + pa.y, a.z + pa.z);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    vm = fmax(vm, __shfl_down_sync(kFullMask, vm, o));
+    am = fmax(am, __shfl_down_sync(kFullMask, am, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&ctl->vmax2_bits, (unsigned long long)__double_as_longlong(vm));
+    atomicMax(&ctl->amax2_bits, (unsigned long long)__double_as_longlong(am));
+  }
+}
+
+__global__ void k_all_region(int n, int L, PState s, uint8_t* __restrict__ cflag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  s.level[i] = L;
+  s.valid[i] = 1;
+  cflag[i] = 1;
+}
+
+// Global comparators (Section 6): plain PCISPH with one step of m dt_b for every particle,
+// m from the finest region the criteria give for the whole fluid (global adaptive) or 1
+// (constant); fresh grid and neighbourhoods every step, delta scaled by 1 / m^2.
+static rts_status pcisph_global(rts_ctx* c, int64_t max_mult) {
+  const int n = c->n;
+  const int g = grid_of(n > 0 ? n : 1);
+  int L = 0;
+  if (c->p.mode == RTS_MODE_GLOBAL_ADAPTIVE && n > 0) {
+    cudaMemsetAsync(&c->ctl->vmax2_bits, 0, 2 * sizeof(unsigned long long), c->stream);
+    {
+      PPhase ph(c, RTS_PHASE_CLASSIFY);
+      note_launch(c, 1);
+      k_pglobal_max<<<g, 256, 0, c->stream>>>(n, c->s, c->ctl);
+    }
+    cudaMemcpyAsync(&c->h_ctl->vmax2_bits, &c->ctl->vmax2_bits, 2 * sizeof(unsigned long long),
+                    cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RTS_ERR_CUDA;
+    double v2, a2;
+    memcpy(&v2, &c->h_ctl->vmax2_bits, sizeof v2);
+    memcpy(&a2, &c->h_ctl->amax2_bits, sizeof a2);
+    for (int l = 0; l < c->dp.n_levels; ++l)
+      if (c->dp.eq1[l] && v2 <= c->dp.vthr2[l] && a2 <= c->dp.athr2[l]) L = l;
+  }
+  int64_t m = c->p.level_mult[L];
+  if (m > max_mult) m = max_mult;
+  if (m < 1) m = 1;
+  DevParams Q = c->dp;
+  Q.dt_b = (float)((double)m * (double)c->p.dt_b);
+  Q.delta = (float)((double)c->dp.delta / (double)(m * m));
+  Q.r1_rings = 1;
+  {
+    PPhase ph(c, RTS_PHASE_BIN);
+    launch_bin(c, 0.0f);
+  }
+  if (n > 0) {
+    note_launch(c, 3);
+    k_all_region<<<g, 256, 0, c->stream>>>(n, 0, c->s, c->cflag);
+    {
+      PPhase ph(c, RTS_PHASE_DENSITY);
+      k_lists<<<g, 256, 0, c->stream>>>(Q, n, c->key, c->cstart, c->bcstart, c->s, c->xb, c->cflag,
+                                        c->nbl, c->ctl);
+    }
+    {
+      PPhase ph(c, RTS_PHASE_FORCE);
+      k_nonpressure<<<g, 256, 0, c->stream>>>(Q, n, c->s, c->xb, c->cflag, c->nbl);
+    }
+  }
+  const size_t n1 = (size_t)(n > 0 ? n : 1);
+  cudaMemsetAsync(c->ob, 0, (size_t)c->dp.nblocks, c->stream);
+  // the sort's spare buffers keep the step's start state for a rejected step
+  if (c->p.mode == RTS_MODE_GLOBAL_ADAPTIVE && m > 1) {
+    cudaMemcpyAsync(c->s2.x, c->s.x, sizeof(float4) * n1, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->s2.v, c->s.v, sizeof(float4) * n1, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  rts_status status;
+  for (;;) {
+    cudaMemsetAsync(c->s.prs, 0, sizeof(float) * n1, c->stream);
+    cudaMemsetAsync(c->s.ap, 0, sizeof(float4) * n1, c->stream);
+    cudaMemsetAsync(c->in_se, 0, n1, c->stream);
+    status = run_correction(c, Q, 0, true);
+    if (status != RTS_OK && status != RTS_ERR_NOT_CONVERGED) return status;
+    // density-error feedback: a step that does not converge is retried with m / 2
+    if (status != RTS_ERR_NOT_CONVERGED || m == 1 || c->p.mode != RTS_MODE_GLOBAL_ADAPTIVE) break;
+    m = m / 2 > 1 ? m / 2 : 1;
+    Q.dt_b = (float)((double)m * (double)c->p.dt_b);
+    Q.delta = (float)((double)c->dp.delta / (double)(m * m));
+    cudaMemcpyAsync(c->s.x, c->s2.x, sizeof(float4) * n1, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->s.v, c->s2.v, sizeof(float4) * n1, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  if (n > 0) {
+    PPhase ph(c, RTS_PHASE_CORRECT);
+    note_launch(c, 2);
+    k_integrate<<<g, 256, 0, c->stream>>>(Q, n, c->s);
+    k_all_region<<<g, 256, 0, c->stream>>>(n, L, c->s, c->cflag);
+  }
+  c->k += m;
+  c->minor = 0;
+  return status;
+}
+
+rts_status pcisph_step(rts_ctx* c, int64_t max_mult) {
+  if (c->p.mode != RTS_MODE_REGIONAL) return pcisph_global(c, max_mult);
+  const int n = c->n;
+  const int g = grid_of(n > 0 ? n : 1);
+  const int fg = filled_grid_size();
+  const size_t nbk = (size_t)c->dp.nblocks;
+  if (c->n_minor_cur <= 0) c->n_minor_cur = c->p.n_minor;
+  if (c->minor == 0) major_start(c);
+  const int j = c->minor;
+  if (n > 0) {
+    PPhase ph(c, RTS_PHASE_DENSITY);
+    note_launch(c, 1);
+    k_lists<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->cstart, c->bcstart, c->s, c->xb,
+                                      c->cflag, c->nbl, c->ctl);
+  }
+  if (n > 0) {
+    PPhase ph(c, RTS_PHASE_FORCE);
+    note_launch(c, 1);
+    k_nonpressure<<<g, 256, 0, c->stream>>>(c->dp, n, c->s, c->xb, c->cflag, c->nbl);
+  }
+  cudaMemsetAsync(c->s.prs, 0, sizeof(float) * (size_t)(n > 0 ? n : 1), c->stream);
+  cudaMemsetAsync(c->s.ap, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c->stream);
+  cudaMemsetAsync(c->in_se, 0, (size_t)(n > 0 ? n : 1), c->stream);
+  cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
+  note_launch(c, 1);
+  k_observed<<<fg, 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->preg, c->in_re, c->ob);
+
+  rts_status status = run_correction(c, c->dp, j, false);
+  if (status != RTS_OK && status != RTS_ERR_NOT_CONVERGED) return status;
   {
     PPhase ph(c, RTS_PHASE_CORRECT);
     note_launch(c, 2);

@@ -173,3 +173,18 @@ def test_full_size_pool_drop_runs_one_major_step():
     P = O.make_params(sc.params)
     assert max(len(l) for l in lists) <= P.max_neighbors
     assert np.mean([len(lists[i]) for i in rng.choice(sc.n, 1000, replace=False)]) > 15
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_global_comparators_match_oracle(mode):
+    sc = scenes.pcisph_drop_small()
+    ctx, S, P = _pair(sc, mode=mode)
+    for _ in range(3):
+        k0 = ctx.substep_index
+        rts.rts_pcisph_step(ctx)
+        m = S.global_step()
+        assert ctx.substep_index - k0 == m == (1 if mode == 2 else m)
+        assert rts.rts_pcisph_last(ctx)["iterations"] == S.S.iters
+    g = rts.rts_get_state(ctx, ("x", "v", "rho"))
+    np.testing.assert_allclose(g["rho"], S.rho, rtol=RHO_RTOL)
+    assert np.abs(g["x"] - S.x).max() < 2e-5
