@@ -71,7 +71,15 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
     b = 0;
   }
   key[i] = b;
-  slot[i] = atomicAdd(&count[b], 1u);
+  // one atomic per distinct block in the warp: consecutive particles mostly share a block
+  const unsigned active = __activemask();
+  const unsigned peers = __match_any_sync(active, b);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&count[b], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  slot[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
 // ---- exclusive scan of the per-block counts (reduce, scan tile sums, apply) ----

@@ -254,32 +254,6 @@ __device__ __forceinline__ Runs block_runs(const DevParams& P, int bx, int by, i
   return R;
 }
 
-// Stage candidates [c0, c0 + cnt) of the concatenated runs into shared memory with
-// asynchronous 16-byte copies, with each candidate's index (boundary: top bit set).
-__device__ __forceinline__ void stage_chunk(const Runs& R, uint32_t c0, uint32_t cnt,
-                                            const float4* __restrict__ xf,
-                                            const float4* __restrict__ xbnd, float4* sx,
-                                            uint32_t* sidx, int lane) {
-#pragma unroll 1
-  for (int r = 0; r < 18; ++r) {
-    uint32_t st = __shfl_sync(kFull, R.start, r);
-    uint32_t ln = __shfl_sync(kFull, R.len, r);
-    uint32_t of = __shfl_sync(kFull, R.off, r);
-    uint32_t lo = of > c0 ? of : c0;
-    uint32_t hi = of + ln < c0 + cnt ? of + ln : c0 + cnt;
-    if (lo >= hi) continue;
-    const float4* src = r < 9 ? xf : xbnd;
-    const uint32_t tag = r < 9 ? 0u : kBoundaryBit;
-    for (uint32_t k = lo + lane; k < hi; k += 32) {
-      uint32_t g = st + (k - of);
-      cp_async16(&sx[k - c0], &src[g]);
-      sidx[k - c0] = g | tag;
-    }
-  }
-  cp_async_wait_all();
-  __syncwarp();
-}
-
 // The evaluated particles of one active block, split over the warp's lanes: lpp lanes
 // per particle (a power of two), particle pid of the group, lane sub within it.
 struct Group {
@@ -308,13 +282,55 @@ __device__ __forceinline__ bool next_group(uint32_t base, uint32_t end,
   return true;
 }
 
+// Stage the candidates of the block's runs that lie within the support radius of the
+// box [lo, hi] bounding the group's evaluated particles (every neighbour of a particle
+// in the box passes), compacted into shared memory with their indices (boundary: top
+// bit).  Only kept candidates with kept index in [skip, skip + kCap) are stored; the
+// return value is the total number kept.  tab holds the 18 runs (start, length, offset).
+__device__ __forceinline__ uint32_t stage_culled(const DevParams& P, const uint32_t* tab,
+                                                 uint32_t total, float3 lo, float3 hi,
+                                                 uint32_t skip, const float4* __restrict__ xf,
+                                                 const float4* __restrict__ xbnd, float4* sx,
+                                                 uint32_t* sidx, int lane) {
+  const float cut2 = P.r2_hi * 1.0001f;
+  const unsigned below = (1u << lane) - 1u;
+  uint32_t kept = 0;
+  int r = 0;
+#pragma unroll 2
+  for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+    const uint32_t k = k0 + lane;
+    bool keep = false;
+    float4 xj = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t tag = 0;
+    if (k < total) {
+      while (k >= tab[3 * r + 2] + tab[3 * r + 1]) ++r;
+      const uint32_t g = tab[3 * r] + (k - tab[3 * r + 2]);
+      xj = r < 9 ? xf[g] : xbnd[g];
+      tag = r < 9 ? g : (g | kBoundaryBit);
+      const float ex = fmaxf(fmaxf(lo.x - xj.x, xj.x - hi.x), 0.f);
+      const float ey = fmaxf(fmaxf(lo.y - xj.y, xj.y - hi.y), 0.f);
+      const float ez = fmaxf(fmaxf(lo.z - xj.z, xj.z - hi.z), 0.f);
+      keep = ex * ex + ey * ey + ez * ez <= cut2;
+    }
+    const unsigned m = __ballot_sync(kFull, keep);
+    const uint32_t pos = kept + (uint32_t)__popc(m & below);
+    if (keep && pos >= skip && pos < skip + (uint32_t)kCap) {
+      sx[pos - skip] = xj;
+      sidx[pos - skip] = tag;
+    }
+    kept += (uint32_t)__popc(m);
+  }
+  __syncwarp();
+  return kept;
+}
+
 // Density pass (Algorithm 1, "find neighborhoods" and "update rho, p"): every evaluated
-// particle tests the staged candidates of its block's 27-block stencil with the exact
-// predicate, sums m W over its neighbours (itself included), applies the Tait equation
-// and records its neighbour list for the force pass.  Each lane keeps a bit per tested
-// candidate and appends its hits every 32 iterations (segmented prefix over the lpp
-// lanes of its particle), so the list order is fixed by the group layout.
-__global__ void __launch_bounds__(kNbThreads) k_density(DevParams P, const uint32_t* __restrict__ act,
+// particle tests the candidates kept for its group with the exact predicate, sums m W
+// over its neighbours (itself included), applies the Tait equation and records its
+// neighbour list for the force pass.  Each round of up to 32 candidates per lane first
+// tests distances only (a bit per candidate inside the guard band), then evaluates the
+// kernel for those, then appends the neighbours in a fixed order.
+__global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const uint32_t* __restrict__ act,
                                                         Ctl* ctl, const uint32_t* __restrict__ cstart,
                                                         const uint32_t* __restrict__ bcstart, PState s,
                                                         const float4* __restrict__ xb,
@@ -325,6 +341,8 @@ __global__ void __launch_bounds__(kNbThreads) k_density(DevParams P, const uint3
   const int wib = threadIdx.x >> 5;
   float4* sx = smem + wib * kCap;
   uint32_t* sidx = reinterpret_cast<uint32_t*>(smem + (kNbThreads / 32) * kCap) + wib * kCap;
+  uint32_t* tab = reinterpret_cast<uint32_t*>(smem + (kNbThreads / 32) * kCap) +
+                  (kNbThreads / 32) * kCap + wib * 64;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n_act = *(volatile int*)&ctl->n_act;
@@ -334,6 +352,18 @@ __global__ void __launch_bounds__(kNbThreads) k_density(DevParams P, const uint3
     const int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
     const uint32_t beg = cstart[b], end = cstart[b + 1];
     const Runs R = block_runs(P, bx, by, bz, cstart, bcstart, lane);
+    __syncwarp();
+    if (lane < 18) {
+      tab[3 * lane] = R.start;
+      tab[3 * lane + 1] = R.len;
+      tab[3 * lane + 2] = R.off;
+    }
+    if (lane == 18) {  // sentinel run: never exhausted
+      tab[3 * 18] = 0;
+      tab[3 * 18 + 1] = 0xffffffffu;
+      tab[3 * 18 + 2] = 0;
+    }
+    __syncwarp();
     for (uint32_t base = beg; base < end; base += 32) {
       Group G;
       if (!next_group(base, end, cflag, lane, G)) continue;
@@ -341,36 +371,61 @@ __global__ void __launch_bounds__(kNbThreads) k_density(DevParams P, const uint3
       const bool gvalid = i >= 0;
       const uint32_t lpp = (uint32_t)G.lpp, sub = (uint32_t)G.sub;
       const float4 xi = gvalid ? s.x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      // box of the group's evaluated particles
+      float3 lo = gvalid ? make_float3(xi.x, xi.y, xi.z) : make_float3(3e38f, 3e38f, 3e38f);
+      float3 hi = gvalid ? make_float3(xi.x, xi.y, xi.z) : make_float3(-3e38f, -3e38f, -3e38f);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, o));
+        lo.y = fminf(lo.y, __shfl_xor_sync(kFull, lo.y, o));
+        lo.z = fminf(lo.z, __shfl_xor_sync(kFull, lo.z, o));
+        hi.x = fmaxf(hi.x, __shfl_xor_sync(kFull, hi.x, o));
+        hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, o));
+        hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
+      }
       uint32_t* list = nbl + (size_t)(gvalid ? i : 0) * P.nbl_cap;
       float wsum = 0.f;
       int nn = 0;
-      for (uint32_t c0 = 0; c0 < R.total; c0 += kCap) {
-        const uint32_t cn = R.total - c0 < (uint32_t)kCap ? R.total - c0 : (uint32_t)kCap;
+      uint32_t kept_total = 1;
+      for (uint32_t skip = 0; skip < kept_total; skip += kCap) {
         __syncwarp();
-        stage_chunk(R, c0, cn, s.x, xb, sx, sidx, lane);
+        kept_total = stage_culled(P, tab, R.total, lo, hi, skip, s.x, xb, sx, sidx, lane);
+        if (kept_total <= skip) break;
+        const uint32_t cn = kept_total - skip < (uint32_t)kCap ? kept_total - skip : (uint32_t)kCap;
         const uint32_t iters = (cn + lpp - 1) / lpp;  // uniform over the warp
         for (uint32_t r0 = 0; r0 < iters; r0 += 32) {
           const uint32_t rn = iters - r0 < 32u ? iters - r0 : 32u;
-          uint32_t bits = 0;
-#pragma unroll 2
-          for (uint32_t j = 0; j < rn; ++j) {
+          // 1. distance test only: candidates below the upper edge of the guard band
+          uint32_t near = 0;
+          if (gvalid) {
+#pragma unroll 4
+            for (uint32_t j = 0; j < rn; ++j) {
+              const uint32_t k = (r0 + j) * lpp + sub;
+              const float4 xj = sx[k < cn ? k : 0u];
+              const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+              const float d2 = dx * dx + dy * dy + dz * dz;
+              near |= (k < cn && d2 < P.r2_hi) ? (1u << j) : 0u;
+            }
+          }
+          // 2. exact predicate, kernel sum and neighbour bits for the near candidates
+          uint32_t put = 0;
+          for (uint32_t m = near; m; m &= m - 1u) {
+            const uint32_t j = (uint32_t)(__ffs(m) - 1);
             const uint32_t k = (r0 + j) * lpp + sub;
-            const bool valid = gvalid && k < cn;
-            const float4 xj = sx[valid ? k : 0u];
+            const float4 xj = sx[k];
             const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
             const float d2 = dx * dx + dy * dy + dz * dz;
-            bool in = valid && d2 < P.r2_lo;
-            if (valid && d2 >= P.r2_lo && d2 < P.r2_hi) in = exact_nbr(xi, xj, P.r2d);
-            const float d = d2 * rsqrtf(d2);
-            const float w = spline_W(P, d * P.inv_h);
-            if (in) wsum += d2 > 0.f ? w : P.sigma;
-            // a neighbour is any candidate passing the predicate except the particle itself
-            bool put = in && d2 > 0.f;
-            if (in && d2 == 0.f) put = sidx[k] != (uint32_t)i;
-            bits |= put ? (1u << j) : 0u;
+            if (!(d2 < P.r2_lo || exact_nbr(xi, xj, P.r2d))) continue;
+            if (d2 > 0.f) {
+              wsum += spline_W(P, d2 * rsqrtf(d2) * P.inv_h);
+              put |= 1u << j;
+            } else {
+              wsum += P.sigma;  // the particle itself, or a coincident neighbour
+              if (sidx[k] != (uint32_t)i) put |= 1u << j;
+            }
           }
-          // append this round's hits: segmented exclusive prefix over the group's lanes
-          const int c = __popc(bits);
+          // 3. append: segmented exclusive prefix over the group's lanes
+          const int c = __popc(put);
           int inc = c;
           for (uint32_t o = 1; o < lpp; o <<= 1) {
             int tv = __shfl_up_sync(kFull, inc, o, lpp);
@@ -378,10 +433,9 @@ __global__ void __launch_bounds__(kNbThreads) k_density(DevParams P, const uint3
           }
           const int tot = __shfl_sync(kFull, inc, lpp - 1, lpp);
           int pos = nn + inc - c;
-          while (bits) {
-            const uint32_t bj = (uint32_t)(__ffs(bits) - 1);
-            bits &= bits - 1u;
-            if (pos < P.nbl_cap) list[pos] = sidx[(r0 + bj) * lpp + sub];
+          for (uint32_t m = put; m; m &= m - 1u) {
+            const uint32_t j = (uint32_t)(__ffs(m) - 1);
+            if (pos < P.nbl_cap) list[pos] = sidx[(r0 + j) * lpp + sub];
             ++pos;
           }
           nn += tot;
@@ -564,7 +618,9 @@ static int sm_count() {
   return g_sms;
 }
 
-static size_t density_smem() { return (size_t)(kNbThreads / 32) * kCap * (sizeof(float4) + sizeof(uint32_t)); }
+static size_t density_smem() {
+  return (size_t)(kNbThreads / 32) * (kCap * (sizeof(float4) + sizeof(uint32_t)) + 64 * sizeof(uint32_t));
+}
 
 int neighbor_grid_size() {
   int occ0 = 1, occ1 = 1;

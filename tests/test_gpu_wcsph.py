@@ -307,3 +307,15 @@ def test_block_over_capacity_is_reported():
         rts.rts_sync(ctx)
         rts.rts_advance(ctx, sc.params["dt_b"])
     assert e.value.status == 5
+
+
+def test_neighbour_lists_of_evaluated_particles_equal_brute_force():
+    sc = scenes.wcsph_dam_break_8k()
+    st = dynamic_state(sc, seed=8)
+    ctx = gpu_ctx(sc)
+    rts.rts_set_state(ctx, st["x"], st["v"], a=st["a"], rho=st["rho"], p=st["p"])
+    rts.rts_evaluate(ctx)
+    lists = rts.rts_get_neighbors(ctx)
+    off, idx = O.neighbors_brute(st["x"], sc.xb, O.make_params(sc.params).r)
+    for i in range(sc.n):
+        assert sorted(lists[i].tolist()) == sorted(idx[off[i]:off[i + 1]].tolist()), i
