@@ -30,13 +30,16 @@ if ROOT not in sys.path:
 
 N_SM = 152
 FP32_LANES_PER_SM = 128
-# algorithmic FP32 flops (FMA = 2): candidate test = 3 sub + 1 mul + 2 fma = 8;
-# density pair = sqrt + scale + cubic-spline branch (~8) + accumulate = 11;
-# force pair = sqrt, scale, dW branch, divide, dot (5), viscosity (6), pressure term and
-# scale (4), 3 fma accumulations (6) = 30.
+# Algorithmic FP32 flops of the neighbour passes (FMA = 2), per unit of work that the
+# standard cell-list formulation does, independent of this implementation's culling:
+#   candidate test (every particle in the evaluated particle's 27-block stencil):
+#     3 sub + 1 mul + 2 fma = 8
+#   density pair (d < r): sqrt + scale + cubic spline (2 fma + 2 mul) + accumulate = 8
+#   force pair: sqrt, 1/d, scale, dW (2 fma), dot (1 mul + 2 fma), viscosity (4),
+#     pressure sum and scale (3), 3 fma accumulations = 24
 FLOPS_TEST = 8
-FLOPS_PAIR_DENSITY = 11
-FLOPS_PAIR_FORCE = 30
+FLOPS_PAIR_DENSITY = 8
+FLOPS_PAIR_FORCE = 24
 
 
 def parse():
@@ -181,7 +184,7 @@ def run_arm(sc, mode, args, torch, rts, profile=False):
         rts.rts_profile_enable(ctx, True)
     rts.rts_profile_read(ctx, reset=True)
     tot = {"substeps": 0, "particle_evals": 0, "pair_interactions": 0, "candidate_tests": 0,
-           "active_blocks": 0, "steps": 0}
+           "tests_performed": 0, "active_blocks": 0, "steps": 0}
     ms = []
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
@@ -366,7 +369,7 @@ def main():
     with ClockSampler(local) as clk:
         ours = run_arm(sc, 0, args, torch, rts, profile=True)
     barrier()
-    glob = None if args.no_global else run_arm(sc, 1, args, torch, rts)
+    glob = None if args.no_global else run_arm(sc, 1, args, torch, rts, profile=True)
     e2e = None if args.no_e2e else run_e2e(sc, args, torch, rts)
     pcisph = None if (args.no_pcisph or args.small) else run_pcisph(args, torch, rts)
 
@@ -385,9 +388,11 @@ def main():
     peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     tests, pairs = ours["tot"]["candidate_tests"], ours["tot"]["pair_interactions"]
     kern = max(("density", "force"), key=lambda k: prof["ms"][k])
-    per_pair = FLOPS_PAIR_FORCE if kern == "force" else FLOPS_PAIR_DENSITY
     launches = max(1, prof["launches"][kern])
-    flops_per_launch = (tests * FLOPS_TEST + pairs * per_pair) / launches
+    if kern == "density":   # the neighbour search and the density sum
+        flops_per_launch = (tests * FLOPS_TEST + pairs * FLOPS_PAIR_DENSITY) / launches
+    else:                   # the force pass walks the pair list of the density pass
+        flops_per_launch = pairs * FLOPS_PAIR_FORCE / launches
     dur_s = prof["ms"][kern] / 1e3 / launches
     achieved = flops_per_launch / dur_s / 1e12 if dur_s > 0 else 0.0
     roofline = {"bound": "alu", "kernel": "k_force" if kern == "force" else "k_density",
@@ -411,6 +416,8 @@ def main():
         "pair_interactions_per_s": pairs / (total_ms / 1e3),
         "active_fraction": ours["tot"]["particle_evals"] / max(1, sc.n * subs),
         "evals_per_active_block": ours["tot"]["particle_evals"] / max(1, ours["tot"]["active_blocks"]),
+        "stencil_candidates_per_eval": tests / max(1, ours["tot"]["particle_evals"]),
+        "tests_per_eval_after_cull": ours["tot"]["tests_performed"] / max(1, ours["tot"]["particle_evals"]),
         "density_error": ours["rho_err"], "level_count": ours["levels"],
         "roofline": roofline, "clocks": clocks,
     }
@@ -421,7 +428,10 @@ def main():
             "value": gval, "ms_per_step": gms / args.steps,
             "wall_s_per_sim_s": (gms / 1e3) / (glob["tot"]["substeps"] * sc.params["dt_b"]),
             "evals_per_s": glob["tot"]["particle_evals"] / (gms / 1e3),
-            "density_error": glob["rho_err"], "steps_per_window": glob["tot"]["steps"] / args.steps}
+            "density_error": glob["rho_err"], "steps_per_window": glob["tot"]["steps"] / args.steps,
+            "phases_ms": {k: round(v, 3) for k, v in glob["prof"]["ms"].items()},
+            "evals_per_active_block": glob["tot"]["particle_evals"] / max(1, glob["tot"]["active_blocks"]),
+            "tests_per_eval_after_cull": glob["tot"]["tests_performed"] / max(1, glob["tot"]["particle_evals"])}
         line["rts_vs_global"] = value / world / gval
     if e2e is not None:
         line["e2e"] = e2e

@@ -103,7 +103,9 @@ typedef struct rts_stats {
   int64_t pair_interactions; /* neighbour pairs (d < r) of those evaluations               */
   int64_t active_blocks;     /* sum over steps of blocks with an evaluated particle        */
   int64_t level_count[8];    /* fluid particles per level at the end of the call           */
-  int64_t candidate_tests;   /* candidate pairs tested against the support radius          */
+  int64_t candidate_tests;   /* candidates in the evaluated particles' 27-block stencils   */
+  int64_t tests_performed;   /* distance tests after culling the stencil to each group's
+                                bounding box (WCSPH)                                       */
   int64_t pcisph_iterations; /* density-correction iterations                              */
   int64_t pcisph_local_iterations;
   int64_t pcisph_global_restarts;

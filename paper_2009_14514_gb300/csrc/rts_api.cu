@@ -328,10 +328,22 @@ static rts_status sync_status(rts_ctx* c) {
 
 // --------------------------------------------------------- WCSPH stepping ---
 
+// Density and forces of the evaluated particles; their Serna correction is deferred to
+// the next key pass (which reads the same flags and accelerations) or to finalize().
 static void run_physics(rts_ctx* c, int64_t k1, int prime) {
   { Phase ph(c, RTS_PHASE_DENSITY); launch_density(c); }
   { Phase ph(c, RTS_PHASE_FORCE); launch_force(c); }
-  { Phase ph(c, RTS_PHASE_CORRECT); launch_correct(c, k1, prime); }
+  c->pend_mode = prime ? kPendPrime : kPendCorrect;
+  c->pend_k1 = k1;
+}
+
+// Apply a deferred correction now (before the state is read or classified directly).
+rts_status rts::finalize(rts_ctx* c) {
+  if (c->pend_mode == kPendNone) return RTS_OK;
+  Phase ph(c, RTS_PHASE_CORRECT);
+  launch_correct(c, c->pend_k1, c->pend_mode == kPendPrime);
+  c->pend_mode = kPendNone;
+  return RTS_OK;
 }
 
 static rts_status wcsph_evaluate(rts_ctx* c) {
@@ -367,6 +379,7 @@ static int host_pick_level(const rts_ctx* c, double v2, double a2) {
 static rts_status wcsph_global(rts_ctx* c, int64_t max_mult) {
   int L = 0;
   if (c->p.mode == RTS_MODE_GLOBAL_ADAPTIVE) {
+    finalize(c);  // the step size is chosen from the corrected state
     {
       Phase ph(c, RTS_PHASE_CLASSIFY);
       launch_global_max(c);
@@ -600,6 +613,7 @@ rts_status rts_bin(rts_ctx* c) {
 
 rts_status rts_classify_blocks(rts_ctx* c) {
   GUARD();
+  finalize(c);
   if (!c->bins_valid) {
     Phase ph(c, RTS_PHASE_BIN);
     launch_bin(c, 0.0f);
@@ -620,20 +634,24 @@ rts_status rts_classify_blocks(rts_ctx* c) {
 rts_status rts_evaluate(rts_ctx* c) {
   GUARD();
   if (c->p.scheme != RTS_WCSPH) return fail(c, RTS_ERR_ARG, "rts_evaluate is the WCSPH evaluation");
-  return wcsph_evaluate(c);
+  rts_status st = wcsph_evaluate(c);
+  if (st == RTS_OK) finalize(c);
+  return st;
 }
 
 rts_status rts_wcsph_substep(rts_ctx* c) {
   GUARD();
   if (c->p.scheme != RTS_WCSPH) return fail(c, RTS_ERR_ARG, "context was created for PCISPH");
-  return wcsph_step(c, (int64_t)1 << 40);
+  rts_status st = wcsph_step(c, (int64_t)1 << 40);
+  finalize(c);
+  return st;
 }
 
 rts_status rts_advance(rts_ctx* c, double t_sim, rts_stats* out) {
   GUARD();
   if (!std::isfinite(t_sim)) return fail(c, RTS_ERR_ARG, "t_sim must be finite");
   int64_t K = llround(t_sim / (double)c->p.dt_b);
-  CK(cudaMemsetAsync(&c->ctl->evals, 0, 4 * sizeof(unsigned long long), c->stream));
+  CK(cudaMemsetAsync(&c->ctl->evals, 0, 5 * sizeof(unsigned long long), c->stream));
   int64_t k0 = c->k, steps = 0;
   int64_t it0 = c->tot_iters, lo0 = c->tot_local, rv0 = c->tot_reverts;
   rts_status nconv = RTS_OK;
@@ -648,6 +666,7 @@ rts_status rts_advance(rts_ctx* c, double t_sim, rts_stats* out) {
     if (st == RTS_ERR_NOT_CONVERGED) nconv = st;
     ++steps;
   }
+  finalize(c);
   {
     Phase ph(c, RTS_PHASE_OTHER);
     launch_level_hist(c);
@@ -661,6 +680,7 @@ rts_status rts_advance(rts_ctx* c, double t_sim, rts_stats* out) {
     out->pair_interactions = (int64_t)c->h_ctl->pairs;
     out->active_blocks = (int64_t)c->h_ctl->act_blocks;
     out->candidate_tests = (int64_t)c->h_ctl->cands;
+    out->tests_performed = (int64_t)c->h_ctl->kept;
     out->pcisph_iterations = c->tot_iters - it0;
     out->pcisph_local_iterations = c->tot_local - lo0;
     out->pcisph_global_restarts = c->tot_reverts - rv0;
@@ -674,6 +694,7 @@ rts_status rts_get_state(rts_ctx* c, float* x, float* v, float* a, float* rho, f
                          int32_t* level, int32_t* validity, int32_t* klast, int32_t* nbr,
                          uint8_t* compute) {
   if (!c) return fail(nullptr, RTS_ERR_ARG, "ctx is NULL");
+  finalize(c);
   int n = c->n;
   if (n == 0) return sync_status(c);
   int g = nblk(n);
@@ -718,6 +739,7 @@ rts_status rts_set_state(rts_ctx* c, const float* x, const float* v, const float
   if (!c) return fail(nullptr, RTS_ERR_ARG, "ctx is NULL");
   if (c->n > 0 && (!x || !v)) return fail(c, RTS_ERR_ARG, "x and v are required");
   if (k < 0) return fail(c, RTS_ERR_ARG, "k must be >= 0");
+  c->pend_mode = kPendNone;  // the new state replaces any deferred correction
   rts_status st = upload_state(c, x, v, a, rho, p, level, validity, klast);
   if (st != RTS_OK) return st;
   CK(cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream));

@@ -44,13 +44,27 @@ __device__ __forceinline__ uint32_t block_key(const DevParams& P, float4 p, int*
   return ((uint32_t)cz * P.ny + cy) * P.nx + cx;
 }
 
-// Predict (dt != 0: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt), then key and slot.
+// Deferred correction of the last step's evaluated particles (pend), then predict
+// (dt != 0: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt), then key and slot.
 __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4* __restrict__ v,
-                              const float4* __restrict__ a, float dt, uint32_t* __restrict__ key,
-                              uint32_t* __restrict__ slot, uint32_t* __restrict__ count, Ctl* ctl) {
+                              float4* __restrict__ a, float dt, uint32_t* __restrict__ key,
+                              uint32_t* __restrict__ slot, uint32_t* __restrict__ count, Ctl* ctl,
+                              int pend, int pend_k1, const uint8_t* __restrict__ cflag,
+                              const float4* __restrict__ anew, int32_t* __restrict__ klast) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 xi = x[i];
+  if (pend != kPendNone && cflag[i]) {
+    float4 vi = v[i];
+    const float4 an = anew[i];
+    if (pend == kPendCorrect) {
+      serna_correct(xi, vi, a[i], an, (float)(pend_k1 - klast[i]) * P.dt_b);
+      x[i] = xi;
+      v[i] = vi;
+    }
+    a[i] = an;
+    klast[i] = pend_k1;
+  }
   if (dt != 0.0f) {
     float4 vi = v[i];
     float4 ai = a[i];
@@ -331,7 +345,9 @@ rts_status launch_bin(rts_ctx* c, float dt) {
   note_launch(c, 6);
   next_stamp(c);
   k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, n, c->s.x, c->s.v, c->s.a, dt, c->key, c->slot,
-                                          c->count, c->ctl);
+                                          c->count, c->ctl, c->pend_mode, (int)c->pend_k1,
+                                          c->cflag, c->anew, c->s.klast);
+  c->pend_mode = kPendNone;
   scan_counts(c, c->filled);
   k_scatter<<<g, tb, 0, c->stream>>>(n, c->key, c->slot, c->s.uid, c->cstart, c->key_tmp,
                                       c->tmp_uid, c->tmp_src);
@@ -368,7 +384,8 @@ rts_status launch_bin_boundary(rts_ctx* c, const float4* xb_unsorted, int nb) {
   int tb = 256, g = (nb + tb - 1) / tb;
   k_iota<<<g, tb, 0, c->stream>>>(nb, uid);
   k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, nb, const_cast<float4*>(xb_unsorted), nullptr,
-                                          nullptr, 0.0f, key, slot, c->count, c->ctl);
+                                          nullptr, 0.0f, key, slot, c->count, c->ctl, kPendNone, 0,
+                                          nullptr, nullptr, nullptr);
   uint32_t* save = c->cstart;
   c->cstart = c->bcstart;
   scan_counts(c, nullptr);

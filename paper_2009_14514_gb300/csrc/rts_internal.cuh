@@ -49,7 +49,8 @@ struct Ctl {
   unsigned long long evals;      // evaluated particles
   unsigned long long pairs;      // neighbour pairs of evaluated particles
   unsigned long long act_blocks; // active blocks summed over steps
-  unsigned long long cands;      // candidate pairs tested
+  unsigned long long cands;      // candidates of the evaluated particles' 27-block stencils
+  unsigned long long kept;       // candidate pairs tested after the per-group cull
   int n_filled;                  // blocks holding a fluid particle (filled list length)
   unsigned long long vmax2_bits; // global max |v|^2 (FP64 bits, non-negative)
   unsigned long long amax2_bits; // global max |a|^2
@@ -78,6 +79,26 @@ struct PState {
 __device__ __forceinline__ void set_status(Ctl* ctl, int code) {
   atomicCAS(&ctl->status, 0, code);
 }
+
+// Section 4.1 correction at the end of a particle's true step of length dt:
+// x += (a_new - a_old) dt^2 / 6, v += (a_new - a_old) dt / 2 (w lanes untouched).
+// Shared by the correction kernel and the key pass that applies a deferred correction,
+// so both give the same bits.
+__device__ __forceinline__ void serna_correct(float4& x, float4& v, const float4 ao,
+                                              const float4 an, float dt) {
+  const float c1 = dt * dt / 6.0f, c2 = 0.5f * dt;
+  const float dax = an.x - ao.x, day = an.y - ao.y, daz = an.z - ao.z;
+  x.x += dax * c1;
+  x.y += day * c1;
+  x.z += daz * c1;
+  v.x += dax * c2;
+  v.y += day * c2;
+  v.z += daz * c2;
+}
+
+// A correction left pending by the last stepping call (applied by the next key pass,
+// or by the correction kernel when the state is read).
+enum PendMode { kPendNone = 0, kPendCorrect = 1, kPendPrime = 2 };
 
 // Activity kernel modes.
 enum ActMode { kActRegional = 0, kActAll = 1, kActGlobal = 2 };
@@ -131,6 +152,8 @@ struct rts_ctx {
   int32_t* io_i;      // n ints
 
   int grid_persistent;  // CTAs of the persistent neighbour kernels
+  int pend_mode;        // PendMode of the deferred correction
+  int64_t pend_k1;      // substep index the deferred correction completes
   uint32_t* nbl;        // neighbour lists of evaluated particles, nbl_cap per particle
   int nbl_cap;
   uint32_t* buid;       // boundary: caller index of each sorted boundary particle
@@ -177,6 +200,7 @@ rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g);
 rts_status launch_density(rts_ctx* c);
 rts_status launch_force(rts_ctx* c);
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime);
+rts_status finalize(rts_ctx* c);
 rts_status launch_global_max(rts_ctx* c);
 rts_status launch_level_hist(rts_ctx* c);
 const char* cuda_err(rts_ctx* c, cudaError_t e, const char* what);

@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n_act = *(volatile int*)&ctl->n_act;
-  unsigned long long pairs = 0, tests = 0;
+  unsigned long long pairs = 0, tests = 0, kept_tests = 0;
   for (int t = warp; t < n_act; t += nwarps) {
     const uint32_t b = act[t];
     const int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
@@ -440,8 +440,9 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
           }
           nn += tot;
         }
-        if (gvalid && sub == 0) tests += cn;
+        if (gvalid && sub == 0) kept_tests += cn;
       }
+      if (gvalid && sub == 0) tests += R.total;
       for (uint32_t o = lpp >> 1; o; o >>= 1) wsum += __shfl_down_sync(kFull, wsum, o, lpp);
       if (sub == 0 && gvalid) {
         if (nn > P.nbl_cap) set_status(ctl, RTS_ERR_CAPACITY);
@@ -460,9 +461,11 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
   for (int o = 16; o; o >>= 1) {
     pairs += __shfl_down_sync(kFull, pairs, o);
     tests += __shfl_down_sync(kFull, tests, o);
+    kept_tests += __shfl_down_sync(kFull, kept_tests, o);
   }
   if (lane == 0 && pairs) atomicAdd(&ctl->pairs, pairs);
   if (lane == 0 && tests) atomicAdd(&ctl->cands, tests);
+  if (lane == 0 && kept_tests) atomicAdd(&ctl->kept, kept_tests);
 }
 
 // Force pass (Algorithm 1, "update F^{p,v,g}"): every evaluated particle walks the
@@ -550,17 +553,8 @@ __global__ void k_correct(DevParams P, const uint32_t* __restrict__ act, Ctl* ct
       if (!cflag[i]) continue;
       float4 an = anew[i];
       if (!prime) {
-        float dt = (float)(k1 - s.klast[i]) * P.dt_b;
-        float4 ao = s.a[i];
-        float c1 = dt * dt / 6.0f, c2 = 0.5f * dt;
-        float dax = an.x - ao.x, day = an.y - ao.y, daz = an.z - ao.z;
         float4 x = s.x[i], v = s.v[i];
-        x.x += dax * c1;
-        x.y += day * c1;
-        x.z += daz * c1;
-        v.x += dax * c2;
-        v.y += day * c2;
-        v.z += daz * c2;
+        serna_correct(x, v, s.a[i], an, (float)(k1 - s.klast[i]) * P.dt_b);
         s.x[i] = x;
         s.v[i] = v;
       }

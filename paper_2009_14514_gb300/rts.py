@@ -58,6 +58,7 @@ class RtsStats(C.Structure):
         ("substeps", C.c_int64), ("steps", C.c_int64), ("particle_evals", C.c_int64),
         ("pair_interactions", C.c_int64), ("active_blocks", C.c_int64),
         ("level_count", C.c_int64 * 8), ("candidate_tests", C.c_int64),
+        ("tests_performed", C.c_int64),
         ("pcisph_iterations", C.c_int64),
         ("pcisph_local_iterations", C.c_int64), ("pcisph_global_restarts", C.c_int64),
         ("t_sim", C.c_double),

@@ -319,3 +319,19 @@ def test_neighbour_lists_of_evaluated_particles_equal_brute_force():
     off, idx = O.neighbors_brute(st["x"], sc.xb, O.make_params(sc.params).r)
     for i in range(sc.n):
         assert sorted(lists[i].tolist()) == sorted(idx[off[i]:off[i + 1]].tolist()), i
+
+
+def test_deferred_corrections_and_reruns_are_bit_identical():
+    # rts_advance defers each substep's Serna correction into the next key pass; single
+    # substeps apply it at once: same function, same bits.  A rerun gives the same bits.
+    sc = scenes.wcsph_dam_break_8k()
+    dt = sc.params["dt_b"]
+    a, b, c = gpu_ctx(sc), gpu_ctx(sc), gpu_ctx(sc)
+    rts.rts_advance(a, 24 * dt)
+    rts.rts_advance(c, 24 * dt)
+    for _ in range(24):
+        rts.rts_wcsph_substep(b)
+    ga, gb, gc = rts.rts_get_state(a), rts.rts_get_state(b), rts.rts_get_state(c)
+    for f in ("x", "v", "a", "rho", "p", "klast", "validity", "level", "nbr"):
+        assert np.array_equal(ga[f], gb[f]), f
+        assert np.array_equal(ga[f], gc[f]), f
