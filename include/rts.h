@@ -47,7 +47,9 @@ typedef enum rts_status {
                                  exceeded max_neighbors                                  */
   RTS_ERR_NOT_CONVERGED = 6,  /* PCISPH: a minor step hit max_iters (state is advanced)  */
   RTS_ERR_TIMEOUT = 7,        /* a bounded device wait gave up                           */
-  RTS_ERR_STATE = 8           /* an earlier device error is pending; call rts_set_state  */
+  RTS_ERR_STATE = 8,          /* an earlier device error is pending; call rts_set_state  */
+  RTS_ERR_INTERNAL = 9        /* a device-side consistency check failed (an index read from
+                                 memory was out of range; the access was skipped)          */
 } rts_status;
 
 enum { RTS_WCSPH = 0, RTS_PCISPH = 1 };
@@ -92,6 +94,12 @@ typedef struct rts_params {
   int32_t sched[4][8];       /* correction iterations of region n in minor step j          */
   int32_t refresh[8];        /* neighbourhood validity of region n, in minor steps         */
   int32_t max_neighbors;     /* PCISPH neighbour list capacity per particle                */
+  /* Container (the paper gives no boundary handling beyond static boundary particles):
+     with wall_project = 1 a fluid particle that crosses a face of the box
+     [wall_lo, wall_hi] after a position update is put back on that face and loses its
+     velocity component into it (non-penetration); 0: off.                            */
+  int32_t wall_project;
+  float wall_lo[3], wall_hi[3];
 } rts_params;
 
 /* Counters accumulated over one rts_advance call. */

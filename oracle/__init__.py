@@ -47,6 +47,9 @@ class OrcParams(C.Structure):
         ("r1_rings", C.c_int32), ("clean_majors", C.c_int32), ("short_minor", C.c_int32),
         ("sched", (C.c_int32 * 8) * 4), ("refresh", C.c_int32 * 8),
         ("max_neighbors", C.c_int32),
+        ("wall_project", C.c_int32),
+        ("wall_lo", C.c_double * 3),
+        ("wall_hi", C.c_double * 3),
     ]
 
 
@@ -91,6 +94,10 @@ def make_params(d: dict) -> OrcParams:
     for L in range(len(d["refresh"])):
         P.refresh[L] = int(d["refresh"][L])
     P.max_neighbors = int(d["max_neighbors"])
+    P.wall_project = int(d.get("wall_project", 0))
+    for k in range(3):
+        P.wall_lo[k] = _f32(d.get("wall_lo", [0.0] * 3)[k])
+        P.wall_hi[k] = _f32(d.get("wall_hi", [0.0] * 3)[k])
     return P
 
 

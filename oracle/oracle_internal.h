@@ -28,4 +28,5 @@ void orci_grid_free(ogrid* G);
 int orci_nbr_list(const orc_params* P, const ogrid* G, int32_t n, const double* x,
                   const double* xb, int32_t i, const int c[3], int rings, double r2,
                   int32_t* out, int cap);
+void orci_wall_project(const orc_params* P, double* x3, double* v3);
 #endif

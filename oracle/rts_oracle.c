@@ -498,13 +498,35 @@ static void serna_correct(double* x, double* v, double* a, const double* anew, d
   }
 }
 
-/* Section 4.1 predictor: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt (all particles). */
-static void serna_predict(int32_t n, double* x, double* v, const double* a, double dt) {
+/* Container walls.  The paper's static boundary particles come with no force law; the
+ * particles exert -m p_i/rho_i^2 grad W, which a fast particle can overcome, so a
+ * position update is followed by the non-penetration correction of particle-based
+ * boundary handling: a coordinate beyond a face of the box is set to the face and the
+ * velocity component into the face is dropped (tangential motion is kept). */
+void orci_wall_project(const orc_params* P, double* x3, double* v3) {
+  if (!P->wall_project) return;
+  for (int k = 0; k < 3; ++k) {
+    if (x3[k] < P->wall_lo[k]) {
+      x3[k] = P->wall_lo[k];
+      if (v3[k] < 0.0) v3[k] = 0.0;
+    }
+    if (x3[k] > P->wall_hi[k]) {
+      x3[k] = P->wall_hi[k];
+      if (v3[k] > 0.0) v3[k] = 0.0;
+    }
+  }
+}
+
+/* Section 4.1 predictor: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt (all particles),
+ * then the container correction. */
+static void serna_predict(const orc_params* P, int32_t n, double* x, double* v, const double* a,
+                          double dt) {
 #pragma omp parallel for schedule(static)
   for (int64_t q = 0; q < 3 * (int64_t)n; ++q) {
     x[q] = x[q] + v[q] * dt + a[q] * dt * dt / 2.0;
     v[q] = v[q] + a[q] * dt;
   }
+  for (int32_t i = 0; i < n; ++i) orci_wall_project(P, x + 3 * (int64_t)i, v + 3 * (int64_t)i);
 }
 
 static int32_t particle_block_level(const orc_params* P, const orc_wstate* S, int32_t i) {
@@ -546,7 +568,7 @@ int orc_wcsph_substep(const orc_params* P, orc_wstate* S) {
   if (!S->primed && (st = orc_wcsph_evaluate(P, S))) return st;
   int32_t n = S->n;
   int64_t k1 = S->k + 1;
-  serna_predict(n, S->x, S->v, S->a, P->dt_b);
+  serna_predict(P, n, S->x, S->v, S->a, P->dt_b);
   st = orc_classify_wcsph(P, n, S->x, S->v, S->a, NULL, S->block_level);
   if (st) return st;
   for (int32_t i = 0; i < n; ++i) {
@@ -600,7 +622,7 @@ int orc_wcsph_global_step(const orc_params* P, orc_wstate* S, int32_t max_mult,
   if (m > max_mult) m = max_mult;
   if (m < 1) m = 1;
   int64_t k1 = S->k + m;
-  serna_predict(n, S->x, S->v, S->a, (double)m * P->dt_b);
+  serna_predict(P, n, S->x, S->v, S->a, (double)m * P->dt_b);
   for (int32_t i = 0; i < n; ++i) {
     S->compute[i] = 1;
     S->level[i] = L;

@@ -53,6 +53,10 @@ typedef struct orc_params {
   int32_t sched[4][8];     /* correction iterations per region per minor step */
   int32_t refresh[8];      /* neighbourhood validity per region, minor steps */
   int32_t max_neighbors;
+  /* Container box: with wall_project = 1 a particle beyond a face after a position
+   * update is put back on the face and its velocity component into it is dropped. */
+  int32_t wall_project;
+  double wall_lo[3], wall_hi[3];
 } orc_params;
 
 /* WCSPH state in user order. */

@@ -419,11 +419,13 @@ int orc_pcisph_step(const orc_params* P, orc_pstate* S) {
   }
   int cst = density_correction(P, S, j);
   /* integrate: v += dt (a_np + a_p), x += dt v */
-  for (int32_t i = 0; i < n; ++i)
+  for (int32_t i = 0; i < n; ++i) {
     for (int k = 0; k < 3; ++k) {
       S->v[3 * i + k] += P->dt_b * (S->anp[3 * i + k] + S->ap[3 * i + k]);
       S->x[3 * i + k] += P->dt_b * S->v[3 * i + k];
     }
+    orci_wall_project(P, S->x + 3 * i, S->v + 3 * i);
+  }
   if (S->global_iters > P->max_global_iters) S->shorten_now = 1;
   int last = (j + 1 >= S->n_minor_cur) || S->shorten_now;
   for (int32_t i = 0; i < n; ++i) {
@@ -511,11 +513,13 @@ int orc_pcisph_plain_step(const orc_params* P, orc_pstate* S) {
     }
   }
   free(xs);
-  for (int32_t i = 0; i < n; ++i)
+  for (int32_t i = 0; i < n; ++i) {
     for (int k = 0; k < 3; ++k) {
       S->v[3 * i + k] += dt * (S->anp[3 * i + k] + S->ap[3 * i + k]);
       S->x[3 * i + k] += dt * S->v[3 * i + k];
     }
+    orci_wall_project(P, S->x + 3 * i, S->v + 3 * i);
+  }
   S->iters = it;
   S->k += 1;
   return status;

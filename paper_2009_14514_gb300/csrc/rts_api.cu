@@ -82,6 +82,10 @@ static const char* validate(const rts_params* p, int32_t n, int32_t nb) {
   if (!(p->dt_b > 0.f)) return "dt_b must be positive";
   if (p->max_per_block < 1 || p->max_per_block > 1024) return "max_per_block must be in [1, 1024]";
   if (p->max_neighbors < 8 || p->max_neighbors > 1024) return "max_neighbors must be in [8, 1024]";
+  if (p->wall_project != 0 && p->wall_project != 1) return "wall_project must be 0 or 1";
+  if (p->wall_project)
+    for (int k = 0; k < 3; ++k)
+      if (!(p->wall_lo[k] < p->wall_hi[k])) return "wall_lo must be below wall_hi on every axis";
   if (!(p->rho0 > 0.f) || !(p->c_s > 0.f) || !(p->gamma > 0.f) || !(p->visc_alpha >= 0.f))
     return "rho0, c_s, gamma must be positive and visc_alpha non-negative";
   if (!(p->lambda_f > 0.f) || !(p->alpha > 0.f) || !(p->lambda_v > 0.f)) return "lambda_v, lambda_f, alpha must be positive";
@@ -132,6 +136,11 @@ static void make_dev_params(const rts_params& p, DevParams& d) {
   d.gx = p.gravity[0];
   d.gy = p.gravity[1];
   d.gz = p.gravity[2];
+  d.wall_project = p.wall_project;
+  for (int k = 0; k < 3; ++k) {
+    d.wlo[k] = p.wall_lo[k];
+    d.whi[k] = p.wall_hi[k];
+  }
   d.n_levels = p.n_levels;
   for (int L = 0; L < p.n_levels; ++L) d.mult[L] = p.level_mult[L];
   level_thresholds(p, d.vthr2, d.athr2, d.eq1);
@@ -244,10 +253,14 @@ __global__ void k_finish_in(int n, PState s) {
 }
 
 __global__ void k_out_vec(int n, const uint32_t* __restrict__ uid, const float4* __restrict__ in,
-                          float* __restrict__ out) {
+                          float* __restrict__ out, Ctl* ctl) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     uint32_t u = uid[i];
+    if (u >= (uint32_t)n) {
+      check_failed(ctl, kChkUid, u);
+      return;
+    }
     float4 q = in[i];
     out[3 * u] = q.x;
     out[3 * u + 1] = q.y;
@@ -257,9 +270,15 @@ __global__ void k_out_vec(int n, const uint32_t* __restrict__ uid, const float4*
 
 template <class T>
 __global__ void k_out_scalar(int n, const uint32_t* __restrict__ uid, const T* __restrict__ in,
-                             T* __restrict__ out) {
+                             T* __restrict__ out, Ctl* ctl) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[uid[i]] = in[i];
+  if (i >= n) return;
+  const uint32_t u = uid[i];
+  if (u >= (uint32_t)n) {
+    check_failed(ctl, kChkUid, u);
+    return;
+  }
+  out[u] = in[i];
 }
 
 static inline int nblk(int n) { return (n + 255) / 256; }
@@ -319,8 +338,17 @@ static rts_status sync_status(rts_ctx* c) {
     const char* what = st == RTS_ERR_DOMAIN     ? "a particle left the block grid (or is NaN)"
                        : st == RTS_ERR_CAPACITY ? "a block or neighbour list exceeded its capacity"
                        : st == RTS_ERR_TIMEOUT  ? "a bounded device wait gave up"
+                       : st == RTS_ERR_INTERNAL ? "a device-side consistency check failed"
                                                 : "device error";
-    snprintf(c->err, sizeof c->err, "device status %d: %s", st, what);
+    const Ctl* h = c->h_ctl;
+    if (st == RTS_ERR_DOMAIN && h->bad_set)
+      snprintf(c->err, sizeof c->err, "device status %d: %s (particle %u at %g %g %g)", st, what,
+               h->bad_uid, (double)h->bad_x, (double)h->bad_y, (double)h->bad_z);
+    else if (st == RTS_ERR_INTERNAL)
+      snprintf(c->err, sizeof c->err, "device status %d: %s (check %d, value %u)", st, what,
+               h->chk_code, h->chk_val);
+    else
+      snprintf(c->err, sizeof c->err, "device status %d: %s", st, what);
     return (rts_status)st;
   }
   return (rts_status)st;
@@ -429,6 +457,8 @@ rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, c
   memset(c, 0, sizeof(*c));
   c->p = *params;
   make_dev_params(c->p, c->dp);
+  c->dp.n_fluid = n_fluid;
+  c->dp.n_bound = n_boundary;
   c->stream = (cudaStream_t)cuda_stream;
   c->n = n_fluid;
   c->nb = n_boundary;
@@ -707,25 +737,25 @@ rts_status rts_get_state(rts_ctx* c, float* x, float* v, float* a, float* rho, f
   float* vdst[3] = {x, v, a};
   for (int k = 0; k < 3; ++k) {
     if (!vdst[k]) continue;
-    k_out_vec<<<g, 256, 0, c->stream>>>(n, c->s.uid, vecs[k], c->io);
+    k_out_vec<<<g, 256, 0, c->stream>>>(n, c->s.uid, vecs[k], c->io, c->ctl);
     CK(cudaMemcpyAsync(vdst[k], c->io, v3, cudaMemcpyDefault, c->stream));
   }
   const float* fs[2] = {c->s.rho, c->s.prs};
   float* fdst[2] = {rho, p};
   for (int k = 0; k < 2; ++k) {
     if (!fdst[k]) continue;
-    k_out_scalar<float><<<g, 256, 0, c->stream>>>(n, c->s.uid, fs[k], c->io);
+    k_out_scalar<float><<<g, 256, 0, c->stream>>>(n, c->s.uid, fs[k], c->io, c->ctl);
     CK(cudaMemcpyAsync(fdst[k], c->io, s1, cudaMemcpyDefault, c->stream));
   }
   const int32_t* is[4] = {c->s.level, c->s.valid, c->s.klast, c->s.nbr};
   int32_t* idst[4] = {level, validity, klast, nbr};
   for (int k = 0; k < 4; ++k) {
     if (!idst[k]) continue;
-    k_out_scalar<int32_t><<<g, 256, 0, c->stream>>>(n, c->s.uid, is[k], c->io_i);
+    k_out_scalar<int32_t><<<g, 256, 0, c->stream>>>(n, c->s.uid, is[k], c->io_i, c->ctl);
     CK(cudaMemcpyAsync(idst[k], c->io_i, s1, cudaMemcpyDefault, c->stream));
   }
   if (compute) {
-    k_out_scalar<uint8_t><<<g, 256, 0, c->stream>>>(n, c->s.uid, c->cflag, (uint8_t*)c->io_i);
+    k_out_scalar<uint8_t><<<g, 256, 0, c->stream>>>(n, c->s.uid, c->cflag, (uint8_t*)c->io_i, c->ctl);
     CK(cudaMemcpyAsync(compute, c->io_i, (size_t)n, cudaMemcpyDefault, c->stream));
   }
   CK(cudaGetLastError());
@@ -863,17 +893,17 @@ rts_status rts_get_pcisph_state(rts_ctx* c, float* ap, float* err, uint8_t* in_s
   Phase ph(c, RTS_PHASE_OTHER);
   if (ap) {
     note_launch(c, 1);
-    k_out_vec<<<g, 256, 0, c->stream>>>(n, c->s.uid, c->s.ap, c->io);
+    k_out_vec<<<g, 256, 0, c->stream>>>(n, c->s.uid, c->s.ap, c->io, c->ctl);
     CK(cudaMemcpyAsync(ap, c->io, sizeof(float) * 3 * (size_t)n, cudaMemcpyDefault, c->stream));
   }
   if (err) {
     note_launch(c, 1);
-    k_out_scalar<float><<<g, 256, 0, c->stream>>>(n, c->s.uid, c->s.err, c->io);
+    k_out_scalar<float><<<g, 256, 0, c->stream>>>(n, c->s.uid, c->s.err, c->io, c->ctl);
     CK(cudaMemcpyAsync(err, c->io, sizeof(float) * (size_t)n, cudaMemcpyDefault, c->stream));
   }
   if (in_se) {
     note_launch(c, 1);
-    k_out_scalar<uint8_t><<<g, 256, 0, c->stream>>>(n, c->s.uid, c->in_se, (uint8_t*)c->io_i);
+    k_out_scalar<uint8_t><<<g, 256, 0, c->stream>>>(n, c->s.uid, c->in_se, (uint8_t*)c->io_i, c->ctl);
     CK(cudaMemcpyAsync(in_se, c->io_i, (size_t)n, cudaMemcpyDefault, c->stream));
   }
   CK(cudaGetLastError());
@@ -894,13 +924,17 @@ rts_status rts_get_neighbors(rts_ctx* c, int32_t* counts, int32_t* idx, int32_t 
   CK(cudaMemcpy(lists.data(), c->nbl, sizeof(uint32_t) * lists.size(), cudaMemcpyDeviceToHost));
   std::vector<int32_t> out(idx ? (size_t)n * cap : 0, -1);
   for (int f = 0; f < n; ++f) {
+    if (uid[f] >= (uint32_t)n) return fail(c, RTS_ERR_INTERNAL, "rts_get_neighbors: caller index out of range");
     int u = (int)uid[f];
     int k = cnt[f] < c->nbl_cap ? cnt[f] : c->nbl_cap;
+    if (k < 0) k = 0;
     ocnt[u] = k;
     if (!idx) continue;
     if (k > cap) return fail(c, RTS_ERR_CAPACITY, "rts_get_neighbors: cap smaller than a list");
     for (int e = 0; e < k; ++e) {
       uint32_t j = lists[(size_t)f * c->nbl_cap + e];
+      if ((j & 0x80000000u) ? (j & 0x7fffffffu) >= (uint32_t)nb : j >= (uint32_t)n)
+        return fail(c, RTS_ERR_INTERNAL, "rts_get_neighbors: neighbour index out of range");
       out[(size_t)u * cap + e] = (j & 0x80000000u) ? n + (int32_t)buid[j & 0x7fffffffu]
                                                    : (int32_t)uid[j];
     }

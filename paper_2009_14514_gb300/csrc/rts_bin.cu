@@ -50,7 +50,8 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
                               float4* __restrict__ a, float dt, uint32_t* __restrict__ key,
                               uint32_t* __restrict__ slot, uint32_t* __restrict__ count, Ctl* ctl,
                               int pend, int pend_k1, const uint8_t* __restrict__ cflag,
-                              const float4* __restrict__ anew, int32_t* __restrict__ klast) {
+                              const float4* __restrict__ anew, int32_t* __restrict__ klast,
+                              const uint32_t* __restrict__ uid) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 xi = x[i];
@@ -75,12 +76,19 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
     vi.x = vi.x + ai.x * dt;
     vi.y = vi.y + ai.y * dt;
     vi.z = vi.z + ai.z * dt;
+    if (P.wall_project) wall_project(P, xi, vi);
     x[i] = xi;
     v[i] = vi;
   }
   int bad = 0;
   uint32_t b = block_key(P, xi, &bad);
   if (bad) {
+    if (atomicCAS(&ctl->bad_set, 0, 1) == 0) {
+      ctl->bad_uid = uid[i];
+      ctl->bad_x = xi.x;
+      ctl->bad_y = xi.y;
+      ctl->bad_z = xi.z;
+    }
     set_status(ctl, RTS_ERR_DOMAIN);
     b = 0;
   }
@@ -108,9 +116,11 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   return v;
 }
 
-// Exclusive scan of one value per thread across the CTA; returns the CTA total.
+// Exclusive scan of one value per thread across the CTA (up to 32 warps); returns the
+// CTA total.  The warp offsets and the total live in separate slots: with 32 warps the
+// last warp's offset and the total would otherwise share one.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
-  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t warp_tot[33];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t inc = warp_incl_scan(v);
   if (lane == 31) warp_tot[w] = inc;
@@ -119,11 +129,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
     uint32_t t = lane < nw ? warp_tot[lane] : 0u;
     uint32_t ti = warp_incl_scan(t);
     if (lane < nw) warp_tot[lane] = ti - t;
-    if (lane == nw - 1) warp_tot[31] = ti;
+    if (lane == nw - 1) warp_tot[32] = ti;
   }
   __syncthreads();
   uint32_t res = inc - v + warp_tot[w];
-  *total = warp_tot[31];
+  *total = warp_tot[32];
   __syncthreads();
   return res;
 }
@@ -224,14 +234,22 @@ __global__ void k_scan_apply(uint32_t* __restrict__ count, int nb, const uint32_
   }
 }
 
-__global__ void k_scatter(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ slot,
-                          const uint32_t* __restrict__ uid, const uint32_t* __restrict__ cstart,
-                          uint32_t* __restrict__ tkey, uint32_t* __restrict__ tuid,
-                          uint32_t* __restrict__ tsrc) {
+__global__ void k_scatter(int n, int nb, const uint32_t* __restrict__ key,
+                          const uint32_t* __restrict__ slot, const uint32_t* __restrict__ uid,
+                          const uint32_t* __restrict__ cstart, uint32_t* __restrict__ tkey,
+                          uint32_t* __restrict__ tuid, uint32_t* __restrict__ tsrc, Ctl* ctl) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t b = key[i];
+  if (b >= (uint32_t)nb) {
+    check_failed(ctl, kChkScatter, b);
+    return;
+  }
   uint32_t q = cstart[b] + slot[i];
+  if (q >= (uint32_t)n || q >= cstart[b + 1]) {
+    check_failed(ctl, kChkScatter, q);
+    return;
+  }
   tkey[q] = b;
   tuid[q] = uid[i];
   tsrc[q] = (uint32_t)i;
@@ -257,7 +275,7 @@ __device__ __forceinline__ void block_max_merge(uint32_t b, bool valid, float va
 
 // Order each block's particles by caller index and move every field to its place; the
 // fluid pass also merges |v|^2 and |a|^2 into the block maxima (Section 3.1 step 2).
-__global__ void k_canon_gather(int n, int max_per_block, const uint32_t* __restrict__ cstart,
+__global__ void k_canon_gather(int n, int nb, int max_per_block, const uint32_t* __restrict__ cstart,
                                const uint32_t* __restrict__ tkey, const uint32_t* __restrict__ tuid,
                                const uint32_t* __restrict__ tsrc, PState src, PState dst,
                                uint32_t* __restrict__ key_out, Ctl* ctl, uint32_t stamp,
@@ -284,6 +302,10 @@ __global__ void k_canon_gather(int n, int max_per_block, const uint32_t* __restr
   }
   if (!valid) return;
   uint32_t b = tkey[q];
+  if (b >= (uint32_t)nb) {
+    check_failed(ctl, kChkGather, b);
+    return;
+  }
   uint32_t beg = cstart[b], end = cstart[b + 1];
   if (q == (int)beg && (int)(end - beg) > max_per_block) set_status(ctl, RTS_ERR_CAPACITY);
   uint32_t u = tuid[q];
@@ -291,6 +313,10 @@ __global__ void k_canon_gather(int n, int max_per_block, const uint32_t* __restr
   for (uint32_t r = beg; r < end; ++r) rank += (tuid[r] < u) ? 1u : 0u;
   uint32_t f = beg + rank;
   uint32_t s = tsrc[q];
+  if (s >= (uint32_t)n || f >= end) {
+    check_failed(ctl, kChkGather, s);
+    return;
+  }
   key_out[f] = b;
   dst.uid[f] = u;
   dst.x[f] = src.x[s];
@@ -346,12 +372,12 @@ rts_status launch_bin(rts_ctx* c, float dt) {
   next_stamp(c);
   k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, n, c->s.x, c->s.v, c->s.a, dt, c->key, c->slot,
                                           c->count, c->ctl, c->pend_mode, (int)c->pend_k1,
-                                          c->cflag, c->anew, c->s.klast);
+                                          c->cflag, c->anew, c->s.klast, c->s.uid);
   c->pend_mode = kPendNone;
   scan_counts(c, c->filled);
-  k_scatter<<<g, tb, 0, c->stream>>>(n, c->key, c->slot, c->s.uid, c->cstart, c->key_tmp,
-                                      c->tmp_uid, c->tmp_src);
-  k_canon_gather<<<g, tb, 0, c->stream>>>(n, c->dp.max_per_block, c->cstart, c->key_tmp,
+  k_scatter<<<g, tb, 0, c->stream>>>(n, c->dp.nblocks, c->key, c->slot, c->s.uid, c->cstart,
+                                      c->key_tmp, c->tmp_uid, c->tmp_src, c->ctl);
+  k_canon_gather<<<g, tb, 0, c->stream>>>(n, c->dp.nblocks, c->dp.max_per_block, c->cstart, c->key_tmp,
                                            c->tmp_uid, c->tmp_src, c->s, c->s2, c->key, c->ctl,
                                            c->stamp, c->bmax_v, c->bmax_a);
   PState t = c->s;
@@ -385,19 +411,20 @@ rts_status launch_bin_boundary(rts_ctx* c, const float4* xb_unsorted, int nb) {
   k_iota<<<g, tb, 0, c->stream>>>(nb, uid);
   k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, nb, const_cast<float4*>(xb_unsorted), nullptr,
                                           nullptr, 0.0f, key, slot, c->count, c->ctl, kPendNone, 0,
-                                          nullptr, nullptr, nullptr);
+                                          nullptr, nullptr, nullptr, uid);
   uint32_t* save = c->cstart;
   c->cstart = c->bcstart;
   scan_counts(c, nullptr);
   c->cstart = save;
-  k_scatter<<<g, tb, 0, c->stream>>>(nb, key, slot, uid, c->bcstart, tkey, tuid, tsrc);
+  k_scatter<<<g, tb, 0, c->stream>>>(nb, c->dp.nblocks, key, slot, uid, c->bcstart, tkey, tuid,
+                                      tsrc, c->ctl);
   PState src{}, dst{};
   src.x = const_cast<float4*>(xb_unsorted);
   src.uid = uid;
   dst.x = c->xb;
   dst.uid = uid2;
-  k_canon_gather<<<g, tb, 0, c->stream>>>(nb, 1 << 30, c->bcstart, tkey, tuid, tsrc, src, dst, key,
-                                           c->ctl, 0u, nullptr, nullptr);
+  k_canon_gather<<<g, tb, 0, c->stream>>>(nb, c->dp.nblocks, 1 << 30, c->bcstart, tkey, tuid, tsrc,
+                                           src, dst, key, c->ctl, 0u, nullptr, nullptr);
   cudaMemcpyAsync(c->buid, uid2, sz, cudaMemcpyDeviceToDevice, c->stream);
   e = cudaStreamSynchronize(c->stream);
   for (auto b : bufs) cudaFree(*b);

@@ -90,8 +90,9 @@ __device__ __forceinline__ uint32_t warp_scan(uint32_t v) {
   return v;
 }
 
+// The total has its own slot: with 32 warps it would overwrite the last warp's offset.
 __device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t* total) {
-  __shared__ uint32_t wt[32];
+  __shared__ uint32_t wt[33];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t inc = warp_scan(v);
   if (lane == 31) wt[w] = inc;
@@ -100,11 +101,11 @@ __device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t* total) {
     uint32_t t = lane < nw ? wt[lane] : 0u;
     uint32_t ti = warp_scan(t);
     if (lane < nw) wt[lane] = ti - t;
-    if (lane == nw - 1) wt[31] = ti;
+    if (lane == nw - 1) wt[32] = ti;
   }
   __syncthreads();
   uint32_t r = inc - v + wt[w];
-  *total = wt[31];
+  *total = wt[32];
   __syncthreads();
   return r;
 }

@@ -27,7 +27,10 @@ struct DevParams {
   float visc_coef;   // 2 alpha h c_s
   float eps_h2;      // 0.01 h^2
   float gx, gy, gz;
+  int wall_project;        // non-penetration projection onto the container box
+  float wlo[3], whi[3];
   int nbl_cap;       // neighbour list capacity per particle
+  int n_fluid, n_bound;  // particle counts (bounds of the consistency checks)
   // PCISPH (Section 5)
   float eta, delta, visc_nu;   // tolerance, pressure scaling, alpha h c / rho0
   int r1_rings, expand_layers, n_minor;
@@ -57,6 +60,18 @@ struct Ctl {
   unsigned long long level_count[kMaxLevels];
   unsigned int err_max_bits;      // PCISPH: max relative error (FP32 bits)
   unsigned long long err_sum_fx;  // PCISPH: sum of relative errors, fixed point 2^-32
+  int chk_code;                   // first failed consistency check (CheckCode), 0 = none
+  unsigned int chk_val;           // the offending value
+  int bad_set;                    // a particle left the grid: its caller index and position
+  unsigned int bad_uid;
+  float bad_x, bad_y, bad_z;
+};
+
+// Device-side consistency checks: an index read from memory is tested before it is
+// used; a failure records its code and value, sets RTS_ERR_INTERNAL and skips the access.
+enum CheckCode {
+  kChkNone = 0, kChkNeighbour = 1, kChkRun = 2, kChkGather = 3, kChkScatter = 4,
+  kChkLevel = 5, kChkUid = 6, kChkActive = 7
 };
 
 // Particle state in block-sorted order.  x.w = p / rho^2 and v.w = rho of the last
@@ -80,6 +95,11 @@ __device__ __forceinline__ void set_status(Ctl* ctl, int code) {
   atomicCAS(&ctl->status, 0, code);
 }
 
+static __device__ __noinline__ void check_failed(Ctl* ctl, int code, unsigned int val) {
+  if (atomicCAS(&ctl->chk_code, 0, code) == 0) ctl->chk_val = val;
+  set_status(ctl, 9 /* RTS_ERR_INTERNAL */);
+}
+
 // Section 4.1 correction at the end of a particle's true step of length dt:
 // x += (a_new - a_old) dt^2 / 6, v += (a_new - a_old) dt / 2 (w lanes untouched).
 // Shared by the correction kernel and the key pass that applies a deferred correction,
@@ -99,6 +119,17 @@ __device__ __forceinline__ void serna_correct(float4& x, float4& v, const float4
 // A correction left pending by the last stepping call (applied by the next key pass,
 // or by the correction kernel when the state is read).
 enum PendMode { kPendNone = 0, kPendCorrect = 1, kPendPrime = 2 };
+
+// Non-penetration of the container box: a particle beyond a face is put back on it and
+// the velocity component into that face is removed.
+__device__ __forceinline__ void wall_project(const DevParams& P, float4& x, float4& v) {
+  if (x.x < P.wlo[0]) { x.x = P.wlo[0]; v.x = fmaxf(v.x, 0.f); }
+  if (x.x > P.whi[0]) { x.x = P.whi[0]; v.x = fminf(v.x, 0.f); }
+  if (x.y < P.wlo[1]) { x.y = P.wlo[1]; v.y = fmaxf(v.y, 0.f); }
+  if (x.y > P.whi[1]) { x.y = P.whi[1]; v.y = fminf(v.y, 0.f); }
+  if (x.z < P.wlo[2]) { x.z = P.wlo[2]; v.z = fmaxf(v.z, 0.f); }
+  if (x.z > P.whi[2]) { x.z = P.whi[2]; v.z = fminf(v.z, 0.f); }
+}
 
 // Activity kernel modes.
 enum ActMode { kActRegional = 0, kActAll = 1, kActGlobal = 2 };

@@ -348,6 +348,7 @@ __global__ void k_integrate(DevParams P, int n, PState s) {
   x.x += dt * v.x;
   x.y += dt * v.y;
   x.z += dt * v.z;
+  if (P.wall_project) wall_project(P, x, v);
   s.x[i] = x;
   s.v[i] = v;
 }

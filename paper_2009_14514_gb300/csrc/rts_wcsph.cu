@@ -127,6 +127,10 @@ __global__ void k_block_activity(DevParams P, int mode, int level_g, int mult_g,
           if (mode == kActRegional) {
             int val = s.valid[i] - 1;
             int li = s.level[i];
+            if (li >= P.n_levels) {
+              check_failed(ctl, kChkLevel, (unsigned)li);
+              li = -1;
+            }
             if (val <= 0 || li < 0 || P.mult[li] != mb) {
               c = 1;
               s.level[i] = L;
@@ -291,7 +295,7 @@ __device__ __forceinline__ uint32_t stage_culled(const DevParams& P, const uint3
                                                  uint32_t total, float3 lo, float3 hi,
                                                  uint32_t skip, const float4* __restrict__ xf,
                                                  const float4* __restrict__ xbnd, float4* sx,
-                                                 uint32_t* sidx, int lane) {
+                                                 uint32_t* sidx, int lane, Ctl* ctl) {
   const float cut2 = P.r2_hi * 1.0001f;
   const unsigned below = (1u << lane) - 1u;
   uint32_t kept = 0;
@@ -305,12 +309,16 @@ __device__ __forceinline__ uint32_t stage_culled(const DevParams& P, const uint3
     if (k < total) {
       while (k >= tab[3 * r + 2] + tab[3 * r + 1]) ++r;
       const uint32_t g = tab[3 * r] + (k - tab[3 * r + 2]);
-      xj = r < 9 ? xf[g] : xbnd[g];
-      tag = r < 9 ? g : (g | kBoundaryBit);
-      const float ex = fmaxf(fmaxf(lo.x - xj.x, xj.x - hi.x), 0.f);
-      const float ey = fmaxf(fmaxf(lo.y - xj.y, xj.y - hi.y), 0.f);
-      const float ez = fmaxf(fmaxf(lo.z - xj.z, xj.z - hi.z), 0.f);
-      keep = ex * ex + ey * ey + ez * ez <= cut2;
+      if (r < 18 && g < (uint32_t)(r < 9 ? P.n_fluid : P.n_bound)) {
+        xj = r < 9 ? xf[g] : xbnd[g];
+        tag = r < 9 ? g : (g | kBoundaryBit);
+        const float ex = fmaxf(fmaxf(lo.x - xj.x, xj.x - hi.x), 0.f);
+        const float ey = fmaxf(fmaxf(lo.y - xj.y, xj.y - hi.y), 0.f);
+        const float ez = fmaxf(fmaxf(lo.z - xj.z, xj.z - hi.z), 0.f);
+        keep = ex * ex + ey * ey + ez * ez <= cut2;
+      } else {
+        check_failed(ctl, kChkRun, g);
+      }
     }
     const unsigned m = __ballot_sync(kFull, keep);
     const uint32_t pos = kept + (uint32_t)__popc(m & below);
@@ -349,6 +357,10 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
   unsigned long long pairs = 0, tests = 0, kept_tests = 0;
   for (int t = warp; t < n_act; t += nwarps) {
     const uint32_t b = act[t];
+    if (b >= (uint32_t)P.nblocks) {
+      if (lane == 0) check_failed(ctl, kChkActive, b);
+      continue;
+    }
     const int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
     const uint32_t beg = cstart[b], end = cstart[b + 1];
     const Runs R = block_runs(P, bx, by, bz, cstart, bcstart, lane);
@@ -389,7 +401,7 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
       uint32_t kept_total = 1;
       for (uint32_t skip = 0; skip < kept_total; skip += kCap) {
         __syncwarp();
-        kept_total = stage_culled(P, tab, R.total, lo, hi, skip, s.x, xb, sx, sidx, lane);
+        kept_total = stage_culled(P, tab, R.total, lo, hi, skip, s.x, xb, sx, sidx, lane, ctl);
         if (kept_total <= skip) break;
         const uint32_t cn = kept_total - skip < (uint32_t)kCap ? kept_total - skip : (uint32_t)kCap;
         const uint32_t iters = (cn + lpp - 1) / lpp;  // uniform over the warp
@@ -486,6 +498,10 @@ __global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_
   const float4* __restrict__ vf = s.v;
   for (int t = warp; t < n_act; t += nwarps) {
     const uint32_t b = act[t];
+    if (b >= (uint32_t)P.nblocks) {
+      if (lane == 0) check_failed(ctl, kChkActive, b);
+      continue;
+    }
     const uint32_t beg = cstart[b], end = cstart[b + 1];
     for (uint32_t base = beg; base < end; base += 32) {
       Group G;
@@ -501,7 +517,12 @@ __global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_
           const uint32_t jg = __ldg(&list[e]);
           float4 xj, vj;
           float pcj;
-          if (jg & kBoundaryBit) {
+          const bool bnd = (jg & kBoundaryBit) != 0;
+          if (bnd ? (jg & ~kBoundaryBit) >= (uint32_t)P.n_bound : jg >= (uint32_t)P.n_fluid) {
+            check_failed(ctl, kChkNeighbour, jg);
+            continue;
+          }
+          if (bnd) {
             xj = __ldg(&xb[jg & ~kBoundaryBit]);
             vj = make_float4(0.f, 0.f, 0.f, vi.w);
             pcj = 0.f;
@@ -548,6 +569,10 @@ __global__ void k_correct(DevParams P, const uint32_t* __restrict__ act, Ctl* ct
   const int n_act = *(volatile int*)&ctl->n_act;
   for (int t = warp; t < n_act; t += nwarps) {
     const uint32_t b = act[t];
+    if (b >= (uint32_t)P.nblocks) {
+      if (lane == 0) check_failed(ctl, kChkActive, b);
+      continue;
+    }
     const uint32_t beg = cstart[b], end = cstart[b + 1];
     for (uint32_t i = beg + lane; i < end; i += 32) {
       if (!cflag[i]) continue;

@@ -17,7 +17,7 @@ from . import build as _build
 RTS_OK = 0
 STATUS_NAMES = {
     0: "RTS_OK", 1: "RTS_ERR_ARG", 2: "RTS_ERR_DOMAIN", 3: "RTS_ERR_CUDA", 4: "RTS_ERR_OOM",
-    5: "RTS_ERR_CAPACITY", 6: "RTS_ERR_NOT_CONVERGED", 7: "RTS_ERR_TIMEOUT", 8: "RTS_ERR_STATE",
+    5: "RTS_ERR_CAPACITY", 6: "RTS_ERR_NOT_CONVERGED", 7: "RTS_ERR_TIMEOUT", 8: "RTS_ERR_STATE", 9: "RTS_ERR_INTERNAL",
 }
 EXPORTED = [
     "rts_init", "rts_bin", "rts_classify_blocks", "rts_evaluate", "rts_wcsph_substep",
@@ -50,6 +50,9 @@ class RtsParams(C.Structure):
         ("clean_majors", C.c_int32), ("short_minor", C.c_int32),
         ("sched", (C.c_int32 * 8) * 4), ("refresh", C.c_int32 * 8),
         ("max_neighbors", C.c_int32),
+        ("wall_project", C.c_int32),
+        ("wall_lo", C.c_float * 3),
+        ("wall_hi", C.c_float * 3),
     ]
 
 
@@ -119,6 +122,10 @@ def make_params(d: dict) -> RtsParams:
             P.sched[n][j] = int(d["sched"][n][j])
     for L in range(len(d["refresh"])):
         P.refresh[L] = int(d["refresh"][L])
+    P.wall_project = int(d.get("wall_project", 0))
+    for k in range(3):
+        P.wall_lo[k] = d.get("wall_lo", [0.0] * 3)[k]
+        P.wall_hi[k] = d.get("wall_hi", [0.0] * 3)[k]
     return P
 
 

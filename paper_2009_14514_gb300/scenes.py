@@ -16,7 +16,8 @@ for them at the paper's scales (about 1M particles, spacing s = 0.01 m):
 Fluid particles sit on the lattice points (i + 1/2) s of the box.  Static boundary
 particles continue that lattice through every wall, face, edge and corner, in
 ``layers`` layers outside the box (Section 6 uses static boundary particles; the
-paper does not give their layout).
+paper does not give their layout).  The box is also passed as the container
+(``wall_project``): a fluid particle that crosses a face is put back on it.
 """
 from __future__ import annotations
 
@@ -105,6 +106,7 @@ def wcsph_params(s, box, dt_b, *, support_factor=2.0):
         clean_majors=10, short_minor=2,
         sched=[[3, 3, 3, 3], [2, 1, 2, 1], [2, 1, 1, 1], [2, 1, 1, 1]],
         refresh=[1, 2, 4, 4], max_neighbors=96,
+        wall_project=1, wall_lo=[0.0, 0.0, 0.0], wall_hi=[float(L) for L in box],
     )
 
 
@@ -133,6 +135,7 @@ def pcisph_params(s, box, dt_b):
         clean_majors=10, short_minor=2,
         sched=[[3, 3, 3, 3], [2, 1, 2, 1], [2, 1, 1, 1], [2, 1, 1, 1]],
         refresh=[1, 2, 4, 4], max_neighbors=96,
+        wall_project=1, wall_lo=[0.0, 0.0, 0.0], wall_hi=[float(L) for L in box],
     )
 
 

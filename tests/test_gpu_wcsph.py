@@ -335,3 +335,54 @@ def test_deferred_corrections_and_reruns_are_bit_identical():
     for f in ("x", "v", "a", "rho", "p", "klast", "validity", "level", "nbr"):
         assert np.array_equal(ga[f], gb[f]), f
         assert np.array_equal(ga[f], gc[f]), f
+
+
+def test_bins_and_lists_on_a_grid_of_more_than_a_thousand_scan_tiles():
+    # The 1M dam-break grid has 202 x 102 x 102 = 2.1M blocks, 1027 scan tiles of 2048
+    # blocks: the scan of the tile sums then spans all 32 warps of its CTA.  Bins over the
+    # whole grid (the top layers included) and the neighbour lists of particles under the
+    # ceiling, boundary neighbours included, against the oracle.
+    sc = scenes.wcsph_dam_break_1m()
+    P = O.make_params(sc.params)
+    rng = np.random.default_rng(21)
+    cloud = rng.uniform([0.0, 0.0, 0.0], [4.0, 2.0, 2.0], (100000, 3))
+    slab = scenes.lattice((50, 50, 10), 0.01, offset=(0.0, 0.0, 1.9))
+    x = np.concatenate([cloud, slab]).astype(np.float32)
+    ctx = rts.rts_init(sc.params, x, np.zeros_like(x), sc.xb)
+    rts.rts_bin(ctx)
+    key, perm, cstart = rts.rts_get_bins(ctx)
+    okey, operm, ocstart = O.bin_particles(P, x)
+    assert np.array_equal(key, okey)
+    assert np.array_equal(perm, operm)
+    assert np.array_equal(cstart, ocstart)
+    rts.rts_evaluate(ctx)
+    lists = rts.rts_get_neighbors(ctx)
+    off, idx = O.neighbors_grid(P, x, sc.xb)
+    top = np.nonzero(x[:, 2] > 1.95)[0]
+    assert len(top) > 10000
+    for i in top[::17]:
+        assert sorted(lists[i].tolist()) == sorted(idx[off[i]:off[i + 1]].tolist()), i
+    assert max(off[i + 1] - off[i] for i in top) > 20
+
+
+def test_container_projection_matches_oracle():
+    # the bottom layer is thrown into the floor at 200 m/s: one constant global step
+    # predicts it 1 cm below the floor face; both sides put it back on the face, drop the
+    # downward velocity and then evaluate and correct it against the same walls
+    sc = scenes.wcsph_dam_break_8k()
+    d = params(sc, mode=2)
+    v = sc.v.copy()
+    bottom = sc.x[:, 2] < 0.015
+    v[bottom, 2] = -200.0
+    ctx = gpu_ctx(sc, d, v=v)
+    o = oracle_state(sc, d, {"x": sc.x, "v": v})
+    rts.rts_wcsph_substep(ctx)
+    o.global_step()
+    g = rts.rts_get_state(ctx, ("x", "v", "a"))
+    assert bottom.sum() == 400
+    # corrected heights: within the correction's reach of the face, far above -1 cm
+    assert np.abs(o.x[bottom, 2]).max() < 2e-3 and np.abs(g["x"][bottom, 2]).max() < 2e-3
+    tol_a = ACC_FRAC * max_norm(o.a)
+    dt = d["dt_b"]
+    assert np.abs(g["x"] - o.x).max() <= tol_a * dt * dt + 2e-6
+    assert np.abs(g["v"] - o.v).max() <= tol_a * dt + 1e-4

@@ -304,6 +304,53 @@ def test_isolated_particle_falls_exactly_under_gravity():
     np.testing.assert_allclose(S.v[0, 2], P.g[2] * T, rtol=1e-12)
 
 
+def _lone_particle(x0, v0, **over):
+    # one particle, no boundary particles: only gravity and the container act on it
+    sc = scenes.dam_break((1, 1, 1), 0.02, (0.4, 0.4, 0.4), 1e-4)
+    P = _params(sc, mode=2, **over)
+    return P, O.WCSPH(P, np.array([x0]), np.array([v0]), np.zeros((0, 3)))
+
+
+def test_container_lands_a_falling_particle_on_the_floor_and_keeps_its_glide():
+    # thrown along x from 5 cm: after landing it sits exactly on the floor face with no
+    # vertical velocity, and slides on at the unchanged 0.5 m/s
+    P, S = _lone_particle([0.05, 0.2, 0.05], [0.5, 0.0, 0.0])
+    n = 1500
+    for _ in range(n):
+        S.global_step()
+    T = n * P.dt_b
+    assert T > math.sqrt(2 * 0.05 / 9.81) + 0.02
+    assert S.x[0, 2] == 0.0 and S.v[0, 2] == 0.0
+    assert S.v[0, 0] == 0.5 and S.x[0, 1] == 0.2
+    assert abs(S.x[0, 0] - (0.05 + 0.5 * T)) < 1e-12
+
+
+def test_container_drops_only_the_velocity_into_the_face():
+    # thrown up into the ceiling: held on it for the contact step with v_z = 0, then it
+    # falls freely from rest (gravity is not cancelled, outward motion is allowed)
+    P, S = _lone_particle([0.2, 0.2, 0.3], [0.0, 0.0, 3.0])
+    top = P.wall_hi[2]
+    for _ in range(800):
+        S.global_step()
+        if S.x[0, 2] == top:
+            break
+    assert S.x[0, 2] == top and S.v[0, 2] == 0.0
+    for _ in range(100):
+        S.global_step()
+    T = 100 * P.dt_b
+    np.testing.assert_allclose(S.x[0, 2], top + 0.5 * P.g[2] * T * T, rtol=1e-13)
+    np.testing.assert_allclose(S.v[0, 2], P.g[2] * T, rtol=1e-12)
+
+
+def test_without_the_container_the_particle_passes_the_floor():
+    P, S = _lone_particle([0.2, 0.2, 0.01], [0.0, 0.0, 0.0], wall_project=0)
+    for _ in range(600):
+        S.global_step()
+    T = 600 * P.dt_b
+    np.testing.assert_allclose(S.x[0, 2], 0.01 + 0.5 * P.g[2] * T * T, rtol=1e-12)
+    assert S.x[0, 2] < 0.0
+
+
 def test_forced_finest_rts_reproduces_global_stepping_exactly():
     sc = scenes.wcsph_dam_break_8k()
     Pr = _params(sc, force_level=0)
