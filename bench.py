@@ -2,16 +2,20 @@
 """Benchmark of regional time stepping (RTS) WCSPH on one GB300: particle-substeps/s.
 
 Workload: the 1M-particle dam break (100^3 column, s = 0.01 m, 4 x 2 x 2 m tank,
-dt_b = 5e-5 s, levels dt_b * {1, 2, 4, 8}), advanced from t = 0 to a dynamic state
-(--preroll, untimed), then timed.  One step = one window of 8 dt_b (a full cycle of
-the coarsest level) of simulated time, advanced through the library's public call
-rts_advance.  value = fluid particles x base substeps / device seconds.
+dt_b = 5e-5 s, levels dt_b * {1, 2, 4, 8}) simulated for 2 s from t = 0.  One step =
+0.1 s of simulated time (2000 base substeps) advanced through the library's public call
+rts_advance; the default 20 steps are the whole rollout.  value = fluid particles x base
+substeps / device seconds (CUDA events on the library's stream, a 256 MB buffer written
+between steps).  W warm-up steps run the start of the same rollout on a throwaway
+context first.
 
 Also measured, on the same GPU in the same run: the global adaptive comparator (every
 particle active, one step of the finest level that the time-step criteria give for the
-whole fluid), the end-to-end rate through the C ABI with host buffers (state uploaded
-from and returned to pinned host memory every step), the FP32-ALU roofline of the
-dominant neighbour kernel, SM clocks, and the CPU oracle on a bounded sample.
+whole fluid) over the same 2 s, the global constant-dt_b arm over the first steps, the
+end-to-end rate through the C ABI with host buffers (state uploaded from and returned to
+pinned host memory every step), the PCISPH pool drop (RTS, global adaptive, constant
+1.66e-4 s), the FP32-ALU roofline of the dominant neighbour kernel, SM clocks, and the
+CPU oracle on a bounded sample.
 
 --impl reference times the FP64 CPU oracle (the reference arm: the paper ships no code).
 """
@@ -45,17 +49,19 @@ FLOPS_PAIR_FORCE = 24
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20, help="timed steps (default: the 2 s rollout)")
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--step-sim", type=float, default=0.1, help="simulated seconds per step")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--preroll", type=float, default=0.3, help="simulated seconds before timing")
-    ap.add_argument("--window", type=int, default=8, help="base substeps per step")
-    ap.add_argument("--no-global", action="store_true", help="skip the global comparator")
+    ap.add_argument("--constant-steps", type=int, default=5,
+                    help="steps of the constant-dt_b arm (compared with the same steps of RTS)")
+    ap.add_argument("--no-global", action="store_true", help="skip the global comparators")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="8k-particle dam break (quick check)")
     ap.add_argument("--no-pcisph", action="store_true", help="skip the PCISPH pool-drop section")
-    ap.add_argument("--pcisph-preroll", type=float, default=0.2)
+    ap.add_argument("--pcisph-sim", type=float, default=1.0, help="simulated seconds of PCISPH")
+    ap.add_argument("--window", type=int, default=8, help="base substeps per --profile-case step")
     ap.add_argument("--profile-case", action="store_true",
                     help="short run for ncu: 1M jittered lattice with a seeded dynamic state, "
                          "primed, then --steps windows (few launches, nothing printed but a line)")
@@ -91,9 +97,10 @@ def workload(small):
 
 
 def workload_name(sc, args):
+    sim = args.steps * args.step_sim
     return (f"{sc.name}: {sc.n} fluid + {sc.nb} boundary particles, WCSPH regional time "
             f"stepping, levels dt_b*{sc.params['level_mult']}, dt_b={sc.params['dt_b']}, "
-            f"step = {args.window} dt_b from t={args.preroll}s")
+            f"{sim:g} s simulated from t=0 in steps of {args.step_sim:g} s")
 
 
 class ClockSampler:
@@ -161,133 +168,158 @@ def measured_peaks():
         return {}
 
 
-def density_error(rho, rho0=1000.0):
+def density_error(rho, nbr=None, rho0=1000.0):
+    """|rho - rho0| / rho0 over the fluid: mean, 99th percentile, max, and the mean over
+    particles with at least 20 neighbours (the bulk, without isolated spray)."""
     import numpy as np
     e = np.abs(rho.astype(np.float64) / rho0 - 1.0)
-    return {"mean": float(e.mean()), "p99": float(np.percentile(e, 99)), "max": float(e.max())}
+    out = {"mean": float(e.mean()), "p99": float(np.percentile(e, 99)), "max": float(e.max())}
+    if nbr is not None:
+        bulk = nbr >= 20
+        out["bulk_mean"] = float(e[bulk].mean()) if bulk.any() else 0.0
+    return out
 
 
-def run_arm(sc, mode, args, torch, rts, profile=False):
-    """Pre-roll, warm up and time one stepping mode; returns timing and counters."""
+COUNTERS = ("substeps", "steps", "particle_evals", "pair_interactions", "candidate_tests",
+            "tests_performed", "active_blocks", "pcisph_iterations", "pcisph_local_iterations")
+
+
+def run_rollout(sc, over, nsteps, args, torch, rts, profile=False, flush=None, name="rts"):
+    """Advance a fresh context from t = 0 by nsteps steps of args.step_sim simulated
+    seconds through rts_advance; each step is timed with CUDA events on the library's
+    stream (a 256 MB buffer is written between steps, outside the events).  After each
+    step the density error is read back, outside the timed region."""
+    import numpy as np
     d = dict(sc.params)
-    d["mode"] = mode
+    d.update(over)
     ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
     dtb = d["dt_b"]
-    rts.rts_advance(ctx, args.preroll)
-    k = ctx.substep_index
-    for _ in range(args.warmup):
-        k += args.window
-        rts.rts_advance(ctx, k * dtb)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    stream = torch.cuda.current_stream()
+    per = int(round(args.step_sim / dtb))
     if profile:
         rts.rts_profile_enable(ctx, True)
-    rts.rts_profile_read(ctx, reset=True)
-    tot = {"substeps": 0, "particle_evals": 0, "pair_interactions": 0, "candidate_tests": 0,
-           "tests_performed": 0, "active_blocks": 0, "steps": 0}
-    ms = []
+        rts.rts_profile_read(ctx, reset=True)
+    stream = torch.cuda.current_stream()
+    tot = {f: 0 for f in COUNTERS}
+    ms, errs = [], []
+    k = 0
+    st = None
     torch.cuda.synchronize()
-    t_wall = time.perf_counter()
-    torch.cuda.nvtx.range_push(f"timed_mode{mode}")   # ncu --nvtx-include timed_mode0/
-    for _ in range(args.steps):
-        flush.zero_()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        k += args.window
-        s0.record(stream)
+    torch.cuda.nvtx.range_push(name)          # ncu --nvtx-include <name>/
+    for _ in range(nsteps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        k += per
+        e0.record(stream)
         st = rts.rts_advance(ctx, k * dtb)
-        s1.record(stream)
-        s1.synchronize()
-        ms.append(s0.elapsed_time(s1))
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
         for f in tot:
             tot[f] += st[f]
+        g = rts.rts_get_state(ctx, ("rho", "nbr"))
+        errs.append(density_error(g["rho"], g["nbr"], d["rho0"]))
     torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t_wall
-    prof = rts.rts_profile_read(ctx, reset=True)
-    g = rts.rts_get_state(ctx, ("rho", "level"))
-    last = st
+    prof = rts.rts_profile_read(ctx, reset=True) if profile else None
     ctx.close()
-    del flush
-    return {"ms": ms, "wall": wall, "tot": tot, "prof": prof,
-            "rho_err": density_error(g["rho"], d["rho0"]), "levels": last["level_count"][:4]}
+    err = {key: float(np.mean([e[key] for e in errs])) for key in errs[0]} if errs else {}
+    return {"ms": ms, "tot": tot, "prof": prof, "err_time_avg": err,
+            "err_final": errs[-1] if errs else {}, "levels": st["level_count"][:4] if st else [],
+            "sim_s": k * dtb}
 
 
-def run_pcisph(args, torch, rts):
-    """The 1M pool + cube drop (PCISPH): regional time stepping against the global
-    adaptive comparator and the paper's constant 1.66e-4 s step, each advanced from t = 0
-    to --pcisph-preroll and then timed over the same simulated time (args.steps major
-    steps of 4 dt_b).  Values are fluid particles x (simulated time / dt_b) per second
-    with the regional dt_b = 3.5e-4 s for every arm."""
+def arm_summary(sc, r, dt_norm):
+    """value = fluid particles x (simulated time / dt_b of the regional arm) / seconds."""
+    sec = sum(r["ms"]) / 1e3
+    out = {"value": sc.n * (r["sim_s"] / dt_norm) / sec, "seconds": sec, "sim_s": r["sim_s"],
+           "wall_s_per_sim_s": sec / r["sim_s"], "steps_advanced": r["tot"]["steps"],
+           "particle_evals": r["tot"]["particle_evals"],
+           "evals_per_s": r["tot"]["particle_evals"] / sec,
+           "density_error_time_avg": r["err_time_avg"], "density_error_final": r["err_final"]}
+    if r["prof"] is not None:
+        out["phases_ms"] = {k: round(v, 1) for k, v in r["prof"]["ms"].items()}
+    return out
+
+
+def run_pcisph(args, torch, rts, flush):
+    """The 1M pool + cube drop (PCISPH) from t = 0: regional time stepping and the global
+    adaptive comparator over args.pcisph_sim seconds, the paper's constant 1.66e-4 s step
+    over the first 0.2 s (compared with the same span of the regional arm).  Values are
+    fluid particles x (simulated time / 3.5e-4 s) per second for every arm."""
+    import numpy as np
     from paper_2009_14514_gb300 import scenes
     sc = scenes.pcisph_drop_1m()
     dtb = sc.params["dt_b"]
-    window = 4 * dtb * args.steps
-    out = {"workload": f"{sc.name}: {sc.n} fluid + {sc.nb} boundary, window {window:.4f} s "
-                       f"from t={args.pcisph_preroll}s"}
     stream = torch.cuda.current_stream()
-    for arm, over in (("rts", {}), ("global_adaptive", {"mode": 1}),
-                      ("constant_dt", {"mode": 2, "dt_b": 1.66e-4})):
+    out = {"workload": f"{sc.name}: {sc.n} fluid + {sc.nb} boundary, {args.pcisph_sim:g} s "
+                       f"from t=0 (constant-dt arm: first 0.2 s)"}
+    chunk = 0.1
+    for arm, over, sim in (("rts", {}, args.pcisph_sim),
+                           ("global_adaptive", {"mode": 1}, args.pcisph_sim),
+                           ("constant_dt", {"mode": 2, "dt_b": 1.66e-4}, 0.2)):
         d = dict(sc.params)
         d.update(over)
         ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
-        rts.rts_advance(ctx, args.pcisph_preroll)
-        t0 = ctx.substep_index * d["dt_b"]
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = rts.rts_advance(ctx, t0 + window)
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        sim = st["substeps"] * d["dt_b"]
-        err = rts.rts_get_pcisph_state(ctx)["err"]
-        out[arm] = {"value": sc.n * (sim / dtb) / (ms / 1e3), "ms": ms, "sim_s": sim,
-                    "wall_s_per_sim_s": (ms / 1e3) / sim, "steps": st["steps"],
-                    "iterations": st["pcisph_iterations"],
-                    "local_iterations": st["pcisph_local_iterations"],
-                    "err_mean": float(err.mean()), "err_max": float(err.max()),
-                    "level_count": st["level_count"][:4]}
+        ms, its, steps, t = [], 0, 0, 0.0
+        errs = []
+        for _ in range(int(round(sim / chunk))):
+            flush.zero_()
+            t += chunk
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = rts.rts_advance(ctx, t)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            its += st["pcisph_iterations"]
+            steps += st["steps"]
+            errs.append(float(rts.rts_get_pcisph_state(ctx)["err"].mean()))
+        sec = sum(ms) / 1e3
+        simd = ctx.substep_index * d["dt_b"]
+        out[arm] = {"value": sc.n * (simd / dtb) / sec, "seconds": sec, "sim_s": simd,
+                    "wall_s_per_sim_s": sec / simd, "steps": steps, "iterations": its,
+                    "err_mean_time_avg": float(np.mean(errs)), "ms_per_chunk": [round(m, 1) for m in ms]}
         ctx.close()
+    first = sum(out["rts"]["ms_per_chunk"][:2]) / 1e3
     out["rts_vs_global"] = out["rts"]["value"] / out["global_adaptive"]["value"]
-    out["rts_vs_constant"] = out["rts"]["value"] / out["constant_dt"]["value"]
+    out["rts_vs_constant_first_0.2s"] = out["constant_dt"]["seconds"] / first
     return out
 
 
 def run_e2e(sc, args, torch, rts):
-    """Every step: upload the full state from pinned host memory (rts_set_state), advance
-    one window, copy the full state back to pinned host memory (rts_get_state)."""
-    import numpy as np
+    """End to end through the C ABI: every step uploads the full state from pinned host
+    memory (rts_set_state), advances one step, and copies the full state back to pinned
+    host memory (rts_get_state); host clock around the three calls."""
     n = sc.n
-    ctx = rts.rts_init(sc.params, sc.x, sc.v, sc.xb)
-    dtb = sc.params["dt_b"]
-    rts.rts_advance(ctx, args.preroll)
-    k = ctx.substep_index
+    d = dict(sc.params)
+    ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
+    dtb = d["dt_b"]
+    per = int(round(args.step_sim / dtb))
     pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True)
     H = {"x": pin((n, 3), torch.float32), "v": pin((n, 3), torch.float32),
          "a": pin((n, 3), torch.float32), "rho": pin((n,), torch.float32),
          "p": pin((n,), torch.float32), "level": pin((n,), torch.int32),
          "validity": pin((n,), torch.int32), "klast": pin((n,), torch.int32)}
-    rts.rts_get_state_into(ctx, **H)
+    rts.rts_get_state_into(ctx, **H)     # the initial state (unprimed)
     nbytes = sum(t.numel() * t.element_size() for t in H.values())
     times = []
-    for it in range(args.warmup + args.steps):
+    k = 0
+    for it in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rts.rts_set_state(ctx, H["x"], H["v"], a=H["a"], rho=H["rho"], p=H["p"], level=H["level"],
-                          validity=H["validity"], klast=H["klast"], k=k, primed=True)
-        k += args.window
+                          validity=H["validity"], klast=H["klast"], k=k, primed=it > 0)
+        k += per
         rts.rts_advance(ctx, k * dtb)
         rts.rts_get_state_into(ctx, **H)
-        t1 = time.perf_counter()
-        if it >= args.warmup:
-            times.append(t1 - t0)
+        times.append(time.perf_counter() - t0)
     ctx.close()
     total = sum(times)
-    return {"value": n * args.window * len(times) / total, "unit": "particle-substeps/s",
+    return {"value": n * per * len(times) / total, "unit": "particle-substeps/s",
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-            "ms_per_step": 1e3 * total / len(times)}
+            "ms_per_step": 1e3 * total / len(times), "steps": len(times)}
 
 
 def cpu_oracle(sc, budget_s=12.0, max_substeps=64):
@@ -328,7 +360,7 @@ def reference_arm(args):
     dt = time.perf_counter() - t0
     value = sc.n * args.steps / dt
     line = {
-        "impl": "reference", "metric": "particle-substeps/s (regional time stepping, WCSPH)",
+        "impl": "reference", "metric": "particle-substeps/s (regional time stepping, WCSPH, 1M particles)",
         "value": value, "unit": "particle-substeps/s", "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -359,20 +391,21 @@ def main():
     from paper_2009_14514_gb300 import rts
     rts.lib()
     sc = workload(args.small)
+    dtb = sc.params["dt_b"]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    if args.warmup > 0:   # untimed: the first steps of the same rollout on a throwaway context
+        run_rollout(sc, {}, args.warmup, args, torch, rts, flush=flush, name="warmup")
     barrier()
     with ClockSampler(local) as clk:
-        ours = run_arm(sc, 0, args, torch, rts, profile=True)
+        ours = run_rollout(sc, {}, args.steps, args, torch, rts, profile=True, flush=flush,
+                           name="timed_rts")
     barrier()
-    glob = None if args.no_global else run_arm(sc, 1, args, torch, rts, profile=True)
-    e2e = None if args.no_e2e else run_e2e(sc, args, torch, rts)
-    pcisph = None if (args.no_pcisph or args.small) else run_pcisph(args, torch, rts)
-
     total_ms = sum(ours["ms"])
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
@@ -380,6 +413,16 @@ def main():
         total_ms = float(t.item())
     subs = ours["tot"]["substeps"]
     value = world * sc.n * subs / (total_ms / 1e3)
+
+    glob = const = None
+    if not args.no_global:
+        glob = run_rollout(sc, {"mode": 1}, args.steps, args, torch, rts, profile=True,
+                           flush=flush, name="timed_global")
+        nc = min(args.constant_steps, args.steps)
+        const = run_rollout(sc, {"mode": 2}, nc, args, torch, rts, flush=flush,
+                            name="timed_constant")
+    e2e = None if args.no_e2e else run_e2e(sc, args, torch, rts)
+    pcisph = None if (args.no_pcisph or args.small) else run_pcisph(args, torch, rts, flush)
 
     # roofline of the dominant neighbour kernel (FP32 ALU bound)
     prof = ours["prof"]
@@ -401,38 +444,36 @@ def main():
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived)",
                 "avg_launch_us": dur_s * 1e6, "launches": launches}
 
-    clocks = clk.summary()
+    sim = ours["sim_s"]
+    tot = ours["tot"]
     line = {
         "metric": "particle-substeps/s (regional time stepping, WCSPH, 1M particles)",
         "value": value, "unit": "particle-substeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(sc, args), "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "256 MB buffer written between timed steps", "window_substeps": args.window},
-        "wall_s_per_sim_s": (total_ms / 1e3) / (args.steps * args.window * sc.params["dt_b"]),
+        "config": {"workload": workload_name(sc, args),
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "256 MB buffer written between timed steps; state 0.3 GB > L2",
+                   "step_substeps": int(round(args.step_sim / dtb))},
+        "wall_s_per_sim_s": (total_ms / 1e3) / sim,
         "gpu_launches": int(prof["kernels"]),
-        "phases_ms": {k: round(v, 3) for k, v in prof["ms"].items()},
-        "evals_per_s": ours["tot"]["particle_evals"] / (total_ms / 1e3),
+        "phases_ms": {k: round(v, 1) for k, v in prof["ms"].items()},
+        "evals_per_s": tot["particle_evals"] / (total_ms / 1e3),
         "pair_interactions_per_s": pairs / (total_ms / 1e3),
-        "active_fraction": ours["tot"]["particle_evals"] / max(1, sc.n * subs),
-        "evals_per_active_block": ours["tot"]["particle_evals"] / max(1, ours["tot"]["active_blocks"]),
-        "stencil_candidates_per_eval": tests / max(1, ours["tot"]["particle_evals"]),
-        "tests_per_eval_after_cull": ours["tot"]["tests_performed"] / max(1, ours["tot"]["particle_evals"]),
-        "density_error": ours["rho_err"], "level_count": ours["levels"],
-        "roofline": roofline, "clocks": clocks,
+        "active_fraction": tot["particle_evals"] / max(1, sc.n * subs),
+        "evals_per_active_block": tot["particle_evals"] / max(1, tot["active_blocks"]),
+        "stencil_candidates_per_eval": tests / max(1, tot["particle_evals"]),
+        "tests_per_eval_after_cull": tot["tests_performed"] / max(1, tot["particle_evals"]),
+        "density_error_time_avg": ours["err_time_avg"], "level_count_final": ours["levels"],
+        "ms_per_step_list": [round(m, 1) for m in ours["ms"]],
+        "roofline": roofline, "clocks": clk.summary(),
     }
     if glob is not None:
-        gms = sum(glob["ms"])
-        gval = sc.n * glob["tot"]["substeps"] / (gms / 1e3)
-        line["global_adaptive"] = {
-            "value": gval, "ms_per_step": gms / args.steps,
-            "wall_s_per_sim_s": (gms / 1e3) / (glob["tot"]["substeps"] * sc.params["dt_b"]),
-            "evals_per_s": glob["tot"]["particle_evals"] / (gms / 1e3),
-            "density_error": glob["rho_err"], "steps_per_window": glob["tot"]["steps"] / args.steps,
-            "phases_ms": {k: round(v, 3) for k, v in glob["prof"]["ms"].items()},
-            "evals_per_active_block": glob["tot"]["particle_evals"] / max(1, glob["tot"]["active_blocks"]),
-            "tests_per_eval_after_cull": glob["tot"]["tests_performed"] / max(1, glob["tot"]["particle_evals"])}
-        line["rts_vs_global"] = value / world / gval
+        line["global_adaptive"] = arm_summary(sc, glob, dtb)
+        line["rts_vs_global"] = (value / world) / line["global_adaptive"]["value"]
+        line["global_constant_dt_b"] = arm_summary(sc, const, dtb)
+        nc = len(const["ms"])
+        line["rts_vs_constant_same_span"] = sum(const["ms"]) / sum(ours["ms"][:nc])
     if e2e is not None:
         line["e2e"] = e2e
     if pcisph is not None:

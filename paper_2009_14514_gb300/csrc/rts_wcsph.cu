@@ -641,14 +641,19 @@ static size_t density_smem() {
   return (size_t)(kNbThreads / 32) * (kCap * (sizeof(float4) + sizeof(uint32_t)) + 64 * sizeof(uint32_t));
 }
 
+// Persistent grids: every resident slot of every SM, per kernel (the force and
+// correction passes hold fewer registers and no shared memory, so more warps fit).
+static int g_grid_force = 0;
 int neighbor_grid_size() {
   int occ0 = 1, occ1 = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_density, kNbThreads, density_smem());
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_force, kNbThreads, 0);
-  int occ = occ0 < occ1 ? occ0 : occ1;
-  if (occ < 1) occ = 1;
-  return sm_count() * occ;
+  if (occ0 < 1) occ0 = 1;
+  if (occ1 < 1) occ1 = 1;
+  g_grid_force = sm_count() * occ1;
+  return sm_count() * occ0;
 }
+static int force_grid(const rts_ctx* c) { return g_grid_force > 0 ? g_grid_force : c->grid_persistent; }
 
 static int filled_grid() { return sm_count() * 8; }
 int filled_grid_size() { return filled_grid(); }
@@ -680,14 +685,14 @@ rts_status launch_density(rts_ctx* c) {
 
 rts_status launch_force(rts_ctx* c) {
   note_launch(c, 1);
-  k_force<<<c->grid_persistent, kNbThreads, 0, c->stream>>>(
+  k_force<<<force_grid(c), kNbThreads, 0, c->stream>>>(
       c->dp, c->act, c->ctl, c->cstart, c->s, c->xb, c->cflag, c->nbl, c->anew);
   return RTS_OK;
 }
 
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime) {
   note_launch(c, 1);
-  k_correct<<<c->grid_persistent, kNbThreads, 0, c->stream>>>(c->dp, c->act, c->ctl, c->cstart,
+  k_correct<<<force_grid(c), kNbThreads, 0, c->stream>>>(c->dp, c->act, c->ctl, c->cstart,
                                                               c->s, c->cflag, c->anew, (int)k1,
                                                               prime);
   return RTS_OK;
