@@ -195,8 +195,8 @@ def run_rollout(sc, over, nsteps, args, torch, rts, profile=False, flush=None, n
     ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
     dtb = d["dt_b"]
     per = int(round(args.step_sim / dtb))
-    if profile:
-        rts.rts_profile_enable(ctx, True)
+    if profile:   # events around the density and force passes only (roofline)
+        rts.rts_profile_enable(ctx, 2)
         rts.rts_profile_read(ctx, reset=True)
     stream = torch.cuda.current_stream()
     tot = {f: 0 for f in COUNTERS}
@@ -238,8 +238,16 @@ def arm_summary(sc, r, dt_norm):
            "evals_per_s": r["tot"]["particle_evals"] / sec,
            "density_error_time_avg": r["err_time_avg"], "density_error_final": r["err_final"]}
     if r["prof"] is not None:
-        out["phases_ms"] = {k: round(v, 1) for k, v in r["prof"]["ms"].items()}
+        out["phases_ms"] = phase_split(r["prof"], sum(r["ms"]))
     return out
+
+
+def phase_split(prof, total_ms):
+    """Density and force passes timed by events inside the run; the rest (binning,
+    classification, activity, launch gaps) is the remainder of the step time."""
+    dens, force = prof["ms"]["density"], prof["ms"]["force"]
+    return {"density": round(dens, 1), "force": round(force, 1),
+            "bin_classify_activity_rest": round(total_ms - dens - force, 1)}
 
 
 def run_pcisph(args, torch, rts, flush):
@@ -457,7 +465,7 @@ def main():
                    "step_substeps": int(round(args.step_sim / dtb))},
         "wall_s_per_sim_s": (total_ms / 1e3) / sim,
         "gpu_launches": int(prof["kernels"]),
-        "phases_ms": {k: round(v, 1) for k, v in prof["ms"].items()},
+        "phases_ms": phase_split(prof, total_ms),
         "evals_per_s": tot["particle_evals"] / (total_ms / 1e3),
         "pair_interactions_per_s": pairs / (total_ms / 1e3),
         "active_fraction": tot["particle_evals"] / max(1, sc.n * subs),

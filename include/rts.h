@@ -209,7 +209,9 @@ typedef struct rts_profile {
   int64_t kernels;                   /* all kernel launches of this library                */
 } rts_profile;
 
-/* Switch per-phase event timing on (1) or off (0).  Launch counts are always kept. */
+/* Per-phase event timing: 0 off, 1 every phase, 2 only the density and force passes
+ * (two event pairs per substep: the lightest way to time the neighbour kernels inside a
+ * long run).  Launch counts are always kept.  RTS_ERR_ARG for other values. */
 rts_status rts_profile_enable(rts_ctx* ctx, int32_t on);
 
 /* Read the accumulated profile (synchronises); reset != 0 clears it afterwards. */

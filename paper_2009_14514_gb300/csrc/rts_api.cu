@@ -187,15 +187,31 @@ static void make_dev_params(const rts_params& p, DevParams& d) {
 // ------------------------------------------------------------- profiling ---
 
 // Accumulate the timed event pairs into prof_ms (synchronises the stream).
-static void prof_flush(rts_ctx* c) {
-  if (!c->ev || c->nev == 0) return;
-  cudaStreamSynchronize(c->stream);
-  for (int k = 0; k < c->nev; ++k) {
+// Accumulate the first `upto` event pairs and move the rest to the front.  Only the
+// last of those pairs is waited for; with upto = half the pool it is hundreds of phases
+// old, so the stream keeps running.
+static void prof_collect(rts_ctx* c, int upto) {
+  if (!c->ev || upto <= 0) return;
+  cudaEventSynchronize(c->ev[2 * (upto - 1) + 1]);
+  for (int k = 0; k < upto; ++k) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]) == cudaSuccess)
       c->prof_ms[c->ev_phase[k]] += ms;
   }
-  c->nev = 0;
+  for (int k = upto; k < c->nev; ++k) {  // keep the newer pairs, recycle the handles
+    cudaEvent_t a = c->ev[2 * (k - upto)], b = c->ev[2 * (k - upto) + 1];
+    c->ev[2 * (k - upto)] = c->ev[2 * k];
+    c->ev[2 * (k - upto) + 1] = c->ev[2 * k + 1];
+    c->ev[2 * k] = a;
+    c->ev[2 * k + 1] = b;
+    c->ev_phase[k - upto] = c->ev_phase[k];
+  }
+  c->nev -= upto;
+}
+
+static void prof_flush(rts_ctx* c) {
+  if (!c->ev || c->nev == 0) return;
+  prof_collect(c, c->nev);
 }
 
 // Scope of one phase: sets the phase that launches are counted against and, when
@@ -205,8 +221,9 @@ struct Phase {
   int prev, slot;
   Phase(rts_ctx* c_, int ph) : c(c_), prev(c_->cur_phase), slot(-1) {
     c->cur_phase = ph;
-    if (c->prof && c->ev) {
-      if (c->nev == kEvPairs) prof_flush(c);
+    if (c->prof && c->ev &&
+        (c->prof == 1 || ph == RTS_PHASE_DENSITY || ph == RTS_PHASE_FORCE)) {
+      if (c->nev == kEvPairs) prof_collect(c, kEvPairs / 2);
       slot = c->nev++;
       c->ev_phase[slot] = ph;
       cudaEventRecord(c->ev[2 * slot], c->stream);
@@ -525,6 +542,7 @@ rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, c
       ALLOC(c->pnew, sizeof(int32_t) * nbk);
     }
     ALLOC(c->act, sizeof(uint32_t) * nbk);
+    ALLOC(c->plist, u1);
     ALLOC(c->ctl, sizeof(Ctl));
     ALLOC(c->xb, sizeof(float4) * (size_t)(n_boundary > 0 ? n_boundary : 1));
     if (cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl)) != cudaSuccess) {
@@ -600,7 +618,7 @@ rts_status rts_destroy(rts_ctx* c) {
   cudaFree(c->anew); cudaFree(c->cflag); cudaFree(c->key); cudaFree(c->key_tmp); cudaFree(c->slot);
   cudaFree(c->tmp_uid); cudaFree(c->tmp_src); cudaFree(c->io); cudaFree(c->io_i);
   cudaFree(c->count); cudaFree(c->cstart); cudaFree(c->bcstart); cudaFree(c->tile_sums);
-  cudaFree(c->raw); cudaFree(c->blevel); cudaFree(c->act); cudaFree(c->ctl); cudaFree(c->xb);
+  cudaFree(c->raw); cudaFree(c->blevel); cudaFree(c->act); cudaFree(c->plist); cudaFree(c->ctl); cudaFree(c->xb);
   cudaFree(c->bmax_v); cudaFree(c->bmax_a); cudaFree(c->filled); cudaFree(c->nbl);
   cudaFree(c->buid); cudaFree(c->s.ap); cudaFree(c->s2.ap); cudaFree(c->s.err); cudaFree(c->s2.err);
   cudaFree(c->xs); cudaFree(c->pbak); cudaFree(c->in_se); cudaFree(c->in_re); cudaFree(c->ob);
@@ -841,8 +859,9 @@ rts_status rts_profile_enable(rts_ctx* c, int32_t on) {
     for (int k = 0; k < 2 * kEvPairs; ++k) CK(cudaEventCreate(&c->ev[k]));
     c->nev = 0;
   }
+  if (on < 0 || on > 2) return fail(c, RTS_ERR_ARG, "profile level must be 0, 1 or 2");
   if (!on) prof_flush(c);
-  c->prof = on ? 1 : 0;
+  c->prof = on;
   return RTS_OK;
 }
 

@@ -65,6 +65,7 @@ struct Ctl {
   int bad_set;                    // a particle left the grid: its caller index and position
   unsigned int bad_uid;
   float bad_x, bad_y, bad_z;
+  int n_plist;                    // evaluated particles in the particle work list
 };
 
 // Device-side consistency checks: an index read from memory is tested before it is
@@ -171,6 +172,7 @@ struct rts_ctx {
   uint32_t* blevel;               // (stamp << 8) | level after smoothing
   uint32_t* filled;               // list of filled blocks of the current pass
   uint32_t* act;      // active block list
+  uint32_t* plist;    // evaluated particles (sorted-order indices), any order
   rts::Ctl* ctl;
   rts::Ctl* h_ctl;    // pinned host mirror
 

@@ -86,7 +86,7 @@ __global__ void k_block_activity(DevParams P, int mode, int level_g, int mult_g,
                                  const uint32_t* __restrict__ cstart,
                                  const uint32_t* __restrict__ raw, uint32_t* __restrict__ blevel,
                                  uint32_t stamp, PState s, uint8_t* __restrict__ cflag,
-                                 uint32_t* __restrict__ act) {
+                                 uint32_t* __restrict__ act, uint32_t* __restrict__ plist) {
   const int nf = ctl->n_filled;
   const int lane = threadIdx.x & 31;
   const int stride = gridDim.x * blockDim.x;
@@ -162,6 +162,19 @@ __global__ void k_block_activity(DevParams P, int mode, int level_g, int mult_g,
       }
       wb = __shfl_sync(kFull, wb, 0);
       if (ncomp > 0) act[wb + __popc(m & ((1u << lane) - 1u))] = b;
+      // the block's evaluated particles into the particle work list
+      int inc = ncomp;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int tv = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += tv;
+      }
+      int pb = 0;
+      if (lane == 31 && inc > 0) pb = atomicAdd(&ctl->n_plist, inc);
+      pb = __shfl_sync(kFull, pb, 31) + inc - ncomp;
+      if (ncomp > 0)
+        for (uint32_t i = cstart[b]; i < cstart[b + 1]; ++i)
+          if (cflag[i]) plist[pb++] = i;
     }
   }
 }
@@ -484,108 +497,104 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
 // neighbour list of the density pass.  Pressure: -m (p_i/rho_i^2 + p_j/rho_j^2) grad W;
 // boundary neighbours: -m p_i/rho_i^2 grad W.  Artificial viscosity for approaching
 // pairs with nu = 2 alpha h c / (rho_i + rho_j) (boundary: rho_j = rho_i, v_j = 0).
-__global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_t* __restrict__ act,
-                                                      Ctl* ctl, const uint32_t* __restrict__ cstart,
-                                                      PState s, const float4* __restrict__ xb,
-                                                      const uint8_t* __restrict__ cflag,
+// Particle-parallel over the evaluated-particle list: kForceLanes lanes per particle,
+// so the cost per particle does not depend on how many particles of a block evaluate.
+constexpr int kForceLanes = 4;
+
+__global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_t* __restrict__ plist,
+                                                      Ctl* ctl, PState s, const float4* __restrict__ xb,
                                                       const uint32_t* __restrict__ nbl,
                                                       float4* __restrict__ anew) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int n_act = *(volatile int*)&ctl->n_act;
+  const int sub = lane & (kForceLanes - 1);
+  const int slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / kForceLanes) +
+                   lane / kForceLanes;
+  const int nslots = ((gridDim.x * blockDim.x) >> 5) * (32 / kForceLanes);
+  const int np = *(volatile int*)&ctl->n_plist;
   const float4* __restrict__ xf = s.x;
   const float4* __restrict__ vf = s.v;
-  for (int t = warp; t < n_act; t += nwarps) {
-    const uint32_t b = act[t];
-    if (b >= (uint32_t)P.nblocks) {
-      if (lane == 0) check_failed(ctl, kChkActive, b);
-      continue;
+  // every lane of a warp runs the same number of rounds (the shuffles below)
+  const int rounds = (np + nslots - 1) / nslots;
+  for (int r = 0; r < rounds; ++r) {
+    const int t = r * nslots + slot;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    int i = -1;
+    if (t < np) {
+      i = (int)plist[t];
+      if ((uint32_t)i >= (uint32_t)P.n_fluid) {
+        if (sub == 0) check_failed(ctl, kChkActive, (unsigned)i);
+        i = -1;
+      }
     }
-    const uint32_t beg = cstart[b], end = cstart[b + 1];
-    for (uint32_t base = beg; base < end; base += 32) {
-      Group G;
-      if (!next_group(base, end, cflag, lane, G)) continue;
-      const int i = G.i;
-      float ax = 0.f, ay = 0.f, az = 0.f;
-      if (i >= 0) {
-        const float4 xi = xf[i], vi = vf[i];
-        int nn = s.nbr[i];
-        if (nn > P.nbl_cap) nn = P.nbl_cap;
-        const uint32_t* list = nbl + (size_t)i * P.nbl_cap;
-        for (int e = G.sub; e < nn; e += G.lpp) {
-          const uint32_t jg = __ldg(&list[e]);
-          float4 xj, vj;
-          float pcj;
-          const bool bnd = (jg & kBoundaryBit) != 0;
-          if (bnd ? (jg & ~kBoundaryBit) >= (uint32_t)P.n_bound : jg >= (uint32_t)P.n_fluid) {
-            check_failed(ctl, kChkNeighbour, jg);
-            continue;
-          }
-          if (bnd) {
-            xj = __ldg(&xb[jg & ~kBoundaryBit]);
-            vj = make_float4(0.f, 0.f, 0.f, vi.w);
-            pcj = 0.f;
-          } else {
-            xj = xf[jg];
-            vj = vf[jg];
-            pcj = xj.w;
-          }
-          const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-          const float d2 = dx * dx + dy * dy + dz * dz;
-          if (d2 > 0.f) {
-            const float inv_d = rsqrtf(d2);
-            const float f = spline_dW(P, d2 * inv_d * P.inv_h) * inv_d;
-            const float vx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
-            const float visc =
-                vx < 0.0f ? -P.visc_coef * __fdividef(vx, (vi.w + vj.w) * (d2 + P.eps_h2)) : 0.0f;
-            const float sc = -P.m * (xi.w + pcj + visc) * f;
-            ax += sc * dx;
-            ay += sc * dy;
-            az += sc * dz;
-          }
+    if (i >= 0) {
+      const float4 xi = xf[i], vi = vf[i];
+      int nn = s.nbr[i];
+      if (nn > P.nbl_cap) nn = P.nbl_cap;
+      const uint32_t* list = nbl + (size_t)i * P.nbl_cap;
+      for (int e = sub; e < nn; e += kForceLanes) {
+        const uint32_t jg = __ldg(&list[e]);
+        float4 xj, vj;
+        float pcj;
+        const bool bnd = (jg & kBoundaryBit) != 0;
+        if (bnd ? (jg & ~kBoundaryBit) >= (uint32_t)P.n_bound : jg >= (uint32_t)P.n_fluid) {
+          check_failed(ctl, kChkNeighbour, jg);
+          continue;
+        }
+        if (bnd) {
+          xj = __ldg(&xb[jg & ~kBoundaryBit]);
+          vj = make_float4(0.f, 0.f, 0.f, vi.w);
+          pcj = 0.f;
+        } else {
+          xj = xf[jg];
+          vj = vf[jg];
+          pcj = xj.w;
+        }
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+        const float d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 > 0.f) {
+          const float inv_d = rsqrtf(d2);
+          const float f = spline_dW(P, d2 * inv_d * P.inv_h) * inv_d;
+          const float vx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+          const float visc =
+              vx < 0.0f ? -P.visc_coef * __fdividef(vx, (vi.w + vj.w) * (d2 + P.eps_h2)) : 0.0f;
+          const float sc = -P.m * (xi.w + pcj + visc) * f;
+          ax += sc * dx;
+          ay += sc * dy;
+          az += sc * dz;
         }
       }
-      for (int o = G.lpp >> 1; o; o >>= 1) {
-        ax += __shfl_down_sync(kFull, ax, o, G.lpp);
-        ay += __shfl_down_sync(kFull, ay, o, G.lpp);
-        az += __shfl_down_sync(kFull, az, o, G.lpp);
-      }
-      if (G.sub == 0 && i >= 0) anew[i] = make_float4(P.gx + ax, P.gy + ay, P.gz + az, 0.f);
     }
+#pragma unroll
+    for (int o = kForceLanes >> 1; o; o >>= 1) {
+      ax += __shfl_down_sync(kFull, ax, o, kForceLanes);
+      ay += __shfl_down_sync(kFull, ay, o, kForceLanes);
+      az += __shfl_down_sync(kFull, az, o, kForceLanes);
+    }
+    if (sub == 0 && i >= 0) anew[i] = make_float4(P.gx + ax, P.gy + ay, P.gz + az, 0.f);
   }
 }
 
 // Section 4.1 correction of the evaluated particles: x += (a_new - a_old) dt^2 / 6,
 // v += (a_new - a_old) dt / 2 with dt = (k1 - k_last) dt_b; a_old <- a_new.
 // prime != 0: no time has passed; only a_old <- a_new, k_last <- k1.
-__global__ void k_correct(DevParams P, const uint32_t* __restrict__ act, Ctl* ctl,
-                          const uint32_t* __restrict__ cstart, PState s,
-                          const uint8_t* __restrict__ cflag, const float4* __restrict__ anew,
-                          int k1, int prime) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int n_act = *(volatile int*)&ctl->n_act;
-  for (int t = warp; t < n_act; t += nwarps) {
-    const uint32_t b = act[t];
-    if (b >= (uint32_t)P.nblocks) {
-      if (lane == 0) check_failed(ctl, kChkActive, b);
+__global__ void k_correct(DevParams P, const uint32_t* __restrict__ plist, Ctl* ctl, PState s,
+                          const float4* __restrict__ anew, int k1, int prime) {
+  const int np = *(volatile int*)&ctl->n_plist;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < np; t += gridDim.x * blockDim.x) {
+    const uint32_t i = plist[t];
+    if (i >= (uint32_t)P.n_fluid) {
+      check_failed(ctl, kChkActive, i);
       continue;
     }
-    const uint32_t beg = cstart[b], end = cstart[b + 1];
-    for (uint32_t i = beg + lane; i < end; i += 32) {
-      if (!cflag[i]) continue;
-      float4 an = anew[i];
-      if (!prime) {
-        float4 x = s.x[i], v = s.v[i];
-        serna_correct(x, v, s.a[i], an, (float)(k1 - s.klast[i]) * P.dt_b);
-        s.x[i] = x;
-        s.v[i] = v;
-      }
-      s.a[i] = an;
-      s.klast[i] = k1;
+    float4 an = anew[i];
+    if (!prime) {
+      float4 x = s.x[i], v = s.v[i];
+      serna_correct(x, v, s.a[i], an, (float)(k1 - s.klast[i]) * P.dt_b);
+      s.x[i] = x;
+      s.v[i] = v;
     }
+    s.a[i] = an;
+    s.klast[i] = k1;
   }
 }
 
@@ -669,10 +678,11 @@ rts_status launch_classify(rts_ctx* c) {
 // mode < 0: smoothing only (public classification); otherwise smoothing + activity.
 rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g) {
   cudaMemsetAsync(&c->ctl->n_act, 0, sizeof(int), c->stream);
+  cudaMemsetAsync(&c->ctl->n_plist, 0, sizeof(int), c->stream);
   note_launch(c, 1);
   k_block_activity<<<filled_grid(), 256, 0, c->stream>>>(c->dp, mode, level_g, mult_g, c->filled,
                                                          c->ctl, c->cstart, c->raw, c->blevel,
-                                                         c->stamp, c->s, c->cflag, c->act);
+                                                         c->stamp, c->s, c->cflag, c->act, c->plist);
   return RTS_OK;
 }
 
@@ -685,16 +695,15 @@ rts_status launch_density(rts_ctx* c) {
 
 rts_status launch_force(rts_ctx* c) {
   note_launch(c, 1);
-  k_force<<<force_grid(c), kNbThreads, 0, c->stream>>>(
-      c->dp, c->act, c->ctl, c->cstart, c->s, c->xb, c->cflag, c->nbl, c->anew);
+  k_force<<<force_grid(c), kNbThreads, 0, c->stream>>>(c->dp, c->plist, c->ctl, c->s, c->xb,
+                                                       c->nbl, c->anew);
   return RTS_OK;
 }
 
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime) {
   note_launch(c, 1);
-  k_correct<<<force_grid(c), kNbThreads, 0, c->stream>>>(c->dp, c->act, c->ctl, c->cstart,
-                                                              c->s, c->cflag, c->anew, (int)k1,
-                                                              prime);
+  k_correct<<<force_grid(c), kNbThreads, 0, c->stream>>>(c->dp, c->plist, c->ctl, c->s, c->anew,
+                                                              (int)k1, prime);
   return RTS_OK;
 }
 

@@ -341,7 +341,9 @@ def rts_get_state_into(ctx, x=None, v=None, a=None, rho=None, p=None, level=None
 
 
 def rts_profile_enable(ctx, on=True):
-    return _check(lib().rts_profile_enable(ctx.handle, 1 if on else 0), "rts_profile_enable", ctx)
+    """on: False/0 off, True/1 every phase, 2 only the density and force passes."""
+    level = int(on) if not isinstance(on, bool) else (1 if on else 0)
+    return _check(lib().rts_profile_enable(ctx.handle, level), "rts_profile_enable", ctx)
 
 
 def rts_profile_read(ctx, reset=False) -> dict:
