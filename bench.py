@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--constant-steps", type=int, default=5,
                     help="steps of the constant-dt_b arm (compared with the same steps of RTS)")
     ap.add_argument("--no-global", action="store_true", help="skip the global comparators")
+    ap.add_argument("--no-aligned", action="store_true",
+                    help="skip the level-aligned activity clock variant")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="8k-particle dam break (quick check)")
@@ -422,6 +424,10 @@ def main():
     subs = ours["tot"]["substeps"]
     value = world * sc.n * subs / (total_ms / 1e3)
 
+    aligned = None
+    if not args.no_aligned:
+        aligned = run_rollout(sc, {"level_clock": 1}, args.steps, args, torch, rts, profile=True,
+                              flush=flush, name="timed_rts_aligned")
     glob = const = None
     if not args.no_global:
         glob = run_rollout(sc, {"mode": 1}, args.steps, args, torch, rts, profile=True,
@@ -476,9 +482,16 @@ def main():
         "ms_per_step_list": [round(m, 1) for m in ours["ms"]],
         "roofline": roofline, "clocks": clk.summary(),
     }
+    if aligned is not None:
+        line["rts_level_aligned"] = arm_summary(sc, aligned, dtb)
+        line["rts_level_aligned"]["evals_per_active_block"] = (
+            aligned["tot"]["particle_evals"] / max(1, aligned["tot"]["active_blocks"]))
     if glob is not None:
         line["global_adaptive"] = arm_summary(sc, glob, dtb)
         line["rts_vs_global"] = (value / world) / line["global_adaptive"]["value"]
+        if aligned is not None:
+            line["rts_level_aligned_vs_global"] = (line["rts_level_aligned"]["value"] /
+                                                   line["global_adaptive"]["value"])
         line["global_constant_dt_b"] = arm_summary(sc, const, dtb)
         nc = len(const["ms"])
         line["rts_vs_constant_same_span"] = sum(const["ms"]) / sum(ours["ms"][:nc])

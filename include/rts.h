@@ -100,6 +100,11 @@ typedef struct rts_params {
      velocity component into it (non-penetration); 0: off.                            */
   int32_t wall_project;
   float wall_lo[3], wall_hi[3];
+  /* WCSPH activity clock.  0: Algorithm 1 as stated: a particle that computes takes
+     validity = its level's multiplier, so particles of one block drift out of phase.
+     1: level-aligned variant: validity = mult - (k mod mult), so every particle of level
+     L computes at the substeps k that are multiples of mult[L] (plus pre-emptions).   */
+  int32_t level_clock;
 } rts_params;
 
 /* Counters accumulated over one rts_advance call. */

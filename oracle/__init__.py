@@ -50,6 +50,7 @@ class OrcParams(C.Structure):
         ("wall_project", C.c_int32),
         ("wall_lo", C.c_double * 3),
         ("wall_hi", C.c_double * 3),
+        ("level_clock", C.c_int32),
     ]
 
 
@@ -95,6 +96,7 @@ def make_params(d: dict) -> OrcParams:
         P.refresh[L] = int(d["refresh"][L])
     P.max_neighbors = int(d["max_neighbors"])
     P.wall_project = int(d.get("wall_project", 0))
+    P.level_clock = int(d.get("level_clock", 0))
     for k in range(3):
         P.wall_lo[k] = _f32(d.get("wall_lo", [0.0] * 3)[k])
         P.wall_hi[k] = _f32(d.get("wall_hi", [0.0] * 3)[k])

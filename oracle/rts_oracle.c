@@ -529,6 +529,13 @@ static void serna_predict(const orc_params* P, int32_t n, double* x, double* v, 
   for (int32_t i = 0; i < n; ++i) orci_wall_project(P, x + 3 * (int64_t)i, v + 3 * (int64_t)i);
 }
 
+/* Validity of a particle that starts a true step of multiplier m at substep k:
+ * Algorithm 1 counts m substeps; the level-aligned variant counts to the next multiple
+ * of m, so the particles of a level compute together. */
+static int32_t new_validity(const orc_params* P, int32_t m, int64_t k) {
+  return P->level_clock ? (int32_t)(m - k % m) : m;
+}
+
 static int32_t particle_block_level(const orc_params* P, const orc_wstate* S, int32_t i) {
   int32_t key;
   if (orc_block_key(P, S->x + 3 * (int64_t)i, &key)) return -1;
@@ -544,7 +551,7 @@ int orc_wcsph_evaluate(const orc_params* P, orc_wstate* S) {
   for (int32_t i = 0; i < n; ++i) {
     int32_t L = particle_block_level(P, S, i);
     S->level[i] = L;
-    S->validity[i] = P->mult[L];
+    S->validity[i] = new_validity(P, P->mult[L], S->k);
     S->compute[i] = 1;
   }
   double* anew = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
@@ -577,7 +584,7 @@ int orc_wcsph_substep(const orc_params* P, orc_wstate* S) {
     if (S->validity[i] <= 0 || S->level[i] < 0 || P->mult[Lb] != P->mult[S->level[i]]) {
       S->compute[i] = 1;
       S->level[i] = Lb;
-      S->validity[i] = P->mult[Lb];
+      S->validity[i] = new_validity(P, P->mult[Lb], k1);
     } else {
       S->compute[i] = 0;
     }

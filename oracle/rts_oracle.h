@@ -57,6 +57,9 @@ typedef struct orc_params {
    * update is put back on the face and its velocity component into it is dropped. */
   int32_t wall_project;
   double wall_lo[3], wall_hi[3];
+  /* WCSPH activity clock: 0 validity = level multiplier (Algorithm 1); 1 validity up to
+   * the next multiple of the multiplier (level-aligned variant). */
+  int32_t level_clock;
 } orc_params;
 
 /* WCSPH state in user order. */

@@ -83,6 +83,7 @@ static const char* validate(const rts_params* p, int32_t n, int32_t nb) {
   if (p->max_per_block < 1 || p->max_per_block > 1024) return "max_per_block must be in [1, 1024]";
   if (p->max_neighbors < 8 || p->max_neighbors > 1024) return "max_neighbors must be in [8, 1024]";
   if (p->wall_project != 0 && p->wall_project != 1) return "wall_project must be 0 or 1";
+  if (p->level_clock != 0 && p->level_clock != 1) return "level_clock must be 0 or 1";
   if (p->wall_project)
     for (int k = 0; k < 3; ++k)
       if (!(p->wall_lo[k] < p->wall_hi[k])) return "wall_lo must be below wall_hi on every axis";
@@ -137,6 +138,7 @@ static void make_dev_params(const rts_params& p, DevParams& d) {
   d.gy = p.gravity[1];
   d.gz = p.gravity[2];
   d.wall_project = p.wall_project;
+  d.level_clock = p.level_clock;
   for (int k = 0; k < 3; ++k) {
     d.wlo[k] = p.wall_lo[k];
     d.whi[k] = p.wall_hi[k];
@@ -394,7 +396,7 @@ rts_status rts::finalize(rts_ctx* c) {
 static rts_status wcsph_evaluate(rts_ctx* c) {
   { Phase ph(c, RTS_PHASE_BIN); launch_bin(c, 0.0f); }
   { Phase ph(c, RTS_PHASE_CLASSIFY); launch_classify(c); }
-  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActAll, 0, 0); }
+  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActAll, 0, 0, c->k); }
   run_physics(c, c->k, 1);
   c->primed = 1;
   c->bins_valid = 1;
@@ -406,7 +408,7 @@ static rts_status wcsph_regional(rts_ctx* c) {
   int64_t k1 = c->k + 1;
   { Phase ph(c, RTS_PHASE_BIN); launch_bin(c, c->p.dt_b); }
   { Phase ph(c, RTS_PHASE_CLASSIFY); launch_classify(c); }
-  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActRegional, 0, 0); }
+  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActRegional, 0, 0, k1); }
   run_physics(c, k1, 0);
   c->k = k1;
   c->bins_valid = 1;
@@ -442,7 +444,7 @@ static rts_status wcsph_global(rts_ctx* c, int64_t max_mult) {
   if (m < 1) m = 1;
   int64_t k1 = c->k + m;
   { Phase ph(c, RTS_PHASE_BIN); launch_bin(c, (float)m * c->p.dt_b); }
-  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActGlobal, L, (int)m); }
+  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActGlobal, L, (int)m, k1); }
   c->last_global_level = L;
   run_physics(c, k1, 0);
   c->k = k1;
@@ -673,7 +675,7 @@ rts_status rts_classify_blocks(rts_ctx* c) {
   }
   {
     Phase ph(c, RTS_PHASE_ACTIVITY);
-    launch_activity(c, -1, 0, 0);
+    launch_activity(c, -1, 0, 0, c->k);
   }
   CK(cudaGetLastError());
   return RTS_OK;

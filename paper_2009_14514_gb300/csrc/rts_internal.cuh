@@ -42,6 +42,7 @@ struct DevParams {
   double vthr2[kMaxLevels], athr2[kMaxLevels];
   int eq1[kMaxLevels];
   int force_level;
+  int level_clock;   // 0: validity = multiplier (Algorithm 1); 1: aligned to multiples
   float dt_b;
 };
 
@@ -229,7 +230,7 @@ namespace rts {
 rts_status launch_bin(rts_ctx* c, float dt_predict);
 rts_status launch_bin_boundary(rts_ctx* c, const float4* xb_unsorted, int nb);
 rts_status launch_classify(rts_ctx* c);
-rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g);
+rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1);
 rts_status launch_density(rts_ctx* c);
 rts_status launch_force(rts_ctx* c);
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime);

@@ -436,7 +436,7 @@ static rts_status major_start(rts_ctx* c) {
   }
   PPhase ph(c, RTS_PHASE_CLASSIFY);
   launch_classify(c);             // Eq. 2-3 from the block maxima (thresholds for PCISPH)
-  launch_activity(c, -1, 0, 0);   // R_min (or the forced region)
+  launch_activity(c, -1, 0, 0, 0);   // R_min (or the forced region)
   cudaMemsetAsync(c->preg, 0xff, sizeof(int32_t) * nbk, c->stream);
   int fg = filled_grid_size();
   note_launch(c, 1);

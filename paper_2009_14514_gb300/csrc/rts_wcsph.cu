@@ -81,7 +81,7 @@ __global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled, 
 // filled 26 neighbours, one Jacobi pass), or the forced / global level; then, with
 // mode >= 0, Algorithm 1's per-particle bookkeeping (validity, pre-emption on a level
 // change) and the work list of blocks holding an evaluated particle.
-__global__ void k_block_activity(DevParams P, int mode, int level_g, int mult_g,
+__global__ void k_block_activity(DevParams P, int mode, int level_g, int mult_g, long long k1,
                                  const uint32_t* __restrict__ filled, Ctl* ctl,
                                  const uint32_t* __restrict__ cstart,
                                  const uint32_t* __restrict__ raw, uint32_t* __restrict__ blevel,
@@ -122,6 +122,9 @@ __global__ void k_block_activity(DevParams P, int mode, int level_g, int mult_g,
       blevel[b] = (stamp << 8) | (uint32_t)L;
       if (mode >= 0) {
         const int mb = mode == kActGlobal ? mult_g : P.mult[L];
+        // validity of a particle that starts a true step now (level-aligned variant:
+        // up to the next multiple of the multiplier)
+        const int vnew = (mode != kActGlobal && P.level_clock) ? mb - (int)(k1 % mb) : mb;
         for (uint32_t i = cstart[b]; i < cstart[b + 1]; ++i) {
           int c;
           if (mode == kActRegional) {
@@ -134,7 +137,7 @@ __global__ void k_block_activity(DevParams P, int mode, int level_g, int mult_g,
             if (val <= 0 || li < 0 || P.mult[li] != mb) {
               c = 1;
               s.level[i] = L;
-              val = mb;
+              val = vnew;
             } else {
               c = 0;
             }
@@ -142,7 +145,7 @@ __global__ void k_block_activity(DevParams P, int mode, int level_g, int mult_g,
           } else {
             c = 1;
             s.level[i] = L;
-            s.valid[i] = mb;
+            s.valid[i] = vnew;
           }
           cflag[i] = (uint8_t)c;
           ncomp += c;
@@ -676,11 +679,11 @@ rts_status launch_classify(rts_ctx* c) {
 }
 
 // mode < 0: smoothing only (public classification); otherwise smoothing + activity.
-rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g) {
+rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1) {
   cudaMemsetAsync(&c->ctl->n_act, 0, sizeof(int), c->stream);
   cudaMemsetAsync(&c->ctl->n_plist, 0, sizeof(int), c->stream);
   note_launch(c, 1);
-  k_block_activity<<<filled_grid(), 256, 0, c->stream>>>(c->dp, mode, level_g, mult_g, c->filled,
+  k_block_activity<<<filled_grid(), 256, 0, c->stream>>>(c->dp, mode, level_g, mult_g, (long long)k1, c->filled,
                                                          c->ctl, c->cstart, c->raw, c->blevel,
                                                          c->stamp, c->s, c->cflag, c->act, c->plist);
   return RTS_OK;

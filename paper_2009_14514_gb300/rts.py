@@ -53,6 +53,7 @@ class RtsParams(C.Structure):
         ("wall_project", C.c_int32),
         ("wall_lo", C.c_float * 3),
         ("wall_hi", C.c_float * 3),
+        ("level_clock", C.c_int32),
     ]
 
 
@@ -126,6 +127,7 @@ def make_params(d: dict) -> RtsParams:
     for k in range(3):
         P.wall_lo[k] = d.get("wall_lo", [0.0] * 3)[k]
         P.wall_hi[k] = d.get("wall_hi", [0.0] * 3)[k]
+    P.level_clock = int(d.get("level_clock", 0))
     return P
 
 

@@ -351,6 +351,34 @@ def test_without_the_container_the_particle_passes_the_floor():
     assert S.x[0, 2] < 0.0
 
 
+@pytest.mark.parametrize("clock", [0, 1])
+def test_activity_schedule_of_algorithm_1_and_of_the_level_aligned_clock(clock):
+    # A particle computes iff its block's level differs from its own (pre-emption) or its
+    # validity ran out: m substeps after its last evaluation (Algorithm 1), or at the next
+    # multiple of m (level-aligned clock), m the multiplier of its level.
+    sc = scenes.wcsph_dam_break_8k()
+    P = _params(sc, level_clock=clock)
+    st = scenes.perturbed_state(sc, seed=5, vmax=3.0, amax=2.0e3)   # levels 0-3 in blocks
+    S = O.WCSPH(P, sc.x, st["v"], sc.xb)
+    S.evaluate()
+    mult = np.array([P.mult[L] for L in range(P.n_levels)])
+    evals = pre = 0
+    for _ in range(64):
+        lev0, kl0 = S.level.copy(), S.klast.copy()
+        S.substep()
+        k = S.k
+        changed = mult[S.level] != mult[lev0]
+        if clock == 0:
+            due = (k - kl0) == mult[lev0]
+        else:
+            due = (k % mult[lev0]) == 0
+        assert np.array_equal(S.compute == 1, changed | due)
+        evals += int(S.compute.sum())
+        pre += int(changed.sum())
+    assert pre > 0 and evals < 64 * sc.n * 0.9     # pre-emptions occur; not everyone computes
+    assert len(np.unique(S.level)) >= 2
+
+
 def test_forced_finest_rts_reproduces_global_stepping_exactly():
     sc = scenes.wcsph_dam_break_8k()
     Pr = _params(sc, force_level=0)
