@@ -45,7 +45,9 @@ __device__ __forceinline__ uint32_t block_key(const DevParams& P, float4 p, int*
 }
 
 // Deferred correction of the last step's evaluated particles (pend), then predict
-// (dt != 0: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt), then key and slot.
+// (dt != 0: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt) and the container correction,
+// then key and slot.  Slots: particles arrive mostly in block order, so each run of
+// equal keys in lane order takes one atomic on its block's counter.
 __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4* __restrict__ v,
                               float4* __restrict__ a, float dt, uint32_t* __restrict__ key,
                               uint32_t* __restrict__ slot, uint32_t* __restrict__ count, Ctl* ctl,
@@ -53,32 +55,38 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
                               const float4* __restrict__ anew, int32_t* __restrict__ klast,
                               const uint32_t* __restrict__ uid) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) ctl->n_filled = 0;   // the scan that follows appends the filled blocks
   if (i >= n) return;
   float4 xi = x[i];
-  if (pend != kPendNone && cflag[i]) {
-    float4 vi = v[i];
-    const float4 an = anew[i];
-    if (pend == kPendCorrect) {
-      serna_correct(xi, vi, a[i], an, (float)(pend_k1 - klast[i]) * P.dt_b);
+  const bool corr = pend != kPendNone && cflag[i];
+  if (corr || dt != 0.0f) {
+    float4 vi = v[i], ai = a[i];
+    bool moved = false;
+    if (corr) {
+      const float4 an = anew[i];
+      if (pend == kPendCorrect) {
+        serna_correct(xi, vi, ai, an, (float)(pend_k1 - klast[i]) * P.dt_b);
+        moved = true;
+      }
+      ai = an;
+      a[i] = an;
+      klast[i] = pend_k1;
+    }
+    if (dt != 0.0f) {
+      const float hdt2 = 0.5f * dt * dt;
+      xi.x = xi.x + vi.x * dt + ai.x * hdt2;
+      xi.y = xi.y + vi.y * dt + ai.y * hdt2;
+      xi.z = xi.z + vi.z * dt + ai.z * hdt2;
+      vi.x = vi.x + ai.x * dt;
+      vi.y = vi.y + ai.y * dt;
+      vi.z = vi.z + ai.z * dt;
+      if (P.wall_project) wall_project(P, xi, vi);
+      moved = true;
+    }
+    if (moved) {
       x[i] = xi;
       v[i] = vi;
     }
-    a[i] = an;
-    klast[i] = pend_k1;
-  }
-  if (dt != 0.0f) {
-    float4 vi = v[i];
-    float4 ai = a[i];
-    float hdt2 = 0.5f * dt * dt;
-    xi.x = xi.x + vi.x * dt + ai.x * hdt2;
-    xi.y = xi.y + vi.y * dt + ai.y * hdt2;
-    xi.z = xi.z + vi.z * dt + ai.z * hdt2;
-    vi.x = vi.x + ai.x * dt;
-    vi.y = vi.y + ai.y * dt;
-    vi.z = vi.z + ai.z * dt;
-    if (P.wall_project) wall_project(P, xi, vi);
-    x[i] = xi;
-    v[i] = vi;
   }
   int bad = 0;
   uint32_t b = block_key(P, xi, &bad);
@@ -93,15 +101,22 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
     b = 0;
   }
   key[i] = b;
-  // one atomic per distinct block in the warp: consecutive particles mostly share a block
-  const unsigned active = __activemask();
-  const unsigned peers = __match_any_sync(active, b);
+  // the warp's lanes with i < n: a prefix of the warp (i = base + lane)
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
+  const int wrem = n - (i - lane);
+  const unsigned act = wrem >= 32 ? 0xffffffffu : ((1u << wrem) - 1u);
+  __syncwarp(act);
+  const uint32_t prevb = __shfl_up_sync(act, b, 1);
+  const bool head = lane == 0 || prevb != b;
+  const unsigned heads = __ballot_sync(act, head);
+  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  const int myhead = 31 - __clz(heads & upto);
+  const unsigned after = heads & ~upto;
+  const int next = after ? __ffs(after) - 1 : __popc(act);
   uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&count[b], (uint32_t)__popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  slot[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+  if (head) base = atomicAdd(&count[b], (uint32_t)(next - lane));
+  base = __shfl_sync(act, base, myhead);
+  slot[i] = base + (uint32_t)(lane - myhead);
 }
 
 // ---- exclusive scan of the per-block counts (reduce, scan tile sums, apply) ----
@@ -164,18 +179,6 @@ __global__ void k_scan_reduce(const uint32_t* __restrict__ count, int nb, uint32
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_tiles(uint32_t* tile_sums, int ntiles) {
-  uint32_t carry = 0;
-  for (int base = 0; base < ntiles; base += blockDim.x) {
-    int i = base + threadIdx.x;
-    uint32_t v = i < ntiles ? tile_sums[i] : 0u;
-    uint32_t tot;
-    uint32_t ex = block_excl_scan(v, &tot);
-    if (i < ntiles) tile_sums[i] = ex + carry;
-    carry += tot;
-  }
-}
-
 // cstart[i] = exclusive prefix of count; count is reset to zero for the next binning.
 // Filled blocks (count > 0) are appended to the filled list (warp-aggregated; the
 // list's order is irrelevant to every consumer).
@@ -192,8 +195,15 @@ __global__ void k_scan_apply(uint32_t* __restrict__ count, int nb, const uint32_
     s += c[k];
     nf += c[k] ? 1 : 0;
   }
+  // this tile's offset: the sum of the preceding tiles' totals (read by every CTA)
+  uint32_t pre = 0;
+  {
+    uint32_t ps = 0;
+    for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) ps += tile_sums[k];
+    block_excl_scan(ps, &pre);
+  }
   uint32_t tot;
-  uint32_t ex = block_excl_scan(s, &tot) + tile_sums[blockIdx.x];
+  uint32_t ex = block_excl_scan(s, &tot) + pre;
   uint32_t o[kScanItems];
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
@@ -336,12 +346,12 @@ __global__ void k_canon_gather(int n, int nb, int max_per_block, const uint32_t*
   }
 }
 
+// Exclusive scan of the block counts into cstart (tile totals, then each tile adds the
+// totals before it); the filled list is appended to (its counter was reset by the key pass).
 static rts_status scan_counts(rts_ctx* c, uint32_t* filled) {
   int nb = c->dp.nblocks;
   int ntiles = (nb + kScanTile - 1) / kScanTile;
-  if (filled) cudaMemsetAsync(&c->ctl->n_filled, 0, sizeof(int), c->stream);
   k_scan_reduce<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums);
-  k_scan_tiles<<<1, 1024, 0, c->stream>>>(c->tile_sums, ntiles);
   k_scan_apply<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums, c->cstart,
                                                         filled, c->ctl);
   return RTS_OK;
@@ -368,7 +378,7 @@ rts_status launch_bin(rts_ctx* c, float dt) {
     return RTS_OK;
   }
   int tb = 256, g = (n + tb - 1) / tb;
-  note_launch(c, 6);
+  note_launch(c, 5);
   next_stamp(c);
   k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, n, c->s.x, c->s.v, c->s.a, dt, c->key, c->slot,
                                           c->count, c->ctl, c->pend_mode, (int)c->pend_k1,

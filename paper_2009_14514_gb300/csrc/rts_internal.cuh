@@ -50,6 +50,7 @@ struct DevParams {
 struct Ctl {
   int status;                    // first device error (rts_status), 0 = none
   int n_act;                     // active blocks in the work list
+  int n_plist;                   // evaluated particles in the particle work list
   unsigned long long evals;      // evaluated particles
   unsigned long long pairs;      // neighbour pairs of evaluated particles
   unsigned long long act_blocks; // active blocks summed over steps
@@ -66,7 +67,6 @@ struct Ctl {
   int bad_set;                    // a particle left the grid: its caller index and position
   unsigned int bad_uid;
   float bad_x, bad_y, bad_z;
-  int n_plist;                    // evaluated particles in the particle work list
 };
 
 // Device-side consistency checks: an index read from memory is tested before it is
