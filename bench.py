@@ -44,6 +44,12 @@ FP32_LANES_PER_SM = 128
 FLOPS_TEST = 8
 FLOPS_PAIR_DENSITY = 8
 FLOPS_PAIR_FORCE = 24
+# DRAM bytes (read + write) per evaluated particle of the density pass, from one ncu
+# capture of k_density on the profiling case (--profile-case; 23.5 MB for 191,176
+# evaluated particles).  A launch of the 2 s rollout is not captured under ncu's size
+# rule, so its traffic is this figure times the launch's evaluations.  Valid for the
+# density kernel as captured; re-measure when k_density changes.
+DENSITY_DRAM_BYTES_PER_EVAL = 123.0
 
 
 def parse():
@@ -454,7 +460,9 @@ def main():
     achieved = flops_per_launch / dur_s / 1e12 if dur_s > 0 else 0.0
     roofline = {"bound": "alu", "kernel": "k_force" if kern == "force" else "k_density",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
+                "frac": achieved / peak_tflops,
+                "traffic": (DENSITY_DRAM_BYTES_PER_EVAL * tot["particle_evals"] / launches
+                            if kern == "density" else None),
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived)",
                 "avg_launch_us": dur_s * 1e6, "launches": launches}
 
