@@ -250,10 +250,18 @@ def arm_summary(sc, r, dt_norm):
     return out
 
 
+def phase_total_ms(prof, ph):
+    """Device time of a phase over the run: the sampled instances' mean times the
+    number of instances (every phase instance launches one kernel for these phases)."""
+    timed = max(1, prof["timed"][ph])
+    return prof["ms"][ph] / timed * prof["launches"][ph]
+
+
 def phase_split(prof, total_ms):
-    """Density and force passes timed by events inside the run; the rest (binning,
-    classification, activity, launch gaps) is the remainder of the step time."""
-    dens, force = prof["ms"]["density"], prof["ms"]["force"]
+    """Density and force passes timed by events inside the run (a sample of every 7th
+    launch); the rest (binning, classification, activity, launch gaps) is the remainder
+    of the step time."""
+    dens, force = phase_total_ms(prof, "density"), phase_total_ms(prof, "force")
     return {"density": round(dens, 1), "force": round(force, 1),
             "bin_classify_activity_rest": round(total_ms - dens - force, 1)}
 
@@ -450,21 +458,22 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     tests, pairs = ours["tot"]["candidate_tests"], ours["tot"]["pair_interactions"]
-    kern = max(("density", "force"), key=lambda k: prof["ms"][k])
+    kern = max(("density", "force"), key=lambda k: phase_total_ms(prof, k))
     launches = max(1, prof["launches"][kern])
     if kern == "density":   # the neighbour search and the density sum
         flops_per_launch = (tests * FLOPS_TEST + pairs * FLOPS_PAIR_DENSITY) / launches
     else:                   # the force pass walks the pair list of the density pass
         flops_per_launch = pairs * FLOPS_PAIR_FORCE / launches
-    dur_s = prof["ms"][kern] / 1e3 / launches
+    dur_s = prof["ms"][kern] / 1e3 / max(1, prof["timed"][kern])   # mean sampled launch
     achieved = flops_per_launch / dur_s / 1e12 if dur_s > 0 else 0.0
     roofline = {"bound": "alu", "kernel": "k_force" if kern == "force" else "k_density",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops,
-                "traffic": (DENSITY_DRAM_BYTES_PER_EVAL * tot["particle_evals"] / launches
+                "traffic": (DENSITY_DRAM_BYTES_PER_EVAL * ours["tot"]["particle_evals"] / launches
                             if kern == "density" else None),
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived)",
-                "avg_launch_us": dur_s * 1e6, "launches": launches}
+                "avg_launch_us": dur_s * 1e6, "launches": launches,
+                "launches_timed": int(prof["timed"][kern])}
 
     sim = ours["sim_s"]
     tot = ours["tot"]

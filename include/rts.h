@@ -209,14 +209,17 @@ enum {
 };
 
 typedef struct rts_profile {
-  double ms[RTS_NUM_PHASES];         /* device time per phase (valid while enabled)        */
+  double ms[RTS_NUM_PHASES];         /* device time of the timed instances of each phase   */
   int64_t launches[RTS_NUM_PHASES];  /* kernel launches per phase                          */
   int64_t kernels;                   /* all kernel launches of this library                */
+  int64_t timed[RTS_NUM_PHASES];     /* phase instances that were timed                    */
 } rts_profile;
 
-/* Per-phase event timing: 0 off, 1 every phase, 2 only the density and force passes
- * (two event pairs per substep: the lightest way to time the neighbour kernels inside a
- * long run).  Launch counts are always kept.  RTS_ERR_ARG for other values. */
+/* Per-phase event timing: 0 off; 1 every phase instance; 2 every 7th instance of the
+ * density and of the force pass only (a sample whose stride is prime to the level
+ * cycles: the lightest way to time the neighbour kernels inside a long run; the
+ * average duration is ms / timed).  Launch counts are always kept.  RTS_ERR_ARG for
+ * other values. */
 rts_status rts_profile_enable(rts_ctx* ctx, int32_t on);
 
 /* Read the accumulated profile (synchronises); reset != 0 clears it afterwards. */

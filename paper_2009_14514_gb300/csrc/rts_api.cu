@@ -113,6 +113,14 @@ static void make_dev_params(const rts_params& p, DevParams& d) {
   d.ny = p.grid_dim[1];
   d.nz = p.grid_dim[2];
   d.nblocks = d.nx * d.ny * d.nz;
+  {
+    // the FP32 block coordinate of a point up to one block outside the grid carries at
+    // most 3 * 2^-24 relative error; 8 * 2^-24 * (largest dim + 2) bounds it with margin
+    int dmax = p.grid_dim[0];
+    if (p.grid_dim[1] > dmax) dmax = p.grid_dim[1];
+    if (p.grid_dim[2] > dmax) dmax = p.grid_dim[2];
+    d.key_band = (float)(8.0 * ldexp(1.0, -24) * (dmax + 2));
+  }
   d.max_per_block = p.max_per_block;
   d.r = p.support_r;
   d.r2 = p.support_r * p.support_r;
@@ -223,9 +231,12 @@ struct Phase {
   int prev, slot;
   Phase(rts_ctx* c_, int ph) : c(c_), prev(c_->cur_phase), slot(-1) {
     c->cur_phase = ph;
-    if (c->prof && c->ev &&
-        (c->prof == 1 || ph == RTS_PHASE_DENSITY || ph == RTS_PHASE_FORCE)) {
+    bool timed = c->prof == 1;
+    if (c->prof == 2 && (ph == RTS_PHASE_DENSITY || ph == RTS_PHASE_FORCE))
+      timed = (c->prof_seen[ph]++ % 7) == 0;
+    if (c->prof && c->ev && timed) {
       if (c->nev == kEvPairs) prof_collect(c, kEvPairs / 2);
+      c->prof_timed[ph] += 1;
       slot = c->nev++;
       c->ev_phase[slot] = ph;
       cudaEventRecord(c->ev[2 * slot], c->stream);
@@ -545,6 +556,7 @@ rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, c
     }
     ALLOC(c->act, sizeof(uint32_t) * nbk);
     ALLOC(c->plist, u1);
+    ALLOC(c->actflag, sizeof(uint32_t) * nbk);
     ALLOC(c->ctl, sizeof(Ctl));
     ALLOC(c->xb, sizeof(float4) * (size_t)(n_boundary > 0 ? n_boundary : 1));
     if (cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl)) != cudaSuccess) {
@@ -558,6 +570,7 @@ rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, c
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->raw, 0, sizeof(uint32_t) * nbk, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->blevel, 0, sizeof(uint32_t) * nbk, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->actflag, 0, sizeof(uint32_t) * nbk, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bmax_v, 0, sizeof(unsigned long long) * nbk, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bmax_a, 0, sizeof(unsigned long long) * nbk, c->stream);
     if (e == cudaSuccess && c->preg) e = cudaMemsetAsync(c->preg, 0xff, sizeof(int32_t) * nbk, c->stream);
@@ -620,7 +633,7 @@ rts_status rts_destroy(rts_ctx* c) {
   cudaFree(c->anew); cudaFree(c->cflag); cudaFree(c->key); cudaFree(c->key_tmp); cudaFree(c->slot);
   cudaFree(c->tmp_uid); cudaFree(c->tmp_src); cudaFree(c->io); cudaFree(c->io_i);
   cudaFree(c->count); cudaFree(c->cstart); cudaFree(c->bcstart); cudaFree(c->tile_sums);
-  cudaFree(c->raw); cudaFree(c->blevel); cudaFree(c->act); cudaFree(c->plist); cudaFree(c->ctl); cudaFree(c->xb);
+  cudaFree(c->raw); cudaFree(c->blevel); cudaFree(c->act); cudaFree(c->plist); cudaFree(c->actflag); cudaFree(c->ctl); cudaFree(c->xb);
   cudaFree(c->bmax_v); cudaFree(c->bmax_a); cudaFree(c->filled); cudaFree(c->nbl);
   cudaFree(c->buid); cudaFree(c->s.ap); cudaFree(c->s2.ap); cudaFree(c->s.err); cudaFree(c->s2.err);
   cudaFree(c->xs); cudaFree(c->pbak); cudaFree(c->in_se); cudaFree(c->in_re); cudaFree(c->ob);
@@ -874,11 +887,14 @@ rts_status rts_profile_read(rts_ctx* c, rts_profile* out, int32_t reset) {
   for (int k = 0; k < RTS_NUM_PHASES; ++k) {
     out->ms[k] = c->prof_ms[k];
     out->launches[k] = c->launches[k];
+    out->timed[k] = c->prof_timed[k];
   }
   out->kernels = c->kernels;
   if (reset) {
     memset(c->prof_ms, 0, sizeof c->prof_ms);
     memset(c->launches, 0, sizeof c->launches);
+    memset(c->prof_timed, 0, sizeof c->prof_timed);
+    memset(c->prof_seen, 0, sizeof c->prof_seen);
     c->kernels = 0;
   }
   return RTS_OK;

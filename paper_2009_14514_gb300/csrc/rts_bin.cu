@@ -17,16 +17,17 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-// Block coordinate floor((x - o) / edge).  The FP32 value is within 1e-3 block of the
-// exact one for grids up to 4096 blocks per axis; within 2e-3 of an integer the FP64
-// quotient decides, so the result is that of the double-precision definition.
+// Block coordinate floor((x - o) / edge).  The FP32 quotient t = (x - o) * (1 / edge)
+// carries three roundings, so it is within 3 * 2^-24 * t of the exact one; within
+// band (8 * 2^-24 * the largest coordinate of the grid, set on the host) of an integer
+// the FP64 quotient decides, so the result is that of the double-precision definition.
 __device__ __forceinline__ int block_coord(float x, float o, double od, float inv_e, double ed,
-                                           int n, int* bad) {
+                                           int n, float band, int* bad) {
   float t = (x - o) * inv_e;
   float f = floorf(t);
   float fr = t - f;
   double fd;
-  if (fr < 2e-3f || fr > 0.998f)
+  if (fr < band || fr > 1.0f - band)
     fd = floor(__ddiv_rn(__dsub_rn((double)x, od), ed));
   else
     fd = (double)f;
@@ -38,9 +39,9 @@ __device__ __forceinline__ int block_coord(float x, float o, double od, float in
 }
 
 __device__ __forceinline__ uint32_t block_key(const DevParams& P, float4 p, int* bad) {
-  int cx = block_coord(p.x, P.ox, P.oxd, P.inv_edge, P.edged, P.nx, bad);
-  int cy = block_coord(p.y, P.oy, P.oyd, P.inv_edge, P.edged, P.ny, bad);
-  int cz = block_coord(p.z, P.oz, P.ozd, P.inv_edge, P.edged, P.nz, bad);
+  int cx = block_coord(p.x, P.ox, P.oxd, P.inv_edge, P.edged, P.nx, P.key_band, bad);
+  int cy = block_coord(p.y, P.oy, P.oyd, P.inv_edge, P.edged, P.ny, P.key_band, bad);
+  int cz = block_coord(p.z, P.oz, P.ozd, P.inv_edge, P.edged, P.nz, P.key_band, bad);
   return ((uint32_t)cz * P.ny + cy) * P.nx + cx;
 }
 
@@ -225,19 +226,13 @@ __global__ void k_scan_apply(uint32_t* __restrict__ count, int nb, const uint32_
   }
   // the thread holding the last element writes the grand total
   if (base <= nb - 1 && nb - 1 < base + kScanItems) cstart[nb] = ex;
-  if (filled) {
-    int lane = threadIdx.x & 31;
-    int inc = nf;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      int t = __shfl_up_sync(0xffffffffu, inc, d);
-      if (lane >= d) inc += t;
-    }
-    int wtot = __shfl_sync(0xffffffffu, inc, 31);
-    int wbase = 0;
-    if (lane == 31 && wtot) wbase = atomicAdd(&ctl->n_filled, wtot);
-    wbase = __shfl_sync(0xffffffffu, wbase, 31);
-    int pos = wbase + inc - nf;
+  if (filled) {   // one atomic per CTA on the list counter
+    __shared__ uint32_t fbase;
+    uint32_t ftot;
+    const uint32_t fpre = block_excl_scan((uint32_t)nf, &ftot);
+    if (threadIdx.x == 0) fbase = ftot ? (uint32_t)atomicAdd(&ctl->n_filled, (int)ftot) : 0u;
+    __syncthreads();
+    uint32_t pos = fbase + fpre;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k)
       if (c[k]) filled[pos++] = (uint32_t)(base + k);
@@ -290,58 +285,75 @@ __global__ void k_canon_gather(int n, int nb, int max_per_block, const uint32_t*
                                const uint32_t* __restrict__ tsrc, PState src, PState dst,
                                uint32_t* __restrict__ key_out, Ctl* ctl, uint32_t stamp,
                                unsigned long long* bmax_v, unsigned long long* bmax_a) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  bool valid = q < n;
-  if (bmax_v) {
-    // every lane reaches the shuffles of block_max_merge
-    uint32_t b = valid ? tkey[q] : 0xffffffffu;
-    float v2 = 0.f, a2 = 0.f;
-    if (valid) {
-      float4 vi = src.v[tsrc[q]], ai = src.a[tsrc[q]];
-      if (src.ap) {  // PCISPH: total acceleration = non-pressure + pressure
-        float4 pa = src.ap[tsrc[q]];
-        ai.x += pa.x;
-        ai.y += pa.y;
-        ai.z += pa.z;
-      }
-      v2 = vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
-      a2 = ai.x * ai.x + ai.y * ai.y + ai.z * ai.z;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t b = 0xffffffffu, s = 0, u = 0;
+  bool ok = false;
+  if (q < n) {
+    b = tkey[q];
+    s = tsrc[q];
+    u = tuid[q];
+    ok = b < (uint32_t)nb && s < (uint32_t)n;
+    if (!ok) {
+      check_failed(ctl, kChkGather, b < (uint32_t)nb ? s : b);
+      b = 0xffffffffu;
     }
-    block_max_merge(b, valid, v2, stamp, bmax_v);
-    block_max_merge(b, valid, a2, stamp, bmax_a);
   }
-  if (!valid) return;
-  uint32_t b = tkey[q];
-  if (b >= (uint32_t)nb) {
-    check_failed(ctl, kChkGather, b);
-    return;
+  // the payload loads do not depend on the in-block rank: issue them first
+  float4 px = make_float4(0.f, 0.f, 0.f, 0.f), pv = px, pa = px, pap = px;
+  float prho = 0.f, pprs = 0.f, perr = 0.f;
+  int32_t pkl = 0, pval = 0, plev = 0, pnbr = 0;
+  if (ok) {
+    px = src.x[s];
+    if (src.v) {
+      pv = src.v[s];
+      pa = src.a[s];
+      prho = src.rho[s];
+      pprs = src.prs[s];
+      pkl = src.klast[s];
+      pval = src.valid[s];
+      plev = src.level[s];
+      pnbr = src.nbr[s];
+      if (src.ap) {
+        pap = src.ap[s];
+        perr = src.err[s];
+      }
+    }
   }
-  uint32_t beg = cstart[b], end = cstart[b + 1];
+  if (bmax_v) {  // every lane reaches the shuffles of block_max_merge
+    float v2 = 0.f, a2 = 0.f;
+    if (ok) {
+      const float ax = pa.x + pap.x, ay = pa.y + pap.y, az = pa.z + pap.z;  // PCISPH: total
+      v2 = pv.x * pv.x + pv.y * pv.y + pv.z * pv.z;
+      a2 = src.ap ? ax * ax + ay * ay + az * az : pa.x * pa.x + pa.y * pa.y + pa.z * pa.z;
+    }
+    block_max_merge(b, ok, v2, stamp, bmax_v);
+    block_max_merge(b, ok, a2, stamp, bmax_a);
+  }
+  if (!ok) return;
+  const uint32_t beg = cstart[b], end = cstart[b + 1];
   if (q == (int)beg && (int)(end - beg) > max_per_block) set_status(ctl, RTS_ERR_CAPACITY);
-  uint32_t u = tuid[q];
   uint32_t rank = 0;
   for (uint32_t r = beg; r < end; ++r) rank += (tuid[r] < u) ? 1u : 0u;
-  uint32_t f = beg + rank;
-  uint32_t s = tsrc[q];
-  if (s >= (uint32_t)n || f >= end) {
-    check_failed(ctl, kChkGather, s);
+  const uint32_t f = beg + rank;
+  if (f >= end) {
+    check_failed(ctl, kChkGather, f);
     return;
   }
   key_out[f] = b;
   dst.uid[f] = u;
-  dst.x[f] = src.x[s];
+  dst.x[f] = px;
   if (src.v) {
-    dst.v[f] = src.v[s];
-    dst.a[f] = src.a[s];
-    dst.rho[f] = src.rho[s];
-    dst.prs[f] = src.prs[s];
-    dst.klast[f] = src.klast[s];
-    dst.valid[f] = src.valid[s];
-    dst.level[f] = src.level[s];
-    dst.nbr[f] = src.nbr[s];
+    dst.v[f] = pv;
+    dst.a[f] = pa;
+    dst.rho[f] = prho;
+    dst.prs[f] = pprs;
+    dst.klast[f] = pkl;
+    dst.valid[f] = pval;
+    dst.level[f] = plev;
+    dst.nbr[f] = pnbr;
     if (src.ap) {
-      dst.ap[f] = src.ap[s];
-      dst.err[f] = src.err[s];
+      dst.ap[f] = pap;
+      dst.err[f] = perr;
     }
   }
 }
@@ -365,6 +377,7 @@ static void next_stamp(rts_ctx* c) {
     cudaMemsetAsync(c->bmax_a, 0, sizeof(unsigned long long) * nb, c->stream);
     cudaMemsetAsync(c->raw, 0, sizeof(uint32_t) * nb, c->stream);
     cudaMemsetAsync(c->blevel, 0, sizeof(uint32_t) * nb, c->stream);
+    cudaMemsetAsync(c->actflag, 0, sizeof(uint32_t) * nb, c->stream);
     c->stamp = 1;
   }
 }

@@ -18,6 +18,7 @@ struct DevParams {
   int nx, ny, nz;
   int nblocks;
   int max_per_block;
+  float key_band;    // FP32 block-coordinate band that defers to FP64 (see block_coord)
   // cubic spline kernel, h = r / 2, support r
   float r, r2, r2_lo, r2_hi, h, inv_h, sigma, sigma_h;  // sigma_h = sigma / h
   double r2d;
@@ -174,6 +175,7 @@ struct rts_ctx {
   uint32_t* filled;               // list of filled blocks of the current pass
   uint32_t* act;      // active block list
   uint32_t* plist;    // evaluated particles (sorted-order indices), any order
+  uint32_t* actflag;  // per block: stamp of the pass that listed it as active
   rts::Ctl* ctl;
   rts::Ctl* h_ctl;    // pinned host mirror
 
@@ -212,6 +214,8 @@ struct rts_ctx {
   int64_t launches[RTS_NUM_PHASES];
   int prof;
   double prof_ms[RTS_NUM_PHASES];
+  int64_t prof_timed[RTS_NUM_PHASES];
+  int64_t prof_seen[RTS_NUM_PHASES];
   cudaEvent_t* ev;    // 2 * kEvPairs events
   int* ev_phase;
   int nev;

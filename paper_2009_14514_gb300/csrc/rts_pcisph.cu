@@ -290,9 +290,21 @@ __global__ void k_se_reduce(DevParams P, int n, const uint32_t* __restrict__ key
     mx = max(mx, __shfl_down_sync(kFullMask, mx, o));
     fx += __shfl_down_sync(kFullMask, fx, o);
   }
+  // one atomic per counter and CTA (256 threads): the counters are shared by every CTA
+  __shared__ unsigned smx[8];
+  __shared__ unsigned long long sfx[8];
   if ((threadIdx.x & 31) == 0) {
-    atomicMax(&ctl->err_max_bits, mx);
-    atomicAdd(&ctl->err_sum_fx, fx);
+    smx[threadIdx.x >> 5] = mx;
+    sfx[threadIdx.x >> 5] = fx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      mx = max(mx, smx[k]);
+      fx += sfx[k];
+    }
+    if (mx) atomicMax(&ctl->err_max_bits, mx);
+    if (fx) atomicAdd(&ctl->err_sum_fx, fx);
   }
 }
 
@@ -564,7 +576,17 @@ __global__ void k_pglobal_max(int n, PState s, Ctl* ctl) {
     vm = fmax(vm, __shfl_down_sync(kFullMask, vm, o));
     am = fmax(am, __shfl_down_sync(kFullMask, am, o));
   }
+  __shared__ double svm[8], sam[8];   // one atomic per counter and CTA (256 threads)
   if ((threadIdx.x & 31) == 0) {
+    svm[threadIdx.x >> 5] = vm;
+    sam[threadIdx.x >> 5] = am;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      vm = fmax(vm, svm[k]);
+      am = fmax(am, sam[k]);
+    }
     atomicMax(&ctl->vmax2_bits, (unsigned long long)__double_as_longlong(vm));
     atomicMax(&ctl->amax2_bits, (unsigned long long)__double_as_longlong(am));
   }

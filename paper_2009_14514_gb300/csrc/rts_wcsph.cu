@@ -78,107 +78,134 @@ __global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled, 
 }
 
 // R_min (Section 4.2: a filled block takes the smallest level among itself and its
-// filled 26 neighbours, one Jacobi pass), or the forced / global level; then, with
-// mode >= 0, Algorithm 1's per-particle bookkeeping (validity, pre-emption on a level
-// change) and the work list of blocks holding an evaluated particle.
-__global__ void k_block_activity(DevParams P, int mode, int level_g, int mult_g, long long k1,
-                                 const uint32_t* __restrict__ filled, Ctl* ctl,
-                                 const uint32_t* __restrict__ cstart,
-                                 const uint32_t* __restrict__ raw, uint32_t* __restrict__ blevel,
-                                 uint32_t stamp, PState s, uint8_t* __restrict__ cflag,
-                                 uint32_t* __restrict__ act, uint32_t* __restrict__ plist) {
+// filled 26 neighbours, one Jacobi pass), or the forced / global level.
+__global__ void k_block_rmin(DevParams P, int mode, int level_g,
+                             const uint32_t* __restrict__ filled, const Ctl* ctl,
+                             const uint32_t* __restrict__ raw, uint32_t* __restrict__ blevel,
+                             uint32_t stamp) {
   const int nf = ctl->n_filled;
-  const int lane = threadIdx.x & 31;
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x; base < nf; base += stride) {
-    const int t = base + threadIdx.x;
-    int ncomp = 0;
-    uint32_t b = 0;
-    if (t < nf) {
-      b = filled[t];
-      int L;
-      if (mode == kActGlobal) {
-        L = level_g;
-      } else if (P.force_level >= 0) {
-        L = P.force_level;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    const uint32_t b = filled[t];
+    int L;
+    if (mode == kActGlobal) {
+      L = level_g;
+    } else if (P.force_level >= 0) {
+      L = P.force_level;
+    } else {
+      L = (int)(raw[b] & 0xffu);
+      const int bx = b % P.nx, r = b / P.nx, by = r % P.ny, bz = r / P.ny;
+      for (int dz = -1; dz <= 1; ++dz) {
+        const int cz = bz + dz;
+        if (cz < 0 || cz >= P.nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int cy = by + dy;
+          if (cy < 0 || cy >= P.ny) continue;
+          const uint32_t row = ((uint32_t)cz * P.ny + cy) * P.nx;
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int cx = bx + dx;
+            if (cx < 0 || cx >= P.nx) continue;
+            const uint32_t rc = raw[row + cx];
+            if ((rc >> 8) == stamp && (int)(rc & 0xffu) < L) L = (int)(rc & 0xffu);
+          }
+        }
+      }
+    }
+    blevel[b] = (stamp << 8) | (uint32_t)L;
+  }
+}
+
+// Algorithm 1's per-particle bookkeeping, one thread per particle in block order:
+// validity -= 1; compute iff validity <= 0 or the block's level differs from the
+// particle's (pre-emption); a computing particle takes the block's level and a new
+// validity.  Work lists: the evaluated particles, and the blocks holding one (each run of
+// equal blocks in a warp claims its block once through a stamped flag).  List positions
+// and counters are aggregated per CTA: one atomic per counter and CTA.
+constexpr int kActThreads = 1024;
+
+__global__ void __launch_bounds__(kActThreads) k_particle_activity(
+    DevParams P, int mode, int mult_g, long long k1, int n, const uint32_t* __restrict__ key,
+    const uint32_t* __restrict__ blevel, uint32_t stamp, PState s, uint8_t* __restrict__ cflag,
+    uint32_t* __restrict__ actflag, uint32_t* __restrict__ act, uint32_t* __restrict__ plist,
+    Ctl* ctl) {
+  __shared__ uint32_t wp[kActThreads / 32], wa[kActThreads / 32], cbase[2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  unsigned long long evals = 0, ablocks = 0;   // thread 0's CTA totals
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    const bool valid = i < n;
+    bool c = false;
+    uint32_t b = 0xffffffffu;
+    if (valid) {
+      b = key[i];
+      const uint32_t rec = blevel[b];
+      int L = (int)(rec & 0xffu);
+      if ((rec >> 8) != stamp || L >= P.n_levels) {
+        check_failed(ctl, kChkLevel, rec);
+        L = 0;
+      }
+      const int mb = mode == kActGlobal ? mult_g : P.mult[L];
+      // validity of a particle that starts a true step now (level-aligned variant: up
+      // to the next multiple of the multiplier)
+      const int vnew = (mode != kActGlobal && P.level_clock) ? mb - (int)(k1 % mb) : mb;
+      if (mode == kActRegional) {
+        int val = s.valid[i] - 1;
+        int li = s.level[i];
+        if (li >= P.n_levels) {
+          check_failed(ctl, kChkLevel, (unsigned)li);
+          li = -1;
+        }
+        if (val <= 0 || li < 0 || P.mult[li] != mb) {
+          c = true;
+          s.level[i] = L;
+          val = vnew;
+        }
+        s.valid[i] = val;
       } else {
-        L = (int)(raw[b] & 0xffu);
-        int bx = b % P.nx, r = b / P.nx, by = r % P.ny, bz = r / P.ny;
-        for (int dz = -1; dz <= 1; ++dz) {
-          int cz = bz + dz;
-          if (cz < 0 || cz >= P.nz) continue;
-          for (int dy = -1; dy <= 1; ++dy) {
-            int cy = by + dy;
-            if (cy < 0 || cy >= P.ny) continue;
-            for (int dx = -1; dx <= 1; ++dx) {
-              int cx = bx + dx;
-              if (cx < 0 || cx >= P.nx) continue;
-              uint32_t rc = raw[((uint32_t)cz * P.ny + cy) * P.nx + cx];
-              if ((rc >> 8) == stamp && (int)(rc & 0xffu) < L) L = (int)(rc & 0xffu);
-            }
-          }
-        }
+        c = true;
+        s.level[i] = L;
+        s.valid[i] = vnew;
       }
-      blevel[b] = (stamp << 8) | (uint32_t)L;
-      if (mode >= 0) {
-        const int mb = mode == kActGlobal ? mult_g : P.mult[L];
-        // validity of a particle that starts a true step now (level-aligned variant:
-        // up to the next multiple of the multiplier)
-        const int vnew = (mode != kActGlobal && P.level_clock) ? mb - (int)(k1 % mb) : mb;
-        for (uint32_t i = cstart[b]; i < cstart[b + 1]; ++i) {
-          int c;
-          if (mode == kActRegional) {
-            int val = s.valid[i] - 1;
-            int li = s.level[i];
-            if (li >= P.n_levels) {
-              check_failed(ctl, kChkLevel, (unsigned)li);
-              li = -1;
-            }
-            if (val <= 0 || li < 0 || P.mult[li] != mb) {
-              c = 1;
-              s.level[i] = L;
-              val = vnew;
-            } else {
-              c = 0;
-            }
-            s.valid[i] = val;
-          } else {
-            c = 1;
-            s.level[i] = L;
-            s.valid[i] = vnew;
-          }
-          cflag[i] = (uint8_t)c;
-          ncomp += c;
-        }
-      }
+      cflag[i] = c ? 1 : 0;
     }
-    if (mode >= 0) {
-      unsigned m = __ballot_sync(kFull, ncomp > 0);
-      unsigned long long tot = ncomp;
-#pragma unroll
-      for (int o = 16; o; o >>= 1) tot += __shfl_down_sync(kFull, tot, o);
-      int wb = 0;
-      if (lane == 0 && m) {
-        wb = atomicAdd(&ctl->n_act, __popc(m));
-        atomicAdd(&ctl->evals, tot);
-        atomicAdd(&ctl->act_blocks, (unsigned long long)__popc(m));
-      }
-      wb = __shfl_sync(kFull, wb, 0);
-      if (ncomp > 0) act[wb + __popc(m & ((1u << lane) - 1u))] = b;
-      // the block's evaluated particles into the particle work list
-      int inc = ncomp;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int tv = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc += tv;
-      }
-      int pb = 0;
-      if (lane == 31 && inc > 0) pb = atomicAdd(&ctl->n_plist, inc);
-      pb = __shfl_sync(kFull, pb, 31) + inc - ncomp;
-      if (ncomp > 0)
-        for (uint32_t i = cstart[b]; i < cstart[b + 1]; ++i)
-          if (cflag[i]) plist[pb++] = i;
+    const unsigned m = __ballot_sync(kFull, c);
+    // runs of equal blocks in lane order; a run with an evaluated particle claims its block
+    const uint32_t prevb = __shfl_up_sync(kFull, b, 1);
+    const bool head = valid && (lane == 0 || prevb != b);
+    const unsigned heads = __ballot_sync(kFull, head);
+    const unsigned after = heads & ~(below | (1u << lane));
+    const int next = after ? __ffs(after) - 1 : 32;
+    const unsigned span = (next - lane >= 32) ? (kFull << lane) : (((1u << (next - lane)) - 1u) << lane);
+    bool claim = false;
+    if (head && (m & span)) claim = atomicExch(&actflag[b], stamp) != stamp;
+    const unsigned cm = __ballot_sync(kFull, claim);
+    if (lane == 0) {
+      wp[w] = __popc(m);
+      wa[w] = __popc(cm);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // CTA prefix of the warp counts, one atomic per list
+      uint32_t tp = 0, ta = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        const uint32_t a = wp[k], c2 = wa[k];
+        wp[k] = tp;
+        wa[k] = ta;
+        tp += a;
+        ta += c2;
+      }
+      cbase[0] = tp ? (uint32_t)atomicAdd(&ctl->n_plist, (int)tp) : 0u;
+      cbase[1] = ta ? (uint32_t)atomicAdd(&ctl->n_act, (int)ta) : 0u;
+      evals += tp;
+      ablocks += ta;
+    }
+    __syncthreads();
+    if (c) plist[cbase[0] + wp[w] + __popc(m & below)] = (uint32_t)i;
+    if (claim) act[cbase[1] + wa[w] + __popc(cm & below)] = b;
+    __syncthreads();   // the shared counts are reused by the next round
+  }
+  if (threadIdx.x == 0 && evals) {
+    atomicAdd(&ctl->evals, evals);
+    atomicAdd(&ctl->act_blocks, ablocks);
   }
 }
 
@@ -491,9 +518,25 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
     tests += __shfl_down_sync(kFull, tests, o);
     kept_tests += __shfl_down_sync(kFull, kept_tests, o);
   }
-  if (lane == 0 && pairs) atomicAdd(&ctl->pairs, pairs);
-  if (lane == 0 && tests) atomicAdd(&ctl->cands, tests);
-  if (lane == 0 && kept_tests) atomicAdd(&ctl->kept, kept_tests);
+  // one atomic per counter and CTA (the counters are shared by every CTA)
+  __shared__ unsigned long long red[3][kNbThreads / 32];
+  if (lane == 0) {
+    red[0][wib] = pairs;
+    red[1][wib] = tests;
+    red[2][wib] = kept_tests;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, b = 0, c = 0;
+    for (int k = 0; k < kNbThreads / 32; ++k) {
+      a += red[0][k];
+      b += red[1][k];
+      c += red[2][k];
+    }
+    if (a) atomicAdd(&ctl->pairs, a);
+    if (b) atomicAdd(&ctl->cands, b);
+    if (c) atomicAdd(&ctl->kept, c);
+  }
 }
 
 // Force pass (Algorithm 1, "update F^{p,v,g}"): every evaluated particle walks the
@@ -616,7 +659,17 @@ __global__ void k_global_max(int n, const float4* __restrict__ v, const float4* 
     vm = fmax(vm, __shfl_down_sync(kFull, vm, o));
     am = fmax(am, __shfl_down_sync(kFull, am, o));
   }
+  __shared__ double svm[8], sam[8];   // one atomic per counter and CTA (256 threads)
   if ((threadIdx.x & 31) == 0) {
+    svm[threadIdx.x >> 5] = vm;
+    sam[threadIdx.x >> 5] = am;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      vm = fmax(vm, svm[k]);
+      am = fmax(am, sam[k]);
+    }
     atomicMax(&ctl->vmax2_bits, (unsigned long long)__double_as_longlong(vm));
     atomicMax(&ctl->amax2_bits, (unsigned long long)__double_as_longlong(am));
   }
@@ -685,9 +738,15 @@ static_assert(offsetof(Ctl, n_plist) == offsetof(Ctl, n_act) + sizeof(int),
 rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1) {
   cudaMemsetAsync(&c->ctl->n_act, 0, 2 * sizeof(int), c->stream);   // n_act, n_plist
   note_launch(c, 1);
-  k_block_activity<<<filled_grid(), 256, 0, c->stream>>>(c->dp, mode, level_g, mult_g, (long long)k1, c->filled,
-                                                         c->ctl, c->cstart, c->raw, c->blevel,
-                                                         c->stamp, c->s, c->cflag, c->act, c->plist);
+  k_block_rmin<<<filled_grid(), 256, 0, c->stream>>>(c->dp, mode, level_g, c->filled, c->ctl,
+                                                     c->raw, c->blevel, c->stamp);
+  if (mode >= 0 && c->n > 0) {
+    note_launch(c, 1);
+    const int g = (c->n + kActThreads - 1) / kActThreads;
+    k_particle_activity<<<g, kActThreads, 0, c->stream>>>(c->dp, mode, mult_g, (long long)k1, c->n,
+                                                   c->key, c->blevel, c->stamp, c->s, c->cflag,
+                                                   c->actflag, c->act, c->plist, c->ctl);
+  }
   return RTS_OK;
 }
 

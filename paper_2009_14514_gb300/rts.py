@@ -89,11 +89,13 @@ class RtsPcisphInfo(C.Structure):
 
 
 class RtsProfile(C.Structure):
-    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_int64 * 8), ("kernels", C.c_int64)]
+    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_int64 * 8), ("kernels", C.c_int64),
+                ("timed", C.c_int64 * 8)]
 
     def as_dict(self):
         return {"ms": dict(zip(PHASES, list(self.ms))),
-                "launches": dict(zip(PHASES, list(self.launches))), "kernels": self.kernels}
+                "launches": dict(zip(PHASES, list(self.launches))), "kernels": self.kernels,
+                "timed": dict(zip(PHASES, list(self.timed)))}
 
 
 def make_params(d: dict) -> RtsParams:
