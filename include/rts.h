@@ -105,6 +105,9 @@ typedef struct rts_params {
      1: level-aligned variant: validity = mult - (k mod mult), so every particle of level
      L computes at the substeps k that are multiples of mult[L] (plus pre-emptions).   */
   int32_t level_clock;
+  /* Tait stiffness B; 0 derives it from the sound speed, B = c_s^2 rho0 / gamma (the
+     viscosity keeps using c_s).  A separate value lets B be varied on its own.        */
+  float tait_B;
 } rts_params;
 
 /* Counters accumulated over one rts_advance call. */

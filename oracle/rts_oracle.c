@@ -229,7 +229,7 @@ double orci_particle_mass(const orc_params* P) { return P->rho0 * P->s * P->s * 
 /* Tait equation of state, p = B ((rho / rho0)^gamma - 1), B = c^2 rho0 / gamma,
  * clamped at zero. */
 static double tait(const orc_params* P, double rho) {
-  double B = P->c_s * P->c_s * P->rho0 / P->gamma;
+  double B = P->tait_B > 0.0 ? P->tait_B : P->c_s * P->c_s * P->rho0 / P->gamma;
   double p = B * (pow(rho / P->rho0, P->gamma) - 1.0);
   return p > 0.0 ? p : 0.0;
 }

@@ -60,6 +60,7 @@ typedef struct orc_params {
   /* WCSPH activity clock: 0 validity = level multiplier (Algorithm 1); 1 validity up to
    * the next multiple of the multiplier (level-aligned variant). */
   int32_t level_clock;
+  double tait_B;           /* Tait stiffness; 0: c_s^2 rho0 / gamma */
 } orc_params;
 
 /* WCSPH state in user order. */

@@ -84,6 +84,7 @@ static const char* validate(const rts_params* p, int32_t n, int32_t nb) {
   if (p->max_neighbors < 8 || p->max_neighbors > 1024) return "max_neighbors must be in [8, 1024]";
   if (p->wall_project != 0 && p->wall_project != 1) return "wall_project must be 0 or 1";
   if (p->level_clock != 0 && p->level_clock != 1) return "level_clock must be 0 or 1";
+  if (!(p->tait_B >= 0.f) || !(p->tait_B < 1e12f)) return "tait_B must be in [0, 1e12)";
   if (p->wall_project)
     for (int k = 0; k < 3; ++k)
       if (!(p->wall_lo[k] < p->wall_hi[k])) return "wall_lo must be below wall_hi on every axis";
@@ -137,7 +138,7 @@ static void make_dev_params(const rts_params& p, DevParams& d) {
   d.m = (float)((double)p.rho0 * s * s * s);
   d.rho0 = p.rho0;
   d.inv_rho0 = (float)(1.0 / (double)p.rho0);
-  d.tait_B = (float)((double)p.c_s * p.c_s * p.rho0 / p.gamma);
+  d.tait_B = p.tait_B > 0.f ? p.tait_B : (float)((double)p.c_s * p.c_s * p.rho0 / p.gamma);
   d.gamma = p.gamma;
   d.gamma_is_7 = p.gamma == 7.0f;
   d.visc_coef = (float)(2.0 * p.visc_alpha * h * p.c_s);

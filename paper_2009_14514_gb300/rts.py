@@ -54,6 +54,7 @@ class RtsParams(C.Structure):
         ("wall_lo", C.c_float * 3),
         ("wall_hi", C.c_float * 3),
         ("level_clock", C.c_int32),
+        ("tait_B", C.c_float),
     ]
 
 
@@ -130,6 +131,7 @@ def make_params(d: dict) -> RtsParams:
         P.wall_lo[k] = d.get("wall_lo", [0.0] * 3)[k]
         P.wall_hi[k] = d.get("wall_hi", [0.0] * 3)[k]
     P.level_clock = int(d.get("level_clock", 0))
+    P.tait_B = float(d.get("tait_B", 0.0))
     return P
 
 
