@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--small", action="store_true", help="8k-particle dam break (quick check)")
     ap.add_argument("--no-pcisph", action="store_true", help="skip the PCISPH pool-drop section")
     ap.add_argument("--pcisph-sim", type=float, default=1.0, help="simulated seconds of PCISPH")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiable rollout")
     ap.add_argument("--window", type=int, default=8, help="base substeps per --profile-case step")
     ap.add_argument("--profile-case", action="store_true",
                     help="short run for ncu: 1M jittered lattice with a seeded dynamic state, "
@@ -312,6 +313,49 @@ def run_pcisph(args, torch, rts, flush):
     return out
 
 
+def run_diff(args, torch):
+    """The differentiable rollout: 250k-particle dam break, 100 steps of global constant
+    stepping, checkpoints every 10 steps; the loss |mean(x_T) - target|^2 + mean
+    |rho_T - rho0| / rho0 and its gradient with respect to the 250k x 3 initial
+    velocities, the Tait stiffness and the viscosity coefficient.  Forward and backward
+    timed with CUDA events (two warm-up passes first)."""
+    from paper_2009_14514_gb300 import diff, scenes
+    sc = scenes.diff_dam_break_250k()
+    steps, ckpt = 100, 10
+    eng = diff.DiffEngine(sc.params, sc.x, sc.xb, steps, ckpt_every=ckpt)
+    v0 = torch.tensor(scenes.seeded_velocities(sc.n, seed=777, scale=0.3), device="cuda")
+    B0 = sc.params["c_s"] ** 2 * sc.params["rho0"] / sc.params["gamma"]
+    target = [0.7, 0.3, 0.2]
+    stream = torch.cuda.current_stream()
+    fw, bw = [], []
+    for it in range(4):
+        vt = v0.clone().requires_grad_(True)
+        B = torch.tensor(B0, dtype=torch.float64, device="cuda", requires_grad=True)
+        a = torch.tensor(sc.params["visc_alpha"], dtype=torch.float64, device="cuda",
+                         requires_grad=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        x, rho = diff.rollout(eng, vt, B, a)
+        e1.record(stream)
+        L = diff.centroid_density_loss(x, rho, target)
+        L.backward()
+        e2.record(stream)
+        e2.synchronize()
+        if it >= 2:
+            fw.append(e0.elapsed_time(e1))
+            bw.append(e1.elapsed_time(e2))
+    f, b = sum(fw) / len(fw), sum(bw) / len(bw)
+    gnorm = float(vt.grad.norm())
+    eng.close()
+    return {"workload": f"{sc.name}: {sc.n} fluid + {sc.nb} boundary, {steps} steps of dt_b = "
+                        f"{sc.params['dt_b']} (global constant), checkpoints every {ckpt}",
+            "forward_ms": f, "backward_ms": b,
+            "forward_particle_steps_per_s": sc.n * steps / (f / 1e3),
+            "gradient_particle_steps_per_s": sc.n * steps / ((f + b) / 1e3),
+            "loss": float(L.detach()), "grad_v0_norm": gnorm,
+            "grad_B": float(B.grad), "grad_alpha": float(a.grad)}
+
+
 def run_e2e(sc, args, torch, rts):
     """End to end through the C ABI: every step uploads the full state from pinned host
     memory (rts_set_state), advances one step, and copies the full state back to pinned
@@ -451,6 +495,7 @@ def main():
                             name="timed_constant")
     e2e = None if args.no_e2e else run_e2e(sc, args, torch, rts)
     pcisph = None if (args.no_pcisph or args.small) else run_pcisph(args, torch, rts, flush)
+    dres = None if (args.no_diff or args.small) else run_diff(args, torch)
 
     # roofline of the dominant neighbour kernel (FP32 ALU bound)
     prof = ours["prof"]
@@ -516,6 +561,8 @@ def main():
         line["e2e"] = e2e
     if pcisph is not None:
         line["pcisph"] = pcisph
+    if dres is not None:
+        line["differentiable"] = dres
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle(sc)
     if rank == 0:

@@ -108,6 +108,9 @@ typedef struct rts_params {
   /* Tait stiffness B; 0 derives it from the sound speed, B = c_s^2 rho0 / gamma (the
      viscosity keeps using c_s).  A separate value lets B be varied on its own.        */
   float tait_B;
+  /* 0: the Tait pressure is clamped at zero (free-surface particles do not attract);
+     1: negative pressure is kept (the equation of state is then smooth everywhere).  */
+  int32_t tait_no_clamp;
 } rts_params;
 
 /* Counters accumulated over one rts_advance call. */
@@ -283,6 +286,47 @@ int64_t rts_num_blocks(const rts_ctx* ctx);
 int64_t rts_substep_index(const rts_ctx* ctx);   /* completed base substeps */
 const char* rts_last_error(const rts_ctx* ctx);  /* never NULL; ctx may be NULL */
 rts_status rts_destroy(rts_ctx* ctx);            /* NULL is a no-op */
+
+/* ------------------------------------------------ differentiable rollout --- */
+/* No counterpart in the paper: a WCSPH rollout under global constant stepping at dt_b
+ * (every particle active every step; the Serna predictor-corrector of Section 4.1 and the
+ * same physics, boundary particles and container as the regional path) with its
+ * hand-written adjoint, for gradients of a loss of the final state with respect to the
+ * initial velocities, the Tait stiffness B and the viscosity coefficient alpha.  The
+ * priming evaluation a_0 = A(x_0, v_0) starts the rollout; after n_steps steps it returns
+ * x_T and rho_T = rho(x_T) (summation density at x_T).  Particles keep the caller's order.
+ * The backward pass stores (x, v, a) every ckpt_every steps during the forward pass and
+ * recomputes each segment (its evaluation points, neighbour lists and container masks)
+ * before reversing it. */
+typedef struct rts_diff rts_diff;
+
+/* params: as for rts_init (scheme RTS_WCSPH; mode, levels and c_s's role in B are ignored:
+ * B and alpha are given per forward call; the viscosity uses c_s).  x0: n_fluid x 3 initial
+ * positions; xb: n_boundary x 3 static boundary positions (host or device, copied).
+ * Device memory grows with n_fluid x max_neighbors x ckpt_every.
+ * Errors: RTS_ERR_ARG, RTS_ERR_OOM, RTS_ERR_CUDA, RTS_ERR_DOMAIN (a boundary particle
+ * outside the grid); the message is rts_last_error(NULL). */
+rts_status rts_diff_create(const rts_params* params, int32_t n_fluid, const float* x0,
+                           int32_t n_boundary, const float* xb, int32_t n_steps,
+                           int32_t ckpt_every, void* cuda_stream, rts_diff** out);
+
+/* Run the rollout from (x0, v0) with stiffness tait_B and viscosity visc_alpha.  v0:
+ * n x 3 (host or device); x_out (n x 3) and rho_out (n) may be NULL.  Synchronises.
+ * Errors: RTS_ERR_ARG, RTS_ERR_DOMAIN (a particle left the grid), RTS_ERR_CAPACITY (a
+ * neighbour list exceeded max_neighbors), RTS_ERR_CUDA; sticky (RTS_ERR_STATE after). */
+rts_status rts_diff_forward(rts_diff* d, const float* v0, float tait_B, float visc_alpha,
+                            float* x_out, float* rho_out);
+
+/* Gradients for the adjoints gx = dL/dx_T (n x 3) and grho = dL/drho_T (n) of the last
+ * forward (either may be NULL for zero): gv0 = dL/dv0 (n x 3, host or device), *gB =
+ * dL/dB and *galpha = dL/dalpha (host doubles, may be NULL).  Synchronises; the forward
+ * must be run again before the next backward.  Errors: RTS_ERR_STATE (no forward),
+ * RTS_ERR_ARG, RTS_ERR_CUDA. */
+rts_status rts_diff_backward(rts_diff* d, const float* gx, const float* grho, float* gv0,
+                             double* gB, double* galpha);
+
+const char* rts_diff_last_error(const rts_diff* d);
+void rts_diff_destroy(rts_diff* d);
 
 #ifdef __cplusplus
 }

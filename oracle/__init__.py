@@ -52,6 +52,7 @@ class OrcParams(C.Structure):
         ("wall_hi", C.c_double * 3),
         ("level_clock", C.c_int32),
         ("tait_B", C.c_double),
+        ("tait_no_clamp", C.c_int32),
     ]
 
 
@@ -99,6 +100,7 @@ def make_params(d: dict) -> OrcParams:
     P.wall_project = int(d.get("wall_project", 0))
     P.level_clock = int(d.get("level_clock", 0))
     P.tait_B = _f32(d.get("tait_B", 0.0))
+    P.tait_no_clamp = int(d.get("tait_no_clamp", 0))
     for k in range(3):
         P.wall_lo[k] = _f32(d.get("wall_lo", [0.0] * 3)[k])
         P.wall_hi[k] = _f32(d.get("wall_hi", [0.0] * 3)[k])

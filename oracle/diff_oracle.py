@@ -144,7 +144,7 @@ class DiffRollout:
         Pbar = np.bincount(I, Sbar, minlength=n)
         g = P.gamma
         ratio = rho / P.rho0
-        posp = p > 0.0
+        posp = (p > 0.0) | bool(P.tait_no_clamp)
         dPdrho = np.where(posp, g * B * ratio ** (g - 1.0) / P.rho0 / rho ** 2 - 2.0 * p / rho ** 3, 0.0)
         dPdB = np.where(posp, (ratio ** g - 1.0) / rho ** 2, 0.0)
         # d Pi / d rho_i: -Pi / (rho_i + rho_j); a boundary neighbour lends rho_i itself

@@ -231,7 +231,7 @@ double orci_particle_mass(const orc_params* P) { return P->rho0 * P->s * P->s * 
 static double tait(const orc_params* P, double rho) {
   double B = P->tait_B > 0.0 ? P->tait_B : P->c_s * P->c_s * P->rho0 / P->gamma;
   double p = B * (pow(rho / P->rho0, P->gamma) - 1.0);
-  return p > 0.0 ? p : 0.0;
+  return (p > 0.0 || P->tait_no_clamp) ? p : 0.0;
 }
 
 /* rho_i = m W(0) + sum_{j in N(i)} m W(|x_i - x_j|), fluid and boundary j. */

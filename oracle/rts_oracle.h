@@ -61,6 +61,7 @@ typedef struct orc_params {
    * the next multiple of the multiplier (level-aligned variant). */
   int32_t level_clock;
   double tait_B;           /* Tait stiffness; 0: c_s^2 rho0 / gamma */
+  int32_t tait_no_clamp;   /* 1: negative Tait pressure kept */
 } orc_params;
 
 /* WCSPH state in user order. */

@@ -59,7 +59,7 @@ static void level_thresholds(const rts_params& p, double* vthr2, double* athr2, 
   }
 }
 
-static const char* validate(const rts_params* p, int32_t n, int32_t nb) {
+const char* rts::validate_params(const rts_params* p, int32_t n, int32_t nb) {
   if (!p) return "params is NULL";
   if (p->scheme != RTS_WCSPH && p->scheme != RTS_PCISPH) return "scheme must be RTS_WCSPH or RTS_PCISPH";
   if (p->mode < 0 || p->mode > 2) return "mode must be 0, 1 or 2";
@@ -85,6 +85,7 @@ static const char* validate(const rts_params* p, int32_t n, int32_t nb) {
   if (p->wall_project != 0 && p->wall_project != 1) return "wall_project must be 0 or 1";
   if (p->level_clock != 0 && p->level_clock != 1) return "level_clock must be 0 or 1";
   if (!(p->tait_B >= 0.f) || !(p->tait_B < 1e12f)) return "tait_B must be in [0, 1e12)";
+  if (p->tait_no_clamp != 0 && p->tait_no_clamp != 1) return "tait_no_clamp must be 0 or 1";
   if (p->wall_project)
     for (int k = 0; k < 3; ++k)
       if (!(p->wall_lo[k] < p->wall_hi[k])) return "wall_lo must be below wall_hi on every axis";
@@ -99,7 +100,7 @@ static const char* validate(const rts_params* p, int32_t n, int32_t nb) {
   return nullptr;
 }
 
-static void make_dev_params(const rts_params& p, DevParams& d) {
+void rts::make_dev_params(const rts_params& p, DevParams& d) {
   memset(&d, 0, sizeof(d));
   d.ox = p.domain_min[0];
   d.oy = p.domain_min[1];
@@ -148,6 +149,7 @@ static void make_dev_params(const rts_params& p, DevParams& d) {
   d.gz = p.gravity[2];
   d.wall_project = p.wall_project;
   d.level_clock = p.level_clock;
+  d.no_clamp = p.tait_no_clamp;
   for (int k = 0; k < 3; ++k) {
     d.wlo[k] = p.wall_lo[k];
     d.whi[k] = p.wall_hi[k];
@@ -480,7 +482,7 @@ rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, c
                     int32_t n_boundary, const float* xb, void* cuda_stream, rts_ctx** out) {
   if (!out) return fail(nullptr, RTS_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (const char* why = validate(params, n_fluid, n_boundary)) return fail(nullptr, RTS_ERR_ARG, why);
+  if (const char* why = validate_params(params, n_fluid, n_boundary)) return fail(nullptr, RTS_ERR_ARG, why);
   if (n_fluid > 0 && (!x || !v)) return fail(nullptr, RTS_ERR_ARG, "x and v are required");
   if (n_boundary > 0 && !xb) return fail(nullptr, RTS_ERR_ARG, "xb is required");
   rts_ctx* c = new (std::nothrow) rts_ctx;

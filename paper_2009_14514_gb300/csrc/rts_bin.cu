@@ -17,34 +17,6 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-// Block coordinate floor((x - o) / edge).  The FP32 quotient t = (x - o) * (1 / edge)
-// carries three roundings, so it is within 3 * 2^-24 * t of the exact one; within
-// band (8 * 2^-24 * the largest coordinate of the grid, set on the host) of an integer
-// the FP64 quotient decides, so the result is that of the double-precision definition.
-__device__ __forceinline__ int block_coord(float x, float o, double od, float inv_e, double ed,
-                                           int n, float band, int* bad) {
-  float t = (x - o) * inv_e;
-  float f = floorf(t);
-  float fr = t - f;
-  double fd;
-  if (fr < band || fr > 1.0f - band)
-    fd = floor(__ddiv_rn(__dsub_rn((double)x, od), ed));
-  else
-    fd = (double)f;
-  if (!(fd >= 0.0 && fd < (double)n)) {
-    *bad = 1;
-    return 0;
-  }
-  return (int)fd;
-}
-
-__device__ __forceinline__ uint32_t block_key(const DevParams& P, float4 p, int* bad) {
-  int cx = block_coord(p.x, P.ox, P.oxd, P.inv_edge, P.edged, P.nx, P.key_band, bad);
-  int cy = block_coord(p.y, P.oy, P.oyd, P.inv_edge, P.edged, P.ny, P.key_band, bad);
-  int cz = block_coord(p.z, P.oz, P.ozd, P.inv_edge, P.edged, P.nz, P.key_band, bad);
-  return ((uint32_t)cz * P.ny + cy) * P.nx + cx;
-}
-
 // Deferred correction of the last step's evaluated particles (pend), then predict
 // (dt != 0: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt) and the container correction,
 // then key and slot.  Slots: particles arrive mostly in block order, so each run of
@@ -356,6 +328,15 @@ __global__ void k_canon_gather(int n, int nb, int max_per_block, const uint32_t*
       dst.err[f] = perr;
     }
   }
+}
+
+// Exclusive scan of nb block counts into cstart (nb + 1 entries); the counts are reset
+// to zero.  tile_sums holds ceil(nb / 2048) entries.
+void scan_block_counts(uint32_t* count, int nb, uint32_t* tile_sums, uint32_t* cstart,
+                       cudaStream_t stream) {
+  int ntiles = (nb + kScanTile - 1) / kScanTile;
+  k_scan_reduce<<<ntiles, kScanThreads, 0, stream>>>(count, nb, tile_sums);
+  k_scan_apply<<<ntiles, kScanThreads, 0, stream>>>(count, nb, tile_sums, cstart, nullptr, nullptr);
 }
 
 // Exclusive scan of the block counts into cstart (tile totals, then each tile adds the

@@ -44,6 +44,7 @@ struct DevParams {
   int eq1[kMaxLevels];
   int force_level;
   int level_clock;   // 0: validity = multiplier (Algorithm 1); 1: aligned to multiples
+  int no_clamp;      // 1: negative Tait pressure kept
   float dt_b;
 };
 
@@ -122,6 +123,34 @@ __device__ __forceinline__ void serna_correct(float4& x, float4& v, const float4
 // A correction left pending by the last stepping call (applied by the next key pass,
 // or by the correction kernel when the state is read).
 enum PendMode { kPendNone = 0, kPendCorrect = 1, kPendPrime = 2 };
+
+// Block coordinate floor((x - o) / edge).  The FP32 quotient t = (x - o) * (1 / edge)
+// carries three roundings, so it is within 3 * 2^-24 * t of the exact one; within
+// band (8 * 2^-24 * the largest coordinate of the grid, set on the host) of an integer
+// the FP64 quotient decides, so the result is that of the double-precision definition.
+__device__ __forceinline__ int block_coord(float x, float o, double od, float inv_e, double ed,
+                                           int n, float band, int* bad) {
+  float t = (x - o) * inv_e;
+  float f = floorf(t);
+  float fr = t - f;
+  double fd;
+  if (fr < band || fr > 1.0f - band)
+    fd = floor(__ddiv_rn(__dsub_rn((double)x, od), ed));
+  else
+    fd = (double)f;
+  if (!(fd >= 0.0 && fd < (double)n)) {
+    *bad = 1;
+    return 0;
+  }
+  return (int)fd;
+}
+
+__device__ __forceinline__ uint32_t block_key(const DevParams& P, float4 p, int* bad) {
+  int cx = block_coord(p.x, P.ox, P.oxd, P.inv_edge, P.edged, P.nx, P.key_band, bad);
+  int cy = block_coord(p.y, P.oy, P.oyd, P.inv_edge, P.edged, P.ny, P.key_band, bad);
+  int cz = block_coord(p.z, P.oz, P.ozd, P.inv_edge, P.edged, P.nz, P.key_band, bad);
+  return ((uint32_t)cz * P.ny + cy) * P.nx + cx;
+}
 
 // Non-penetration of the container box: a particle beyond a face is put back on it and
 // the velocity component into that face is removed.
@@ -235,6 +264,10 @@ rts_status launch_bin(rts_ctx* c, float dt_predict);
 rts_status launch_bin_boundary(rts_ctx* c, const float4* xb_unsorted, int nb);
 rts_status launch_classify(rts_ctx* c);
 rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1);
+void scan_block_counts(uint32_t* count, int nb, uint32_t* tile_sums, uint32_t* cstart,
+                       cudaStream_t stream);
+const char* validate_params(const rts_params* p, int32_t n, int32_t nb);  // nullptr if valid
+void make_dev_params(const rts_params& p, DevParams& d);
 rts_status launch_density(rts_ctx* c);
 rts_status launch_force(rts_ctx* c);
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime);

@@ -242,7 +242,8 @@ __device__ __forceinline__ float tait(const DevParams& P, float rho) {
   } else {
     rg = powf(r, P.gamma);
   }
-  return fmaxf(0.0f, P.tait_B * (rg - 1.0f));
+  const float p = P.tait_B * (rg - 1.0f);
+  return P.no_clamp ? p : fmaxf(0.0f, p);
 }
 
 // ------------------------------------------------------ neighbour passes ---

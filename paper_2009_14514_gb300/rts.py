@@ -25,6 +25,8 @@ EXPORTED = [
     "rts_get_blocks", "rts_sync", "rts_num_blocks", "rts_substep_index", "rts_last_error",
     "rts_destroy", "rts_profile_enable", "rts_profile_read", "rts_bin_noalloc",
     "rts_pcisph_last", "rts_get_pcisph_state", "rts_get_neighbors",
+    "rts_diff_create", "rts_diff_forward", "rts_diff_backward", "rts_diff_last_error",
+    "rts_diff_destroy",
 ]
 
 
@@ -55,6 +57,7 @@ class RtsParams(C.Structure):
         ("wall_hi", C.c_float * 3),
         ("level_clock", C.c_int32),
         ("tait_B", C.c_float),
+        ("tait_no_clamp", C.c_int32),
     ]
 
 
@@ -132,6 +135,7 @@ def make_params(d: dict) -> RtsParams:
         P.wall_hi[k] = d.get("wall_hi", [0.0] * 3)[k]
     P.level_clock = int(d.get("level_clock", 0))
     P.tait_B = float(d.get("tait_B", 0.0))
+    P.tait_no_clamp = int(d.get("tait_no_clamp", 0))
     return P
 
 
@@ -158,6 +162,9 @@ def lib():
             "rts_bin_noalloc": [vp, i32, vp, vp, vp, vp, vp],
             "rts_pcisph_last": [vp, vp], "rts_get_pcisph_state": [vp, vp, vp, vp],
             "rts_get_neighbors": [vp, vp, vp, i32],
+            "rts_diff_create": [vp, i32, vp, i32, vp, i32, i32, vp, vp],
+            "rts_diff_forward": [vp, vp, C.c_float, C.c_float, vp, vp],
+            "rts_diff_backward": [vp, vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -169,6 +176,10 @@ def lib():
         L.rts_num_blocks.restype = i64
         L.rts_substep_index.argtypes = [vp]
         L.rts_substep_index.restype = i64
+        L.rts_diff_last_error.argtypes = [vp]
+        L.rts_diff_last_error.restype = C.c_char_p
+        L.rts_diff_destroy.argtypes = [vp]
+        L.rts_diff_destroy.restype = None
         _LIB = L
     return _LIB
 

@@ -171,6 +171,26 @@ def wcsph_dam_break_1m(seed=1234):
                      name="wcsph_dam_break_1m")
 
 
+def diff_dam_break_250k(seed=1234):
+    """Differentiable rollout: 100 x 50 x 50 = 250,000 particles, s = 0.01 m, in the corner
+    of a 2 x 1 x 1 m tank, dt_b = 5e-5 s."""
+    return dam_break((100, 50, 50), 0.01, (2.0, 1.0, 1.0), 5e-5, jitter=0.0, seed=seed,
+                     name="diff_dam_break_250k")
+
+
+def diff_dam_break_4k(seed=1234):
+    """The same setup at 16^3 = 4,096 particles (gradient checks), 0.32 x 0.16 x 0.32 m,
+    jittered +-1e-4 m."""
+    return dam_break((16, 16, 16), 0.01, (0.32, 0.16, 0.32), 5e-5, jitter=1e-4, seed=seed,
+                     name="diff_dam_break_4k")
+
+
+def seeded_velocities(n, seed=777, scale=0.5):
+    """A smooth-ish seeded initial velocity field (normal components, m/s)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return (scale * rng.standard_normal((n, 3))).astype(np.float32)
+
+
 def pool_drop(pool_counts, cube_side, gap, s, box, dt_b, *, jitter=0.0, seed=1234, name="pool_drop"):
     """A resting pool filling the box floor plus a cube of fluid centred above it."""
     pool = lattice(pool_counts, s)

@@ -27,14 +27,14 @@ def _loss(R, v0, B, a, steps):
     return centroid_density_loss(xT, rhoT, TARGET, 1000.0)[0]
 
 
-@pytest.mark.parametrize("wall_shift,vz", [(0.0, 0.0), (-0.0098, -0.6)])
-def test_reference_gradient_matches_central_differences(wall_shift, vz):
+@pytest.mark.parametrize("wall_shift,vz,no_clamp", [(0.0, 0.0, 0), (-0.0098, -0.6, 0), (0.0, 0.0, 1)])
+def test_reference_gradient_matches_central_differences(wall_shift, vz, no_clamp):
     # second case: the bottom layer starts 0.2 mm above the floor moving down, so the
-    # container clamps it during the rollout
+    # container clamps it during the rollout; third: negative Tait pressure kept
     sc, x, v0 = _case(wall_shift)
     v0[:, 2] += vz
     steps = 20
-    R = DiffRollout(sc.params, x, sc.xb)
+    R = DiffRollout(dict(sc.params, tait_no_clamp=no_clamp), x, sc.xb)
     xT, rhoT, recs = R.forward(v0, B0, A0, steps)
     if vz:
         assert any(r["mx"].any() for r in recs[1:])
