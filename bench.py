@@ -70,7 +70,13 @@ def parse():
     ap.add_argument("--no-pcisph", action="store_true", help="skip the PCISPH pool-drop section")
     ap.add_argument("--pcisph-sim", type=float, default=1.0, help="simulated seconds of PCISPH")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable rollout")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched PCISPH scenes")
+    ap.add_argument("--batch-sim", type=float, default=0.05,
+                    help="simulated seconds of the batched PCISPH section")
     ap.add_argument("--window", type=int, default=8, help="base substeps per --profile-case step")
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="SCENES",
+                    help="short run for ncu: the first SCENES scenes of the batched PCISPH "
+                         "workload for --steps minor steps (nothing printed but a line)")
     ap.add_argument("--profile-case", action="store_true",
                     help="short run for ncu: 1M jittered lattice with a seeded dynamic state, "
                          "primed, then --steps windows (few launches, nothing printed but a line)")
@@ -90,6 +96,19 @@ def profile_case(args):
     st_all = rts.rts_advance(ctx, args.steps * args.window * dtb)
     print(json.dumps({"profile_case": sc.name, "substeps": st_all["substeps"],
                       "particle_evals": st_all["particle_evals"]}), flush=True)
+
+
+def profile_batch(args):
+    """A bounded batched case for ncu: the first args.profile_batch scenes of the 64-scene
+    PCISPH workload from t = 0 for args.steps minor steps (default launch shape)."""
+    from paper_2009_14514_gb300 import rts, scenes
+    b = scenes.pcisph_batch(n_scenes=args.profile_batch)
+    ctx = rts.rts_batch_init(b.params, b.desc, b.x, b.v, b.xb)
+    st = rts.rts_advance(ctx, args.steps * b.params["dt_b"])
+    print(json.dumps({"profile_batch": b.name, "particles": b.n, "substeps": st["substeps"],
+                      "scene_iterations": st["pcisph_iterations"],
+                      "iterations_run": rts.rts_batch_get_launch(ctx)["iterations_run"]}),
+          flush=True)
 
 
 def dist_env():
@@ -313,6 +332,67 @@ def run_pcisph(args, torch, rts, flush):
     return out
 
 
+def run_batch(args, torch, rts, flush):
+    """64 independent PCISPH scenes (dam breaks and pool drops, 10k-200k particles drawn
+    log-uniformly, seed 4321) from t = 0 for args.batch_sim seconds: all scenes in one
+    batched context (iterations as a CUDA graph over the work queue, launch shape from the
+    autotuner), against the same scenes advanced one after another through single-scene
+    contexts.  Values: fluid particles x (simulated time / dt_b) per second."""
+    from paper_2009_14514_gb300 import scenes
+    b = scenes.pcisph_batch()
+    dtb = b.params["dt_b"]
+    stream = torch.cuda.current_stream()
+    nsteps = int(round(args.batch_sim / dtb))
+    sim = nsteps * dtb
+    counts = [sc.n for sc in b.scenes]
+    out = {"workload": f"{b.name}: {len(b.scenes)} scenes, {b.n} fluid + {b.nb} boundary "
+                       f"particles (per scene {min(counts)}-{max(counts)}), {nsteps} minor "
+                       f"steps of {dtb:g} s from t=0"}
+    # autotune on a throwaway context after one step (the tuner needs neighbour lists)
+    tctx = rts.rts_batch_init(b.params, b.desc, b.x, b.v, b.xb)
+    rts.rts_pcisph_step(tctx)
+    tuned = rts.rts_batch_autotune(tctx, reps=3)
+    tctx.close()
+    out["autotuned"] = tuned
+
+    def timed(ctx, t_end):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = rts.rts_advance(ctx, t_end)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3, st
+
+    for arm, graph in (("batched", True), ("batched_host_loop", False)):
+        ctx = rts.rts_batch_init(b.params, b.desc, b.x, b.v, b.xb)
+        rts.rts_batch_set_launch(ctx, tuned["threads"], tuned["tile"], graph)
+        rts.rts_profile_enable(ctx, 0)
+        rts.rts_profile_read(ctx, reset=True)
+        sec, st = timed(ctx, sim)
+        prof = rts.rts_profile_read(ctx)
+        errs = [rts.rts_batch_scene_info(ctx, k)["err_max"] for k in range(len(b.scenes))]
+        out[arm] = {"value": b.n * nsteps / sec, "seconds": sec, "sim_s": sim,
+                    "scene_iterations": st["pcisph_iterations"],
+                    "iterations_run": rts.rts_batch_get_launch(ctx)["iterations_run"],
+                    "gpu_launches": int(prof["kernels"]),
+                    "err_max_last_step": max(errs)}
+        ctx.close()
+    seq_sec, seq_its = 0.0, 0
+    for sc in b.scenes:
+        ctx = rts.rts_init(sc.params, sc.x, sc.v, sc.xb)
+        sec, st = timed(ctx, sim)
+        seq_sec += sec
+        seq_its += st["pcisph_iterations"]
+        ctx.close()
+    out["sequential"] = {"value": b.n * nsteps / seq_sec, "seconds": seq_sec, "sim_s": sim,
+                         "scene_iterations": seq_its}
+    out["batched_vs_sequential"] = out["batched"]["value"] / out["sequential"]["value"]
+    out["graph_vs_host_loop"] = out["batched"]["value"] / out["batched_host_loop"]["value"]
+    return out
+
+
 def run_diff(args, torch):
     """The differentiable rollout: 250k-particle dam break, 100 steps of global constant
     stepping, checkpoints every 10 steps; the loss |mean(x_T) - target|^2 + mean
@@ -447,6 +527,9 @@ def main():
     if args.profile_case:
         profile_case(args)
         return
+    if args.profile_batch:
+        profile_batch(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -496,6 +579,7 @@ def main():
     e2e = None if args.no_e2e else run_e2e(sc, args, torch, rts)
     pcisph = None if (args.no_pcisph or args.small) else run_pcisph(args, torch, rts, flush)
     dres = None if (args.no_diff or args.small) else run_diff(args, torch)
+    bres = None if (args.no_batch or args.small) else run_batch(args, torch, rts, flush)
 
     # roofline of the dominant neighbour kernel (FP32 ALU bound)
     prof = ours["prof"]
@@ -563,6 +647,8 @@ def main():
         line["pcisph"] = pcisph
     if dres is not None:
         line["differentiable"] = dres
+    if bres is not None:
+        line["batched_pcisph"] = bres
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle(sc)
     if rank == 0:

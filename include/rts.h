@@ -287,6 +287,76 @@ int64_t rts_substep_index(const rts_ctx* ctx);   /* completed base substeps */
 const char* rts_last_error(const rts_ctx* ctx);  /* never NULL; ctx may be NULL */
 rts_status rts_destroy(rts_ctx* ctx);            /* NULL is a no-op */
 
+/* -------------------------------------------------------- batched scenes --- */
+/* Many independent RTS-PCISPH scenes (Section 5, Algorithms 2 and 3) advanced together.
+ * The paper treats one scene; batching is this library's addition.  Each scene keeps its
+ * own block grid, container and density-correction control: every scene runs the
+ * iterations, S_e / R_ob sets, local runs and reverts of Algorithm 3 on its own errors,
+ * exactly as it would alone.  The scenes share the parameters (physics, dt_b, regions,
+ * schedule) and the major-step clock: when any scene exceeds max_global_iters the batch
+ * shortens its major step (Section 5.5).  One launch of each pass serves all scenes;
+ * the iterations of a minor step run as one CUDA graph (a while node driven by the
+ * device-side control) over a work queue of the scenes still iterating.
+ *
+ * The context is an ordinary rts_ctx: rts_pcisph_step / rts_advance step every scene by
+ * one minor step / to t_sim; rts_get_state, rts_set_state, rts_get_pcisph_state,
+ * rts_get_neighbors, rts_sync, rts_destroy work on the concatenation of the scenes in
+ * the caller's order (scene 0's particles first).  rts_get_bins / rts_get_blocks return
+ * the stacked grid (rts_batch_layout gives each scene's place in it).  In rts_stats,
+ * pcisph_iterations counts scene-iterations (the sum over scenes); rts_pcisph_last
+ * reports the iterations the batch ran in its last minor step (the largest scene count),
+ * the largest global and local counts and the largest error of any scene. */
+typedef struct rts_scene {
+  int32_t n_fluid;           /* fluid particles of the scene (consecutive in x, v)        */
+  int32_t n_boundary;        /* boundary particles of the scene (consecutive in xb)       */
+  float domain_min[3];       /* origin of the scene's block grid, in its own coordinates  */
+  int32_t grid_dim[3];       /* blocks per axis of the scene's grid, each in [1, 4096]    */
+  float wall_lo[3], wall_hi[3];  /* the scene's container (when params->wall_project)    */
+} rts_scene;
+
+/* params: shared parameters (scheme RTS_PCISPH, mode RTS_MODE_REGIONAL; domain_min,
+ * grid_dim, wall_lo and wall_hi are taken from each scene instead).  scenes: n_scenes
+ * descriptions, 1 <= n_scenes <= 1024.  x, v: all scenes' fluid particles concatenated
+ * (sum of n_fluid x 3); xb: all boundary particles concatenated.  Pointers as for
+ * rts_init (host or device, copied).  The scenes are stacked along z in one grid with
+ * max(expand_layers, r1_search_rings, 1) empty block layers between two scenes.
+ * Errors: RTS_ERR_ARG, RTS_ERR_OOM, RTS_ERR_CUDA, RTS_ERR_DOMAIN (a boundary particle
+ * outside its scene's grid). */
+rts_status rts_batch_init(const rts_params* params, int32_t n_scenes, const rts_scene* scenes,
+                          const float* x, const float* v, const float* xb, void* cuda_stream,
+                          rts_ctx** out);
+
+/* Algorithm 3 statistics of one scene in the last minor step (iterations, global, local,
+ * reverts, not_converged, err_max, err_avg are the scene's; minor, n_minor_current and
+ * clean_majors the batch's).  Reads what the last step copied back: no synchronisation.
+ * RTS_ERR_ARG for a context that is not a batch or a scene out of range. */
+rts_status rts_batch_scene_info(rts_ctx* ctx, int32_t scene, rts_pcisph_info* out);
+
+/* Placement of the scenes: grid_dim (3) of the stacked grid; z0 (n_scenes + 1) first z
+ * layer of each scene (z0[n_scenes] = the grid's layers); fluid_base and boundary_base
+ * (n_scenes + 1) first particle of each scene in the concatenated arrays.  A block
+ * (bx, by, bz) of scene s is the stacked block ((bz + z0[s]) * ny + by) * nx + bx.
+ * Any pointer may be NULL. */
+rts_status rts_batch_layout(const rts_ctx* ctx, int32_t* grid_dim, int32_t* z0,
+                            int32_t* fluid_base, int32_t* boundary_base);
+
+/* Launch shape of the iteration passes: threads per CTA of the persistent work-queue
+ * kernels (a multiple of 32 in [64, 1024]); tile, particles per queue item (a multiple
+ * of 32 in [32, 8192]); use_graph 1 runs the iterations as a captured CUDA graph, 0 from
+ * the host (one round trip per iteration).  The results do not depend on any of these.
+ * Defaults: 256, 128, 1.  RTS_ERR_ARG otherwise. */
+rts_status rts_batch_set_launch(rts_ctx* ctx, int32_t threads, int32_t tile, int32_t use_graph);
+rts_status rts_batch_get_launch(const rts_ctx* ctx, int32_t* threads, int32_t* tile,
+                                int32_t* use_graph, int64_t* iterations_run);
+
+/* Autotuner: times one full iteration (every particle of every scene participating) for
+ * threads in {128, 256, 512} x tile in {64, 128, 256, 512}, reps timed runs each after a
+ * warm-up, on the current state, which it restores afterwards; keeps the fastest shape
+ * and returns it with its time per iteration (ms).  Needs the neighbour lists of a
+ * previous step (RTS_ERR_STATE before the first step).  Synchronises. */
+rts_status rts_batch_autotune(rts_ctx* ctx, int32_t reps, int32_t* threads, int32_t* tile,
+                              float* ms_per_iteration);
+
 /* ------------------------------------------------ differentiable rollout --- */
 /* No counterpart in the paper: a WCSPH rollout under global constant stepping at dt_b
  * (every particle active every step; the Serna predictor-corrector of Section 4.1 and the

@@ -59,7 +59,7 @@ static void level_thresholds(const rts_params& p, double* vthr2, double* athr2, 
   }
 }
 
-const char* rts::validate_params(const rts_params* p, int32_t n, int32_t nb) {
+const char* rts::validate_params(const rts_params* p, int32_t n, int32_t nb, int max_dim) {
   if (!p) return "params is NULL";
   if (p->scheme != RTS_WCSPH && p->scheme != RTS_PCISPH) return "scheme must be RTS_WCSPH or RTS_PCISPH";
   if (p->mode < 0 || p->mode > 2) return "mode must be 0, 1 or 2";
@@ -68,7 +68,7 @@ const char* rts::validate_params(const rts_params* p, int32_t n, int32_t nb) {
     return "spacing, support_r and block_edge must be positive";
   if (p->block_edge < p->support_r) return "block_edge must be >= support_r";
   for (int d = 0; d < 3; ++d) {
-    if (p->grid_dim[d] < 1 || p->grid_dim[d] > 4096) return "grid_dim must be in [1, 4096]";
+    if (p->grid_dim[d] < 1 || p->grid_dim[d] > max_dim) return "grid_dim must be in [1, 4096]";
     if (!std::isfinite(p->domain_min[d]) || !std::isfinite(p->gravity[d])) return "non-finite domain_min or gravity";
   }
   if ((double)p->grid_dim[0] * p->grid_dim[1] * p->grid_dim[2] > 2.0e9) return "too many blocks";
@@ -478,20 +478,43 @@ static rts_status wcsph_step(rts_ctx* c, int64_t max_mult) {
 
 extern "C" {
 
-rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, const float* v,
-                    int32_t n_boundary, const float* xb, void* cuda_stream, rts_ctx** out) {
-  if (!out) return fail(nullptr, RTS_ERR_ARG, "out is NULL");
+}  // extern "C"
+
+// Context constructor behind rts_init and rts_batch_init (batch: the stacked grid's
+// parameters and the scene tables, owned by the context from here on).
+static rts_status init_ctx(const rts_params* params, int32_t n_fluid, const float* x,
+                           const float* v, int32_t n_boundary, const float* xb, void* cuda_stream,
+                           rts_ctx** out, BatchState* batch) {
+  if (!out) {
+    rts::batch_delete(batch);
+    return fail(nullptr, RTS_ERR_ARG, "out is NULL");
+  }
   *out = nullptr;
-  if (const char* why = validate_params(params, n_fluid, n_boundary)) return fail(nullptr, RTS_ERR_ARG, why);
-  if (n_fluid > 0 && (!x || !v)) return fail(nullptr, RTS_ERR_ARG, "x and v are required");
-  if (n_boundary > 0 && !xb) return fail(nullptr, RTS_ERR_ARG, "xb is required");
+  const char* why = validate_params(params, n_fluid, n_boundary, batch ? 65536 : 4096);
+  if (!why && n_fluid > 0 && (!x || !v)) why = "x and v are required";
+  if (!why && n_boundary > 0 && !xb) why = "xb is required";
+  if (why) {
+    rts::batch_delete(batch);
+    return fail(nullptr, RTS_ERR_ARG, why);
+  }
   rts_ctx* c = new (std::nothrow) rts_ctx;
-  if (!c) return fail(nullptr, RTS_ERR_OOM, "host allocation failed");
+  if (!c) {
+    rts::batch_delete(batch);
+    return fail(nullptr, RTS_ERR_OOM, "host allocation failed");
+  }
   memset(c, 0, sizeof(*c));
   c->p = *params;
   make_dev_params(c->p, c->dp);
   c->dp.n_fluid = n_fluid;
   c->dp.n_bound = n_boundary;
+  if (batch) {
+    rts_status bst = rts_batch_attach(c, batch);
+    if (bst != RTS_OK) {
+      snprintf(g_noctx_err, sizeof g_noctx_err, "%s", c->err);
+      rts_destroy(c);
+      return bst;
+    }
+  }
   c->stream = (cudaStream_t)cuda_stream;
   c->n = n_fluid;
   c->nb = n_boundary;
@@ -625,9 +648,30 @@ fail_alloc:
   return st;
 }
 
+extern "C" {
+
+rts_status rts_init(const rts_params* params, int32_t n_fluid, const float* x, const float* v,
+                    int32_t n_boundary, const float* xb, void* cuda_stream, rts_ctx** out) {
+  return init_ctx(params, n_fluid, x, v, n_boundary, xb, cuda_stream, out, nullptr);
+}
+
+rts_status rts_batch_init(const rts_params* params, int32_t n_scenes, const rts_scene* scenes,
+                          const float* x, const float* v, const float* xb, void* cuda_stream,
+                          rts_ctx** out) {
+  if (!out) return fail(nullptr, RTS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  rts_params p2;
+  int32_t nf = 0, nbd = 0;
+  BatchState* b = nullptr;
+  if (const char* why = rts_batch_plan(params, n_scenes, scenes, &p2, &nf, &nbd, &b))
+    return fail(nullptr, RTS_ERR_ARG, why);
+  return init_ctx(&p2, nf, x, v, nbd, xb, cuda_stream, out, b);
+}
+
 rts_status rts_destroy(rts_ctx* c) {
   if (!c) return RTS_OK;
   cudaStreamSynchronize(c->stream);
+  batch_free(c);
   PState* ss[2] = {&c->s, &c->s2};
   for (PState* s : ss) {
     cudaFree(s->x); cudaFree(s->v); cudaFree(s->a); cudaFree(s->rho); cudaFree(s->prs);

@@ -1,0 +1,872 @@
+// rts_batch.cu - many independent RTS-PCISPH scenes advanced together in one context.
+//
+// Layout.  The scenes' block grids are stacked along z in one grid of
+// max(nx) x max(ny) x (sum of nz + gaps) blocks.  Each scene keeps its particles in its
+// own coordinates and is binned in its own grid (its origin and dims, Section 5.6 block
+// edge), shifted by its z offset; positions are never translated, so every FP32 value a
+// scene sees is the one it would see alone.  Between two scenes lie `gap` empty z
+// layers, gap >= every stencil reach of the method (region expansion, R_1 search rings,
+// R_min, R_ob, pre-emption), so no stencil of one scene reaches another scene's blocks
+// and each single-scene kernel (binning, regions, lists, forces, integration) serves all
+// scenes in one launch.  In block order each scene's particles are one contiguous range
+// (the scenes' z ranges are disjoint and ordered), the same range as in caller order.
+//
+// Density correction (Algorithm 3) per scene.  Every scene has its own iteration state
+// (row, mode, local run, revert, minimum count), its own error reductions (exact maximum
+// on FP32 bits, fixed-point sum) and its own stopping test; a control kernel evaluates
+// them on the device after every iteration.  The particle passes of an iteration are
+// persistent kernels over one global work queue: the tiles (runs of `tile` consecutive
+// particles in block order) of the scenes still iterating; each warp takes the next tile
+// from an atomic counter.  The iteration loop is a CUDA graph whose while node repeats
+// the passes as long as the control kernel reports a scene still iterating, so a minor
+// step runs all its iterations without a host round trip.  Scenes share the major-step
+// clock: the batch shortens its major step (Section 5.5) when any scene exceeds the
+// global-iteration limit.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rts_pcisph_dev.cuh"
+
+namespace rts {
+
+constexpr int kMaxScenes = 1024;
+constexpr int kFlagBackup = 1, kFlagRevert = 2;
+
+// Algorithm 3 state of one scene in the current minor step.
+struct SceneIt {
+  int active;        // still iterating
+  int done, row, mode, min_iter, local_run, stay_global;
+  int flags;         // kFlagBackup / kFlagRevert, applied by the next predict pass
+  int it_global, it_local, it_reverts, it_notconv;
+  unsigned err_max_bits;           // max latest error of the scene (FP32 bits)
+  int n;                           // fluid particles of the scene
+  unsigned long long err_sum_fx;   // sum of latest errors, fixed point 2^-32
+  float err_max;
+  int pad;
+  double err_avg;
+};
+
+struct BatchCtl {
+  int iter;          // iterations run in this minor step
+  int j, min_sched;  // minor step and the smallest scheduled count of any region in it
+  int any;           // a scene is still iterating
+  unsigned q[3];     // work-queue counters: predict, density, pressure
+  int qtot;          // tiles in the queue
+  int qpre[kMaxScenes + 1];   // first tile of each scene (exclusive prefix)
+};
+
+// Device pointers that change between minor steps (the sort and the region field swap
+// buffers); the iteration kernels read them from device memory so that one captured
+// graph serves every minor step.
+struct BatchView {
+  PState s;
+  const uint32_t* key;
+  const int32_t* preg;
+  float4* xs;
+  const float4* xb;
+  const uint32_t* nbl;
+  uint8_t* in_se;
+  uint8_t* in_re;
+  uint8_t* ob;
+  float* pbak;
+  const uint32_t* filled;
+  const Ctl* ctl;
+};
+
+struct BatchState {
+  int ns;
+  std::vector<uint32_t> fbase, bbase;
+  std::vector<int> zbase;
+  std::vector<SceneGeo> geo;
+  int dims[3];
+  int gap;
+  SceneGeo* d_geo;
+  uint32_t* d_fbase;
+  uint32_t* d_bbase;
+  int* d_zbase;
+  BatchCtl* bctl;
+  SceneIt* sit;
+  SceneIt* h_sit;    // pinned
+  int* h_small;      // pinned: iter, any
+  BatchView* d_view;
+  BatchView* h_view; // pinned
+  int threads, tile, use_graph;
+  int grid[3];
+  int ctl_threads;
+  cudaStream_t cap;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int64_t body_runs;
+};
+
+// ----------------------------------------------------------------- kernels ---
+
+// Exclusive scan of one int per thread across the CTA (blockDim.x a multiple of 32,
+// <= 1024); *total receives the CTA sum.
+__device__ int cta_excl_scan(int v, int* total) {
+  __shared__ int wsum[32];
+  __shared__ int tot;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFullMask, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const int t = lane < nw ? wsum[lane] : 0;
+    int ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(kFullMask, ti, o);
+      if (lane >= o) ti += u;
+    }
+    if (lane < nw) wsum[lane] = ti - t;
+    if (lane == 31) tot = ti;
+  }
+  __syncthreads();
+  const int r = inc - v + wsum[w];
+  *total = tot;
+  __syncthreads();
+  return r;
+}
+
+// First iteration of a minor step: every scene with particles iterates, starting with
+// the scheduled turns of row 1.
+__global__ void k_b_begin(int ns, const uint32_t* __restrict__ fbase, int tile, int j,
+                          int min_sched, BatchCtl* B, SceneIt* S) {
+  const int s = threadIdx.x;
+  int tiles = 0;
+  if (s < ns) {
+    SceneIt t;
+    memset(&t, 0, sizeof t);
+    t.n = (int)(fbase[s + 1] - fbase[s]);
+    t.active = t.n > 0;
+    t.row = 1;
+    t.mode = kModeSched;
+    t.min_iter = 3;
+    S[s] = t;
+    tiles = t.active ? (t.n + tile - 1) / tile : 0;
+  }
+  int tot;
+  const int pre = cta_excl_scan(tiles, &tot);
+  if (s < ns) B->qpre[s] = pre;
+  if (s == 0) {
+    B->qpre[ns] = tot;
+    B->qtot = tot;
+    B->iter = 0;
+    B->j = j;
+    B->min_sched = min_sched;
+    B->any = tot > 0;
+    B->q[0] = B->q[1] = B->q[2] = 0u;
+  }
+}
+
+// The warp's next tile of the queue (scene and particle range), false when the queue
+// is exhausted.  qpre: the queue's scene prefix in shared memory.
+__device__ __forceinline__ bool next_tile(BatchCtl* B, int which, const int* qpre, int ns,
+                                          int qtot, const uint32_t* __restrict__ fbase,
+                                          int tile, int* sc, uint32_t* i0, uint32_t* i1) {
+  unsigned q = 0;
+  if ((threadIdx.x & 31) == 0) q = atomicAdd(&B->q[which], 1u);
+  q = __shfl_sync(kFullMask, q, 0);
+  if (q >= (unsigned)qtot) return false;
+  // the owning scene: the largest s with qpre[s] <= q (scenes without tiles in the
+  // queue share their successor's prefix)
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (qpre[mid] <= (int)q) lo = mid; else hi = mid - 1;
+  }
+  *sc = lo;
+  const uint32_t b = fbase[lo] + (q - (unsigned)qpre[lo]) * (uint32_t)tile;
+  const uint32_t e = fbase[lo + 1];
+  *i0 = b;
+  *i1 = b + (uint32_t)tile < e ? b + (uint32_t)tile : e;
+  return true;
+}
+
+__device__ __forceinline__ void load_queue(const BatchCtl* B, int ns, int* qpre) {
+  for (int k = threadIdx.x; k <= ns; k += blockDim.x) qpre[k] = B->qpre[k];
+  __syncthreads();
+}
+
+// Pending pressure backup / revert of the scene (Section 5.5), then x* of every particle
+// of the iterating scenes; R_e of their blocks is cleared for this iteration.
+__global__ void k_b_predict(DevParams P, const BatchView* __restrict__ Vp, BatchCtl* B,
+                            const SceneIt* __restrict__ S, int tile) {
+  extern __shared__ int qpre[];
+  const int ns = P.n_scenes;
+  load_queue(B, ns, qpre);
+  const BatchView V = *Vp;
+  const int qtot = B->qtot;
+  const int lane = threadIdx.x & 31;
+  int sc;
+  uint32_t i0, i1;
+  while (next_tile(B, 0, qpre, ns, qtot, P.fbase, tile, &sc, &i0, &i1)) {
+    const int flags = S[sc].flags;
+    for (uint32_t i = i0 + lane; i < i1; i += 32) {
+      if (flags & kFlagBackup) V.pbak[i] = V.s.prs[i];
+      if (flags & kFlagRevert) V.s.prs[i] = V.pbak[i];
+      V.xs[i] = predict_one(P, V.s, (int)i);
+      V.in_re[V.key[i]] = 0;
+    }
+  }
+}
+
+// Predicted density and pressure of the participants (turn, S_e, R_ob), then S_e, R_e and
+// the scene's error reductions over all its particles' latest errors.
+__global__ void k_b_density(DevParams P, const BatchView* __restrict__ Vp, BatchCtl* B,
+                            SceneIt* S, int tile) {
+  extern __shared__ int qpre[];
+  const int ns = P.n_scenes;
+  load_queue(B, ns, qpre);
+  const BatchView V = *Vp;
+  const int qtot = B->qtot, j = B->j;
+  const int lane = threadIdx.x & 31;
+  const float half_eta = 0.5f * P.eta;
+  int sc;
+  uint32_t i0, i1;
+  while (next_tile(B, 1, qpre, ns, qtot, P.fbase, tile, &sc, &i0, &i1)) {
+    const int mode = S[sc].mode, row = S[sc].row;
+    unsigned mx = 0;
+    unsigned long long fx = 0;
+    for (uint32_t base = i0; base < i1; base += 32) {
+      const uint32_t i = base + lane;
+      if (i < i1) {
+        const uint32_t b = V.key[i];
+        if (has_turn(P, mode, row, j, V.s.level[i]) || V.in_se[i] || V.ob[b])
+          pdensity_one(P, V.s, (int)i, V.xs, V.xb, V.nbl);
+        const float e = V.s.err[i];
+        const bool se = e > half_eta;
+        V.in_se[i] = se ? 1 : 0;
+        if (se) V.in_re[b] = 1;
+        mx = max(mx, __float_as_uint(e));
+        fx += err_fixed(e);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      mx = max(mx, __shfl_down_sync(kFullMask, mx, o));
+      fx += __shfl_down_sync(kFullMask, fx, o);
+    }
+    if (lane == 0) {
+      if (mx) atomicMax(&S[sc].err_max_bits, mx);
+      if (fx) atomicAdd(&S[sc].err_sum_fx, fx);
+    }
+  }
+}
+
+// R_ob of the filled blocks of the iterating scenes.
+__global__ void k_b_observed(DevParams P, const BatchView* __restrict__ Vp,
+                             const SceneIt* __restrict__ S) {
+  const BatchView V = *Vp;
+  const int nf = V.ctl->n_filled;
+  const uint32_t nxy = (uint32_t)P.nx * (uint32_t)P.ny;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    const uint32_t b = V.filled[t];
+    const int sc = scene_of_z(P.zbase, P.n_scenes, (int)(b / nxy));
+    if (!S[sc].active) continue;
+    V.ob[b] = observed_one(P, b, V.preg, V.in_re);
+  }
+}
+
+// Pressure acceleration of the particles with a turn and of S_e.
+__global__ void k_b_pressure(DevParams P, const BatchView* __restrict__ Vp, BatchCtl* B,
+                             const SceneIt* __restrict__ S, int tile) {
+  extern __shared__ int qpre[];
+  const int ns = P.n_scenes;
+  load_queue(B, ns, qpre);
+  const BatchView V = *Vp;
+  const int qtot = B->qtot, j = B->j;
+  const int lane = threadIdx.x & 31;
+  int sc;
+  uint32_t i0, i1;
+  while (next_tile(B, 2, qpre, ns, qtot, P.fbase, tile, &sc, &i0, &i1)) {
+    const int mode = S[sc].mode, row = S[sc].row;
+    for (uint32_t i = i0 + lane; i < i1; i += 32)
+      if (has_turn(P, mode, row, j, V.s.level[i]) || V.in_se[i])
+        ppressure_one(P, V.s, (int)i, V.xs, V.xb, V.nbl);
+  }
+}
+
+// Algorithm 3's decisions for every iterating scene after an iteration (Section 5.5):
+// stop when at least the minimum count ran and the maximum error is within eta, or at
+// max_iters; rows 1-3 follow the schedule; later iterations are global when the average
+// error is >= eta_T, else local on S_e (pressures backed up when a local run starts,
+// restored and global from then on after max_local_iters failed local iterations).
+// Then the queue of the next iteration and the while node's condition.
+__global__ void k_b_control(int ns, int tile, float eta, float eta_T, int max_iters,
+                            int max_local_iters, BatchCtl* B, SceneIt* S,
+                            cudaGraphConditionalHandle cond, int in_graph) {
+  const int s = threadIdx.x;
+  int tiles = 0;
+  if (s < ns) {
+    SceneIt t = S[s];
+    if (t.active) {
+      t.flags = 0;
+      const bool all_turn = t.mode == kModeGlobal || (t.mode == kModeSched && t.row <= B->min_sched);
+      ++t.done;
+      if (all_turn) ++t.it_global;
+      if (t.mode == kModeLocal) ++t.it_local;
+      const float emax = __uint_as_float(t.err_max_bits);
+      t.err_max = emax;
+      t.err_avg = (double)t.err_sum_fx / 4294967296.0 / t.n;
+      bool finish = false;
+      if (t.done >= t.min_iter && emax <= eta) {
+        finish = true;
+      } else if (t.done >= max_iters) {
+        t.it_notconv = 1;
+        finish = true;
+      } else if (t.done < 3) {
+        ++t.row;
+      } else {
+        t.min_iter = t.done + 1;
+        if (t.stay_global || t.err_avg >= (double)eta_T) {
+          t.mode = kModeGlobal;
+          t.local_run = 0;
+        } else {
+          if (t.mode != kModeLocal) {
+            t.flags |= kFlagBackup;
+            t.local_run = 0;
+          }
+          t.mode = kModeLocal;
+          if (++t.local_run > max_local_iters) {
+            t.flags |= kFlagRevert;
+            ++t.it_reverts;
+            t.mode = kModeGlobal;
+            t.stay_global = 1;
+            t.local_run = 0;
+          }
+        }
+      }
+      if (finish) {
+        t.active = 0;
+      } else {
+        t.err_max_bits = 0;
+        t.err_sum_fx = 0;
+        tiles = (t.n + tile - 1) / tile;
+      }
+      S[s] = t;
+    }
+  }
+  int tot;
+  const int pre = cta_excl_scan(tiles, &tot);
+  if (s < ns) B->qpre[s] = pre;
+  if (s == 0) {
+    B->qpre[ns] = tot;
+    B->qtot = tot;
+    B->iter += 1;
+    B->q[0] = B->q[1] = B->q[2] = 0u;
+    B->any = tot > 0;
+    // every iterating scene stops by max_iters: the bound below is never the reason
+    if (in_graph) cudaGraphSetConditional(cond, (tot > 0 && B->iter <= max_iters) ? 1u : 0u);
+  }
+}
+
+// ------------------------------------------------------------------- host ---
+
+int filled_grid_size();
+
+static int sm_count() {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return nsm > 0 ? nsm : 1;
+}
+
+static size_t queue_smem(const BatchState* b) { return sizeof(int) * (size_t)(b->ns + 1); }
+
+// Persistent grids: as many CTAs as fit on the SMs at once.
+static void size_grids(BatchState* b) {
+  const int nsm = sm_count();
+  const void* ks[3] = {(const void*)k_b_predict, (const void*)k_b_density, (const void*)k_b_pressure};
+  for (int k = 0; k < 3; ++k) {
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ks[k], b->threads, queue_smem(b));
+    b->grid[k] = nsm * (per > 0 ? per : 1);
+  }
+}
+
+static void fill_view(const rts_ctx* c, BatchView* v) {
+  v->s = c->s;
+  v->key = c->key;
+  v->preg = c->preg;
+  v->xs = c->xs;
+  v->xb = c->xb;
+  v->nbl = c->nbl;
+  v->in_se = c->in_se;
+  v->in_re = c->in_re;
+  v->ob = c->ob;
+  v->pbak = c->pbak;
+  v->filled = c->filled;
+  v->ctl = c->ctl;
+}
+
+// The five launches of one iteration on stream st.
+static void launch_body(rts_ctx* c, cudaStream_t st, cudaGraphConditionalHandle cond,
+                        int in_graph) {
+  BatchState* b = c->batch;
+  const size_t sm = queue_smem(b);
+  k_b_predict<<<b->grid[0], b->threads, sm, st>>>(c->dp, b->d_view, b->bctl, b->sit, b->tile);
+  k_b_density<<<b->grid[1], b->threads, sm, st>>>(c->dp, b->d_view, b->bctl, b->sit, b->tile);
+  k_b_observed<<<filled_grid_size(), 256, 0, st>>>(c->dp, b->d_view, b->sit);
+  k_b_pressure<<<b->grid[2], b->threads, sm, st>>>(c->dp, b->d_view, b->bctl, b->sit, b->tile);
+  k_b_control<<<1, b->ctl_threads, 0, st>>>(b->ns, b->tile, c->p.eta, c->p.eta_T, c->p.max_iters,
+                                           c->p.max_local_iters, b->bctl, b->sit, cond, in_graph);
+}
+
+static void drop_graph(BatchState* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// The iteration loop as a graph: one while node whose body is the five launches.
+static rts_status build_graph(rts_ctx* c) {
+  BatchState* b = c->batch;
+  drop_graph(b);
+  cudaError_t e = cudaSuccess;
+  {
+    // load the kernels before the capture
+    cudaFuncAttributes fa;
+    const void* ks[5] = {(const void*)k_b_predict, (const void*)k_b_density,
+                         (const void*)k_b_observed, (const void*)k_b_pressure,
+                         (const void*)k_b_control};
+    for (const void* k : ks)
+      if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+  }
+  if (e == cudaSuccess && !b->cap) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaGraphCreate(&b->graph, 0);
+  cudaGraphConditionalHandle cond = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, b->graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &np);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(b->cap, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      launch_body(c, b->cap, cond, 1);
+      cudaGraph_t got = nullptr;
+      e = cudaStreamEndCapture(b->cap, &got);
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    drop_graph(b);
+    cuda_err(c, e, "batched iteration graph");
+    return RTS_ERR_CUDA;
+  }
+  return RTS_OK;
+}
+
+// Density correction of minor step j for every scene (graph or host-driven loop).
+static rts_status batch_correction(rts_ctx* c, int j) {
+  BatchState* b = c->batch;
+  int min_sched = 1 << 30;
+  for (int r = 0; r < c->p.n_levels && r < 4; ++r)
+    if (c->p.sched[r][j] < min_sched) min_sched = c->p.sched[r][j];
+  fill_view(c, b->h_view);
+  cudaError_t e = cudaMemcpyAsync(b->d_view, b->h_view, sizeof(BatchView), cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e != cudaSuccess) {
+    cuda_err(c, e, "batch view upload");
+    return RTS_ERR_CUDA;
+  }
+  const int prev = c->cur_phase;
+  c->cur_phase = RTS_PHASE_ITERATE;
+  note_launch(c, 1);
+  k_b_begin<<<1, b->ctl_threads, 0, c->stream>>>(b->ns, b->d_fbase, b->tile, j, min_sched, b->bctl,
+                                                b->sit);
+  rts_status st = RTS_OK;
+  if (b->use_graph) {
+    if (!b->exec) st = build_graph(c);
+    if (st == RTS_OK && (e = cudaGraphLaunch(b->exec, c->stream)) != cudaSuccess) {
+      cuda_err(c, e, "batched iteration graph launch");
+      st = RTS_ERR_CUDA;
+    }
+  } else {
+    for (int it = 0; it <= c->p.max_iters && st == RTS_OK; ++it) {
+      launch_body(c, c->stream, 0, 0);
+      e = cudaMemcpyAsync(&b->h_small[1], &b->bctl->any, sizeof(int), cudaMemcpyDeviceToHost,
+                          c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) {
+        cuda_err(c, e, "batched iteration");
+        st = RTS_ERR_CUDA;
+      }
+      if (!b->h_small[1]) break;
+    }
+  }
+  if (st == RTS_OK) {
+    e = cudaMemcpyAsync(b->h_sit, b->sit, sizeof(SceneIt) * (size_t)b->ns, cudaMemcpyDeviceToHost,
+                        c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&b->h_small[0], &b->bctl->iter, sizeof(int), cudaMemcpyDeviceToHost,
+                          c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      cuda_err(c, e, "batched iteration results");
+      st = RTS_ERR_CUDA;
+    }
+  }
+  c->cur_phase = prev;
+  if (st != RTS_OK) return st;
+  const int iters = b->h_small[0];
+  b->body_runs += iters;
+  c->kernels += 5 * (int64_t)iters;
+  c->launches[RTS_PHASE_ITERATE] += 5 * (int64_t)iters;
+  // the batch's summary of the minor step: per-scene counts summed or maximised
+  int gmax = 0, lmax = 0, rsum = 0, nconv = 0;
+  double emax = 0.0, esum = 0.0;
+  int64_t ntot = 0;
+  for (int s = 0; s < b->ns; ++s) {
+    const SceneIt& t = b->h_sit[s];
+    c->tot_iters += t.done;
+    c->tot_local += t.it_local;
+    c->tot_reverts += t.it_reverts;
+    if (t.it_global > gmax) gmax = t.it_global;
+    if (t.it_local > lmax) lmax = t.it_local;
+    rsum += t.it_reverts;
+    nconv |= t.it_notconv;
+    if (t.err_max > emax) emax = t.err_max;
+    esum += t.err_avg * t.n;
+    ntot += t.n;
+  }
+  c->tot_steps += 1;
+  c->it_iters = iters;
+  c->it_global = gmax;
+  c->it_local = lmax;
+  c->it_reverts = rsum;
+  c->it_notconv = nconv;
+  c->it_errmax = emax;
+  c->it_erravg = ntot > 0 ? esum / (double)ntot : 0.0;
+  if (gmax > c->p.max_global_iters) c->shorten_now = 1;
+  return nconv ? RTS_ERR_NOT_CONVERGED : RTS_OK;
+}
+
+rts_status batch_step(rts_ctx* c) {
+  pcisph_minor_begin(c);
+  const int j = c->minor;
+  rts_status status = batch_correction(c, j);
+  if (status != RTS_OK && status != RTS_ERR_NOT_CONVERGED) return status;
+  rts_status st = pcisph_minor_end(c, j);
+  return st != RTS_OK ? st : status;
+}
+
+void batch_delete(BatchState* b) { delete b; }
+
+void batch_free(rts_ctx* c) {
+  BatchState* b = c->batch;
+  if (!b) return;
+  drop_graph(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  cudaFree(b->d_geo);
+  cudaFree(b->d_fbase);
+  cudaFree(b->d_bbase);
+  cudaFree(b->d_zbase);
+  cudaFree(b->bctl);
+  cudaFree(b->sit);
+  cudaFree(b->d_view);
+  if (b->h_sit) cudaFreeHost(b->h_sit);
+  if (b->h_small) cudaFreeHost(b->h_small);
+  if (b->h_view) cudaFreeHost(b->h_view);
+  delete b;
+  c->batch = nullptr;
+}
+
+}  // namespace rts
+
+using namespace rts;
+
+// Set-up of a batched context (called by the context constructor in rts_api.cu before
+// the boundary is binned): device tables, scene fields of the kernel parameters.
+rts_status rts_batch_attach(rts_ctx* c, BatchState* b) {
+  c->batch = b;
+  const int ns = b->ns;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  A((void**)&b->d_geo, sizeof(SceneGeo) * ns);
+  A((void**)&b->d_fbase, sizeof(uint32_t) * (ns + 1));
+  A((void**)&b->d_bbase, sizeof(uint32_t) * (ns + 1));
+  A((void**)&b->d_zbase, sizeof(int) * (ns + 1));
+  A((void**)&b->bctl, sizeof(BatchCtl));
+  A((void**)&b->sit, sizeof(SceneIt) * ns);
+  A((void**)&b->d_view, sizeof(BatchView));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_sit, sizeof(SceneIt) * ns);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_small, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_view, sizeof(BatchView));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_geo, b->geo.data(), sizeof(SceneGeo) * ns, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_fbase, b->fbase.data(), sizeof(uint32_t) * (ns + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_bbase, b->bbase.data(), sizeof(uint32_t) * (ns + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_zbase, b->zbase.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->sit, 0, sizeof(SceneIt) * ns);
+  if (e == cudaSuccess) e = cudaMemset(b->bctl, 0, sizeof(BatchCtl));
+  if (e != cudaSuccess) {
+    cuda_err(c, e, "batch tables");
+    return e == cudaErrorMemoryAllocation ? RTS_ERR_OOM : RTS_ERR_CUDA;
+  }
+  memset(b->h_sit, 0, sizeof(SceneIt) * ns);
+  c->dp.n_scenes = ns;
+  c->dp.geo = b->d_geo;
+  c->dp.fbase = b->d_fbase;
+  c->dp.bbase = b->d_bbase;
+  c->dp.zbase = b->d_zbase;
+  b->ctl_threads = ((ns + 31) / 32) * 32;
+  size_grids(b);
+  return RTS_OK;
+}
+
+// Validation and layout of a batch; on success *out owns the host tables and *p2 holds
+// the parameters of the stacked grid.
+const char* rts_batch_plan(const rts_params* params, int32_t n_scenes, const rts_scene* scenes,
+                           rts_params* p2, int32_t* n_fluid, int32_t* n_boundary,
+                           BatchState** out) {
+  *out = nullptr;
+  if (!params || !scenes) return "params and scenes are required";
+  if (params->scheme != RTS_PCISPH || params->mode != RTS_MODE_REGIONAL)
+    return "a batch runs regional PCISPH (scheme RTS_PCISPH, mode RTS_MODE_REGIONAL)";
+  if (n_scenes < 1 || n_scenes > kMaxScenes) return "n_scenes must be in [1, 1024]";
+  int gap = params->expand_layers;
+  if (params->r1_search_rings > gap) gap = params->r1_search_rings;
+  if (gap < 1) gap = 1;
+  int64_t nf = 0, nbd = 0, z = 0;
+  int nx = 1, ny = 1;
+  BatchState* b = new (std::nothrow) BatchState();
+  if (!b) return "host allocation failed";
+  b->ns = n_scenes;
+  b->gap = gap;
+  b->fbase.assign(n_scenes + 1, 0);
+  b->bbase.assign(n_scenes + 1, 0);
+  b->zbase.assign(n_scenes + 1, 0);
+  b->geo.assign(n_scenes, SceneGeo());
+  for (int s = 0; s < n_scenes; ++s) {
+    const rts_scene& q = scenes[s];
+    const char* why = nullptr;
+    if (q.n_fluid < 0 || q.n_boundary < 0) why = "negative particle count in a scene";
+    for (int d = 0; d < 3 && !why; ++d) {
+      if (q.grid_dim[d] < 1 || q.grid_dim[d] > 4096) why = "scene grid_dim must be in [1, 4096]";
+      else if (!std::isfinite(q.domain_min[d])) why = "non-finite scene domain_min";
+      else if (params->wall_project && !(q.wall_lo[d] < q.wall_hi[d]))
+        why = "scene wall_lo must be below wall_hi on every axis";
+    }
+    if (why) {
+      delete b;
+      return why;
+    }
+    b->fbase[s] = (uint32_t)nf;
+    b->bbase[s] = (uint32_t)nbd;
+    b->zbase[s] = (int)z;
+    nf += q.n_fluid;
+    nbd += q.n_boundary;
+    SceneGeo& g = b->geo[s];
+    int dmax = 1;
+    for (int d = 0; d < 3; ++d) {
+      g.o[d] = q.domain_min[d];
+      g.od[d] = (double)q.domain_min[d];
+      g.n[d] = q.grid_dim[d];
+      g.wlo[d] = q.wall_lo[d];
+      g.whi[d] = q.wall_hi[d];
+      if (q.grid_dim[d] > dmax) dmax = q.grid_dim[d];
+    }
+    g.z0 = (int)z;
+    g.band = (float)(8.0 * ldexp(1.0, -24) * (dmax + 2));
+    if (q.grid_dim[0] > nx) nx = q.grid_dim[0];
+    if (q.grid_dim[1] > ny) ny = q.grid_dim[1];
+    z += q.grid_dim[2] + (s + 1 < n_scenes ? gap : 0);
+  }
+  if (nf > 0x7fffffff || nbd > 0x7fffffff || z > 65536) {
+    delete b;
+    return "batch too large (particles or stacked grid layers)";
+  }
+  b->fbase[n_scenes] = (uint32_t)nf;
+  b->bbase[n_scenes] = (uint32_t)nbd;
+  b->zbase[n_scenes] = (int)z;
+  b->dims[0] = nx;
+  b->dims[1] = ny;
+  b->dims[2] = (int)z;
+  b->threads = 256;
+  b->tile = 128;
+  b->use_graph = 1;
+  *p2 = *params;
+  p2->grid_dim[0] = nx;
+  p2->grid_dim[1] = ny;
+  p2->grid_dim[2] = (int)z;
+  for (int d = 0; d < 3; ++d) {
+    p2->domain_min[d] = 0.0f;   // unused: every scene has its own origin
+    p2->wall_lo[d] = 0.0f;      // unused: every scene has its own container
+    p2->wall_hi[d] = 1.0f;
+  }
+  *n_fluid = (int32_t)nf;
+  *n_boundary = (int32_t)nbd;
+  *out = b;
+  return nullptr;
+}
+
+// ------------------------------------------------------------------ C ABI ---
+
+extern "C" {
+
+rts_status rts_batch_scene_info(rts_ctx* c, int32_t scene, rts_pcisph_info* out) {
+  if (!c || !out || !c->batch) return RTS_ERR_ARG;
+  BatchState* b = c->batch;
+  if (scene < 0 || scene >= b->ns) return RTS_ERR_ARG;
+  const SceneIt& t = b->h_sit[scene];
+  out->iterations = t.done;
+  out->global_iterations = t.it_global;
+  out->local_iterations = t.it_local;
+  out->reverts = t.it_reverts;
+  out->not_converged = t.it_notconv;
+  out->minor = c->minor;
+  out->n_minor_current = c->n_minor_cur;
+  out->clean_majors = c->clean;
+  out->err_max = t.err_max;
+  out->err_avg = t.err_avg;
+  return RTS_OK;
+}
+
+rts_status rts_batch_layout(const rts_ctx* c, int32_t* grid_dim, int32_t* z0, int32_t* fluid_base,
+                            int32_t* boundary_base) {
+  if (!c || !c->batch) return RTS_ERR_ARG;
+  const BatchState* b = c->batch;
+  if (grid_dim)
+    for (int d = 0; d < 3; ++d) grid_dim[d] = b->dims[d];
+  for (int s = 0; s <= b->ns; ++s) {
+    if (z0) z0[s] = b->zbase[s];
+    if (fluid_base) fluid_base[s] = (int32_t)b->fbase[s];
+    if (boundary_base) boundary_base[s] = (int32_t)b->bbase[s];
+  }
+  return RTS_OK;
+}
+
+rts_status rts_batch_set_launch(rts_ctx* c, int32_t threads, int32_t tile, int32_t use_graph) {
+  if (!c || !c->batch) return RTS_ERR_ARG;
+  if (threads % 32 != 0 || threads < 64 || threads > 1024) return RTS_ERR_ARG;
+  if (tile % 32 != 0 || tile < 32 || tile > 8192) return RTS_ERR_ARG;
+  if (use_graph != 0 && use_graph != 1) return RTS_ERR_ARG;
+  BatchState* b = c->batch;
+  if (threads != b->threads || tile != b->tile) drop_graph(b);
+  b->threads = threads;
+  b->tile = tile;
+  b->use_graph = use_graph;
+  size_grids(b);
+  return RTS_OK;
+}
+
+rts_status rts_batch_get_launch(const rts_ctx* c, int32_t* threads, int32_t* tile,
+                                int32_t* use_graph, int64_t* iterations_run) {
+  if (!c || !c->batch) return RTS_ERR_ARG;
+  const BatchState* b = c->batch;
+  if (threads) *threads = b->threads;
+  if (tile) *tile = b->tile;
+  if (use_graph) *use_graph = b->use_graph;
+  if (iterations_run) *iterations_run = b->body_runs;
+  return RTS_OK;
+}
+
+rts_status rts_batch_autotune(rts_ctx* c, int32_t reps, int32_t* threads_out, int32_t* tile_out,
+                              float* ms_out) {
+  if (!c || !c->batch || reps < 1 || reps > 100) return RTS_ERR_ARG;
+  if (c->sticky) return RTS_ERR_STATE;
+  if (c->k == 0 && c->minor == 0) {
+    snprintf(c->err, sizeof c->err, "rts_batch_autotune: take a step first (neighbour lists)");
+    return RTS_ERR_STATE;
+  }
+  BatchState* b = c->batch;
+  const int n = c->n;
+  const size_t n1 = (size_t)(n > 0 ? n : 1), nbk = (size_t)c->dp.nblocks;
+  cudaStream_t st = c->stream;
+  // the iteration passes write these: keep them in the sort's spare buffers meanwhile
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void* d, const void* s, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, s, bytes, cudaMemcpyDeviceToDevice, st);
+  };
+  cp(c->s2.rho, c->s.rho, sizeof(float) * n1);
+  cp(c->s2.prs, c->s.prs, sizeof(float) * n1);
+  cp(c->s2.err, c->s.err, sizeof(float) * n1);
+  cp(c->s2.ap, c->s.ap, sizeof(float4) * n1);
+  cp(c->tmp_src, c->in_se, n1);
+  cp(c->act, c->ob, nbk);
+  const int cand_threads[3] = {128, 256, 512};
+  const int cand_tile[4] = {64, 128, 256, 512};
+  const int t0 = b->threads, l0 = b->tile;
+  int best_t = t0, best_l = l0;
+  float best = 3.4e38f;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&ea);
+  if (e == cudaSuccess) e = cudaEventCreate(&eb);
+  fill_view(c, b->h_view);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_view, b->h_view, sizeof(BatchView), cudaMemcpyHostToDevice, st);
+  for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+    for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+      b->threads = cand_threads[a];
+      b->tile = cand_tile[l];
+      size_grids(b);
+      float tot = 0.f;
+      for (int r = 0; r <= reps && e == cudaSuccess; ++r) {   // r = 0 warms up
+        k_b_begin<<<1, b->ctl_threads, 0, st>>>(b->ns, b->d_fbase, b->tile, 0, 1, b->bctl, b->sit);
+        e = cudaEventRecord(ea, st);
+        launch_body(c, st, 0, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(eb, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(eb);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ea, eb);
+        if (r > 0) tot += ms;
+      }
+      const float ms = tot / (float)reps;
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_t = b->threads;
+        best_l = b->tile;
+      }
+    }
+  }
+  c->kernels += (int64_t)12 * (reps + 1) * 6;
+  cp(c->s.rho, c->s2.rho, sizeof(float) * n1);
+  cp(c->s.prs, c->s2.prs, sizeof(float) * n1);
+  cp(c->s.err, c->s2.err, sizeof(float) * n1);
+  cp(c->s.ap, c->s2.ap, sizeof(float4) * n1);
+  cp(c->in_se, c->tmp_src, n1);
+  cp(c->ob, c->act, nbk);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (ea) cudaEventDestroy(ea);
+  if (eb) cudaEventDestroy(eb);
+  if (e != cudaSuccess) {
+    b->threads = t0;
+    b->tile = l0;
+    size_grids(b);
+    cuda_err(c, e, "rts_batch_autotune");
+    return RTS_ERR_CUDA;
+  }
+  drop_graph(b);
+  b->threads = best_t;
+  b->tile = best_l;
+  size_grids(b);
+  if (threads_out) *threads_out = best_t;
+  if (tile_out) *tile_out = best_l;
+  if (ms_out) *ms_out = best;
+  return RTS_OK;
+}
+
+}  // extern "C"

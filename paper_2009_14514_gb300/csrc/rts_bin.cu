@@ -62,7 +62,10 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
     }
   }
   int bad = 0;
-  uint32_t b = block_key(P, xi, &bad);
+  // a batch: each particle is binned in its own scene's grid (the fluid pass has v, the
+  // boundary pass not; the caller index gives the scene)
+  uint32_t b = P.n_scenes ? batch_key(P, xi, scene_of(v ? P.fbase : P.bbase, P.n_scenes, uid[i]), &bad)
+                          : block_key(P, xi, &bad);
   if (bad) {
     if (atomicCAS(&ctl->bad_set, 0, 1) == 0) {
       ctl->bad_uid = uid[i];

@@ -10,6 +10,17 @@ namespace rts {
 
 constexpr int kMaxLevels = 8;
 
+// One scene of a batch: its own block grid (origin in its own coordinates, dims) placed
+// in the stacked grid at z offset z0, and its container.
+struct SceneGeo {
+  float o[3];
+  double od[3];
+  int n[3];
+  int z0;
+  float band;        // FP32 block-coordinate band of this scene's grid (see block_coord)
+  float wlo[3], whi[3];
+};
+
 // Parameters as the kernels use them (FP32 physics, FP64 decision thresholds).
 struct DevParams {
   // block grid (Section 3)
@@ -46,6 +57,13 @@ struct DevParams {
   int level_clock;   // 0: validity = multiplier (Algorithm 1); 1: aligned to multiples
   int no_clamp;      // 1: negative Tait pressure kept
   float dt_b;
+  // batched scenes (n_scenes = 0: one scene, the fields above describe its grid)
+  int n_scenes;
+  const SceneGeo* geo;       // per scene
+  const uint32_t* fbase;     // n_scenes + 1: first fluid particle of each scene (caller
+                             // order, and block order: scenes occupy disjoint z ranges)
+  const uint32_t* bbase;     // n_scenes + 1: first boundary particle of each scene
+  const int* zbase;          // n_scenes + 1: first z layer of each scene in the stacked grid
 };
 
 // Device control block: status and counters written by kernels.
@@ -94,6 +112,8 @@ struct PState {
   float4* ap;       // PCISPH: pressure acceleration of the current minor step (else null)
   float* err;       // PCISPH: latest relative compression error (else null)
 };
+
+struct BatchState;  // batched scenes (rts_batch.cu)
 
 __device__ __forceinline__ void set_status(Ctl* ctl, int code) {
   atomicCAS(&ctl->status, 0, code);
@@ -154,13 +174,59 @@ __device__ __forceinline__ uint32_t block_key(const DevParams& P, float4 p, int*
 
 // Non-penetration of the container box: a particle beyond a face is put back on it and
 // the velocity component into that face is removed.
+__device__ __forceinline__ void wall_project_box(const float* lo, const float* hi, float4& x,
+                                                 float4& v) {
+  if (x.x < lo[0]) { x.x = lo[0]; v.x = fmaxf(v.x, 0.f); }
+  if (x.x > hi[0]) { x.x = hi[0]; v.x = fminf(v.x, 0.f); }
+  if (x.y < lo[1]) { x.y = lo[1]; v.y = fmaxf(v.y, 0.f); }
+  if (x.y > hi[1]) { x.y = hi[1]; v.y = fminf(v.y, 0.f); }
+  if (x.z < lo[2]) { x.z = lo[2]; v.z = fmaxf(v.z, 0.f); }
+  if (x.z > hi[2]) { x.z = hi[2]; v.z = fminf(v.z, 0.f); }
+}
+
 __device__ __forceinline__ void wall_project(const DevParams& P, float4& x, float4& v) {
-  if (x.x < P.wlo[0]) { x.x = P.wlo[0]; v.x = fmaxf(v.x, 0.f); }
-  if (x.x > P.whi[0]) { x.x = P.whi[0]; v.x = fminf(v.x, 0.f); }
-  if (x.y < P.wlo[1]) { x.y = P.wlo[1]; v.y = fmaxf(v.y, 0.f); }
-  if (x.y > P.whi[1]) { x.y = P.whi[1]; v.y = fminf(v.y, 0.f); }
-  if (x.z < P.wlo[2]) { x.z = P.wlo[2]; v.z = fmaxf(v.z, 0.f); }
-  if (x.z > P.whi[2]) { x.z = P.whi[2]; v.z = fminf(v.z, 0.f); }
+  wall_project_box(P.wlo, P.whi, x, v);
+}
+
+// Scene of entry i of a base table (largest s with base[s] <= i; empty scenes share
+// their successor's base and are skipped).
+__device__ __forceinline__ int scene_of(const uint32_t* base, int ns, uint32_t i) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(base + mid) <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int scene_of_z(const int* zbase, int ns, int z) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(zbase + mid) <= z) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Block of a particle of scene sc in the stacked grid: the scene's own block coordinates
+// (from its origin, in its own coordinates), shifted by the scene's z offset.
+__device__ __forceinline__ uint32_t batch_key(const DevParams& P, float4 p, int sc, int* bad) {
+  const SceneGeo& g = P.geo[sc];
+  int cx = block_coord(p.x, g.o[0], g.od[0], P.inv_edge, P.edged, g.n[0], g.band, bad);
+  int cy = block_coord(p.y, g.o[1], g.od[1], P.inv_edge, P.edged, g.n[1], g.band, bad);
+  int cz = block_coord(p.z, g.o[2], g.od[2], P.inv_edge, P.edged, g.n[2], g.band, bad);
+  return ((uint32_t)(cz + g.z0) * P.ny + cy) * P.nx + cx;
+}
+
+// Container of the particle at block-order index i (its scene's box in a batch).
+__device__ __forceinline__ void wall_project_at(const DevParams& P, uint32_t i, float4& x,
+                                                float4& v) {
+  if (P.n_scenes) {
+    const SceneGeo& g = P.geo[scene_of(P.fbase, P.n_scenes, i)];
+    wall_project_box(g.wlo, g.whi, x, v);
+  } else {
+    wall_project(P, x, v);
+  }
 }
 
 // Activity kernel modes.
@@ -238,6 +304,9 @@ struct rts_ctx {
   int last_global_level;
 
   // launch counting and optional per-phase event timing
+  // batched scenes (null for a single scene)
+  rts::BatchState* batch;
+
   int cur_phase;
   int64_t kernels;
   int64_t launches[RTS_NUM_PHASES];
@@ -266,7 +335,8 @@ rts_status launch_classify(rts_ctx* c);
 rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1);
 void scan_block_counts(uint32_t* count, int nb, uint32_t* tile_sums, uint32_t* cstart,
                        cudaStream_t stream);
-const char* validate_params(const rts_params* p, int32_t n, int32_t nb);  // nullptr if valid
+const char* validate_params(const rts_params* p, int32_t n, int32_t nb,
+                            int max_dim = 4096);  // nullptr if valid
 void make_dev_params(const rts_params& p, DevParams& d);
 rts_status launch_density(rts_ctx* c);
 rts_status launch_force(rts_ctx* c);
@@ -276,4 +346,18 @@ rts_status launch_global_max(rts_ctx* c);
 rts_status launch_level_hist(rts_ctx* c);
 const char* cuda_err(rts_ctx* c, cudaError_t e, const char* what);
 rts_status pcisph_step(rts_ctx* c, int64_t max_mult);
+// PCISPH minor step in three parts (shared by the single-scene and the batched step):
+// major-step start when due, list refresh, non-pressure forces and the minor step's
+// resets; then the density correction; then integration, validity and pre-emption.
+void pcisph_minor_begin(rts_ctx* c);
+rts_status pcisph_minor_end(rts_ctx* c, int j);
+rts_status batch_step(rts_ctx* c);
+void batch_free(rts_ctx* c);
+void batch_delete(BatchState* b);   // a state not attached to a context
 }  // namespace rts
+
+// Batched scenes (rts_batch.cu): validation and layout, then the device tables.
+const char* rts_batch_plan(const rts_params* params, int32_t n_scenes, const rts_scene* scenes,
+                           rts_params* p2, int32_t* n_fluid, int32_t* n_boundary,
+                           rts::BatchState** out);
+rts_status rts_batch_attach(rts_ctx* c, rts::BatchState* b);

@@ -17,41 +17,9 @@
 #include <cmath>
 #include <cstring>
 
-#include "rts_internal.cuh"
+#include "rts_pcisph_dev.cuh"
 
 namespace rts {
-
-constexpr unsigned kFullMask = 0xffffffffu;
-constexpr uint32_t kBnd = 0x80000000u;
-constexpr int kModeSched = 0, kModeGlobal = 1, kModeLocal = 2;
-
-__device__ __forceinline__ float pW(const DevParams& P, float q) {
-  if (q < 1.0f) return P.sigma * (1.0f + q * q * (-1.5f + 0.75f * q));
-  float t = 2.0f - q;
-  return q < 2.0f ? 0.25f * P.sigma * t * t * t : 0.0f;
-}
-
-__device__ __forceinline__ float pdW(const DevParams& P, float q) {
-  if (q < 1.0f) return P.sigma_h * q * (-3.0f + 2.25f * q);
-  float t = 2.0f - q;
-  return q < 2.0f ? -0.75f * P.sigma_h * t * t : 0.0f;
-}
-
-__device__ __forceinline__ bool pexact(float4 a, float4 b, double r2d) {
-  double dx = __dsub_rn((double)a.x, (double)b.x);
-  double dy = __dsub_rn((double)a.y, (double)b.y);
-  double dz = __dsub_rn((double)a.z, (double)b.z);
-  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) < r2d;
-}
-
-__device__ __forceinline__ double pnorm2(float x, float y, float z) {
-  double dx = x, dy = y, dz = z;
-  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-}
-
-__device__ __forceinline__ bool has_turn(const DevParams& P, int mode, int row, int j, int L) {
-  return mode == kModeGlobal || (mode == kModeSched && row <= P.sched[L][j]);
-}
 
 // ------------------------------------------------------------- regions ---
 
@@ -119,28 +87,7 @@ __global__ void k_observed(DevParams P, const uint32_t* __restrict__ filled, con
   const int nf = ctl->n_filled;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
     uint32_t b = filled[t];
-    uint8_t o = 0;
-    if (!in_re[b]) {
-      int L = preg[b];
-      int bx = b % P.nx, r = b / P.nx, by = r % P.ny, bz = r / P.ny;
-      for (int dz = -1; dz <= 1 && !o; ++dz) {
-        int cz = bz + dz;
-        if (cz < 0 || cz >= P.nz) continue;
-        for (int dy = -1; dy <= 1 && !o; ++dy) {
-          int cy = by + dy;
-          if (cy < 0 || cy >= P.ny) continue;
-          for (int dx = -1; dx <= 1 && !o; ++dx) {
-            int cx = bx + dx;
-            if (cx < 0 || cx >= P.nx || (!dx && !dy && !dz)) continue;
-            size_t c = ((size_t)cz * P.ny + cy) * P.nx + cx;
-            int Lc = preg[c];
-            if (Lc < 0) continue;
-            if (in_re[c] || Lc < L) o = 1;
-          }
-        }
-      }
-    }
-    ob[b] = o;
+    ob[b] = observed_one(P, b, preg, in_re);
   }
 }
 
@@ -236,14 +183,10 @@ __global__ void k_nonpressure(DevParams P, int n, PState s, const float4* __rest
 __global__ void k_predict(DevParams P, int n, PState s, float4* __restrict__ xs) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float4 x = s.x[i], v = s.v[i], a = s.a[i], pa = s.ap[i];
-  float dt = P.dt_b;
-  float vx = v.x + dt * (a.x + pa.x), vy = v.y + dt * (a.y + pa.y), vz = v.z + dt * (a.z + pa.z);
-  xs[i] = make_float4(x.x + dt * vx, x.y + dt * vy, x.z + dt * vz, 0.f);
+  xs[i] = predict_one(P, s, i);
 }
 
-// Predicted density, relative error and pressure of the participants (turn, S_e, S_ob):
-// rho* = m W(0) + sum m W(|x*_i - x*_j|), p += delta max(0, rho* - rho0).
+// Predicted density, relative error and pressure of the participants (turn, S_e, S_ob).
 __global__ void k_pdensity(DevParams P, int n, int j_minor, int row, int mode,
                            const uint32_t* __restrict__ key, PState s,
                            const uint8_t* __restrict__ in_se, const uint8_t* __restrict__ ob,
@@ -252,23 +195,7 @@ __global__ void k_pdensity(DevParams P, int n, int j_minor, int row, int mode,
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (!(has_turn(P, mode, row, j_minor, s.level[i]) || in_se[i] || ob[key[i]])) return;
-  float4 xi = xs[i];
-  float w = P.sigma;  // W(0): the particle itself
-  const uint32_t* list = nbl + (size_t)i * P.nbl_cap;
-  int cnt = s.nbr[i];
-  for (int e = 0; e < cnt; ++e) {
-    uint32_t j = list[e];
-    float4 xj = (j & kBnd) ? xb[j & ~kBnd] : xs[j];
-    float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-    float d2 = dx * dx + dy * dy + dz * dz;
-    w += pW(P, sqrtf(d2) * P.inv_h);
-  }
-  float rho = P.m * w;
-  float comp = fmaxf(0.f, rho - P.rho0);
-  float p = s.prs[i] + P.delta * comp;
-  s.rho[i] = rho;
-  s.err[i] = comp * P.inv_rho0;
-  s.prs[i] = p;
+  pdensity_one(P, s, i, xs, xb, nbl);
 }
 
 // S_e = {err > eta / 2}; R_e = blocks holding an S_e particle; max and sum of the latest
@@ -284,7 +211,7 @@ __global__ void k_se_reduce(DevParams P, int n, const uint32_t* __restrict__ key
     if (se) in_re[key[i]] = 1;
   }
   unsigned mx = __float_as_uint(e);
-  unsigned long long fx = (unsigned long long)((double)e * 4294967296.0 + 0.5);
+  unsigned long long fx = err_fixed(e);
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     mx = max(mx, __shfl_down_sync(kFullMask, mx, o));
@@ -308,43 +235,14 @@ __global__ void k_se_reduce(DevParams P, int n, const uint32_t* __restrict__ key
   }
 }
 
-// Pressure acceleration of turn and S_e: -m sum (p_i/rho_i*^2 + p_j/rho_j*^2) grad W(x*_ij);
-// boundary neighbours contribute the p_i/rho_i*^2 term only.
+// Pressure acceleration of turn and S_e.
 __global__ void k_ppressure(DevParams P, int n, int j_minor, int row, int mode, PState s,
                             const uint8_t* __restrict__ in_se, const float4* __restrict__ xs,
                             const float4* __restrict__ xb, const uint32_t* __restrict__ nbl) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (!(has_turn(P, mode, row, j_minor, s.level[i]) || in_se[i])) return;
-  float4 xi = xs[i];
-  const float ri = s.rho[i];
-  float ci = s.prs[i] / (ri * ri);
-  float ax = 0.f, ay = 0.f, az = 0.f;
-  const uint32_t* list = nbl + (size_t)i * P.nbl_cap;
-  int cnt = s.nbr[i];
-  for (int e = 0; e < cnt; ++e) {
-    uint32_t j = list[e];
-    float4 xj;
-    float cj;
-    if (j & kBnd) {
-      xj = xb[j & ~kBnd];
-      cj = 0.f;
-    } else {
-      xj = xs[j];
-      const float rj = s.rho[j];
-      cj = s.prs[j] / (rj * rj);
-    }
-    float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-    float d2 = dx * dx + dy * dy + dz * dz;
-    if (!(d2 > 0.f)) continue;
-    float d = sqrtf(d2);
-    float f = pdW(P, d * P.inv_h) / d;
-    float sc = -P.m * (ci + cj) * f;
-    ax += sc * dx;
-    ay += sc * dy;
-    az += sc * dz;
-  }
-  s.ap[i] = make_float4(ax, ay, az, 0.f);
+  ppressure_one(P, s, i, xs, xb, nbl);
 }
 
 // ------------------------------------------------------- Algorithm 2 ---
@@ -360,7 +258,7 @@ __global__ void k_integrate(DevParams P, int n, PState s) {
   x.x += dt * v.x;
   x.y += dt * v.y;
   x.z += dt * v.z;
-  if (P.wall_project) wall_project(P, x, v);
+  if (P.wall_project) wall_project_at(P, (uint32_t)i, x, v);
   s.x[i] = x;
   s.v[i] = v;
 }
@@ -680,15 +578,15 @@ static rts_status pcisph_global(rts_ctx* c, int64_t max_mult) {
   return status;
 }
 
-rts_status pcisph_step(rts_ctx* c, int64_t max_mult) {
-  if (c->p.mode != RTS_MODE_REGIONAL) return pcisph_global(c, max_mult);
+// Major-step start when due, neighbourhood refresh and non-pressure forces of the
+// refreshing particles, and the resets of the minor step (pressures, S_e, R_e, R_ob).
+void pcisph_minor_begin(rts_ctx* c) {
   const int n = c->n;
   const int g = grid_of(n > 0 ? n : 1);
   const int fg = filled_grid_size();
   const size_t nbk = (size_t)c->dp.nblocks;
   if (c->n_minor_cur <= 0) c->n_minor_cur = c->p.n_minor;
   if (c->minor == 0) major_start(c);
-  const int j = c->minor;
   if (n > 0) {
     PPhase ph(c, RTS_PHASE_DENSITY);
     note_launch(c, 1);
@@ -706,47 +604,61 @@ rts_status pcisph_step(rts_ctx* c, int64_t max_mult) {
   cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
   note_launch(c, 1);
   k_observed<<<fg, 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->preg, c->in_re, c->ob);
+}
 
-  rts_status status = run_correction(c, c->dp, j, false);
-  if (status != RTS_OK && status != RTS_ERR_NOT_CONVERGED) return status;
-  {
-    PPhase ph(c, RTS_PHASE_CORRECT);
+// Integration, validity, pre-emption and the major-step bookkeeping after the density
+// correction of minor step j (c->shorten_now set by the correction).
+rts_status pcisph_minor_end(rts_ctx* c, int j) {
+  const int n = c->n;
+  const int g = grid_of(n > 0 ? n : 1);
+  const size_t nbk = (size_t)c->dp.nblocks;
+  PPhase ph(c, RTS_PHASE_CORRECT);
+  note_launch(c, 2);
+  k_integrate<<<g, 256, 0, c->stream>>>(c->dp, n, c->s);
+  const int last = (j + 1 >= c->n_minor_cur) || c->shorten_now;
+  k_validity<<<g, 256, 0, c->stream>>>(c->dp, n, c->s, c->cflag);
+  if (!last && n > 0) {
     note_launch(c, 2);
-    k_integrate<<<g, 256, 0, c->stream>>>(c->dp, n, c->s);
-    if (c->it_global > c->p.max_global_iters) c->shorten_now = 1;
-    const int last = (j + 1 >= c->n_minor_cur) || c->shorten_now;
-    k_validity<<<g, 256, 0, c->stream>>>(c->dp, n, c->s, c->cflag);
-    if (!last && n > 0) {
-      note_launch(c, 2);
-      cudaMemcpyAsync(c->pnew, c->preg, sizeof(int32_t) * nbk, cudaMemcpyDeviceToDevice, c->stream);
-      k_preempt_mark<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->s, c->pnew);
-      k_preempt_apply<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->pnew, c->s, c->cflag);
-      int32_t* t = c->preg;
-      c->preg = c->pnew;
-      c->pnew = t;
-    }
-    c->k += 1;
-    if (last) {
-      if (c->shorten_now) {
-        c->n_minor_cur = c->p.short_minor;
+    cudaMemcpyAsync(c->pnew, c->preg, sizeof(int32_t) * nbk, cudaMemcpyDeviceToDevice, c->stream);
+    k_preempt_mark<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->s, c->pnew);
+    k_preempt_apply<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->pnew, c->s, c->cflag);
+    int32_t* t = c->preg;
+    c->preg = c->pnew;
+    c->pnew = t;
+  }
+  c->k += 1;
+  if (last) {
+    if (c->shorten_now) {
+      c->n_minor_cur = c->p.short_minor;
+      c->clean = 0;
+    } else if (c->n_minor_cur != c->p.n_minor) {
+      if (++c->clean >= c->p.clean_majors) {
+        c->n_minor_cur = c->p.n_minor;
         c->clean = 0;
-      } else if (c->n_minor_cur != c->p.n_minor) {
-        if (++c->clean >= c->p.clean_majors) {
-          c->n_minor_cur = c->p.n_minor;
-          c->clean = 0;
-        }
       }
-      c->minor = 0;
-    } else {
-      c->minor = j + 1;
     }
+    c->minor = 0;
+  } else {
+    c->minor = j + 1;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     cuda_err(c, e, "PCISPH step");
     return RTS_ERR_CUDA;
   }
-  return status;
+  return RTS_OK;
+}
+
+rts_status pcisph_step(rts_ctx* c, int64_t max_mult) {
+  if (c->p.mode != RTS_MODE_REGIONAL) return pcisph_global(c, max_mult);
+  if (c->batch) return batch_step(c);
+  pcisph_minor_begin(c);
+  const int j = c->minor;
+  rts_status status = run_correction(c, c->dp, j, false);
+  if (status != RTS_OK && status != RTS_ERR_NOT_CONVERGED) return status;
+  if (c->it_global > c->p.max_global_iters) c->shorten_now = 1;
+  rts_status st = pcisph_minor_end(c, j);
+  return st != RTS_OK ? st : status;
 }
 
 }  // namespace rts

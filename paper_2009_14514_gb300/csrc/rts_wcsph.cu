@@ -120,7 +120,7 @@ __global__ void k_block_rmin(DevParams P, int mode, int level_g,
 // validity.  Work lists: the evaluated particles, and the blocks holding one (each run of
 // equal blocks in a warp claims its block once through a stamped flag).  List positions
 // and counters are aggregated per CTA: one atomic per counter and CTA.
-constexpr int kActThreads = 1024;
+constexpr int kActThreads = 256;
 
 __global__ void __launch_bounds__(kActThreads) k_particle_activity(
     DevParams P, int mode, int mult_g, long long k1, int n, const uint32_t* __restrict__ key,

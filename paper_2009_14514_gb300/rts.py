@@ -27,6 +27,8 @@ EXPORTED = [
     "rts_pcisph_last", "rts_get_pcisph_state", "rts_get_neighbors",
     "rts_diff_create", "rts_diff_forward", "rts_diff_backward", "rts_diff_last_error",
     "rts_diff_destroy",
+    "rts_batch_init", "rts_batch_scene_info", "rts_batch_layout", "rts_batch_set_launch",
+    "rts_batch_get_launch", "rts_batch_autotune",
 ]
 
 
@@ -76,6 +78,12 @@ class RtsStats(C.Structure):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "level_count"}
         d["level_count"] = list(self.level_count)
         return d
+
+
+class RtsScene(C.Structure):
+    _fields_ = [("n_fluid", C.c_int32), ("n_boundary", C.c_int32),
+                ("domain_min", C.c_float * 3), ("grid_dim", C.c_int32 * 3),
+                ("wall_lo", C.c_float * 3), ("wall_hi", C.c_float * 3)]
 
 
 PHASES = ["bin", "classify", "activity", "density", "force", "correct", "iterate", "other"]
@@ -165,6 +173,12 @@ def lib():
             "rts_diff_create": [vp, i32, vp, i32, vp, i32, i32, vp, vp],
             "rts_diff_forward": [vp, vp, C.c_float, C.c_float, vp, vp],
             "rts_diff_backward": [vp, vp, vp, vp, vp, vp],
+            "rts_batch_init": [vp, i32, vp, vp, vp, vp, vp, vp],
+            "rts_batch_scene_info": [vp, i32, vp],
+            "rts_batch_layout": [vp, vp, vp, vp, vp],
+            "rts_batch_set_launch": [vp, i32, i32, i32],
+            "rts_batch_get_launch": [vp, vp, vp, vp, vp],
+            "rts_batch_autotune": [vp, i32, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -441,3 +455,72 @@ def rts_get_neighbors(ctx, cap=None):
     idx = np.zeros(max(n, 1) * cap, np.int32)
     _check(lib().rts_get_neighbors(ctx.handle, _ptr(counts), _ptr(idx), cap), "rts_get_neighbors", ctx)
     return [idx[i * cap: i * cap + counts[i]] for i in range(n)]
+
+
+# ------------------------------------------------------------ batched scenes ---
+
+def rts_batch_init(params, scenes_desc, x, v, xb, stream=None) -> Ctx:
+    """Batched RTS-PCISPH over many scenes (see rts.h).  scenes_desc: one dict per scene
+    with n_fluid, n_boundary, domain_min, grid_dim, wall_lo, wall_hi; x, v: all scenes'
+    fluid particles concatenated, xb: all boundary particles concatenated."""
+    P = params if isinstance(params, RtsParams) else make_params(params)
+    ns = len(scenes_desc)
+    arr = (RtsScene * max(ns, 1))()
+    for k, d in enumerate(scenes_desc):
+        arr[k].n_fluid = int(d["n_fluid"])
+        arr[k].n_boundary = int(d["n_boundary"])
+        for a in range(3):
+            arr[k].domain_min[a] = float(d["domain_min"][a])
+            arr[k].grid_dim[a] = int(d["grid_dim"][a])
+            arr[k].wall_lo[a] = float(d.get("wall_lo", [0.0] * 3)[a])
+            arr[k].wall_hi[a] = float(d.get("wall_hi", [0.0] * 3)[a])
+    n = int(x.shape[0])
+    nb = int(xb.shape[0])
+    x, v, xb = _f32(x, n), _f32(v, n), _f32(xb, nb)
+    h = C.c_void_p()
+    st = lib().rts_batch_init(C.byref(P), ns, arr, _ptr(x), _ptr(v), _ptr(xb), _stream(stream),
+                              C.byref(h))
+    _check(st, "rts_batch_init")
+    ctx = Ctx(h, P, n, nb)
+    ctx.n_scenes = ns
+    return ctx
+
+
+def rts_batch_scene_info(ctx, scene) -> dict:
+    info = RtsPcisphInfo()
+    _check(lib().rts_batch_scene_info(ctx.handle, int(scene), C.byref(info)),
+           "rts_batch_scene_info", ctx)
+    return info.as_dict()
+
+
+def rts_batch_layout(ctx) -> dict:
+    ns = ctx.n_scenes
+    dims = np.zeros(3, np.int32)
+    z0 = np.zeros(ns + 1, np.int32)
+    fb = np.zeros(ns + 1, np.int32)
+    bb = np.zeros(ns + 1, np.int32)
+    _check(lib().rts_batch_layout(ctx.handle, _ptr(dims), _ptr(z0), _ptr(fb), _ptr(bb)),
+           "rts_batch_layout", ctx)
+    return {"grid_dim": dims, "z0": z0, "fluid_base": fb, "boundary_base": bb}
+
+
+def rts_batch_set_launch(ctx, threads=256, tile=128, use_graph=True):
+    return _check(lib().rts_batch_set_launch(ctx.handle, int(threads), int(tile),
+                                             1 if use_graph else 0), "rts_batch_set_launch", ctx)
+
+
+def rts_batch_get_launch(ctx) -> dict:
+    t, l, g = C.c_int32(), C.c_int32(), C.c_int32()
+    it = C.c_int64()
+    _check(lib().rts_batch_get_launch(ctx.handle, C.byref(t), C.byref(l), C.byref(g), C.byref(it)),
+           "rts_batch_get_launch", ctx)
+    return {"threads": t.value, "tile": l.value, "use_graph": bool(g.value),
+            "iterations_run": it.value}
+
+
+def rts_batch_autotune(ctx, reps=3) -> dict:
+    t, l = C.c_int32(), C.c_int32()
+    ms = C.c_float()
+    _check(lib().rts_batch_autotune(ctx.handle, int(reps), C.byref(t), C.byref(l), C.byref(ms)),
+           "rts_batch_autotune", ctx)
+    return {"threads": t.value, "tile": l.value, "ms_per_iteration": ms.value}

@@ -245,3 +245,88 @@ def perturbed_state(scene, seed=777, *, vmax=40.0, amax=6e5, frac_levels=None):
     rho = (scene.params["rho0"] * (1.0 + 0.01 * rng.uniform(-1, 1, size=n))).astype(np.float32)
     prs = np.maximum(0.0, 2000.0 * rng.uniform(-0.2, 1.0, size=n)).astype(np.float32)
     return dict(v=v, a=a, level=level, validity=validity, klast=klast, rho=rho, p=prs)
+
+
+# ------------------------------------------------------------ batched scenes ---
+
+@dataclasses.dataclass
+class Batch:
+    """Independent scenes advanced together: shared parameters, per-scene grids and
+    containers, particles concatenated scene after scene."""
+    name: str
+    scenes: list
+    params: dict
+    desc: list             # per scene: n_fluid, n_boundary, domain_min, grid_dim, wall_lo, wall_hi
+    x: np.ndarray
+    v: np.ndarray
+    xb: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    @property
+    def nb(self) -> int:
+        return int(self.xb.shape[0])
+
+
+def make_batch(scenes_list, name="batch") -> Batch:
+    """Concatenate scenes that share every parameter but their grid and container."""
+    p0 = dict(scenes_list[0].params)
+    desc = []
+    for sc in scenes_list:
+        p = sc.params
+        for k, val in p.items():
+            if k not in ("domain_min", "grid_dim", "wall_lo", "wall_hi") and val != p0[k]:
+                raise ValueError(f"scene {sc.name} differs from the batch in {k}")
+        desc.append(dict(n_fluid=sc.n, n_boundary=sc.nb, domain_min=list(p["domain_min"]),
+                         grid_dim=list(p["grid_dim"]), wall_lo=list(p["wall_lo"]),
+                         wall_hi=list(p["wall_hi"])))
+    x = np.ascontiguousarray(np.concatenate([sc.x for sc in scenes_list]), np.float32)
+    v = np.ascontiguousarray(np.concatenate([sc.v for sc in scenes_list]), np.float32)
+    xb = np.ascontiguousarray(np.concatenate([sc.xb for sc in scenes_list]), np.float32)
+    return Batch(name=name, scenes=list(scenes_list), params=p0, desc=desc, x=x, v=v, xb=xb)
+
+
+def batch_counts(n_scenes=64, seed=4321, lo=1.0e4, hi=2.0e5):
+    """Target particle counts drawn log-uniformly in [lo, hi] (seeded)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.round(np.exp(rng.uniform(np.log(lo), np.log(hi), n_scenes))).astype(np.int64)
+
+
+def batch_member(i, n_target, s=0.01, dt_b=3.5e-4):
+    """Scene i of a batch: even i a dam break, a column of ceil(N^(1/3))^3 particles in the
+    corner of a (4, 2, 2) x column-side tank; odd i the 1M pool drop scaled to about N
+    particles (pool a x a x a/8, cube 0.15 a on a side, dropped from 0.1 a s above the
+    pool, tank a x a x a/2 spacings).  PCISPH parameters of the 1M pool drop."""
+    if i % 2 == 0:
+        c = int(math.ceil(n_target ** (1.0 / 3.0) - 1e-9))
+        box = (4 * c * s, 2 * c * s, 2 * c * s)
+        fluid = lattice((c, c, c), s)
+        name = f"dam_break_{c}^3"
+    else:
+        a = max(8, int(round((8.0 * n_target / (1.0 + 8 * 0.15 ** 3)) ** (1.0 / 3.0))))
+        hz = max(2, int(round(a / 8)))
+        k = max(2, int(round(0.15 * a)))
+        box = (a * s, a * s, int(round(a / 2)) * s)
+        pool = lattice((a, a, hz), s)
+        c0 = [0.5 * box[0] - 0.5 * k * s, 0.5 * box[1] - 0.5 * k * s, hz * s + 0.1 * a * s]
+        cube = lattice((k, k, k), s, offset=c0)
+        fluid = np.concatenate([pool, cube], axis=0)
+        name = f"pool_{a}x{a}x{hz}_drop_{k}^3"
+    return _finish(f"batch{i}_{name}", fluid, box, s, pcisph_params(s, box, dt_b), 1234, 0.0)
+
+
+def pcisph_batch(n_scenes=64, seed=4321, lo=1.0e4, hi=2.0e5, s=0.01, dt_b=3.5e-4) -> Batch:
+    """The batched workload: n_scenes dam breaks and pool drops with particle counts
+    drawn log-uniformly in [lo, hi] (seed 4321)."""
+    counts = batch_counts(n_scenes, seed, lo, hi)
+    members = [batch_member(i, int(n), s, dt_b) for i, n in enumerate(counts)]
+    return make_batch(members, name=f"pcisph_batch_{n_scenes}")
+
+
+def pcisph_batch_small() -> Batch:
+    """Three small scenes for parity tests: the small pool drop, a 12^3 dam break and a
+    16 x 16 x 2 pool with a 3^3 drop (about 12k particles in all)."""
+    return make_batch([pcisph_drop_small(), batch_member(0, 1728), batch_member(1, 600)],
+                      name="pcisph_batch_small")
