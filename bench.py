@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--profile-batch", type=int, default=0, metavar="SCENES",
                     help="short run for ncu: the first SCENES scenes of the batched PCISPH "
                          "workload for --steps minor steps (nothing printed but a line)")
+    ap.add_argument("--batch-host-loop", action="store_true",
+                    help="--profile-batch: iterations launched from the host (no graph)")
     ap.add_argument("--profile-case", action="store_true",
                     help="short run for ncu: 1M jittered lattice with a seeded dynamic state, "
                          "primed, then --steps windows (few launches, nothing printed but a line)")
@@ -104,6 +106,8 @@ def profile_batch(args):
     from paper_2009_14514_gb300 import rts, scenes
     b = scenes.pcisph_batch(n_scenes=args.profile_batch)
     ctx = rts.rts_batch_init(b.params, b.desc, b.x, b.v, b.xb)
+    if args.batch_host_loop:
+        rts.rts_batch_set_launch(ctx, 256, 128, False)
     st = rts.rts_advance(ctx, args.steps * b.params["dt_b"])
     print(json.dumps({"profile_batch": b.name, "particles": b.n, "substeps": st["substeps"],
                       "scene_iterations": st["pcisph_iterations"],
