@@ -127,6 +127,9 @@ void rts::make_dev_params(const rts_params& p, DevParams& d) {
   d.r = p.support_r;
   d.r2 = p.support_r * p.support_r;
   d.r2d = (double)p.support_r * (double)p.support_r;
+  d.r2_dh = (float)d.r2d;
+  d.r2_dl = (float)(d.r2d - (double)d.r2_dh);
+  d.r2_win = (float)ldexp(d.r2d, -38);
   d.r2_lo = (float)(d.r2d * (1.0 - 1e-5));
   d.r2_hi = (float)(d.r2d * (1.0 + 1e-5));
   double h = 0.5 * (double)p.support_r;

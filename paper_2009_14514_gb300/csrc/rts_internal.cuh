@@ -33,6 +33,7 @@ struct DevParams {
   // cubic spline kernel, h = r / 2, support r
   float r, r2, r2_lo, r2_hi, h, inv_h, sigma, sigma_h;  // sigma_h = sigma / h
   double r2d;
+  float r2_dh, r2_dl, r2_win;  // r2d = r2_dh + r2_dl exactly; undecided window 2^-38 r2d
   // WCSPH physics
   float m, rho0, inv_rho0, tait_B, gamma;
   int gamma_is_7;
@@ -163,6 +164,51 @@ __device__ __forceinline__ int block_coord(float x, float o, double od, float in
     return 0;
   }
   return (int)fd;
+}
+
+// ------------------------------------------------ exact neighbour predicate ---
+//
+// The neighbour test of the double-precision definition, |x_i - x_j|^2 < r^2 with the
+// squared distance formed in FP64 from the FP32 positions, for pairs inside the FP32
+// guard band.  FP64 runs at a small fraction of the FP32 rate on this GPU, and lattice
+// states (resting pools, an undisturbed column) put many pairs at exactly r, so the
+// squared distance S is first formed without rounding error in FP32 pieces: the
+// coordinate differences by Knuth's TwoSum (d = dh + dl exactly), their squares by the
+// FMA TwoProduct (dh^2 = p + e exactly), the three p summed by TwoSum; the small terms
+// (e, 2 dh dl, the TwoSum errors; dl^2 <= 2^-48 dh^2 is dropped) are added in FP32.  S
+// is then known within 2^-42 S, and FP64 forms it within 3 * 2^-53 S, so whenever the
+// computed S - r^2 lies outside +-2^-38 r^2 both give the same answer; inside that
+// window (a near or exact tie) the FP64 expression itself decides.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+static __device__ __noinline__ bool nbr_exact_fp64(float4 a, float4 b, double r2d) {
+  const double dx = __dsub_rn((double)a.x, (double)b.x);
+  const double dy = __dsub_rn((double)a.y, (double)b.y);
+  const double dz = __dsub_rn((double)a.z, (double)b.z);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) < r2d;
+}
+
+__device__ __forceinline__ bool nbr_exact(const DevParams& P, float4 a, float4 b) {
+  float hx, lx, hy, ly, hz, lz;
+  two_sum(a.x, -b.x, hx, lx);
+  two_sum(a.y, -b.y, hy, ly);
+  two_sum(a.z, -b.z, hz, lz);
+  const float px = __fmul_rn(hx, hx), py = __fmul_rn(hy, hy), pz = __fmul_rn(hz, hz);
+  const float ex = __fmaf_rn(hx, hx, -px), ey = __fmaf_rn(hy, hy, -py), ez = __fmaf_rn(hz, hz, -pz);
+  float s1, t1, s2, t2;
+  two_sum(px, py, s1, t1);
+  two_sum(s1, pz, s2, t2);
+  const float cross = __fmul_rn(2.0f, __fadd_rn(__fadd_rn(__fmul_rn(hx, lx), __fmul_rn(hy, ly)),
+                                                  __fmul_rn(hz, lz)));
+  const float small = __fadd_rn(__fadd_rn(__fadd_rn(ex, ey), __fadd_rn(ez, cross)), __fadd_rn(t1, t2));
+  const float diff = __fadd_rn(__fsub_rn(s2, P.r2_dh), __fsub_rn(small, P.r2_dl));
+  if (diff < -P.r2_win) return true;
+  if (diff > P.r2_win) return false;
+  return nbr_exact_fp64(a, b, P.r2d);
 }
 
 __device__ __forceinline__ uint32_t block_key(const DevParams& P, float4 p, int* bad) {

@@ -126,7 +126,7 @@ __global__ void k_lists(DevParams P, int n, const uint32_t* __restrict__ key,
           float dx = xi.x - xj.x, dy2 = xi.y - xj.y, dz2 = xi.z - xj.z;
           float d2 = dx * dx + dy2 * dy2 + dz2 * dz2;
           bool in = d2 < P.r2_lo;
-          if (d2 >= P.r2_lo && d2 < P.r2_hi) in = pexact(xi, xj, P.r2d);
+          if (d2 >= P.r2_lo && d2 < P.r2_hi) in = nbr_exact(P, xi, xj);
           if (in) {
             if (cnt < P.nbl_cap) list[cnt] = pass ? (j | kBnd) : j;
             ++cnt;

@@ -25,13 +25,6 @@ __device__ __forceinline__ float pdW(const DevParams& P, float q) {
   return q < 2.0f ? -0.75f * P.sigma_h * t * t : 0.0f;
 }
 
-__device__ __forceinline__ bool pexact(float4 a, float4 b, double r2d) {
-  double dx = __dsub_rn((double)a.x, (double)b.x);
-  double dy = __dsub_rn((double)a.y, (double)b.y);
-  double dz = __dsub_rn((double)a.z, (double)b.z);
-  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) < r2d;
-}
-
 __device__ __forceinline__ double pnorm2(float x, float y, float z) {
   double dx = x, dy = y, dz = z;
   return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));

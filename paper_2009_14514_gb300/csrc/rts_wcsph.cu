@@ -223,16 +223,6 @@ __device__ __forceinline__ float spline_dW(const DevParams& P, float q) {  // dW
   return q < 2.0f ? -0.75f * P.sigma_h * t * t : 0.0f;
 }
 
-// Exact neighbour predicate of the double-precision definition (used in the FP32
-// guard band around r^2).
-__device__ __forceinline__ bool exact_nbr(float4 a, float4 b, double r2d) {
-  double dx = __dsub_rn((double)a.x, (double)b.x);
-  double dy = __dsub_rn((double)a.y, (double)b.y);
-  double dz = __dsub_rn((double)a.z, (double)b.z);
-  double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-  return d2 < r2d;
-}
-
 __device__ __forceinline__ float tait(const DevParams& P, float rho) {
   float r = rho * P.inv_rho0;
   float rg;
@@ -471,7 +461,7 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
             const float4 xj = sx[k];
             const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
             const float d2 = dx * dx + dy * dy + dz * dz;
-            if (!(d2 < P.r2_lo || exact_nbr(xi, xj, P.r2d))) continue;
+            if (!(d2 < P.r2_lo || nbr_exact(P, xi, xj))) continue;
             if (d2 > 0.f) {
               wsum += spline_W(P, d2 * rsqrtf(d2) * P.inv_h);
               put |= 1u << j;
