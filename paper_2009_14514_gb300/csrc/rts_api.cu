@@ -160,6 +160,10 @@ void rts::make_dev_params(const rts_params& p, DevParams& d) {
   d.n_levels = p.n_levels;
   for (int L = 0; L < p.n_levels; ++L) d.mult[L] = p.level_mult[L];
   level_thresholds(p, d.vthr2, d.athr2, d.eq1);
+  for (int L = 0; L < kMaxLevels; ++L) {
+    d.vthr2f[L] = (float)d.vthr2[L];
+    d.athr2f[L] = (float)d.athr2[L];
+  }
   d.force_level = p.force_level;
   d.dt_b = p.dt_b;
   d.nbl_cap = p.max_neighbors > 0 ? p.max_neighbors : 96;
@@ -440,21 +444,47 @@ static int host_pick_level(const rts_ctx* c, double v2, double a2) {
   return L;
 }
 
+int rts::pick_level_from_f32_max(const DevParams& d, float v2, float a2) {
+  int L = 0;
+  for (int l = 0; l < d.n_levels; ++l) {
+    const float tv = d.vthr2f[l], ta = d.athr2f[l];
+    if ((std::isfinite(tv) && std::fabs(v2 - tv) <= 1e-5f * tv) ||
+        (std::isfinite(ta) && std::fabs(a2 - ta) <= 1e-5f * ta) || !std::isfinite(v2) ||
+        !std::isfinite(a2))
+      return -1;
+    if (d.eq1[l] && v2 <= tv && a2 <= ta) L = l;
+  }
+  return L;
+}
+
 static rts_status wcsph_global(rts_ctx* c, int64_t max_mult) {
   int L = 0;
   if (c->p.mode == RTS_MODE_GLOBAL_ADAPTIVE) {
     finalize(c);  // the step size is chosen from the corrected state
     {
       Phase ph(c, RTS_PHASE_CLASSIFY);
-      launch_global_max(c);
+      launch_global_max(c, 0);
     }
-    CK(cudaMemcpyAsync(&c->h_ctl->vmax2_bits, &c->ctl->vmax2_bits, 2 * sizeof(unsigned long long),
+    CK(cudaMemcpyAsync(&c->h_ctl->vmax2f_bits, &c->ctl->vmax2f_bits, 2 * sizeof(unsigned int),
                        cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    double v2, a2;
-    memcpy(&v2, &c->h_ctl->vmax2_bits, sizeof v2);
-    memcpy(&a2, &c->h_ctl->amax2_bits, sizeof a2);
-    L = host_pick_level(c, v2, a2);
+    float v2f, a2f;
+    memcpy(&v2f, &c->h_ctl->vmax2f_bits, sizeof v2f);
+    memcpy(&a2f, &c->h_ctl->amax2f_bits, sizeof a2f);
+    L = pick_level_from_f32_max(c->dp, v2f, a2f);
+    if (L < 0) {   // a maximum at a threshold: the FP64 maxima decide
+      {
+        Phase ph(c, RTS_PHASE_CLASSIFY);
+        launch_global_max(c, 1);
+      }
+      CK(cudaMemcpyAsync(&c->h_ctl->vmax2_bits, &c->ctl->vmax2_bits,
+                         2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      double v2, a2;
+      memcpy(&v2, &c->h_ctl->vmax2_bits, sizeof v2);
+      memcpy(&a2, &c->h_ctl->amax2_bits, sizeof a2);
+      L = host_pick_level(c, v2, a2);
+    }
   }
   int64_t m = c->p.level_mult[L];
   if (m > max_mult) m = max_mult;

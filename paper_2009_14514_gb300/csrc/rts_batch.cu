@@ -222,7 +222,8 @@ __global__ void k_b_predict(DevParams P, const BatchView* __restrict__ Vp, Batch
 }
 
 // Predicted density and pressure of the participants (turn, S_e, R_ob), then S_e, R_e and
-// the scene's error reductions over all its particles' latest errors.
+// the scene's error reductions over all its particles' latest errors (lane 0 of each
+// particle's group does the per-particle part).
 __global__ void k_b_density(DevParams P, const BatchView* __restrict__ Vp, BatchCtl* B,
                             SceneIt* S, int tile) {
   extern __shared__ int qpre[];
@@ -234,16 +235,26 @@ __global__ void k_b_density(DevParams P, const BatchView* __restrict__ Vp, Batch
   const float half_eta = 0.5f * P.eta;
   int sc;
   uint32_t i0, i1;
+  const int min_sched = B->min_sched;
   while (next_tile(B, 1, qpre, ns, qtot, P.fbase, tile, &sc, &i0, &i1)) {
     const int mode = S[sc].mode, row = S[sc].row;
+    // every particle of the scene takes part: kPLanes lanes per particle, else one (as
+    // the single-scene path chooses)
+    const bool dense = mode == kModeGlobal || (mode == kModeSched && row <= min_sched);
+    const int lanes = dense ? kPLanes : 1;
+    const int sub = lane % lanes;
     unsigned mx = 0;
     unsigned long long fx = 0;
-    for (uint32_t base = i0; base < i1; base += 32) {
-      const uint32_t i = base + lane;
-      if (i < i1) {
-        const uint32_t b = V.key[i];
-        if (has_turn(P, mode, row, j, V.s.level[i]) || V.in_se[i] || V.ob[b])
-          pdensity_one(P, V.s, (int)i, V.xs, V.xb, V.nbl);
+    for (uint32_t base = i0; base < i1; base += 32 / lanes) {
+      const uint32_t i = base + (uint32_t)(lane / lanes);
+      const bool in = i < i1;
+      const uint32_t b = in ? V.key[i] : 0u;
+      const bool part = in && (has_turn(P, mode, row, j, V.s.level[i]) || V.in_se[i] || V.ob[b]);
+      if (dense)
+        pdensity_group<kPLanes>(P, V.s, (int)i, part, sub, V.xs, V.xb, V.nbl);
+      else
+        pdensity_group<1>(P, V.s, (int)i, part, sub, V.xs, V.xb, V.nbl);
+      if (in && sub == 0) {
         const float e = V.s.err[i];
         const bool se = e > half_eta;
         V.in_se[i] = se ? 1 : 0;
@@ -289,11 +300,20 @@ __global__ void k_b_pressure(DevParams P, const BatchView* __restrict__ Vp, Batc
   const int lane = threadIdx.x & 31;
   int sc;
   uint32_t i0, i1;
+  const int min_sched = B->min_sched;
   while (next_tile(B, 2, qpre, ns, qtot, P.fbase, tile, &sc, &i0, &i1)) {
     const int mode = S[sc].mode, row = S[sc].row;
-    for (uint32_t i = i0 + lane; i < i1; i += 32)
-      if (has_turn(P, mode, row, j, V.s.level[i]) || V.in_se[i])
-        ppressure_one(P, V.s, (int)i, V.xs, V.xb, V.nbl);
+    const bool dense = mode == kModeGlobal || (mode == kModeSched && row <= min_sched);
+    const int lanes = dense ? kPLanes : 1;
+    const int sub = lane % lanes;
+    for (uint32_t base = i0; base < i1; base += 32 / lanes) {
+      const uint32_t i = base + (uint32_t)(lane / lanes);
+      const bool part = i < i1 && (has_turn(P, mode, row, j, V.s.level[i]) || V.in_se[i]);
+      if (dense)
+        ppressure_group<kPLanes>(P, V.s, (int)i, part, sub, V.xs, V.xb, V.nbl);
+      else
+        ppressure_group<1>(P, V.s, (int)i, part, sub, V.xs, V.xb, V.nbl);
+    }
   }
 }
 

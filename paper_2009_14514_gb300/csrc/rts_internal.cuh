@@ -53,6 +53,7 @@ struct DevParams {
   int n_levels;
   int mult[kMaxLevels];
   double vthr2[kMaxLevels], athr2[kMaxLevels];
+  float vthr2f[kMaxLevels], athr2f[kMaxLevels];   // the same thresholds rounded to FP32
   int eq1[kMaxLevels];
   int force_level;
   int level_clock;   // 0: validity = multiplier (Algorithm 1); 1: aligned to multiples
@@ -80,6 +81,8 @@ struct Ctl {
   int n_filled;                  // blocks holding a fluid particle (filled list length)
   unsigned long long vmax2_bits; // global max |v|^2 (FP64 bits, non-negative)
   unsigned long long amax2_bits; // global max |a|^2
+  unsigned int vmax2f_bits;      // the same maxima of the FP32 norms (FP32 bits)
+  unsigned int amax2f_bits;
   unsigned long long level_count[kMaxLevels];
   unsigned int err_max_bits;      // PCISPH: max relative error (FP32 bits)
   unsigned long long err_sum_fx;  // PCISPH: sum of relative errors, fixed point 2^-32
@@ -149,21 +152,27 @@ enum PendMode { kPendNone = 0, kPendCorrect = 1, kPendPrime = 2 };
 // carries three roundings, so it is within 3 * 2^-24 * t of the exact one; within
 // band (8 * 2^-24 * the largest coordinate of the grid, set on the host) of an integer
 // the FP64 quotient decides, so the result is that of the double-precision definition.
+// Outside the band the FP32 floor is the answer; its range test and conversion stay in
+// FP32 (exact: n < 2^24), so FP64 (a small fraction of the FP32 rate here) runs only in
+// the band.
 __device__ __forceinline__ int block_coord(float x, float o, double od, float inv_e, double ed,
                                            int n, float band, int* bad) {
   float t = (x - o) * inv_e;
   float f = floorf(t);
   float fr = t - f;
-  double fd;
-  if (fr < band || fr > 1.0f - band)
-    fd = floor(__ddiv_rn(__dsub_rn((double)x, od), ed));
-  else
-    fd = (double)f;
-  if (!(fd >= 0.0 && fd < (double)n)) {
+  if (fr < band || fr > 1.0f - band) {
+    const double fd = floor(__ddiv_rn(__dsub_rn((double)x, od), ed));
+    if (!(fd >= 0.0 && fd < (double)n)) {
+      *bad = 1;
+      return 0;
+    }
+    return (int)fd;
+  }
+  if (!(f >= 0.0f && f < (float)n)) {
     *bad = 1;
     return 0;
   }
-  return (int)fd;
+  return (int)f;
 }
 
 // ------------------------------------------------ exact neighbour predicate ---
@@ -384,11 +393,14 @@ void scan_block_counts(uint32_t* count, int nb, uint32_t* tile_sums, uint32_t* c
 const char* validate_params(const rts_params* p, int32_t n, int32_t nb,
                             int max_dim = 4096);  // nullptr if valid
 void make_dev_params(const rts_params& p, DevParams& d);
+// Level of the global adaptive comparator from the FP32 maxima (as from the FP64 maxima);
+// -1 when a maximum lies within 1e-5 of a threshold and the FP64 maxima must decide.
+int pick_level_from_f32_max(const DevParams& d, float v2, float a2);
 rts_status launch_density(rts_ctx* c);
 rts_status launch_force(rts_ctx* c);
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime);
 rts_status finalize(rts_ctx* c);
-rts_status launch_global_max(rts_ctx* c);
+rts_status launch_global_max(rts_ctx* c, int fp64);
 rts_status launch_level_hist(rts_ctx* c);
 const char* cuda_err(rts_ctx* c, cudaError_t e, const char* what);
 rts_status pcisph_step(rts_ctx* c, int64_t max_mult);

@@ -32,37 +32,62 @@ __global__ void k_preg_from_blevel(const uint32_t* __restrict__ filled, const Ct
   }
 }
 
-// Section 5.5: blocks within Chebyshev distance <= layers of a filled block of region
-// <= target take min(region, target) (Jacobi: reads in, writes out; filled blocks only).
-__global__ void k_dilate(DevParams P, const uint32_t* __restrict__ filled, const Ctl* ctl,
-                         const int32_t* __restrict__ in, int32_t* __restrict__ out, int target,
-                         int layers) {
+// Section 5.5 expansion: a filled block within Chebyshev distance <= layers of a block
+// of region <= target takes min(region, target) (Jacobi: reads in, writes out; filled
+// blocks only).  The box is the product of three clipped intervals, so it is done as
+// three separable passes: an x pass marks the blocks with a block of region <= target
+// within `layers` along x (from the region field), a y pass widens the marks along y,
+// and a pass over the filled blocks widens along z and applies the minimum; each block
+// reads 2 layers + 1 values per pass instead of (2 layers + 1)^3.
+__global__ void k_dilate_x(DevParams P, const int32_t* __restrict__ in, int target, int layers,
+                           uint8_t* __restrict__ mx) {
+  const int64_t nb = (int64_t)P.nblocks;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int bx = (int)(b % P.nx);
+    const int x0 = bx - layers < 0 ? 0 : bx - layers;
+    const int x1 = bx + layers >= P.nx ? P.nx - 1 : bx + layers;
+    const int32_t* row = in + (b - bx);
+    uint8_t m = 0;
+    for (int cx = x0; cx <= x1; ++cx) {
+      const int Lc = row[cx];
+      m |= (Lc >= 0 && Lc <= target) ? 1 : 0;
+    }
+    mx[b] = m;
+  }
+}
+
+__global__ void k_dilate_y(DevParams P, const uint8_t* __restrict__ mx, int layers,
+                           uint8_t* __restrict__ my) {
+  const int64_t nb = (int64_t)P.nblocks;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int by = (int)((b / P.nx) % P.ny);
+    const int y0 = by - layers < 0 ? 0 : by - layers;
+    const int y1 = by + layers >= P.ny ? P.ny - 1 : by + layers;
+    const int64_t base = b - (int64_t)by * P.nx;
+    uint8_t m = 0;
+    for (int cy = y0; cy <= y1; ++cy) m |= mx[base + (int64_t)cy * P.nx];
+    my[b] = m;
+  }
+}
+
+__global__ void k_dilate_z(DevParams P, const uint32_t* __restrict__ filled, const Ctl* ctl,
+                           const int32_t* __restrict__ in, const uint8_t* __restrict__ my,
+                           int target, int layers, int32_t* __restrict__ out) {
   const int nf = ctl->n_filled;
+  const int64_t nxy = (int64_t)P.nx * P.ny;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
-    uint32_t b = filled[t];
+    const uint32_t b = filled[t];
     int L = in[b];
     if (L > target) {
-      int bx = b % P.nx, r = b / P.nx, by = r % P.ny, bz = r / P.ny;
-      bool hit = false;
-      for (int dz = -layers; dz <= layers && !hit; ++dz) {
-        int cz = bz + dz;
-        if (cz < 0 || cz >= P.nz) continue;
-        for (int dy = -layers; dy <= layers && !hit; ++dy) {
-          int cy = by + dy;
-          if (cy < 0 || cy >= P.ny) continue;
-          int x0 = bx - layers < 0 ? 0 : bx - layers;
-          int x1 = bx + layers >= P.nx ? P.nx - 1 : bx + layers;
-          const int32_t* row = in + ((size_t)cz * P.ny + cy) * P.nx;
-          for (int cx = x0; cx <= x1; ++cx) {
-            int Lc = row[cx];
-            if (Lc >= 0 && Lc <= target) {
-              hit = true;
-              break;
-            }
-          }
-        }
-      }
-      if (hit) L = target;
+      const int bz = (int)(b / nxy);
+      const int z0 = bz - layers < 0 ? 0 : bz - layers;
+      const int z1 = bz + layers >= P.nz ? P.nz - 1 : bz + layers;
+      const int64_t base = (int64_t)b - (int64_t)bz * nxy;
+      uint8_t m = 0;
+      for (int cz = z0; cz <= z1; ++cz) m |= my[base + (int64_t)cz * nxy];
+      if (m) L = target;
     }
     out[b] = L;
   }
@@ -144,37 +169,44 @@ __global__ void k_lists(DevParams P, int n, const uint32_t* __restrict__ key,
 
 // Non-pressure acceleration of refreshing particles: gravity + artificial viscosity
 // (nu = alpha h c / rho0) over the neighbourhood; boundary particles are at rest.
+template <int LANES>
 __global__ void k_nonpressure(DevParams P, int n, PState s, const float4* __restrict__ xb,
                               const uint8_t* __restrict__ cflag, const uint32_t* __restrict__ nbl) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || !cflag[i]) return;
-  float4 xi = s.x[i], vi = s.v[i];
-  float ax = P.gx, ay = P.gy, az = P.gz;
-  const uint32_t* list = nbl + (size_t)i * P.nbl_cap;
-  int cnt = s.nbr[i];
-  for (int e = 0; e < cnt; ++e) {
-    uint32_t j = list[e];
-    float4 xj, vj = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (j & kBnd) {
-      xj = xb[j & ~kBnd];
-    } else {
-      xj = s.x[j];
-      vj = s.v[j];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;   // LANES lanes per particle
+  const int i = t / LANES, sub = t % LANES;
+  const bool valid = i < n && cflag[i];
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  if (valid) {
+    const float4 xi = s.x[i], vi = s.v[i];
+    const uint32_t* list = nbl + (size_t)i * P.nbl_cap;
+    const int cnt = s.nbr[i];
+    for (int e = sub; e < cnt; e += LANES) {
+      const uint32_t j = list[e];
+      float4 xj, vj = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j & kBnd) {
+        xj = xb[j & ~kBnd];
+      } else {
+        xj = s.x[j];
+        vj = s.v[j];
+      }
+      const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+      const float d2 = dx * dx + dy * dy + dz * dz;
+      if (!(d2 > 0.f)) continue;
+      const float vx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+      if (vx >= 0.f) continue;
+      const float id = inv_len(d2);
+      const float Pi = -P.visc_nu * __fdividef(vx, d2 + P.eps_h2);
+      const float f = pdW(P, d2 * id * P.inv_h) * id;
+      const float sc = -P.m * Pi * f;
+      ax += sc * dx;
+      ay += sc * dy;
+      az += sc * dz;
     }
-    float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-    float d2 = dx * dx + dy * dy + dz * dz;
-    if (!(d2 > 0.f)) continue;
-    float vx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
-    if (vx >= 0.f) continue;
-    float d = sqrtf(d2);
-    float Pi = -P.visc_nu * vx / (d2 + P.eps_h2);
-    float f = pdW(P, d * P.inv_h) / d;
-    float sc = -P.m * Pi * f;
-    ax += sc * dx;
-    ay += sc * dy;
-    az += sc * dz;
   }
-  s.a[i] = make_float4(ax, ay, az, 0.f);
+  ax = group_sum<LANES>(ax);
+  ay = group_sum<LANES>(ay);
+  az = group_sum<LANES>(az);
+  if (valid && sub == 0) s.a[i] = make_float4(P.gx + ax, P.gy + ay, P.gz + az, 0.f);
 }
 
 // ------------------------------------------------------- Algorithm 3 ---
@@ -187,15 +219,17 @@ __global__ void k_predict(DevParams P, int n, PState s, float4* __restrict__ xs)
 }
 
 // Predicted density, relative error and pressure of the participants (turn, S_e, S_ob).
+template <int LANES>
 __global__ void k_pdensity(DevParams P, int n, int j_minor, int row, int mode,
                            const uint32_t* __restrict__ key, PState s,
                            const uint8_t* __restrict__ in_se, const uint8_t* __restrict__ ob,
-                           const float4* __restrict__ xs, const float4* __restrict__ xb,
+                           float4* xs, const float4* __restrict__ xb,
                            const uint32_t* __restrict__ nbl) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (!(has_turn(P, mode, row, j_minor, s.level[i]) || in_se[i] || ob[key[i]])) return;
-  pdensity_one(P, s, i, xs, xb, nbl);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;   // LANES lanes per particle
+  const int i = t / LANES, sub = t % LANES;
+  const bool valid =
+      i < n && (has_turn(P, mode, row, j_minor, s.level[i]) || in_se[i] || ob[key[i]]);
+  pdensity_group<LANES>(P, s, i, valid, sub, xs, xb, nbl);
 }
 
 // S_e = {err > eta / 2}; R_e = blocks holding an S_e particle; max and sum of the latest
@@ -236,13 +270,14 @@ __global__ void k_se_reduce(DevParams P, int n, const uint32_t* __restrict__ key
 }
 
 // Pressure acceleration of turn and S_e.
+template <int LANES>
 __global__ void k_ppressure(DevParams P, int n, int j_minor, int row, int mode, PState s,
                             const uint8_t* __restrict__ in_se, const float4* __restrict__ xs,
                             const float4* __restrict__ xb, const uint32_t* __restrict__ nbl) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (!(has_turn(P, mode, row, j_minor, s.level[i]) || in_se[i])) return;
-  ppressure_one(P, s, i, xs, xb, nbl);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;   // LANES lanes per particle
+  const int i = t / LANES, sub = t % LANES;
+  const bool valid = i < n && (has_turn(P, mode, row, j_minor, s.level[i]) || in_se[i]);
+  ppressure_group<LANES>(P, s, i, valid, sub, xs, xb, nbl);
 }
 
 // ------------------------------------------------------- Algorithm 2 ---
@@ -283,13 +318,31 @@ __device__ __forceinline__ int ppick(const DevParams& P, double v2, double a2) {
   return L;
 }
 
+// The region Eq. 2-3 give a particle (as ppick on the FP64 norms): decided in FP32 where
+// the FP32 squared norms are farther than 1e-5 relative from every finite threshold
+// (their error is below 3e-7 relative), by the FP64 norms otherwise.
+__device__ __forceinline__ int ppick_particle(const DevParams& P, float4 v, float4 a, float4 pa) {
+  const float ax = a.x + pa.x, ay = a.y + pa.y, az = a.z + pa.z;
+  const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z));
+  const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)), __fmul_rn(az, az));
+  bool undecided = false;
+  int L = 0;
+  for (int l = 0; l < P.n_levels; ++l) {
+    const float tv = P.vthr2f[l], ta = P.athr2f[l];
+    if (isfinite(tv) && fabsf(v2 - tv) <= 1e-5f * tv) undecided = true;
+    if (isfinite(ta) && fabsf(a2 - ta) <= 1e-5f * ta) undecided = true;
+    if (P.eq1[l] && v2 <= tv && a2 <= ta) L = l;
+  }
+  if (undecided) L = ppick(P, pnorm2(v.x, v.y, v.z), pnorm2(ax, ay, az));
+  return L;
+}
+
 // Section 5.6: a particle needing a smaller region lowers its block and the 26 around.
 __global__ void k_preempt_mark(DevParams P, int n, const uint32_t* __restrict__ key, PState s,
                                int32_t* __restrict__ pnew) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float4 v = s.v[i], a = s.a[i], pa = s.ap[i];
-  int L = ppick(P, pnorm2(v.x, v.y, v.z), pnorm2(a.x + pa.x, a.y + pa.y, a.z + pa.z));
+  int L = ppick_particle(P, s.v[i], s.a[i], s.ap[i]);
   if (P.force_level >= 0) L = P.force_level;
   if (L >= s.level[i]) return;
   uint32_t b = key[i];
@@ -326,6 +379,10 @@ __global__ void k_preempt_apply(DevParams P, int n, const uint32_t* __restrict__
 // ------------------------------------------------------------- host ---
 
 static inline int grid_of(int n) { return (n + 255) / 256; }
+// CTAs of 256 threads for `lanes` lanes per particle
+static inline int grid_lanes(int n, int lanes) {
+  return (int)(((int64_t)(n > 0 ? n : 1) * lanes + 255) / 256);
+}
 
 int filled_grid_size();
 
@@ -352,11 +409,15 @@ static rts_status major_start(rts_ctx* c) {
   note_launch(c, 1);
   k_preg_from_blevel<<<fg, 256, 0, c->stream>>>(c->filled, c->ctl, c->blevel, c->preg);
   if (c->p.force_level < 0 && c->p.expand_layers > 0) {
+    // R_e and R_ob are rebuilt at the next minor step: their bytes hold the marks here
+    const int gg = (int)((nbk + 255) / 256 < (size_t)(fg * 4) ? (nbk + 255) / 256 : (size_t)(fg * 4));
     for (int target = 0; target <= 1; ++target) {
       cudaMemsetAsync(c->pnew, 0xff, sizeof(int32_t) * nbk, c->stream);
-      note_launch(c, 1);
-      k_dilate<<<fg, 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->preg, c->pnew, target,
-                                          c->p.expand_layers);
+      note_launch(c, 3);
+      k_dilate_x<<<gg, 256, 0, c->stream>>>(c->dp, c->preg, target, c->p.expand_layers, c->in_re);
+      k_dilate_y<<<gg, 256, 0, c->stream>>>(c->dp, c->in_re, c->p.expand_layers, c->ob);
+      k_dilate_z<<<fg, 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->preg, c->ob, target,
+                                            c->p.expand_layers, c->pnew);
       int32_t* t = c->preg;
       c->preg = c->pnew;
       c->pnew = t;
@@ -393,15 +454,24 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
       PPhase ph(c, RTS_PHASE_ITERATE);
       note_launch(c, 5);
       k_predict<<<g, 256, 0, c->stream>>>(Q, n, c->s, c->xs);
-      k_pdensity<<<g, 256, 0, c->stream>>>(Q, n, j, row, mode, c->key, c->s, c->in_se, c->ob,
-                                           c->xs, c->xb, c->nbl);
+      // every particle takes part (all_turn): kPLanes lanes each; else one
+      if (all_turn)
+        k_pdensity<kPLanes><<<grid_lanes(n, kPLanes), 256, 0, c->stream>>>(
+            Q, n, j, row, mode, c->key, c->s, c->in_se, c->ob, c->xs, c->xb, c->nbl);
+      else
+        k_pdensity<1><<<grid_lanes(n, 1), 256, 0, c->stream>>>(
+            Q, n, j, row, mode, c->key, c->s, c->in_se, c->ob, c->xs, c->xb, c->nbl);
       cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
       cudaMemsetAsync(&c->ctl->err_max_bits, 0, sizeof(unsigned int), c->stream);
       cudaMemsetAsync(&c->ctl->err_sum_fx, 0, sizeof(unsigned long long), c->stream);
       k_se_reduce<<<g, 256, 0, c->stream>>>(Q, n, c->key, c->s, c->in_se, c->in_re, c->ctl);
       k_observed<<<fg, 256, 0, c->stream>>>(Q, c->filled, c->ctl, c->preg, c->in_re, c->ob);
-      k_ppressure<<<g, 256, 0, c->stream>>>(Q, n, j, row, mode, c->s, c->in_se, c->xs, c->xb,
-                                            c->nbl);
+      if (all_turn)
+        k_ppressure<kPLanes><<<grid_lanes(n, kPLanes), 256, 0, c->stream>>>(
+            Q, n, j, row, mode, c->s, c->in_se, c->xs, c->xb, c->nbl);
+      else
+        k_ppressure<1><<<grid_lanes(n, 1), 256, 0, c->stream>>>(
+            Q, n, j, row, mode, c->s, c->in_se, c->xs, c->xb, c->nbl);
     }
     cudaMemcpyAsync(&c->h_ctl->err_max_bits, &c->ctl->err_max_bits, sizeof(unsigned int),
                     cudaMemcpyDeviceToHost, c->stream);
@@ -460,9 +530,41 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
   return status;
 }
 
-// Maxima of |v|^2 and |a_np + a_p|^2 over the fluid (FP64, order independent).
-__global__ void k_pglobal_max(int n, PState s, Ctl* ctl) {
+// Maxima of |v|^2 and |a_np + a_p|^2 over the fluid, order independent: of the FP32
+// norms (fp64 = 0, maximum on FP32 bits) or of the FP64 norms (fp64 = 1, asked for only
+// when the FP32 maxima lie at a threshold).
+__global__ void k_pglobal_max(int n, PState s, Ctl* ctl, int fp64) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double svm[8], sam[8];   // one atomic per counter and CTA (256 threads)
+  __shared__ unsigned svf[8], saf[8];
+  if (!fp64) {
+    unsigned vm = 0, am = 0;
+    if (i < n) {
+      const float4 v = s.v[i], a = s.a[i], pa = s.ap[i];
+      const float ax = a.x + pa.x, ay = a.y + pa.y, az = a.z + pa.z;
+      vm = __float_as_uint(__fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z)));
+      am = __float_as_uint(__fadd_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)), __fmul_rn(az, az)));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      vm = max(vm, __shfl_down_sync(kFullMask, vm, o));
+      am = max(am, __shfl_down_sync(kFullMask, am, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      svf[threadIdx.x >> 5] = vm;
+      saf[threadIdx.x >> 5] = am;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+        vm = max(vm, svf[k]);
+        am = max(am, saf[k]);
+      }
+      atomicMax(&ctl->vmax2f_bits, vm);
+      atomicMax(&ctl->amax2f_bits, am);
+    }
+    return;
+  }
   double vm = 0.0, am = 0.0;
   if (i < n) {
     float4 v = s.v[i], a = s.a[i], pa = s.ap[i];
@@ -474,7 +576,6 @@ __global__ void k_pglobal_max(int n, PState s, Ctl* ctl) {
     vm = fmax(vm, __shfl_down_sync(kFullMask, vm, o));
     am = fmax(am, __shfl_down_sync(kFullMask, am, o));
   }
-  __shared__ double svm[8], sam[8];   // one atomic per counter and CTA (256 threads)
   if ((threadIdx.x & 31) == 0) {
     svm[threadIdx.x >> 5] = vm;
     sam[threadIdx.x >> 5] = am;
@@ -506,20 +607,36 @@ static rts_status pcisph_global(rts_ctx* c, int64_t max_mult) {
   const int g = grid_of(n > 0 ? n : 1);
   int L = 0;
   if (c->p.mode == RTS_MODE_GLOBAL_ADAPTIVE && n > 0) {
-    cudaMemsetAsync(&c->ctl->vmax2_bits, 0, 2 * sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(&c->ctl->vmax2f_bits, 0, 2 * sizeof(unsigned int), c->stream);
     {
       PPhase ph(c, RTS_PHASE_CLASSIFY);
       note_launch(c, 1);
-      k_pglobal_max<<<g, 256, 0, c->stream>>>(n, c->s, c->ctl);
+      k_pglobal_max<<<g, 256, 0, c->stream>>>(n, c->s, c->ctl, 0);
     }
-    cudaMemcpyAsync(&c->h_ctl->vmax2_bits, &c->ctl->vmax2_bits, 2 * sizeof(unsigned long long),
+    cudaMemcpyAsync(&c->h_ctl->vmax2f_bits, &c->ctl->vmax2f_bits, 2 * sizeof(unsigned int),
                     cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RTS_ERR_CUDA;
-    double v2, a2;
-    memcpy(&v2, &c->h_ctl->vmax2_bits, sizeof v2);
-    memcpy(&a2, &c->h_ctl->amax2_bits, sizeof a2);
-    for (int l = 0; l < c->dp.n_levels; ++l)
-      if (c->dp.eq1[l] && v2 <= c->dp.vthr2[l] && a2 <= c->dp.athr2[l]) L = l;
+    float v2f, a2f;
+    memcpy(&v2f, &c->h_ctl->vmax2f_bits, sizeof v2f);
+    memcpy(&a2f, &c->h_ctl->amax2f_bits, sizeof a2f);
+    L = pick_level_from_f32_max(c->dp, v2f, a2f);
+    if (L < 0) {   // a maximum at a threshold: the FP64 maxima decide
+      L = 0;
+      cudaMemsetAsync(&c->ctl->vmax2_bits, 0, 2 * sizeof(unsigned long long), c->stream);
+      {
+        PPhase ph(c, RTS_PHASE_CLASSIFY);
+        note_launch(c, 1);
+        k_pglobal_max<<<g, 256, 0, c->stream>>>(n, c->s, c->ctl, 1);
+      }
+      cudaMemcpyAsync(&c->h_ctl->vmax2_bits, &c->ctl->vmax2_bits, 2 * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost, c->stream);
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RTS_ERR_CUDA;
+      double v2, a2;
+      memcpy(&v2, &c->h_ctl->vmax2_bits, sizeof v2);
+      memcpy(&a2, &c->h_ctl->amax2_bits, sizeof a2);
+      for (int l = 0; l < c->dp.n_levels; ++l)
+        if (c->dp.eq1[l] && v2 <= c->dp.vthr2[l] && a2 <= c->dp.athr2[l]) L = l;
+    }
   }
   int64_t m = c->p.level_mult[L];
   if (m > max_mult) m = max_mult;
@@ -542,7 +659,8 @@ static rts_status pcisph_global(rts_ctx* c, int64_t max_mult) {
     }
     {
       PPhase ph(c, RTS_PHASE_FORCE);
-      k_nonpressure<<<g, 256, 0, c->stream>>>(Q, n, c->s, c->xb, c->cflag, c->nbl);
+      k_nonpressure<kPLanes><<<grid_lanes(n, kPLanes), 256, 0, c->stream>>>(Q, n, c->s, c->xb,
+                                                                          c->cflag, c->nbl);
     }
   }
   const size_t n1 = (size_t)(n > 0 ? n : 1);
@@ -596,7 +714,13 @@ void pcisph_minor_begin(rts_ctx* c) {
   if (n > 0) {
     PPhase ph(c, RTS_PHASE_FORCE);
     note_launch(c, 1);
-    k_nonpressure<<<g, 256, 0, c->stream>>>(c->dp, n, c->s, c->xb, c->cflag, c->nbl);
+    // at a major-step start every particle refreshes: kPLanes lanes each; later few
+    if (c->minor == 0)
+      k_nonpressure<kPLanes><<<grid_lanes(n, kPLanes), 256, 0, c->stream>>>(c->dp, n, c->s, c->xb,
+                                                                          c->cflag, c->nbl);
+    else
+      k_nonpressure<1><<<grid_lanes(n, 1), 256, 0, c->stream>>>(c->dp, n, c->s, c->xb, c->cflag,
+                                                                c->nbl);
   }
   cudaMemsetAsync(c->s.prs, 0, sizeof(float) * (size_t)(n > 0 ? n : 1), c->stream);
   cudaMemsetAsync(c->s.ap, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c->stream);

@@ -188,3 +188,25 @@ def test_global_comparators_match_oracle(mode):
     g = rts.rts_get_state(ctx, ("x", "v", "rho"))
     np.testing.assert_allclose(g["rho"], S.rho, rtol=RHO_RTOL)
     assert np.abs(g["x"] - S.x).max() < 2e-5
+
+
+def test_region_expansion_matches_oracle():
+    # a resting pool with two fast spots: one needs region 1, the other region 2; the
+    # regions grow by expand_layers = 4 blocks around them (Section 5.5) on a domain large
+    # enough that a quarter of the blocks stay in region 4
+    sc = scenes.pool_drop((48, 48, 6), 4, 0.03, 0.01, (0.48, 0.48, 0.16), 3.5e-4)
+    v = np.zeros_like(sc.x)
+    for c, speed, rad in (((0.10, 0.12, 0.03), 15.0, 0.012), ((0.36, 0.30, 0.03), 3.0, 0.02)):
+        m = np.linalg.norm(sc.x - np.asarray(c, np.float32), axis=1) < rad
+        v[m] = (speed, 0.0, 0.0)
+    a = np.zeros_like(sc.x)
+    ctx, S, P = _pair(sc, v=v, a=a, n_minor=1)
+    rts.rts_pcisph_step(ctx)
+    S.step()
+    _, lev = rts.rts_get_blocks(ctx)
+    assert np.array_equal(lev, S.block_level)
+    filled = S.block_level[S.block_level >= 0]
+    assert set(np.unique(filled).tolist()) == {0, 1, 3}
+    assert (filled == 3).sum() > 100 and (filled == 0).sum() > 100
+    g = rts.rts_get_state(ctx, ("level",))
+    assert np.array_equal(g["level"], S.level)
