@@ -34,7 +34,7 @@ __device__ __forceinline__ int pick_level(const DevParams& P, double v2, double 
 __device__ __forceinline__ int pick_level_f(const DevParams& P, float v2, float a2, bool* undecided) {
   int L = 0;
   for (int l = 0; l < P.n_levels; ++l) {
-    float tv = (float)P.vthr2[l], ta = (float)P.athr2[l];
+    const float tv = P.vthr2f[l], ta = P.athr2f[l];
     if (isfinite(tv) && fabsf(v2 - tv) <= 1e-5f * tv) *undecided = true;
     if (isfinite(ta) && fabsf(a2 - ta) <= 1e-5f * ta) *undecided = true;
     if (P.eq1[l] && v2 <= tv && a2 <= ta) L = l;
@@ -122,12 +122,27 @@ __global__ void k_block_rmin(DevParams P, int mode, int level_g,
 // and counters are aggregated per CTA: one atomic per counter and CTA.
 constexpr int kActThreads = 256;
 
+// k1 mod mult[L] for every level (the level-aligned clock), computed once on the host.
+struct LevelPhase {
+  int v[kMaxLevels];
+};
+
 __global__ void __launch_bounds__(kActThreads) k_particle_activity(
-    DevParams P, int mode, int mult_g, long long k1, int n, const uint32_t* __restrict__ key,
+    DevParams P, int mode, int mult_g, LevelPhase kmod, int n, const uint32_t* __restrict__ key,
     const uint32_t* __restrict__ blevel, uint32_t stamp, PState s, uint8_t* __restrict__ cflag,
     uint32_t* __restrict__ actflag, uint32_t* __restrict__ act, uint32_t* __restrict__ plist,
     Ctl* ctl) {
   __shared__ uint32_t wp[kActThreads / 32], wa[kActThreads / 32], cbase[2];
+  __shared__ int s_kmod[kMaxLevels];   // kmod in shared memory (a parameter array indexed
+                                       // at run time would be copied to local memory)
+  if (threadIdx.x < kMaxLevels) {
+    int val = 0;
+#pragma unroll
+    for (int l = 0; l < kMaxLevels; ++l)
+      if ((int)threadIdx.x == l) val = kmod.v[l];
+    s_kmod[threadIdx.x] = val;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned below = (1u << lane) - 1u;
   unsigned long long evals = 0, ablocks = 0;   // thread 0's CTA totals
@@ -147,7 +162,7 @@ __global__ void __launch_bounds__(kActThreads) k_particle_activity(
       const int mb = mode == kActGlobal ? mult_g : P.mult[L];
       // validity of a particle that starts a true step now (level-aligned variant: up
       // to the next multiple of the multiplier)
-      const int vnew = (mode != kActGlobal && P.level_clock) ? mb - (int)(k1 % mb) : mb;
+      const int vnew = (mode != kActGlobal && P.level_clock) ? mb - s_kmod[L] : mb;
       if (mode == kActRegional) {
         int val = s.valid[i] - 1;
         int li = s.level[i];
@@ -635,10 +650,46 @@ __global__ void k_correct(DevParams P, const uint32_t* __restrict__ plist, Ctl* 
   }
 }
 
-// Global maxima of |v|^2 and |a|^2 over the fluid (global adaptive comparator).
+// FP32 squared norm without contraction (3 products, 2 sums, each rounded).
+__device__ __forceinline__ float norm2f(float x, float y, float z) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
+}
+
+// Global maxima of |v|^2 and |a|^2 over the fluid (global adaptive comparator): of the
+// FP32 norms (fp64 = 0, exact maximum on FP32 bits), or of the FP64 norms (fp64 = 1),
+// which the host asks for only when the FP32 maxima lie at a threshold.
 __global__ void k_global_max(int n, const float4* __restrict__ v, const float4* __restrict__ a,
-                             Ctl* ctl) {
+                             Ctl* ctl, int fp64) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double svm[8], sam[8];   // one atomic per counter and CTA (256 threads)
+  __shared__ unsigned svf[8], saf[8];
+  if (!fp64) {
+    unsigned vm = 0, am = 0;
+    if (i < n) {
+      const float4 vi = v[i], ai = a[i];
+      vm = __float_as_uint(norm2f(vi.x, vi.y, vi.z));
+      am = __float_as_uint(norm2f(ai.x, ai.y, ai.z));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      vm = max(vm, __shfl_down_sync(kFull, vm, o));
+      am = max(am, __shfl_down_sync(kFull, am, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      svf[threadIdx.x >> 5] = vm;
+      saf[threadIdx.x >> 5] = am;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+        vm = max(vm, svf[k]);
+        am = max(am, saf[k]);
+      }
+      atomicMax(&ctl->vmax2f_bits, vm);
+      atomicMax(&ctl->amax2f_bits, am);
+    }
+    return;
+  }
   double vm = 0.0, am = 0.0;
   if (i < n) {
     float4 vi = v[i], ai = a[i];
@@ -650,7 +701,6 @@ __global__ void k_global_max(int n, const float4* __restrict__ v, const float4* 
     vm = fmax(vm, __shfl_down_sync(kFull, vm, o));
     am = fmax(am, __shfl_down_sync(kFull, am, o));
   }
-  __shared__ double svm[8], sam[8];   // one atomic per counter and CTA (256 threads)
   if ((threadIdx.x & 31) == 0) {
     svm[threadIdx.x >> 5] = vm;
     sam[threadIdx.x >> 5] = am;
@@ -734,7 +784,10 @@ rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_
   if (mode >= 0 && c->n > 0) {
     note_launch(c, 1);
     const int g = (c->n + kActThreads - 1) / kActThreads;
-    k_particle_activity<<<g, kActThreads, 0, c->stream>>>(c->dp, mode, mult_g, (long long)k1, c->n,
+    LevelPhase kmod;
+    for (int L = 0; L < kMaxLevels; ++L)
+      kmod.v[L] = L < c->p.n_levels ? (int)(k1 % (int64_t)c->p.level_mult[L]) : 0;
+    k_particle_activity<<<g, kActThreads, 0, c->stream>>>(c->dp, mode, mult_g, kmod, c->n,
                                                    c->key, c->blevel, c->stamp, c->s, c->cflag,
                                                    c->actflag, c->act, c->plist, c->ctl);
   }
@@ -762,11 +815,14 @@ rts_status launch_correct(rts_ctx* c, int64_t k1, int prime) {
   return RTS_OK;
 }
 
-rts_status launch_global_max(rts_ctx* c) {
-  cudaMemsetAsync(&c->ctl->vmax2_bits, 0, 2 * sizeof(unsigned long long), c->stream);
+rts_status launch_global_max(rts_ctx* c, int fp64) {
+  if (fp64)
+    cudaMemsetAsync(&c->ctl->vmax2_bits, 0, 2 * sizeof(unsigned long long), c->stream);
+  else
+    cudaMemsetAsync(&c->ctl->vmax2f_bits, 0, 2 * sizeof(unsigned int), c->stream);
   int tb = 256, g = (c->n + tb - 1) / tb;
   if (c->n > 0) note_launch(c, 1);
-  if (c->n > 0) k_global_max<<<g, tb, 0, c->stream>>>(c->n, c->s.v, c->s.a, c->ctl);
+  if (c->n > 0) k_global_max<<<g, tb, 0, c->stream>>>(c->n, c->s.v, c->s.a, c->ctl, fp64);
   return RTS_OK;
 }
 
