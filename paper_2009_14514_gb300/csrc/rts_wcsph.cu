@@ -114,13 +114,16 @@ __global__ void k_block_rmin(DevParams P, int mode, int level_g,
   }
 }
 
-// Algorithm 1's per-particle bookkeeping, one thread per particle in block order:
-// validity -= 1; compute iff validity <= 0 or the block's level differs from the
-// particle's (pre-emption); a computing particle takes the block's level and a new
-// validity.  Work lists: the evaluated particles, and the blocks holding one (each run of
-// equal blocks in a warp claims its block once through a stamped flag).  List positions
-// and counters are aggregated per CTA: one atomic per counter and CTA.
+// Algorithm 1's per-particle bookkeeping, in block order: validity -= 1; compute iff
+// validity <= 0 or the block's level differs from the particle's (pre-emption); a
+// computing particle takes the block's level and a new validity.  Work lists: the
+// evaluated particles, and the blocks holding one (each run of equal blocks in a warp
+// claims its block once through a stamped flag).  Each CTA takes kActItems chunks of 32
+// particles per warp, gathers its list entries in shared memory (warp-aggregated shared
+// atomics) and appends them with one global atomic per list: the lists' order is
+// irrelevant to every consumer.
 constexpr int kActThreads = 256;
+constexpr int kActItems = 4;
 
 // k1 mod mult[L] for every level (the level-aligned clock), computed once on the host.
 struct LevelPhase {
@@ -132,7 +135,8 @@ __global__ void __launch_bounds__(kActThreads) k_particle_activity(
     const uint32_t* __restrict__ blevel, uint32_t stamp, PState s, uint8_t* __restrict__ cflag,
     uint32_t* __restrict__ actflag, uint32_t* __restrict__ act, uint32_t* __restrict__ plist,
     Ctl* ctl) {
-  __shared__ uint32_t wp[kActThreads / 32], wa[kActThreads / 32], cbase[2];
+  __shared__ uint32_t sp[kActThreads * kActItems], sa[kActThreads * kActItems];
+  __shared__ uint32_t scount[2], sbase[2];
   __shared__ int s_kmod[kMaxLevels];   // kmod in shared memory (a parameter array indexed
                                        // at run time would be copied to local memory)
   if (threadIdx.x < kMaxLevels) {
@@ -142,21 +146,33 @@ __global__ void __launch_bounds__(kActThreads) k_particle_activity(
       if ((int)threadIdx.x == l) val = kmod.v[l];
     s_kmod[threadIdx.x] = val;
   }
+  if (threadIdx.x < 2) scount[threadIdx.x] = 0u;
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned below = (1u << lane) - 1u;
-  unsigned long long evals = 0, ablocks = 0;   // thread 0's CTA totals
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-    const int i = base + threadIdx.x;
+  const int base0 = blockIdx.x * (kActThreads * kActItems) + w * (32 * kActItems) + lane;
+  // loads of every item first (the block record depends on the key)
+  uint32_t bk[kActItems], rec[kActItems];
+  int vold[kActItems], lold[kActItems];
+#pragma unroll
+  for (int it = 0; it < kActItems; ++it) {
+    const int i = base0 + 32 * it;
+    bk[it] = i < n ? key[i] : 0xffffffffu;
+    vold[it] = (i < n && mode == kActRegional) ? s.valid[i] : 0;
+    lold[it] = (i < n && mode == kActRegional) ? s.level[i] : 0;
+  }
+#pragma unroll
+  for (int it = 0; it < kActItems; ++it) rec[it] = bk[it] != 0xffffffffu ? blevel[bk[it]] : 0u;
+#pragma unroll
+  for (int it = 0; it < kActItems; ++it) {
+    const int i = base0 + 32 * it;
     const bool valid = i < n;
     bool c = false;
-    uint32_t b = 0xffffffffu;
+    const uint32_t b = bk[it];
     if (valid) {
-      b = key[i];
-      const uint32_t rec = blevel[b];
-      int L = (int)(rec & 0xffu);
-      if ((rec >> 8) != stamp || L >= P.n_levels) {
-        check_failed(ctl, kChkLevel, rec);
+      int L = (int)(rec[it] & 0xffu);
+      if ((rec[it] >> 8) != stamp || L >= P.n_levels) {
+        check_failed(ctl, kChkLevel, rec[it]);
         L = 0;
       }
       const int mb = mode == kActGlobal ? mult_g : P.mult[L];
@@ -164,8 +180,8 @@ __global__ void __launch_bounds__(kActThreads) k_particle_activity(
       // to the next multiple of the multiplier)
       const int vnew = (mode != kActGlobal && P.level_clock) ? mb - s_kmod[L] : mb;
       if (mode == kActRegional) {
-        int val = s.valid[i] - 1;
-        int li = s.level[i];
+        int val = vold[it] - 1;
+        int li = lold[it];
         if (li >= P.n_levels) {
           check_failed(ctl, kChkLevel, (unsigned)li);
           li = -1;
@@ -194,34 +210,29 @@ __global__ void __launch_bounds__(kActThreads) k_particle_activity(
     bool claim = false;
     if (head && (m & span)) claim = atomicExch(&actflag[b], stamp) != stamp;
     const unsigned cm = __ballot_sync(kFull, claim);
+    uint32_t op = 0, oa = 0;
     if (lane == 0) {
-      wp[w] = __popc(m);
-      wa[w] = __popc(cm);
+      if (m) op = atomicAdd(&scount[0], (uint32_t)__popc(m));
+      if (cm) oa = atomicAdd(&scount[1], (uint32_t)__popc(cm));
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {   // CTA prefix of the warp counts, one atomic per list
-      uint32_t tp = 0, ta = 0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-        const uint32_t a = wp[k], c2 = wa[k];
-        wp[k] = tp;
-        wa[k] = ta;
-        tp += a;
-        ta += c2;
-      }
-      cbase[0] = tp ? (uint32_t)atomicAdd(&ctl->n_plist, (int)tp) : 0u;
-      cbase[1] = ta ? (uint32_t)atomicAdd(&ctl->n_act, (int)ta) : 0u;
-      evals += tp;
-      ablocks += ta;
+    op = __shfl_sync(kFull, op, 0);
+    oa = __shfl_sync(kFull, oa, 0);
+    if (c) sp[op + __popc(m & below)] = (uint32_t)i;
+    if (claim) sa[oa + __popc(cm & below)] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {   // one atomic per list and counter
+    const uint32_t tp = scount[0], ta = scount[1];
+    sbase[0] = tp ? (uint32_t)atomicAdd(&ctl->n_plist, (int)tp) : 0u;
+    sbase[1] = ta ? (uint32_t)atomicAdd(&ctl->n_act, (int)ta) : 0u;
+    if (tp) {
+      atomicAdd(&ctl->evals, (unsigned long long)tp);
+      atomicAdd(&ctl->act_blocks, (unsigned long long)ta);
     }
-    __syncthreads();
-    if (c) plist[cbase[0] + wp[w] + __popc(m & below)] = (uint32_t)i;
-    if (claim) act[cbase[1] + wa[w] + __popc(cm & below)] = b;
-    __syncthreads();   // the shared counts are reused by the next round
   }
-  if (threadIdx.x == 0 && evals) {
-    atomicAdd(&ctl->evals, evals);
-    atomicAdd(&ctl->act_blocks, ablocks);
-  }
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k < scount[0]; k += blockDim.x) plist[sbase[0] + k] = sp[k];
+  for (uint32_t k = threadIdx.x; k < scount[1]; k += blockDim.x) act[sbase[1] + k] = sa[k];
 }
 
 // ---------------------------------------------------------------- kernel W ---
@@ -783,7 +794,7 @@ rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_
                                                      c->raw, c->blevel, c->stamp);
   if (mode >= 0 && c->n > 0) {
     note_launch(c, 1);
-    const int g = (c->n + kActThreads - 1) / kActThreads;
+    const int g = (c->n + kActThreads * kActItems - 1) / (kActThreads * kActItems);
     LevelPhase kmod;
     for (int L = 0; L < kMaxLevels; ++L)
       kmod.v[L] = L < c->p.n_levels ? (int)(k1 % (int64_t)c->p.level_mult[L]) : 0;
