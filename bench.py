@@ -45,11 +45,11 @@ FLOPS_TEST = 8
 FLOPS_PAIR_DENSITY = 8
 FLOPS_PAIR_FORCE = 24
 # DRAM bytes (read + write) per evaluated particle of the density pass, from one ncu
-# capture of k_density on the profiling case (--profile-case; 23.5 MB for 191,176
+# capture of k_density on the profiling case (--profile-case; 23.49 MB for 191,176
 # evaluated particles).  A launch of the 2 s rollout is not captured under ncu's size
 # rule, so its traffic is this figure times the launch's evaluations.  Valid for the
 # density kernel as captured; re-measure when k_density changes.
-DENSITY_DRAM_BYTES_PER_EVAL = 123.0
+DENSITY_DRAM_BYTES_PER_EVAL = 122.9
 
 
 def parse():
@@ -79,6 +79,8 @@ def parse():
                          "workload for --steps minor steps (nothing printed but a line)")
     ap.add_argument("--batch-host-loop", action="store_true",
                     help="--profile-batch: iterations launched from the host (no graph)")
+    ap.add_argument("--profile-evals", action="store_true",
+                    help="--profile-case: also print the evaluations of every density launch")
     ap.add_argument("--profile-case", action="store_true",
                     help="short run for ncu: 1M jittered lattice with a seeded dynamic state, "
                          "primed, then --steps windows (few launches, nothing printed but a line)")
@@ -96,8 +98,17 @@ def profile_case(args):
     rts.rts_set_state(ctx, sc.x, st["v"], a=st["a"])
     dtb = sc.params["dt_b"]
     st_all = rts.rts_advance(ctx, args.steps * args.window * dtb)
-    print(json.dumps({"profile_case": sc.name, "substeps": st_all["substeps"],
-                      "particle_evals": st_all["particle_evals"]}), flush=True)
+    out = {"profile_case": sc.name, "substeps": st_all["substeps"],
+           "particle_evals": st_all["particle_evals"]}
+    if args.profile_evals:   # evaluations of each k_density launch (priming first), rerun
+        ctx = rts.rts_init(sc.params, sc.x, st["v"], sc.xb)
+        rts.rts_set_state(ctx, sc.x, st["v"], a=st["a"])
+        per = [sc.n]   # the first call primes: every particle, then its first substep
+        for k in range(1, args.steps * args.window + 1):
+            per.append(int(rts.rts_advance(ctx, k * dtb)["particle_evals"]))
+        per[1] -= sc.n
+        out["evals_per_density_launch"] = per
+    print(json.dumps(out), flush=True)
 
 
 def profile_batch(args):
