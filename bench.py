@@ -79,6 +79,9 @@ def parse():
                          "workload for --steps minor steps (nothing printed but a line)")
     ap.add_argument("--batch-host-loop", action="store_true",
                     help="--profile-batch: iterations launched from the host (no graph)")
+    ap.add_argument("--profile-drift", action="store_true",
+                    help="--profile-case: start primed with seeded per-particle levels and "
+                         "validity (particles of a block out of phase, as under Algorithm 1)")
     ap.add_argument("--profile-evals", action="store_true",
                     help="--profile-case: also print the evaluations of every density launch")
     ap.add_argument("--profile-case", action="store_true",
@@ -95,7 +98,9 @@ def profile_case(args):
     sc = scenes.dam_break((100, 100, 100), 0.01, (4.0, 2.0, 2.0), 5e-5, jitter=1e-3, seed=1234)
     st = scenes.perturbed_state(sc, seed=777, vmax=3.0, amax=3.0e3)
     ctx = rts.rts_init(sc.params, sc.x, st["v"], sc.xb)
-    rts.rts_set_state(ctx, sc.x, st["v"], a=st["a"])
+    drift = dict(level=st["level"], validity=st["validity"], klast=st["klast"], primed=True,
+                 rho=st["rho"], p=st["p"]) if args.profile_drift else {}
+    rts.rts_set_state(ctx, sc.x, st["v"], a=st["a"], **drift)
     dtb = sc.params["dt_b"]
     st_all = rts.rts_advance(ctx, args.steps * args.window * dtb)
     out = {"profile_case": sc.name, "substeps": st_all["substeps"],
