@@ -52,7 +52,7 @@ FLOPS_PAIR_FORCE = 24
 DENSITY_DRAM_BYTES_PER_EVAL = 122.9
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20, help="timed steps (default: the 2 s rollout)")
@@ -87,7 +87,7 @@ def parse():
     ap.add_argument("--profile-case", action="store_true",
                     help="short run for ncu: 1M jittered lattice with a seeded dynamic state, "
                          "primed, then --steps windows (few launches, nothing printed but a line)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def profile_case(args):
@@ -129,6 +129,21 @@ def profile_batch(args):
                       "scene_iterations": st["pcisph_iterations"],
                       "iterations_run": rts.rts_batch_get_launch(ctx)["iterations_run"]}),
           flush=True)
+
+
+def max_over_ranks(ms, world, device):
+    """The timed region of the job: the slowest rank's (replicas: one per GPU)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, n, substeps, total_ms):
+    """Whole-job particle-substeps/s: every replica advances n particles by substeps."""
+    return world * n * substeps / (total_ms / 1e3)
 
 
 def dist_env():
@@ -577,13 +592,9 @@ def main():
         ours = run_rollout(sc, {}, args.steps, args, torch, rts, profile=True, flush=flush,
                            name="timed_rts")
     barrier()
-    total_ms = sum(ours["ms"])
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ours["ms"]), world, "cuda")
     subs = ours["tot"]["substeps"]
-    value = world * sc.n * subs / (total_ms / 1e3)
+    value = job_value(world, sc.n, subs, total_ms)
 
     aligned = None
     if not args.no_aligned:
