@@ -592,8 +592,6 @@ static rts_status init_ctx(const rts_params* params, int32_t n_fluid, const floa
     ALLOC(c->cstart, sizeof(uint32_t) * (nbk + 1));
     ALLOC(c->bcstart, sizeof(uint32_t) * (nbk + 1));
     ALLOC(c->tile_sums, sizeof(uint32_t) * (size_t)c->ntiles);
-    ALLOC(c->tile_acc[0], sizeof(uint32_t) * (size_t)c->ntiles);
-    ALLOC(c->tile_acc[1], sizeof(uint32_t) * (size_t)c->ntiles);
     ALLOC(c->raw, sizeof(uint32_t) * nbk);
     ALLOC(c->blevel, sizeof(uint32_t) * nbk);
     ALLOC(c->bmax_v, sizeof(unsigned long long) * nbk);
@@ -628,8 +626,6 @@ static rts_status init_ctx(const rts_params* params, int32_t n_fluid, const floa
 #undef ALLOC
   {
     cudaError_t e = cudaMemsetAsync(c->count, 0, sizeof(uint32_t) * nbk, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->tile_acc[0], 0, sizeof(uint32_t) * c->ntiles, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->tile_acc[1], 0, sizeof(uint32_t) * c->ntiles, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->raw, 0, sizeof(uint32_t) * nbk, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->blevel, 0, sizeof(uint32_t) * nbk, c->stream);
@@ -717,7 +713,6 @@ rts_status rts_destroy(rts_ctx* c) {
   cudaFree(c->anew); cudaFree(c->cflag); cudaFree(c->key); cudaFree(c->key_tmp); cudaFree(c->slot);
   cudaFree(c->tmp_uid); cudaFree(c->tmp_src); cudaFree(c->io); cudaFree(c->io_i);
   cudaFree(c->count); cudaFree(c->cstart); cudaFree(c->bcstart); cudaFree(c->tile_sums);
-  cudaFree(c->tile_acc[0]); cudaFree(c->tile_acc[1]);
   cudaFree(c->raw); cudaFree(c->blevel); cudaFree(c->act); cudaFree(c->plist); cudaFree(c->actflag); cudaFree(c->ctl); cudaFree(c->xb);
   cudaFree(c->bmax_v); cudaFree(c->bmax_a); cudaFree(c->filled); cudaFree(c->nbl);
   cudaFree(c->buid); cudaFree(c->s.ap); cudaFree(c->s2.ap); cudaFree(c->s.err); cudaFree(c->s2.err);

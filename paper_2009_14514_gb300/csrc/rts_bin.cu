@@ -20,14 +20,13 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 // Deferred correction of the last step's evaluated particles (pend), then predict
 // (dt != 0: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt) and the container correction,
 // then key and slot.  Slots: particles arrive mostly in block order, so each run of
-// equal keys in lane order takes one atomic on its block's counter; with tile_acc, each
-// run of equal scan tiles adds its count to the tile's total (the scan's first pass).
+// equal keys in lane order takes one atomic on its block's counter.
 __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4* __restrict__ v,
                               float4* __restrict__ a, float dt, uint32_t* __restrict__ key,
                               uint32_t* __restrict__ slot, uint32_t* __restrict__ count, Ctl* ctl,
                               int pend, int pend_k1, const uint8_t* __restrict__ cflag,
                               const float4* __restrict__ anew, int32_t* __restrict__ klast,
-                              const uint32_t* __restrict__ uid, uint32_t* __restrict__ tile_acc) {
+                              const uint32_t* __restrict__ uid) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) ctl->n_filled = 0;   // the scan that follows appends the filled blocks
   if (i >= n) return;
@@ -94,15 +93,6 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
   if (head) base = atomicAdd(&count[b], (uint32_t)(next - lane));
   base = __shfl_sync(act, base, myhead);
   slot[i] = base + (uint32_t)(lane - myhead);
-  if (tile_acc) {   // the scan's tile totals: one atomic per run of equal tiles in lane order
-    const uint32_t t = b / (uint32_t)kScanTile;
-    const uint32_t prevt = __shfl_up_sync(act, t, 1);
-    const bool thead = lane == 0 || prevt != t;
-    const unsigned theads = __ballot_sync(act, thead);
-    const unsigned tafter = theads & ~upto;
-    const int tnext = tafter ? __ffs(tafter) - 1 : __popc(act);
-    if (thead) atomicAdd(&tile_acc[t], (uint32_t)(tnext - lane));
-  }
 }
 
 // ---- exclusive scan of the per-block counts (reduce, scan tile sums, apply) ----
@@ -170,9 +160,7 @@ __global__ void k_scan_reduce(const uint32_t* __restrict__ count, int nb, uint32
 // list's order is irrelevant to every consumer).
 __global__ void k_scan_apply(uint32_t* __restrict__ count, int nb, const uint32_t* __restrict__ tile_sums,
                              uint32_t* __restrict__ cstart, uint32_t* __restrict__ filled,
-                             Ctl* ctl, uint32_t* __restrict__ tile_zero) {
-  // the next binning pass accumulates its tile totals into tile_zero
-  if (tile_zero && threadIdx.x == 0) tile_zero[blockIdx.x] = 0u;
+                             Ctl* ctl) {
   int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
   uint32_t c[kScanItems];
   load8(count, nb, base, c);
@@ -351,23 +339,17 @@ void scan_block_counts(uint32_t* count, int nb, uint32_t* tile_sums, uint32_t* c
                        cudaStream_t stream) {
   int ntiles = (nb + kScanTile - 1) / kScanTile;
   k_scan_reduce<<<ntiles, kScanThreads, 0, stream>>>(count, nb, tile_sums);
-  k_scan_apply<<<ntiles, kScanThreads, 0, stream>>>(count, nb, tile_sums, cstart, nullptr, nullptr,
-                                                    nullptr);
+  k_scan_apply<<<ntiles, kScanThreads, 0, stream>>>(count, nb, tile_sums, cstart, nullptr, nullptr);
 }
 
 // Exclusive scan of the block counts into cstart (tile totals, then each tile adds the
 // totals before it); the filled list is appended to (its counter was reset by the key pass).
-// acc: the tile totals the key pass accumulated (then zero: the other buffer is cleared
-// for the next pass), or null (a reduce pass forms them).
-static rts_status scan_counts(rts_ctx* c, uint32_t* filled, uint32_t* acc, uint32_t* zero) {
+static rts_status scan_counts(rts_ctx* c, uint32_t* filled) {
   int nb = c->dp.nblocks;
   int ntiles = (nb + kScanTile - 1) / kScanTile;
-  if (!acc) {
-    note_launch(c, 1);
-    k_scan_reduce<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums);
-  }
-  k_scan_apply<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, acc ? acc : c->tile_sums,
-                                                        c->cstart, filled, c->ctl, zero);
+  k_scan_reduce<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums);
+  k_scan_apply<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums, c->cstart,
+                                                        filled, c->ctl);
   return RTS_OK;
 }
 
@@ -393,16 +375,13 @@ rts_status launch_bin(rts_ctx* c, float dt) {
     return RTS_OK;
   }
   int tb = 256, g = (n + tb - 1) / tb;
-  note_launch(c, 4);
+  note_launch(c, 5);
   next_stamp(c);
-  uint32_t* acc = c->tile_acc[c->tile_par];
-  uint32_t* zero = c->tile_acc[c->tile_par ^ 1];
-  c->tile_par ^= 1;
   k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, n, c->s.x, c->s.v, c->s.a, dt, c->key, c->slot,
                                           c->count, c->ctl, c->pend_mode, (int)c->pend_k1,
-                                          c->cflag, c->anew, c->s.klast, c->s.uid, acc);
+                                          c->cflag, c->anew, c->s.klast, c->s.uid);
   c->pend_mode = kPendNone;
-  scan_counts(c, c->filled, acc, zero);
+  scan_counts(c, c->filled);
   k_scatter<<<g, tb, 0, c->stream>>>(n, c->dp.nblocks, c->key, c->slot, c->s.uid, c->cstart,
                                       c->key_tmp, c->tmp_uid, c->tmp_src, c->ctl);
   k_canon_gather<<<g, tb, 0, c->stream>>>(n, c->dp.nblocks, c->dp.max_per_block, c->cstart, c->key_tmp,
@@ -439,10 +418,10 @@ rts_status launch_bin_boundary(rts_ctx* c, const float4* xb_unsorted, int nb) {
   k_iota<<<g, tb, 0, c->stream>>>(nb, uid);
   k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, nb, const_cast<float4*>(xb_unsorted), nullptr,
                                           nullptr, 0.0f, key, slot, c->count, c->ctl, kPendNone, 0,
-                                          nullptr, nullptr, nullptr, uid, nullptr);
+                                          nullptr, nullptr, nullptr, uid);
   uint32_t* save = c->cstart;
   c->cstart = c->bcstart;
-  scan_counts(c, nullptr, nullptr, nullptr);
+  scan_counts(c, nullptr);
   c->cstart = save;
   k_scatter<<<g, tb, 0, c->stream>>>(nb, c->dp.nblocks, key, slot, uid, c->bcstart, tkey, tuid,
                                       tsrc, c->ctl);

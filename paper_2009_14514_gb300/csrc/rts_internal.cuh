@@ -314,8 +314,6 @@ struct rts_ctx {
   uint32_t* count;    // per block, kept zero between bins
   uint32_t* cstart;   // nblocks + 1
   uint32_t* tile_sums;
-  uint32_t* tile_acc[2];  // per-tile particle counts accumulated by the key pass (one
-  int tile_par;           // buffer per binning pass, alternating; each scan zeroes the other)
   int ntiles;
   // Per-block records stamped with the binning pass that wrote them, so nothing has to
   // be cleared between passes: a record is current iff its stamp equals c->stamp.
