@@ -71,6 +71,8 @@ def parse(argv=None):
     ap.add_argument("--pcisph-sim", type=float, default=1.0, help="simulated seconds of PCISPH")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable rollout")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched PCISPH scenes")
+    ap.add_argument("--no-ablations", action="store_true",
+                    help="skip the ablations (Serna correction off, wide kernel) on the 8k scene")
     ap.add_argument("--batch-sim", type=float, default=0.05,
                     help="simulated seconds of the batched PCISPH section")
     ap.add_argument("--window", type=int, default=8, help="base substeps per --profile-case step")
@@ -428,6 +430,48 @@ def run_batch(args, torch, rts, flush):
     return out
 
 
+def run_ablations(args, torch, rts):
+    """Ablations of the paper's choices on the 8k dam break (0.5 s from t = 0, frames every
+    10 substeps): regional stepping with and without the Section 4.1 correction (Fig. 3:
+    density error and kinetic-energy noise), the constant-dt_b reference, and the literal
+    kernel reading h = 2 s, r = 4 s.  KE noise: RMS over frames of the second difference
+    of the total kinetic energy, relative to its mean."""
+    import numpy as np
+    from paper_2009_14514_gb300 import scenes
+    stream = torch.cuda.current_stream()
+    out = {"workload": "wcsph_dam_break_8k: 8000 fluid particles, 0.5 s from t=0, frames every 10 substeps"}
+    arms = (("rts", scenes.wcsph_dam_break_8k(), {}),
+            ("rts_serna_off", scenes.wcsph_dam_break_8k(), {"serna_off": 1}),
+            ("global_constant_dt_b", scenes.wcsph_dam_break_8k(), {"mode": 2}),
+            ("rts_wide_kernel_r4s", scenes.wcsph_dam_break_8k_wide_kernel(), {}))
+    for name, sc, over in arms:
+        d = dict(sc.params)
+        d.update(over)
+        ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
+        dtb = d["dt_b"]
+        nframes = int(round(0.5 / (10 * dtb)))
+        ke, errs, sec = [], [], 0.0
+        for f in range(1, nframes + 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rts.rts_advance(ctx, f * 10 * dtb)
+            e1.record(stream)
+            e1.synchronize()
+            sec += e0.elapsed_time(e1) / 1e3
+            g = rts.rts_get_state(ctx, ("v", "rho", "nbr"))
+            ke.append(0.5 * float((g["v"].astype(np.float64) ** 2).sum()))
+            errs.append(density_error(g["rho"], g["nbr"], d["rho0"])["bulk_mean"])
+        ke = np.asarray(ke)
+        d2 = ke[2:] - 2 * ke[1:-1] + ke[:-2]
+        noise = float(np.sqrt(np.mean(d2 ** 2)) / max(ke.mean(), 1e-30))
+        out[name] = {"seconds": sec, "value": sc.n * ctx.substep_index / sec,
+                     "bulk_density_error_time_avg": float(np.mean(errs)),
+                     "ke_noise": noise, "ke_final": float(ke[-1])}
+        ctx.close()
+    return out
+
+
 def run_diff(args, torch):
     """The differentiable rollout: 250k-particle dam break, 100 steps of global constant
     stepping, checkpoints every 10 steps; the loss |mean(x_T) - target|^2 + mean
@@ -611,6 +655,7 @@ def main():
     pcisph = None if (args.no_pcisph or args.small) else run_pcisph(args, torch, rts, flush)
     dres = None if (args.no_diff or args.small) else run_diff(args, torch)
     bres = None if (args.no_batch or args.small) else run_batch(args, torch, rts, flush)
+    ares = None if args.no_ablations else run_ablations(args, torch, rts)
 
     # roofline of the dominant neighbour kernel (FP32 ALU bound)
     prof = ours["prof"]
@@ -680,6 +725,8 @@ def main():
         line["differentiable"] = dres
     if bres is not None:
         line["batched_pcisph"] = bres
+    if ares is not None:
+        line["ablations"] = ares
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle(sc)
     if rank == 0:

@@ -111,6 +111,13 @@ typedef struct rts_params {
   /* 0: the Tait pressure is clamped at zero (free-surface particles do not attract);
      1: negative pressure is kept (the equation of state is then smooth everywhere).  */
   int32_t tait_no_clamp;
+  /* Ablations of the paper's choices (off by default).  serna_off = 1: the Section 4.1
+     correction is skipped (an evaluated particle keeps its predicted position and
+     velocity; its held acceleration is still replaced), the paper's Fig. 3 comparison.
+     r2_search_rings: neighbour search rings of PCISPH region 2 (0 or 1 = one ring; the
+     paper searches two rings for region 1 only).                                      */
+  int32_t serna_off;
+  int32_t r2_search_rings;
 } rts_params;
 
 /* Counters accumulated over one rts_advance call. */
@@ -319,7 +326,8 @@ typedef struct rts_scene {
  * descriptions, 1 <= n_scenes <= 1024.  x, v: all scenes' fluid particles concatenated
  * (sum of n_fluid x 3); xb: all boundary particles concatenated.  Pointers as for
  * rts_init (host or device, copied).  The scenes are stacked along z in one grid with
- * max(expand_layers, r1_search_rings, 1) empty block layers between two scenes.
+ * max(expand_layers, r1_search_rings, r2_search_rings, 1) empty block layers between two
+ * scenes.
  * Errors: RTS_ERR_ARG, RTS_ERR_OOM, RTS_ERR_CUDA, RTS_ERR_DOMAIN (a boundary particle
  * outside its scene's grid). */
 rts_status rts_batch_init(const rts_params* params, int32_t n_scenes, const rts_scene* scenes,

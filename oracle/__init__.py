@@ -53,6 +53,8 @@ class OrcParams(C.Structure):
         ("level_clock", C.c_int32),
         ("tait_B", C.c_double),
         ("tait_no_clamp", C.c_int32),
+        ("serna_off", C.c_int32),
+        ("r2_rings", C.c_int32),
     ]
 
 
@@ -101,6 +103,8 @@ def make_params(d: dict) -> OrcParams:
     P.level_clock = int(d.get("level_clock", 0))
     P.tait_B = _f32(d.get("tait_B", 0.0))
     P.tait_no_clamp = int(d.get("tait_no_clamp", 0))
+    P.serna_off = int(d.get("serna_off", 0))
+    P.r2_rings = int(d.get("r2_search_rings", 1))
     for k in range(3):
         P.wall_lo[k] = _f32(d.get("wall_lo", [0.0] * 3)[k])
         P.wall_hi[k] = _f32(d.get("wall_hi", [0.0] * 3)[k])

@@ -489,11 +489,14 @@ static int evaluate_masked(const orc_params* P, orc_wstate* S, const uint8_t* ma
 
 /* Section 4.1 correction at the end of a particle's true step of length dt:
  * x += (a_new - a_old) dt^2 / 6, v += (a_new - a_old) dt / 2. */
-static void serna_correct(double* x, double* v, double* a, const double* anew, double dt) {
+static void serna_correct(const orc_params* P, double* x, double* v, double* a,
+                          const double* anew, double dt) {
   for (int k = 0; k < 3; ++k) {
     double da = anew[k] - a[k];
-    x[k] = x[k] + da * dt * dt / 6.0;
-    v[k] = v[k] + da * dt / 2.0;
+    if (!P->serna_off) {
+      x[k] = x[k] + da * dt * dt / 6.0;
+      v[k] = v[k] + da * dt / 2.0;
+    }
     a[k] = anew[k];
   }
 }
@@ -595,7 +598,7 @@ int orc_wcsph_substep(const orc_params* P, orc_wstate* S) {
     for (int32_t i = 0; i < n; ++i) {
       if (!S->compute[i]) continue;
       double dt = (double)(k1 - S->klast[i]) * P->dt_b;
-      serna_correct(S->x + 3 * (int64_t)i, S->v + 3 * (int64_t)i, S->a + 3 * (int64_t)i,
+      serna_correct(P, S->x + 3 * (int64_t)i, S->v + 3 * (int64_t)i, S->a + 3 * (int64_t)i,
                     anew + 3 * (int64_t)i, dt);
       S->klast[i] = (int32_t)k1;
     }
@@ -640,7 +643,7 @@ int orc_wcsph_global_step(const orc_params* P, orc_wstate* S, int32_t max_mult,
   if (!st) {
     for (int32_t i = 0; i < n; ++i) {
       double dt = (double)(k1 - S->klast[i]) * P->dt_b;
-      serna_correct(S->x + 3 * (int64_t)i, S->v + 3 * (int64_t)i, S->a + 3 * (int64_t)i,
+      serna_correct(P, S->x + 3 * (int64_t)i, S->v + 3 * (int64_t)i, S->a + 3 * (int64_t)i,
                     anew + 3 * (int64_t)i, dt);
       S->klast[i] = (int32_t)k1;
     }

@@ -62,6 +62,11 @@ typedef struct orc_params {
   int32_t level_clock;
   double tait_B;           /* Tait stiffness; 0: c_s^2 rho0 / gamma */
   int32_t tait_no_clamp;   /* 1: negative Tait pressure kept */
+  /* Ablations.  serna_off = 1: the Section 4.1 correction is not applied (an evaluated
+   * particle keeps its predicted position and velocity; the held acceleration is still
+   * replaced).  r2_rings: neighbour search rings of region 2 (PCISPH), 0 or 1 = one. */
+  int32_t serna_off;
+  int32_t r2_rings;
 } orc_params;
 
 /* WCSPH state in user order. */

@@ -157,12 +157,13 @@ static const double* pos_of(const orc_pstate* S, const double* xs, int32_t j) {
   return j < S->n ? xs + 3 * (int64_t)j : S->xb + 3 * (int64_t)(j - S->n);
 }
 
-/* Neighbourhood N_i around the particle's major-start block (rings 1, or 2 for R_1). */
+/* Neighbourhood N_i around the particle's major-start block (rings 1, or 2 for R_1; the
+ * r2_rings ablation searches R_2 with more rings as well). */
 static int refresh_list(const orc_params* P, orc_pstate* S, const ogrid* G, int32_t i,
                         int32_t* buf) {
   int32_t b = S->pblock[i];
   int c[3] = {b % P->dim[0], (b / P->dim[0]) % P->dim[1], b / (P->dim[0] * P->dim[1])};
-  int rings = S->level[i] == 0 ? P->r1_rings : 1;
+  int rings = S->level[i] == 0 ? P->r1_rings : (S->level[i] == 1 && P->r2_rings > 1 ? P->r2_rings : 1);
   int cnt = orci_nbr_list(P, G, S->n, S->x, S->xb, i, c, rings, P->r * P->r, buf, NBR_CAP);
   if (cnt < 0 || cnt > S->cap) return ORC_ERR_CAPACITY;
   memcpy(S->nbr_idx + (int64_t)i * S->cap, buf, sizeof(int32_t) * (size_t)cnt);

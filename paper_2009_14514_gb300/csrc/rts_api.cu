@@ -86,6 +86,9 @@ const char* rts::validate_params(const rts_params* p, int32_t n, int32_t nb, int
   if (p->level_clock != 0 && p->level_clock != 1) return "level_clock must be 0 or 1";
   if (!(p->tait_B >= 0.f) || !(p->tait_B < 1e12f)) return "tait_B must be in [0, 1e12)";
   if (p->tait_no_clamp != 0 && p->tait_no_clamp != 1) return "tait_no_clamp must be 0 or 1";
+  if (p->serna_off != 0 && p->serna_off != 1) return "serna_off must be 0 or 1";
+  if (p->r2_search_rings < 0 || p->r2_search_rings > 3) return "r2_search_rings must be in [0, 3]";
+  if (p->r1_search_rings < 0 || p->r1_search_rings > 3) return "r1_search_rings must be in [0, 3]";
   if (p->wall_project)
     for (int k = 0; k < 3; ++k)
       if (!(p->wall_lo[k] < p->wall_hi[k])) return "wall_lo must be below wall_hi on every axis";
@@ -153,6 +156,8 @@ void rts::make_dev_params(const rts_params& p, DevParams& d) {
   d.wall_project = p.wall_project;
   d.level_clock = p.level_clock;
   d.no_clamp = p.tait_no_clamp;
+  d.serna_off = p.serna_off;
+  d.r2_rings = p.r2_search_rings > 1 ? p.r2_search_rings : 1;
   for (int k = 0; k < 3; ++k) {
     d.wlo[k] = p.wall_lo[k];
     d.whi[k] = p.wall_hi[k];

@@ -669,6 +669,7 @@ const char* rts_batch_plan(const rts_params* params, int32_t n_scenes, const rts
   if (n_scenes < 1 || n_scenes > kMaxScenes) return "n_scenes must be in [1, 1024]";
   int gap = params->expand_layers;
   if (params->r1_search_rings > gap) gap = params->r1_search_rings;
+  if (params->r2_search_rings > gap) gap = params->r2_search_rings;
   if (gap < 1) gap = 1;
   int64_t nf = 0, nbd = 0, z = 0;
   int nx = 1, ny = 1;

@@ -38,8 +38,10 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
     if (corr) {
       const float4 an = anew[i];
       if (pend == kPendCorrect) {
-        serna_correct(xi, vi, ai, an, (float)(pend_k1 - klast[i]) * P.dt_b);
-        moved = true;
+        if (!P.serna_off) {
+          serna_correct(xi, vi, ai, an, (float)(pend_k1 - klast[i]) * P.dt_b);
+          moved = true;
+        }
       }
       ai = an;
       a[i] = an;

@@ -58,6 +58,8 @@ struct DevParams {
   int force_level;
   int level_clock;   // 0: validity = multiplier (Algorithm 1); 1: aligned to multiples
   int no_clamp;      // 1: negative Tait pressure kept
+  int serna_off;     // 1: the Section 4.1 correction is skipped (ablation)
+  int r2_rings;      // PCISPH neighbour search rings of region 2
   float dt_b;
   // batched scenes (n_scenes = 0: one scene, the fields above describe its grid)
   int n_scenes;

@@ -119,7 +119,8 @@ __global__ void k_observed(DevParams P, const uint32_t* __restrict__ filled, con
 // ---------------------------------------------------------- neighbours ---
 
 // Section 5.6: the neighbourhood of a refreshing particle is searched in the blocks
-// around its block of the major-step start (2 rings for R_1) with current positions.
+// around its block of the major-step start (2 rings for R_1; r2_rings for R_2, one
+// unless the ablation asks for more) with current positions.
 __global__ void k_lists(DevParams P, int n, const uint32_t* __restrict__ key,
                         const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ bcstart,
                         PState s, const float4* __restrict__ xb, const uint8_t* __restrict__ cflag,
@@ -128,7 +129,7 @@ __global__ void k_lists(DevParams P, int n, const uint32_t* __restrict__ key,
   if (i >= n || !cflag[i]) return;
   uint32_t b = key[i];
   int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
-  int R = s.level[i] == 0 ? P.r1_rings : 1;
+  int R = s.level[i] == 0 ? P.r1_rings : (s.level[i] == 1 ? P.r2_rings : 1);
   float4 xi = s.x[i];
   uint32_t* list = nbl + (size_t)i * P.nbl_cap;
   int cnt = 0;
@@ -645,6 +646,7 @@ static rts_status pcisph_global(rts_ctx* c, int64_t max_mult) {
   Q.dt_b = (float)((double)m * (double)c->p.dt_b);
   Q.delta = (float)((double)c->dp.delta / (double)(m * m));
   Q.r1_rings = 1;
+  Q.r2_rings = 1;
   {
     PPhase ph(c, RTS_PHASE_BIN);
     launch_bin(c, 0.0f);

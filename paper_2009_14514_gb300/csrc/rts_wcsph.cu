@@ -650,7 +650,7 @@ __global__ void k_correct(DevParams P, const uint32_t* __restrict__ plist, Ctl* 
       continue;
     }
     float4 an = anew[i];
-    if (!prime) {
+    if (!prime && !P.serna_off) {
       float4 x = s.x[i], v = s.v[i];
       serna_correct(x, v, s.a[i], an, (float)(k1 - s.klast[i]) * P.dt_b);
       s.x[i] = x;

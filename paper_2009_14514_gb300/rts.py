@@ -60,6 +60,8 @@ class RtsParams(C.Structure):
         ("level_clock", C.c_int32),
         ("tait_B", C.c_float),
         ("tait_no_clamp", C.c_int32),
+        ("serna_off", C.c_int32),
+        ("r2_search_rings", C.c_int32),
     ]
 
 
@@ -144,6 +146,8 @@ def make_params(d: dict) -> RtsParams:
     P.level_clock = int(d.get("level_clock", 0))
     P.tait_B = float(d.get("tait_B", 0.0))
     P.tait_no_clamp = int(d.get("tait_no_clamp", 0))
+    P.serna_off = int(d.get("serna_off", 0))
+    P.r2_search_rings = int(d.get("r2_search_rings", 1))
     return P
 
 

@@ -165,6 +165,17 @@ def wcsph_dam_break_8k(seed=1234):
                      name="wcsph_dam_break_8k")
 
 
+def wcsph_dam_break_8k_wide_kernel(seed=1234):
+    """The 8k dam break under the literal reading of the kernel size: h = 2 s, support
+    r = 4 s (block edge r), boundary of 4 layers; blocks hold 64 particles at rest and a
+    particle about 270 neighbours (max_per_block 160, max_neighbors 512)."""
+    s, box = 0.02, (0.8, 0.4, 0.4)
+    p = wcsph_params(s, box, 1e-4, support_factor=4.0)
+    p.update(max_per_block=160, max_neighbors=512)
+    fluid = lattice((20, 20, 20), s)
+    return _finish("wcsph_dam_break_8k_wide_kernel", fluid, box, s, p, seed, 1e-4, layers=4)
+
+
 def wcsph_dam_break_1m(seed=1234):
     """100^3 = 1,000,000 particles, s = 0.01 m, 4 x 2 x 2 m box, dt_b = 5e-5 s."""
     return dam_break((100, 100, 100), 0.01, (4.0, 2.0, 2.0), 5e-5, jitter=0.0, seed=seed,

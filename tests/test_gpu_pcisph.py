@@ -210,3 +210,20 @@ def test_region_expansion_matches_oracle():
     assert (filled == 3).sum() > 100 and (filled == 0).sum() > 100
     g = rts.rts_get_state(ctx, ("level",))
     assert np.array_equal(g["level"], S.level)
+
+
+def test_region2_two_ring_ablation_matches_oracle():
+    # r2_search_rings = 2: region-2 particles search two rings (the paper: region 1 only);
+    # over a major step of 4 minor steps the refreshed lists, iterations and states match
+    sc = scenes.pcisph_drop_small()
+    v, a = _dynamic(sc, seed=21, vscale=2.0, ascale=2.0)
+    ctx, S, P = _pair(sc, v=v, a=a, r2_search_rings=2)
+    for _ in range(4):
+        rts.rts_pcisph_step(ctx)
+        S.step()
+        _compare_step(ctx, S, P)
+        lists = rts.rts_get_neighbors(ctx)
+        r2 = np.nonzero(S.level == 1)[0]
+        for i in r2[:300]:
+            assert set(lists[i].tolist()) == set(S.neighbors(i).tolist()), i
+    assert (S.level == 1).sum() > 0

@@ -88,8 +88,10 @@ def _check_eval(g, o, mask=None, xpred=None):
     assert err.max() <= tol, (err.max(), tol)
 
 
-def test_evaluate_density_neighbours_forces_match_oracle():
-    sc = scenes.wcsph_dam_break_8k()
+@pytest.mark.parametrize("wide", [False, True])
+def test_evaluate_density_neighbours_forces_match_oracle(wide):
+    # wide: the literal reading h = 2 s, r = 4 s with four boundary layers
+    sc = scenes.wcsph_dam_break_8k_wide_kernel() if wide else scenes.wcsph_dam_break_8k()
     st = dynamic_state(sc, seed=5)
     ctx = gpu_ctx(sc)
     rts.rts_set_state(ctx, st["x"], st["v"], a=st["a"], rho=st["rho"], p=st["p"])
@@ -142,12 +144,14 @@ def _near_threshold(P, xt, vt, a, blocks, rel=1e-5):
     return near
 
 
-@pytest.mark.parametrize("seed,clock", [(1, 0), (2, 0), (3, 1), (4, 1)])
-def test_one_regional_substep_matches_oracle(seed, clock):
+@pytest.mark.parametrize("seed,clock,serna_off", [(1, 0, 0), (2, 0, 0), (3, 1, 0), (4, 1, 0),
+                                                  (5, 0, 1)])
+def test_one_regional_substep_matches_oracle(seed, clock, serna_off):
+    # serna_off = 1: the ablation without the Section 4.1 correction
     sc = scenes.wcsph_dam_break_8k()
     st = dynamic_state(sc, seed=seed)
     k0 = 8 + clock      # the aligned clock: an odd substep follows
-    d = params(sc, level_clock=clock)
+    d = params(sc, level_clock=clock, serna_off=serna_off)
     ctx = gpu_ctx(sc, d)
     rts.rts_set_state(ctx, st["x"], st["v"], a=st["a"], rho=st["rho"], p=st["p"],
                       level=st["level"], validity=st["validity"], klast=st["klast"], k=k0,

@@ -214,3 +214,21 @@ def test_major_step_shortening_and_restoration():
     S.step()
     S.step()
     assert S.S.n_minor_cur == 4 and S.S.clean == 0
+
+
+def test_region2_two_ring_search_equals_brute_force_at_the_major_start():
+    # the r2_rings ablation: region-2 particles search two rings; at the major-step start
+    # their lists are still exactly the particles within r (brute force), and a region-2
+    # particle in a block far from its neighbours' blocks finds them only with 2 rings
+    sc = scenes.pcisph_drop_small()
+    st = scenes.perturbed_state(sc, 11, vmax=15.0, amax=2.0e4)
+    d = dict(sc.params, n_minor=1, expand_layers=0, r2_search_rings=2)
+    P = O.make_params(d)
+    S = O.PCISPH(P, sc.x, st["v"], sc.xb)
+    S.anp[:] = st["a"]
+    S.step()
+    off, idx = O.neighbors_brute(sc.x, sc.xb, P.r)
+    r2 = np.nonzero(S.level == 1)[0]
+    assert len(r2) > 0
+    for i in r2[:200]:
+        assert set(S.neighbors(i).tolist()) == set(idx[off[i]:off[i + 1]].tolist())

@@ -290,6 +290,27 @@ def test_serna_substeps_are_pure_interpolation_then_correct():
     assert S.klast[0] == 8
 
 
+def test_serna_off_keeps_the_predictor_and_replaces_the_held_acceleration():
+    # the ablation of Section 4.1's correction (Fig. 3): at the end of the true step the
+    # particle keeps x + v T + A T^2 / 2 and v + A T, and only a <- the new acceleration
+    s = 0.02
+    sc = scenes.dam_break((1, 1, 1), s, (0.4, 0.4, 0.4), 1e-4)
+    P = _params(sc, force_level=3, serna_off=1)
+    x0 = np.array([[0.2, 0.2, 0.2]])
+    v0 = np.array([[0.03, -0.02, 0.01]])
+    A = np.array([[1.5, -2.0, 0.7]])
+    S = O.WCSPH(P, x0, v0, np.zeros((0, 3)), a=A, level=[3], validity=[8], klast=[0],
+                rho=[1000.0], p=[0.0], k=0, primed=True)
+    for _ in range(8):
+        S.substep()
+    T = 8 * P.dt_b
+    assert S.compute[0] == 1
+    np.testing.assert_allclose(S.x, x0 + v0 * T + 0.5 * A * T * T, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(S.v, v0 + A * T, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(S.a, np.array([[0.0, 0.0, P.g[2]]]), rtol=0, atol=0)
+    assert S.klast[0] == 8
+
+
 def test_isolated_particle_falls_exactly_under_gravity():
     # constant acceleration: the correction is a no-op and the fall is exact
     s = 0.02
