@@ -358,7 +358,7 @@ rts_status rts_batch_get_launch(const rts_ctx* ctx, int32_t* threads, int32_t* t
                                 int32_t* use_graph, int64_t* iterations_run);
 
 /* Autotuner: times one full iteration (every particle of every scene participating) for
- * threads in {128, 256, 512} x tile in {64, 128, 256, 512}, reps timed runs each after a
+ * threads in {128, 256, 512} x tile in {32, 64, 128, 256, 512}, reps timed runs each after a
  * warm-up, on the current state, which it restores afterwards; keeps the fastest shape
  * and returns it with its time per iteration (ms).  Needs the neighbour lists of a
  * previous step (RTS_ERR_STATE before the first step).  Synchronises. */

@@ -15,9 +15,9 @@
 // (row, mode, local run, revert, minimum count), its own error reductions (exact maximum
 // on FP32 bits, fixed-point sum) and its own stopping test; a control kernel evaluates
 // them on the device after every iteration.  The particle passes of an iteration are
-// persistent kernels over one global work queue: the tiles (runs of `tile` consecutive
-// particles in block order) of the scenes still iterating; each warp takes the next tile
-// from an atomic counter.  The iteration loop is a CUDA graph whose while node repeats
+// kernels over one global work queue: the tiles (runs of `tile` consecutive particles in
+// block order) of the scenes still iterating, prefix-summed per scene by the control
+// kernel; one warp per tile.  The iteration loop is a CUDA graph whose while node repeats
 // the passes as long as the control kernel reports a scene still iterating, so a minor
 // step runs all its iterations without a host round trip.  Scenes share the major-step
 // clock: the batch shortens its major step (Section 5.5) when any scene exceeds the
@@ -55,7 +55,6 @@ struct BatchCtl {
   int iter;          // iterations run in this minor step
   int j, min_sched;  // minor step and the smallest scheduled count of any region in it
   int any;           // a scene is still iterating
-  unsigned q[3];     // work-queue counters: predict, density, pressure
   int qtot;          // tiles in the queue
   int qpre[kMaxScenes + 1];   // first tile of each scene (exclusive prefix)
 };
@@ -165,21 +164,19 @@ __global__ void k_b_begin(int ns, const uint32_t* __restrict__ fbase, int tile, 
     B->j = j;
     B->min_sched = min_sched;
     B->any = tot > 0;
-    B->q[0] = B->q[1] = B->q[2] = 0u;
   }
 }
 
-// The warp's next tile of the queue (scene and particle range), false when the queue
-// is exhausted.  qpre: the queue's scene prefix in shared memory.
-__device__ __forceinline__ bool next_tile(BatchCtl* B, int which, const int* qpre, int ns,
-                                          int qtot, const uint32_t* __restrict__ fbase,
-                                          int tile, int* sc, uint32_t* i0, uint32_t* i1) {
-  unsigned q = 0;
-  if ((threadIdx.x & 31) == 0) q = atomicAdd(&B->q[which], 1u);
-  q = __shfl_sync(kFullMask, q, 0);
+// Tile q of the queue: its scene and particle range; false beyond the queue.  qpre: the
+// queue's scene prefix in shared memory; the owning scene is the largest s with
+// qpre[s] <= q (scenes without tiles in the queue share their successor's prefix).  One
+// warp per tile, over a grid sized for every tile of every scene (the hardware scheduler
+// balances the tiles as warps finish).
+__device__ __forceinline__ bool tile_of(int qtot, const int* qpre, int ns,
+                                        const uint32_t* __restrict__ fbase, int tile, int* sc,
+                                        uint32_t* i0, uint32_t* i1) {
+  const unsigned q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (q >= (unsigned)qtot) return false;
-  // the owning scene: the largest s with qpre[s] <= q (scenes without tiles in the
-  // queue share their successor's prefix)
   int lo = 0, hi = ns - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -210,7 +207,7 @@ __global__ void k_b_predict(DevParams P, const BatchView* __restrict__ Vp, Batch
   const int lane = threadIdx.x & 31;
   int sc;
   uint32_t i0, i1;
-  while (next_tile(B, 0, qpre, ns, qtot, P.fbase, tile, &sc, &i0, &i1)) {
+  if (tile_of(qtot, qpre, ns, P.fbase, tile, &sc, &i0, &i1)) {
     const int flags = S[sc].flags;
     for (uint32_t i = i0 + lane; i < i1; i += 32) {
       if (flags & kFlagBackup) V.pbak[i] = V.s.prs[i];
@@ -236,7 +233,7 @@ __global__ void k_b_density(DevParams P, const BatchView* __restrict__ Vp, Batch
   int sc;
   uint32_t i0, i1;
   const int min_sched = B->min_sched;
-  while (next_tile(B, 1, qpre, ns, qtot, P.fbase, tile, &sc, &i0, &i1)) {
+  if (tile_of(qtot, qpre, ns, P.fbase, tile, &sc, &i0, &i1)) {
     const int mode = S[sc].mode, row = S[sc].row;
     // every particle of the scene takes part: kPLanes lanes per particle, else one (as
     // the single-scene path chooses)
@@ -301,7 +298,7 @@ __global__ void k_b_pressure(DevParams P, const BatchView* __restrict__ Vp, Batc
   int sc;
   uint32_t i0, i1;
   const int min_sched = B->min_sched;
-  while (next_tile(B, 2, qpre, ns, qtot, P.fbase, tile, &sc, &i0, &i1)) {
+  if (tile_of(qtot, qpre, ns, P.fbase, tile, &sc, &i0, &i1)) {
     const int mode = S[sc].mode, row = S[sc].row;
     const bool dense = mode == kModeGlobal || (mode == kModeSched && row <= min_sched);
     const int lanes = dense ? kPLanes : 1;
@@ -384,7 +381,6 @@ __global__ void k_b_control(int ns, int tile, float eta, float eta_T, int max_it
     B->qpre[ns] = tot;
     B->qtot = tot;
     B->iter += 1;
-    B->q[0] = B->q[1] = B->q[2] = 0u;
     B->any = tot > 0;
     // every iterating scene stops by max_iters: the bound below is never the reason
     if (in_graph) cudaGraphSetConditional(cond, (tot > 0 && B->iter <= max_iters) ? 1u : 0u);
@@ -395,24 +391,17 @@ __global__ void k_b_control(int ns, int tile, float eta, float eta_T, int max_it
 
 int filled_grid_size();
 
-static int sm_count() {
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  return nsm > 0 ? nsm : 1;
-}
-
 static size_t queue_smem(const BatchState* b) { return sizeof(int) * (size_t)(b->ns + 1); }
 
-// Persistent grids: as many CTAs as fit on the SMs at once.
+// Grids of the queue kernels: one warp per tile, for the queue of every scene's tiles.
 static void size_grids(BatchState* b) {
-  const int nsm = sm_count();
-  const void* ks[3] = {(const void*)k_b_predict, (const void*)k_b_density, (const void*)k_b_pressure};
-  for (int k = 0; k < 3; ++k) {
-    int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ks[k], b->threads, queue_smem(b));
-    b->grid[k] = nsm * (per > 0 ? per : 1);
-  }
+  int64_t tiles = 0;
+  for (int sc = 0; sc < b->ns; ++sc)
+    tiles += ((int64_t)(b->fbase[sc + 1] - b->fbase[sc]) + b->tile - 1) / b->tile;
+  const int64_t warps_per_cta = b->threads / 32;
+  int64_t g = (tiles + warps_per_cta - 1) / warps_per_cta;
+  if (g < 1) g = 1;
+  for (int k = 0; k < 3; ++k) b->grid[k] = (int)g;
 }
 
 static void fill_view(const rts_ctx* c, BatchView* v) {
@@ -829,7 +818,7 @@ rts_status rts_batch_autotune(rts_ctx* c, int32_t reps, int32_t* threads_out, in
   cp(c->tmp_src, c->in_se, n1);
   cp(c->act, c->ob, nbk);
   const int cand_threads[3] = {128, 256, 512};
-  const int cand_tile[4] = {64, 128, 256, 512};
+  const int cand_tile[5] = {32, 64, 128, 256, 512};
   const int t0 = b->threads, l0 = b->tile;
   int best_t = t0, best_l = l0;
   float best = 3.4e38f;
@@ -840,7 +829,7 @@ rts_status rts_batch_autotune(rts_ctx* c, int32_t reps, int32_t* threads_out, in
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_view, b->h_view, sizeof(BatchView), cudaMemcpyHostToDevice, st);
   for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
-    for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+    for (int l = 0; l < 5 && e == cudaSuccess; ++l) {
       b->threads = cand_threads[a];
       b->tile = cand_tile[l];
       size_grids(b);
@@ -863,7 +852,7 @@ rts_status rts_batch_autotune(rts_ctx* c, int32_t reps, int32_t* threads_out, in
       }
     }
   }
-  c->kernels += (int64_t)12 * (reps + 1) * 6;
+  c->kernels += (int64_t)15 * (reps + 1) * 6;
   cp(c->s.rho, c->s2.rho, sizeof(float) * n1);
   cp(c->s.prs, c->s2.prs, sizeof(float) * n1);
   cp(c->s.err, c->s2.err, sizeof(float) * n1);
