@@ -86,6 +86,8 @@ def parse(argv=None):
                          "validity (particles of a block out of phase, as under Algorithm 1)")
     ap.add_argument("--profile-evals", action="store_true",
                     help="--profile-case: also print the evaluations of every density launch")
+    ap.add_argument("--profile-pcisph", action="store_true",
+                    help="short run for ncu: the 1M pool drop from t=0 for --steps minor steps")
     ap.add_argument("--profile-case", action="store_true",
                     help="short run for ncu: 1M jittered lattice with a seeded dynamic state, "
                          "primed, then --steps windows (few launches, nothing printed but a line)")
@@ -146,6 +148,17 @@ def max_over_ranks(ms, world, device):
 def job_value(world, n, substeps, total_ms):
     """Whole-job particle-substeps/s: every replica advances n particles by substeps."""
     return world * n * substeps / (total_ms / 1e3)
+
+
+def profile_pcisph(args):
+    """A bounded PCISPH case for ncu: the 1M pool + cube drop from t = 0 for args.steps
+    minor steps (regional time stepping)."""
+    from paper_2009_14514_gb300 import rts, scenes
+    sc = scenes.pcisph_drop_1m()
+    ctx = rts.rts_init(sc.params, sc.x, sc.v, sc.xb)
+    st = rts.rts_advance(ctx, args.steps * sc.params["dt_b"])
+    print(json.dumps({"profile_pcisph": sc.name, "substeps": st["substeps"],
+                      "iterations": st["pcisph_iterations"]}), flush=True)
 
 
 def dist_env():
@@ -615,6 +628,9 @@ def main():
         return
     if args.profile_batch:
         profile_batch(args)
+        return
+    if args.profile_pcisph:
+        profile_pcisph(args)
         return
     if args.impl == "reference":
         reference_arm(args)
