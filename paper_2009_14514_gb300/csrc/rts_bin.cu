@@ -28,7 +28,11 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
                               const float4* __restrict__ anew, int32_t* __restrict__ klast,
                               const uint32_t* __restrict__ uid) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) ctl->n_filled = 0;   // the scan that follows appends the filled blocks
+  if (i == 0) {   // the scan that follows appends the filled blocks, the activity pass
+    ctl->n_filled = 0;   // the active blocks and the evaluated particles
+    ctl->n_act = 0;
+    ctl->n_plist = 0;
+  }
   if (i >= n) return;
   float4 xi = x[i];
   const bool corr = pend != kPendNone && cflag[i];

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 
 #include "rts_pcisph_dev.cuh"
@@ -212,9 +213,14 @@ __global__ void k_nonpressure(DevParams P, int n, PState s, const float4* __rest
 
 // ------------------------------------------------------- Algorithm 3 ---
 
-// Predict v* = v + dt (a_np + a_p), x* = x + dt v* (every particle).
-__global__ void k_predict(DevParams P, int n, PState s, float4* __restrict__ xs) {
+// Predict v* = v + dt (a_np + a_p), x* = x + dt v* (every particle); the iteration's
+// error reductions start from zero (the previous ones were read back before).
+__global__ void k_predict(DevParams P, int n, PState s, float4* __restrict__ xs, Ctl* ctl) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    ctl->err_max_bits = 0u;
+    ctl->err_sum_fx = 0ull;
+  }
   if (i >= n) return;
   xs[i] = predict_one(P, s, i);
 }
@@ -454,7 +460,7 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
     {
       PPhase ph(c, RTS_PHASE_ITERATE);
       note_launch(c, 5);
-      k_predict<<<g, 256, 0, c->stream>>>(Q, n, c->s, c->xs);
+      k_predict<<<g, 256, 0, c->stream>>>(Q, n, c->s, c->xs, c->ctl);
       // every particle takes part (all_turn): kPLanes lanes each; else one
       if (all_turn)
         k_pdensity<kPLanes><<<grid_lanes(n, kPLanes), 256, 0, c->stream>>>(
@@ -463,8 +469,6 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
         k_pdensity<1><<<grid_lanes(n, 1), 256, 0, c->stream>>>(
             Q, n, j, row, mode, c->key, c->s, c->in_se, c->ob, c->xs, c->xb, c->nbl);
       cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
-      cudaMemsetAsync(&c->ctl->err_max_bits, 0, sizeof(unsigned int), c->stream);
-      cudaMemsetAsync(&c->ctl->err_sum_fx, 0, sizeof(unsigned long long), c->stream);
       k_se_reduce<<<g, 256, 0, c->stream>>>(Q, n, c->key, c->s, c->in_se, c->in_re, c->ctl);
       k_observed<<<fg, 256, 0, c->stream>>>(Q, c->filled, c->ctl, c->preg, c->in_re, c->ob);
       if (all_turn)
@@ -474,9 +478,10 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
         k_ppressure<1><<<grid_lanes(n, 1), 256, 0, c->stream>>>(
             Q, n, j, row, mode, c->s, c->in_se, c->xs, c->xb, c->nbl);
     }
-    cudaMemcpyAsync(&c->h_ctl->err_max_bits, &c->ctl->err_max_bits, sizeof(unsigned int),
-                    cudaMemcpyDeviceToHost, c->stream);
-    cudaMemcpyAsync(&c->h_ctl->err_sum_fx, &c->ctl->err_sum_fx, sizeof(unsigned long long),
+    // both reductions in one copy (err_max_bits and err_sum_fx are adjacent in Ctl)
+    constexpr size_t kErrBytes =
+        offsetof(Ctl, err_sum_fx) + sizeof(unsigned long long) - offsetof(Ctl, err_max_bits);
+    cudaMemcpyAsync(&c->h_ctl->err_max_bits, &c->ctl->err_max_bits, kErrBytes,
                     cudaMemcpyDeviceToHost, c->stream);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {

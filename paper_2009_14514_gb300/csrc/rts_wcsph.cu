@@ -784,11 +784,10 @@ rts_status launch_classify(rts_ctx* c) {
 }
 
 // mode < 0: smoothing only (public classification); otherwise smoothing + activity.
-static_assert(offsetof(Ctl, n_plist) == offsetof(Ctl, n_act) + sizeof(int),
-              "n_act and n_plist are reset together");
 
+// The work-list counters n_act and n_plist were reset by the key pass of this step's
+// binning (every step bins before its activity pass).
 rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1) {
-  cudaMemsetAsync(&c->ctl->n_act, 0, 2 * sizeof(int), c->stream);   // n_act, n_plist
   note_launch(c, 1);
   k_block_rmin<<<filled_grid(), 256, 0, c->stream>>>(c->dp, mode, level_g, c->filled, c->ctl,
                                                      c->raw, c->blevel, c->stamp);
