@@ -119,6 +119,14 @@ __global__ void k_observed(DevParams P, const uint32_t* __restrict__ filled, con
 
 // ---------------------------------------------------------- neighbours ---
 
+// The neighbour predicate of the list refresh: FP32 outside the guard band, exact inside.
+__device__ __forceinline__ bool list_test(const DevParams& P, float4 xi, float4 xj) {
+  const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+  const float d2 = dx * dx + dy * dy + dz * dz;
+  if (d2 < P.r2_lo) return true;
+  return d2 < P.r2_hi && nbr_exact(P, xi, xj);
+}
+
 // Section 5.6: the neighbourhood of a refreshing particle is searched in the blocks
 // around its block of the major-step start (2 rings for R_1; r2_rings for R_2, one
 // unless the ablation asks for more) with current positions.
@@ -146,16 +154,26 @@ __global__ void k_lists(DevParams P, int n, const uint32_t* __restrict__ key,
       for (int pass = 0; pass < 2; ++pass) {
         const uint32_t* cs = pass ? bcstart : cstart;
         const float4* src = pass ? xb : s.x;
-        uint32_t j0 = cs[rb + x0], j1 = cs[rb + x1 + 1];
-        for (uint32_t j = j0; j < j1; ++j) {
-          if (!pass && j == (uint32_t)i) continue;
-          float4 xj = src[j];
-          float dx = xi.x - xj.x, dy2 = xi.y - xj.y, dz2 = xi.z - xj.z;
-          float d2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-          bool in = d2 < P.r2_lo;
-          if (d2 >= P.r2_lo && d2 < P.r2_hi) in = nbr_exact(P, xi, xj);
-          if (in) {
-            if (cnt < P.nbl_cap) list[cnt] = pass ? (j | kBnd) : j;
+        const uint32_t self = pass ? 0xffffffffu : (uint32_t)i;
+        const uint32_t tag = pass ? kBnd : 0u;
+        uint32_t j = cs[rb + x0];
+        const uint32_t j1 = cs[rb + x1 + 1];
+        // four candidate loads in flight, then the tests and appends in index order
+        for (; j + 4 <= j1; j += 4) {
+          float4 xq[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xq[q] = __ldg(&src[j + q]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (j + q != self && list_test(P, xi, xq[q])) {
+              if (cnt < P.nbl_cap) list[cnt] = (j + q) | tag;
+              ++cnt;
+            }
+          }
+        }
+        for (; j < j1; ++j) {
+          if (j != self && list_test(P, xi, __ldg(&src[j]))) {
+            if (cnt < P.nbl_cap) list[cnt] = j | tag;
             ++cnt;
           }
         }
@@ -715,8 +733,13 @@ void pcisph_minor_begin(rts_ctx* c) {
   if (n > 0) {
     PPhase ph(c, RTS_PHASE_DENSITY);
     note_launch(c, 1);
-    k_lists<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->cstart, c->bcstart, c->s, c->xb,
-                                      c->cflag, c->nbl, c->ctl);
+    // At a major-step start the grid was just built from these positions: every particle
+    // within r of another lies in the 27 blocks around its block (edge >= r), so one ring
+    // gives the same list, in the same order, as the wider search of R_1 (and R_2).
+    DevParams Q = c->dp;
+    if (c->minor == 0) Q.r1_rings = Q.r2_rings = 1;
+    k_lists<<<g, 256, 0, c->stream>>>(Q, n, c->key, c->cstart, c->bcstart, c->s, c->xb, c->cflag,
+                                      c->nbl, c->ctl);
   }
   if (n > 0) {
     PPhase ph(c, RTS_PHASE_FORCE);
