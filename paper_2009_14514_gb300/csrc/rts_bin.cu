@@ -27,6 +27,7 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
                               int pend, int pend_k1, const uint8_t* __restrict__ cflag,
                               const float4* __restrict__ anew, int32_t* __restrict__ klast,
                               const uint32_t* __restrict__ uid) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {   // the scan that follows appends the filled blocks, the activity pass
     ctl->n_filled = 0;   // the active blocks and the evaluated particles
@@ -150,6 +151,7 @@ __device__ __forceinline__ void load8(const uint32_t* __restrict__ count, int nb
 }
 
 __global__ void k_scan_reduce(const uint32_t* __restrict__ count, int nb, uint32_t* tile_sums) {
+  pdl_wait();
   int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
   uint32_t c[kScanItems];
   load8(count, nb, base, c);
@@ -167,6 +169,7 @@ __global__ void k_scan_reduce(const uint32_t* __restrict__ count, int nb, uint32
 __global__ void k_scan_apply(uint32_t* __restrict__ count, int nb, const uint32_t* __restrict__ tile_sums,
                              uint32_t* __restrict__ cstart, uint32_t* __restrict__ filled,
                              Ctl* ctl) {
+  pdl_wait();
   int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
   uint32_t c[kScanItems];
   load8(count, nb, base, c);
@@ -224,6 +227,7 @@ __global__ void k_scatter(int n, int nb, const uint32_t* __restrict__ key,
                           const uint32_t* __restrict__ slot, const uint32_t* __restrict__ uid,
                           const uint32_t* __restrict__ cstart, uint32_t* __restrict__ tkey,
                           uint32_t* __restrict__ tuid, uint32_t* __restrict__ tsrc, Ctl* ctl) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t b = key[i];
@@ -266,6 +270,7 @@ __global__ void k_canon_gather(int n, int nb, int max_per_block, const uint32_t*
                                const uint32_t* __restrict__ tsrc, PState src, PState dst,
                                uint32_t* __restrict__ key_out, Ctl* ctl, uint32_t stamp,
                                unsigned long long* bmax_v, unsigned long long* bmax_a) {
+  pdl_wait();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t b = 0xffffffffu, s = 0, u = 0;
   bool ok = false;
@@ -353,9 +358,9 @@ void scan_block_counts(uint32_t* count, int nb, uint32_t* tile_sums, uint32_t* c
 static rts_status scan_counts(rts_ctx* c, uint32_t* filled) {
   int nb = c->dp.nblocks;
   int ntiles = (nb + kScanTile - 1) / kScanTile;
-  k_scan_reduce<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums);
-  k_scan_apply<<<ntiles, kScanThreads, 0, c->stream>>>(c->count, nb, c->tile_sums, c->cstart,
-                                                        filled, c->ctl);
+  launch_pdl(c->stream, k_scan_reduce, ntiles, kScanThreads, 0, c->count, nb, c->tile_sums);
+  launch_pdl(c->stream, k_scan_apply, ntiles, kScanThreads, 0, c->count, nb, c->tile_sums,
+             c->cstart, filled, c->ctl);
   return RTS_OK;
 }
 
@@ -383,16 +388,18 @@ rts_status launch_bin(rts_ctx* c, float dt) {
   int tb = 256, g = (n + tb - 1) / tb;
   note_launch(c, 5);
   next_stamp(c);
-  k_predict_key<<<g, tb, 0, c->stream>>>(c->dp, n, c->s.x, c->s.v, c->s.a, dt, c->key, c->slot,
-                                          c->count, c->ctl, c->pend_mode, (int)c->pend_k1,
-                                          c->cflag, c->anew, c->s.klast, c->s.uid);
+  // the binning chain is launched with programmatic dependencies (each kernel waits for
+  // the previous one before its first access; see launch_pdl)
+  launch_pdl(c->stream, k_predict_key, g, tb, 0, c->dp, n, c->s.x, c->s.v, c->s.a, dt, c->key,
+             c->slot, c->count, c->ctl, c->pend_mode, (int)c->pend_k1, c->cflag, c->anew,
+             c->s.klast, c->s.uid);
   c->pend_mode = kPendNone;
   scan_counts(c, c->filled);
-  k_scatter<<<g, tb, 0, c->stream>>>(n, c->dp.nblocks, c->key, c->slot, c->s.uid, c->cstart,
-                                      c->key_tmp, c->tmp_uid, c->tmp_src, c->ctl);
-  k_canon_gather<<<g, tb, 0, c->stream>>>(n, c->dp.nblocks, c->dp.max_per_block, c->cstart, c->key_tmp,
-                                           c->tmp_uid, c->tmp_src, c->s, c->s2, c->key, c->ctl,
-                                           c->stamp, c->bmax_v, c->bmax_a);
+  launch_pdl(c->stream, k_scatter, g, tb, 0, n, c->dp.nblocks, c->key, c->slot, c->s.uid,
+             c->cstart, c->key_tmp, c->tmp_uid, c->tmp_src, c->ctl);
+  launch_pdl(c->stream, k_canon_gather, g, tb, 0, n, c->dp.nblocks, c->dp.max_per_block,
+             c->cstart, c->key_tmp, c->tmp_uid, c->tmp_src, c->s, c->s2, c->key, c->ctl,
+             c->stamp, c->bmax_v, c->bmax_a);
   PState t = c->s;
   c->s = c->s2;
   c->s2 = t;

@@ -382,6 +382,30 @@ inline void note_launch(rts_ctx* c, int k) {
   c->kernels += k;
   c->launches[c->cur_phase] += k;
 }
+
+// Programmatic dependent launch.  A kernel launched with launch_pdl is scheduled as soon
+// as every CTA of the kernel before it in the stream has exited, without waiting for that
+// grid's completion to be signalled; its first statement is pdl_wait(), which returns
+// once the previous kernel has completed and its writes are visible, so no memory access
+// of the two overlaps.  Launched plainly, pdl_wait() is a no-op.  (Signalling dependents
+// early, at the start of each CTA, was measured slower: the waiting CTAs of the next
+// kernel crowd the tail of the current one.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(cudaStream_t st, void (*k)(KArgs...), int grid, int block, size_t smem,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, args...);   // a failure is left for cudaGetLastError
+}
 }  // namespace rts
 
 // Host helpers implemented in rts_api.cu / kernels implemented in the .cu files.

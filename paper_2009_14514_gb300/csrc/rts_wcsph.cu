@@ -51,6 +51,7 @@ __global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled, 
                               const unsigned long long* __restrict__ bmax_v,
                               const unsigned long long* __restrict__ bmax_a, uint32_t stamp,
                               uint32_t* __restrict__ raw) {
+  pdl_wait();
   const int nf = ctl->n_filled;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
     uint32_t b = filled[t];
@@ -83,6 +84,7 @@ __global__ void k_block_rmin(DevParams P, int mode, int level_g,
                              const uint32_t* __restrict__ filled, const Ctl* ctl,
                              const uint32_t* __restrict__ raw, uint32_t* __restrict__ blevel,
                              uint32_t stamp) {
+  pdl_wait();
   const int nf = ctl->n_filled;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
     const uint32_t b = filled[t];
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(kActThreads) k_particle_activity(
     const uint32_t* __restrict__ blevel, uint32_t stamp, PState s, uint8_t* __restrict__ cflag,
     uint32_t* __restrict__ actflag, uint32_t* __restrict__ act, uint32_t* __restrict__ plist,
     Ctl* ctl) {
+  pdl_wait();
   __shared__ uint32_t sp[kActThreads * kActItems], sa[kActThreads * kActItems];
   __shared__ uint32_t scount[2], sbase[2];
   __shared__ int s_kmod[kMaxLevels];   // kmod in shared memory (a parameter array indexed
@@ -404,6 +407,7 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
                                                         const float4* __restrict__ xb,
                                                         const uint8_t* __restrict__ cflag,
                                                         uint32_t* __restrict__ nbl) {
+  pdl_wait();
   extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -568,6 +572,7 @@ __global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_
                                                       Ctl* ctl, PState s, const float4* __restrict__ xb,
                                                       const uint32_t* __restrict__ nbl,
                                                       float4* __restrict__ anew) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int sub = lane & (kForceLanes - 1);
   const int slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / kForceLanes) +
@@ -642,6 +647,7 @@ __global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_
 // prime != 0: no time has passed; only a_old <- a_new, k_last <- k1.
 __global__ void k_correct(DevParams P, const uint32_t* __restrict__ plist, Ctl* ctl, PState s,
                           const float4* __restrict__ anew, int k1, int prime) {
+  pdl_wait();
   const int np = *(volatile int*)&ctl->n_plist;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < np; t += gridDim.x * blockDim.x) {
     const uint32_t i = plist[t];
@@ -777,9 +783,8 @@ int filled_grid_size() { return filled_grid(); }
 
 rts_status launch_classify(rts_ctx* c) {
   note_launch(c, 1);
-  k_block_level<<<filled_grid(), 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->cstart, c->s.v,
-                                                      c->s.a, c->s.ap, c->bmax_v, c->bmax_a,
-                                                      c->stamp, c->raw);
+  launch_pdl(c->stream, k_block_level, filled_grid(), 256, 0, c->dp, c->filled, c->ctl, c->cstart,
+             c->s.v, c->s.a, c->s.ap, c->bmax_v, c->bmax_a, c->stamp, c->raw);
   return RTS_OK;
 }
 
@@ -789,39 +794,39 @@ rts_status launch_classify(rts_ctx* c) {
 // binning (every step bins before its activity pass).
 rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1) {
   note_launch(c, 1);
-  k_block_rmin<<<filled_grid(), 256, 0, c->stream>>>(c->dp, mode, level_g, c->filled, c->ctl,
-                                                     c->raw, c->blevel, c->stamp);
+  launch_pdl(c->stream, k_block_rmin, filled_grid(), 256, 0, c->dp, mode, level_g, c->filled,
+             c->ctl, c->raw, c->blevel, c->stamp);
   if (mode >= 0 && c->n > 0) {
     note_launch(c, 1);
     const int g = (c->n + kActThreads * kActItems - 1) / (kActThreads * kActItems);
     LevelPhase kmod;
     for (int L = 0; L < kMaxLevels; ++L)
       kmod.v[L] = L < c->p.n_levels ? (int)(k1 % (int64_t)c->p.level_mult[L]) : 0;
-    k_particle_activity<<<g, kActThreads, 0, c->stream>>>(c->dp, mode, mult_g, kmod, c->n,
-                                                   c->key, c->blevel, c->stamp, c->s, c->cflag,
-                                                   c->actflag, c->act, c->plist, c->ctl);
+    launch_pdl(c->stream, k_particle_activity, g, kActThreads, 0, c->dp, mode, mult_g, kmod, c->n,
+               c->key, c->blevel, c->stamp, c->s, c->cflag, c->actflag, c->act, c->plist,
+               c->ctl);
   }
   return RTS_OK;
 }
 
 rts_status launch_density(rts_ctx* c) {
   note_launch(c, 1);
-  k_density<<<c->grid_persistent, kNbThreads, density_smem(), c->stream>>>(
-      c->dp, c->act, c->ctl, c->cstart, c->bcstart, c->s, c->xb, c->cflag, c->nbl);
+  launch_pdl(c->stream, k_density, c->grid_persistent, kNbThreads, density_smem(), c->dp, c->act,
+             c->ctl, c->cstart, c->bcstart, c->s, c->xb, c->cflag, c->nbl);
   return RTS_OK;
 }
 
 rts_status launch_force(rts_ctx* c) {
   note_launch(c, 1);
-  k_force<<<force_grid(c), kNbThreads, 0, c->stream>>>(c->dp, c->plist, c->ctl, c->s, c->xb,
-                                                       c->nbl, c->anew);
+  launch_pdl(c->stream, k_force, force_grid(c), kNbThreads, 0, c->dp, c->plist, c->ctl, c->s,
+             c->xb, c->nbl, c->anew);
   return RTS_OK;
 }
 
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime) {
   note_launch(c, 1);
-  k_correct<<<force_grid(c), kNbThreads, 0, c->stream>>>(c->dp, c->plist, c->ctl, c->s, c->anew,
-                                                              (int)k1, prime);
+  launch_pdl(c->stream, k_correct, force_grid(c), kNbThreads, 0, c->dp, c->plist, c->ctl, c->s,
+             c->anew, (int)k1, prime);
   return RTS_OK;
 }
 
