@@ -110,6 +110,7 @@ __global__ void k_assign_regions(DevParams P, int n, const uint32_t* __restrict_
 __global__ void k_observed(DevParams P, const uint32_t* __restrict__ filled, const Ctl* ctl,
                            const int32_t* __restrict__ preg, const uint8_t* __restrict__ in_re,
                            uint8_t* __restrict__ ob) {
+  pdl_wait();
   const int nf = ctl->n_filled;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
     uint32_t b = filled[t];
@@ -134,6 +135,7 @@ __global__ void k_lists(DevParams P, int n, const uint32_t* __restrict__ key,
                         const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ bcstart,
                         PState s, const float4* __restrict__ xb, const uint8_t* __restrict__ cflag,
                         uint32_t* __restrict__ nbl, Ctl* ctl) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || !cflag[i]) return;
   uint32_t b = key[i];
@@ -192,6 +194,7 @@ __global__ void k_lists(DevParams P, int n, const uint32_t* __restrict__ key,
 template <int LANES>
 __global__ void k_nonpressure(DevParams P, int n, PState s, const float4* __restrict__ xb,
                               const uint8_t* __restrict__ cflag, const uint32_t* __restrict__ nbl) {
+  pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;   // LANES lanes per particle
   const int i = t / LANES, sub = t % LANES;
   const bool valid = i < n && cflag[i];
@@ -232,13 +235,17 @@ __global__ void k_nonpressure(DevParams P, int n, PState s, const float4* __rest
 // ------------------------------------------------------- Algorithm 3 ---
 
 // Predict v* = v + dt (a_np + a_p), x* = x + dt v* (every particle); the iteration's
-// error reductions start from zero (the previous ones were read back before).
-__global__ void k_predict(DevParams P, int n, PState s, float4* __restrict__ xs, Ctl* ctl) {
+// error reductions and R_e flags (nbk blocks) start from zero (the previous ones were
+// read before).
+__global__ void k_predict(DevParams P, int n, PState s, float4* __restrict__ xs, Ctl* ctl,
+                          uint8_t* __restrict__ in_re, size_t nbk) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     ctl->err_max_bits = 0u;
     ctl->err_sum_fx = 0ull;
   }
+  for (size_t b = (size_t)i; b < nbk; b += (size_t)gridDim.x * blockDim.x) in_re[b] = 0;
   if (i >= n) return;
   xs[i] = predict_one(P, s, i);
 }
@@ -250,6 +257,7 @@ __global__ void k_pdensity(DevParams P, int n, int j_minor, int row, int mode,
                            const uint8_t* __restrict__ in_se, const uint8_t* __restrict__ ob,
                            float4* xs, const float4* __restrict__ xb,
                            const uint32_t* __restrict__ nbl) {
+  pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;   // LANES lanes per particle
   const int i = t / LANES, sub = t % LANES;
   const bool valid =
@@ -261,6 +269,7 @@ __global__ void k_pdensity(DevParams P, int n, int j_minor, int row, int mode,
 // errors of all particles (exact max on FP32 bits, fixed-point sum).
 __global__ void k_se_reduce(DevParams P, int n, const uint32_t* __restrict__ key, PState s,
                             uint8_t* __restrict__ in_se, uint8_t* __restrict__ in_re, Ctl* ctl) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   float e = 0.f;
   if (i < n) {
@@ -299,6 +308,7 @@ template <int LANES>
 __global__ void k_ppressure(DevParams P, int n, int j_minor, int row, int mode, PState s,
                             const uint8_t* __restrict__ in_se, const float4* __restrict__ xs,
                             const float4* __restrict__ xb, const uint32_t* __restrict__ nbl) {
+  pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;   // LANES lanes per particle
   const int i = t / LANES, sub = t % LANES;
   const bool valid = i < n && (has_turn(P, mode, row, j_minor, s.level[i]) || in_se[i]);
@@ -308,6 +318,7 @@ __global__ void k_ppressure(DevParams P, int n, int j_minor, int row, int mode, 
 // ------------------------------------------------------- Algorithm 2 ---
 
 __global__ void k_integrate(DevParams P, int n, PState s) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 x = s.x[i], v = s.v[i], a = s.a[i], pa = s.ap[i];
@@ -324,6 +335,7 @@ __global__ void k_integrate(DevParams P, int n, PState s) {
 }
 
 __global__ void k_validity(DevParams P, int n, PState s, uint8_t* __restrict__ cflag) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int val = s.valid[i] - 1;
@@ -391,6 +403,7 @@ __global__ void k_preempt_mark(DevParams P, int n, const uint32_t* __restrict__ 
 __global__ void k_preempt_apply(DevParams P, int n, const uint32_t* __restrict__ key,
                                 const int32_t* __restrict__ pnew, PState s,
                                 uint8_t* __restrict__ cflag) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int L = pnew[key[i]];
@@ -478,23 +491,24 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
     {
       PPhase ph(c, RTS_PHASE_ITERATE);
       note_launch(c, 5);
-      k_predict<<<g, 256, 0, c->stream>>>(Q, n, c->s, c->xs, c->ctl);
+      // one chain of programmatically dependent launches (see launch_pdl)
+      cudaStream_t st = c->stream;
+      launch_pdl(st, k_predict, g, 256, 0, Q, n, c->s, c->xs, c->ctl, c->in_re, nbk);
       // every particle takes part (all_turn): kPLanes lanes each; else one
       if (all_turn)
-        k_pdensity<kPLanes><<<grid_lanes(n, kPLanes), 256, 0, c->stream>>>(
-            Q, n, j, row, mode, c->key, c->s, c->in_se, c->ob, c->xs, c->xb, c->nbl);
+        launch_pdl(st, k_pdensity<kPLanes>, grid_lanes(n, kPLanes), 256, 0, Q, n, j, row, mode,
+                   c->key, c->s, c->in_se, c->ob, c->xs, c->xb, c->nbl);
       else
-        k_pdensity<1><<<grid_lanes(n, 1), 256, 0, c->stream>>>(
-            Q, n, j, row, mode, c->key, c->s, c->in_se, c->ob, c->xs, c->xb, c->nbl);
-      cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
-      k_se_reduce<<<g, 256, 0, c->stream>>>(Q, n, c->key, c->s, c->in_se, c->in_re, c->ctl);
-      k_observed<<<fg, 256, 0, c->stream>>>(Q, c->filled, c->ctl, c->preg, c->in_re, c->ob);
+        launch_pdl(st, k_pdensity<1>, grid_lanes(n, 1), 256, 0, Q, n, j, row, mode, c->key, c->s,
+                   c->in_se, c->ob, c->xs, c->xb, c->nbl);
+      launch_pdl(st, k_se_reduce, g, 256, 0, Q, n, c->key, c->s, c->in_se, c->in_re, c->ctl);
+      launch_pdl(st, k_observed, fg, 256, 0, Q, c->filled, c->ctl, c->preg, c->in_re, c->ob);
       if (all_turn)
-        k_ppressure<kPLanes><<<grid_lanes(n, kPLanes), 256, 0, c->stream>>>(
-            Q, n, j, row, mode, c->s, c->in_se, c->xs, c->xb, c->nbl);
+        launch_pdl(st, k_ppressure<kPLanes>, grid_lanes(n, kPLanes), 256, 0, Q, n, j, row, mode,
+                   c->s, c->in_se, c->xs, c->xb, c->nbl);
       else
-        k_ppressure<1><<<grid_lanes(n, 1), 256, 0, c->stream>>>(
-            Q, n, j, row, mode, c->s, c->in_se, c->xs, c->xb, c->nbl);
+        launch_pdl(st, k_ppressure<1>, grid_lanes(n, 1), 256, 0, Q, n, j, row, mode, c->s,
+                   c->in_se, c->xs, c->xb, c->nbl);
     }
     // both reductions in one copy (err_max_bits and err_sum_fx are adjacent in Ctl)
     constexpr size_t kErrBytes =
@@ -738,19 +752,19 @@ void pcisph_minor_begin(rts_ctx* c) {
     // gives the same list, in the same order, as the wider search of R_1 (and R_2).
     DevParams Q = c->dp;
     if (c->minor == 0) Q.r1_rings = Q.r2_rings = 1;
-    k_lists<<<g, 256, 0, c->stream>>>(Q, n, c->key, c->cstart, c->bcstart, c->s, c->xb, c->cflag,
-                                      c->nbl, c->ctl);
+    launch_pdl(c->stream, k_lists, g, 256, 0, Q, n, c->key, c->cstart, c->bcstart, c->s, c->xb,
+               c->cflag, c->nbl, c->ctl);
   }
   if (n > 0) {
     PPhase ph(c, RTS_PHASE_FORCE);
     note_launch(c, 1);
     // at a major-step start every particle refreshes: kPLanes lanes each; later few
     if (c->minor == 0)
-      k_nonpressure<kPLanes><<<grid_lanes(n, kPLanes), 256, 0, c->stream>>>(c->dp, n, c->s, c->xb,
-                                                                          c->cflag, c->nbl);
+      launch_pdl(c->stream, k_nonpressure<kPLanes>, grid_lanes(n, kPLanes), 256, 0, c->dp, n, c->s,
+                 c->xb, c->cflag, c->nbl);
     else
-      k_nonpressure<1><<<grid_lanes(n, 1), 256, 0, c->stream>>>(c->dp, n, c->s, c->xb, c->cflag,
-                                                                c->nbl);
+      launch_pdl(c->stream, k_nonpressure<1>, grid_lanes(n, 1), 256, 0, c->dp, n, c->s, c->xb,
+                 c->cflag, c->nbl);
   }
   cudaMemsetAsync(c->s.prs, 0, sizeof(float) * (size_t)(n > 0 ? n : 1), c->stream);
   cudaMemsetAsync(c->s.ap, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c->stream);
@@ -770,12 +784,12 @@ rts_status pcisph_minor_end(rts_ctx* c, int j) {
   note_launch(c, 2);
   k_integrate<<<g, 256, 0, c->stream>>>(c->dp, n, c->s);
   const int last = (j + 1 >= c->n_minor_cur) || c->shorten_now;
-  k_validity<<<g, 256, 0, c->stream>>>(c->dp, n, c->s, c->cflag);
+  launch_pdl(c->stream, k_validity, g, 256, 0, c->dp, n, c->s, c->cflag);
   if (!last && n > 0) {
     note_launch(c, 2);
     cudaMemcpyAsync(c->pnew, c->preg, sizeof(int32_t) * nbk, cudaMemcpyDeviceToDevice, c->stream);
     k_preempt_mark<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->s, c->pnew);
-    k_preempt_apply<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->pnew, c->s, c->cflag);
+    launch_pdl(c->stream, k_preempt_apply, g, 256, 0, c->dp, n, c->key, c->pnew, c->s, c->cflag);
     int32_t* t = c->preg;
     c->preg = c->pnew;
     c->pnew = t;
