@@ -510,6 +510,15 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
         launch_pdl(st, k_ppressure<1>, grid_lanes(n, 1), 256, 0, Q, n, j, row, mode, c->s,
                    c->in_se, c->xs, c->xb, c->nbl);
     }
+    ++done;
+    if (all_turn) ++c->it_global;
+    if (mode == kModeLocal) ++c->it_local;
+    // At least three iterations run, so the first two decide nothing: their reductions
+    // are not read, and the next iteration is queued without a round trip to the host.
+    if (done < 3 && done < c->p.max_iters) {
+      ++row;
+      continue;
+    }
     // both reductions in one copy (err_max_bits and err_sum_fx are adjacent in Ctl)
     constexpr size_t kErrBytes =
         offsetof(Ctl, err_sum_fx) + sizeof(unsigned long long) - offsetof(Ctl, err_max_bits);
@@ -520,9 +529,6 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
       cuda_err(c, e, "PCISPH iteration");
       return RTS_ERR_CUDA;
     }
-    ++done;
-    if (all_turn) ++c->it_global;
-    if (mode == kModeLocal) ++c->it_local;
     float emax;
     unsigned bits = c->h_ctl->err_max_bits;
     memcpy(&emax, &bits, sizeof emax);
@@ -534,10 +540,6 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
       status = RTS_ERR_NOT_CONVERGED;
       c->it_notconv = 1;
       break;
-    }
-    if (done < 3) {
-      ++row;
-      continue;
     }
     min_iter = done + 1;
     if (stay_global || c->it_erravg >= (double)c->p.eta_T) {
