@@ -190,13 +190,23 @@ __global__ void k_lists(DevParams P, int n, const uint32_t* __restrict__ key,
 }
 
 // Non-pressure acceleration of refreshing particles: gravity + artificial viscosity
-// (nu = alpha h c / rho0) over the neighbourhood; boundary particles are at rest.
+// (nu = alpha h c / rho0) over the neighbourhood; boundary particles are at rest.  The
+// minor step's resets ride along: pressure, pressure acceleration and S_e of every
+// particle, and the R_e flags of the nbk blocks, are zeroed (none is read here).
 template <int LANES>
 __global__ void k_nonpressure(DevParams P, int n, PState s, const float4* __restrict__ xb,
-                              const uint8_t* __restrict__ cflag, const uint32_t* __restrict__ nbl) {
+                              const uint8_t* __restrict__ cflag, const uint32_t* __restrict__ nbl,
+                              uint8_t* __restrict__ in_se, uint8_t* __restrict__ in_re,
+                              size_t nbk) {
   pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;   // LANES lanes per particle
   const int i = t / LANES, sub = t % LANES;
+  for (size_t b = (size_t)t; b < nbk; b += (size_t)gridDim.x * blockDim.x) in_re[b] = 0;
+  if (i < n && sub == 0) {
+    s.prs[i] = 0.f;
+    s.ap[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    in_se[i] = 0;
+  }
   const bool valid = i < n && cflag[i];
   float ax = 0.f, ay = 0.f, az = 0.f;
   if (valid) {
@@ -700,8 +710,8 @@ static rts_status pcisph_global(rts_ctx* c, int64_t max_mult) {
     }
     {
       PPhase ph(c, RTS_PHASE_FORCE);
-      k_nonpressure<kPLanes><<<grid_lanes(n, kPLanes), 256, 0, c->stream>>>(Q, n, c->s, c->xb,
-                                                                          c->cflag, c->nbl);
+      k_nonpressure<kPLanes><<<grid_lanes(n, kPLanes), 256, 0, c->stream>>>(
+          Q, n, c->s, c->xb, c->cflag, c->nbl, c->in_se, c->in_re, (size_t)0);
     }
   }
   const size_t n1 = (size_t)(n > 0 ? n : 1);
@@ -763,17 +773,16 @@ void pcisph_minor_begin(rts_ctx* c) {
     // at a major-step start every particle refreshes: kPLanes lanes each; later few
     if (c->minor == 0)
       launch_pdl(c->stream, k_nonpressure<kPLanes>, grid_lanes(n, kPLanes), 256, 0, c->dp, n, c->s,
-                 c->xb, c->cflag, c->nbl);
+                 c->xb, c->cflag, c->nbl, c->in_se, c->in_re, nbk);
     else
       launch_pdl(c->stream, k_nonpressure<1>, grid_lanes(n, 1), 256, 0, c->dp, n, c->s, c->xb,
-                 c->cflag, c->nbl);
+                 c->cflag, c->nbl, c->in_se, c->in_re, nbk);
+  } else {
+    cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
   }
-  cudaMemsetAsync(c->s.prs, 0, sizeof(float) * (size_t)(n > 0 ? n : 1), c->stream);
-  cudaMemsetAsync(c->s.ap, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c->stream);
-  cudaMemsetAsync(c->in_se, 0, (size_t)(n > 0 ? n : 1), c->stream);
-  cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
   note_launch(c, 1);
-  k_observed<<<fg, 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->preg, c->in_re, c->ob);
+  launch_pdl(c->stream, k_observed, fg, 256, 0, c->dp, c->filled, c->ctl, c->preg, c->in_re,
+             c->ob);
 }
 
 // Integration, validity, pre-emption and the major-step bookkeeping after the density
