@@ -24,12 +24,16 @@ namespace rts {
 
 // ------------------------------------------------------------- regions ---
 
-__global__ void k_preg_from_blevel(const uint32_t* __restrict__ filled, const Ctl* ctl,
-                                   const uint32_t* __restrict__ blevel, int32_t* __restrict__ preg) {
-  const int nf = ctl->n_filled;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
-    uint32_t b = filled[t];
-    preg[b] = (int32_t)(blevel[b] & 0xffu);
+// Region of every block: a filled block's smoothed level (blevel carries this binning's
+// stamp above the level for exactly the filled blocks), -1 for any other block.
+__global__ void k_preg_from_blevel(DevParams P, const uint32_t* __restrict__ blevel,
+                                   uint32_t stamp, int32_t* __restrict__ preg) {
+  pdl_wait();
+  const int64_t nb = (int64_t)P.nblocks;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = blevel[b];
+    preg[b] = (v >> 8) == stamp ? (int32_t)(v & 0xffu) : -1;
   }
 }
 
@@ -39,9 +43,11 @@ __global__ void k_preg_from_blevel(const uint32_t* __restrict__ filled, const Ct
 // three separable passes: an x pass marks the blocks with a block of region <= target
 // within `layers` along x (from the region field), a y pass widens the marks along y,
 // and a pass over the filled blocks widens along z and applies the minimum; each block
-// reads 2 layers + 1 values per pass instead of (2 layers + 1)^3.
+// reads 2 layers + 1 values per pass instead of (2 layers + 1)^3.  The x pass also sets
+// every block of the output field to -1 (the z pass writes the filled ones).
 __global__ void k_dilate_x(DevParams P, const int32_t* __restrict__ in, int target, int layers,
-                           uint8_t* __restrict__ mx) {
+                           uint8_t* __restrict__ mx, int32_t* __restrict__ out) {
+  pdl_wait();
   const int64_t nb = (int64_t)P.nblocks;
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
        b += (int64_t)gridDim.x * blockDim.x) {
@@ -55,11 +61,13 @@ __global__ void k_dilate_x(DevParams P, const int32_t* __restrict__ in, int targ
       m |= (Lc >= 0 && Lc <= target) ? 1 : 0;
     }
     mx[b] = m;
+    out[b] = -1;
   }
 }
 
 __global__ void k_dilate_y(DevParams P, const uint8_t* __restrict__ mx, int layers,
                            uint8_t* __restrict__ my) {
+  pdl_wait();
   const int64_t nb = (int64_t)P.nblocks;
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
        b += (int64_t)gridDim.x * blockDim.x) {
@@ -76,6 +84,7 @@ __global__ void k_dilate_y(DevParams P, const uint8_t* __restrict__ mx, int laye
 __global__ void k_dilate_z(DevParams P, const uint32_t* __restrict__ filled, const Ctl* ctl,
                            const int32_t* __restrict__ in, const uint8_t* __restrict__ my,
                            int target, int layers, int32_t* __restrict__ out) {
+  pdl_wait();
   const int nf = ctl->n_filled;
   const int64_t nxy = (int64_t)P.nx * P.ny;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
@@ -98,6 +107,7 @@ __global__ void k_dilate_z(DevParams P, const uint32_t* __restrict__ filled, con
 __global__ void k_assign_regions(DevParams P, int n, const uint32_t* __restrict__ key,
                                  const int32_t* __restrict__ preg, PState s,
                                  uint8_t* __restrict__ cflag) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int L = preg[key[i]];
@@ -344,9 +354,15 @@ __global__ void k_integrate(DevParams P, int n, PState s) {
   s.v[i] = v;
 }
 
-__global__ void k_validity(DevParams P, int n, PState s, uint8_t* __restrict__ cflag) {
+// Validity countdown (Algorithm 2); with rdst set, the nb block regions are copied from
+// rsrc to rdst as well (the pre-emption pass that follows marks the copy).
+__global__ void k_validity(DevParams P, int n, PState s, uint8_t* __restrict__ cflag,
+                           const int32_t* __restrict__ rsrc, int32_t* __restrict__ rdst,
+                           size_t nb) {
   pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rdst)
+    for (size_t b = (size_t)i; b < nb; b += (size_t)gridDim.x * blockDim.x) rdst[b] = rsrc[b];
   if (i >= n) return;
   int val = s.valid[i] - 1;
   if (val <= 0) {
@@ -387,6 +403,7 @@ __device__ __forceinline__ int ppick_particle(const DevParams& P, float4 v, floa
 // Section 5.6: a particle needing a smaller region lowers its block and the 26 around.
 __global__ void k_preempt_mark(DevParams P, int n, const uint32_t* __restrict__ key, PState s,
                                int32_t* __restrict__ pnew) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int L = ppick_particle(P, s.v[i], s.a[i], s.ap[i]);
@@ -452,20 +469,19 @@ static rts_status major_start(rts_ctx* c) {
   PPhase ph(c, RTS_PHASE_CLASSIFY);
   launch_classify(c);             // Eq. 2-3 from the block maxima (thresholds for PCISPH)
   launch_activity(c, -1, 0, 0, 0);   // R_min (or the forced region)
-  cudaMemsetAsync(c->preg, 0xff, sizeof(int32_t) * nbk, c->stream);
   int fg = filled_grid_size();
+  const int gg = (int)((nbk + 255) / 256 < (size_t)(fg * 4) ? (nbk + 255) / 256 : (size_t)(fg * 4));
   note_launch(c, 1);
-  k_preg_from_blevel<<<fg, 256, 0, c->stream>>>(c->filled, c->ctl, c->blevel, c->preg);
+  launch_pdl(c->stream, k_preg_from_blevel, gg, 256, 0, c->dp, c->blevel, c->stamp, c->preg);
   if (c->p.force_level < 0 && c->p.expand_layers > 0) {
     // R_e and R_ob are rebuilt at the next minor step: their bytes hold the marks here
-    const int gg = (int)((nbk + 255) / 256 < (size_t)(fg * 4) ? (nbk + 255) / 256 : (size_t)(fg * 4));
     for (int target = 0; target <= 1; ++target) {
-      cudaMemsetAsync(c->pnew, 0xff, sizeof(int32_t) * nbk, c->stream);
       note_launch(c, 3);
-      k_dilate_x<<<gg, 256, 0, c->stream>>>(c->dp, c->preg, target, c->p.expand_layers, c->in_re);
-      k_dilate_y<<<gg, 256, 0, c->stream>>>(c->dp, c->in_re, c->p.expand_layers, c->ob);
-      k_dilate_z<<<fg, 256, 0, c->stream>>>(c->dp, c->filled, c->ctl, c->preg, c->ob, target,
-                                            c->p.expand_layers, c->pnew);
+      launch_pdl(c->stream, k_dilate_x, gg, 256, 0, c->dp, c->preg, target, c->p.expand_layers,
+                 c->in_re, c->pnew);
+      launch_pdl(c->stream, k_dilate_y, gg, 256, 0, c->dp, c->in_re, c->p.expand_layers, c->ob);
+      launch_pdl(c->stream, k_dilate_z, fg, 256, 0, c->dp, c->filled, c->ctl, c->preg, c->ob,
+                 target, c->p.expand_layers, c->pnew);
       int32_t* t = c->preg;
       c->preg = c->pnew;
       c->pnew = t;
@@ -473,7 +489,8 @@ static rts_status major_start(rts_ctx* c) {
   }
   if (n > 0) {
     note_launch(c, 1);
-    k_assign_regions<<<grid_of(n), 256, 0, c->stream>>>(c->dp, n, c->key, c->preg, c->s, c->cflag);
+    launch_pdl(c->stream, k_assign_regions, grid_of(n), 256, 0, c->dp, n, c->key, c->preg, c->s,
+               c->cflag);
   }
   c->shorten_now = 0;
   return RTS_OK;
@@ -795,11 +812,13 @@ rts_status pcisph_minor_end(rts_ctx* c, int j) {
   note_launch(c, 2);
   k_integrate<<<g, 256, 0, c->stream>>>(c->dp, n, c->s);
   const int last = (j + 1 >= c->n_minor_cur) || c->shorten_now;
-  launch_pdl(c->stream, k_validity, g, 256, 0, c->dp, n, c->s, c->cflag);
-  if (!last && n > 0) {
+  // pre-emption follows unless the major step ends: the validity pass copies the regions
+  const bool pre = !last && n > 0;
+  launch_pdl(c->stream, k_validity, g, 256, 0, c->dp, n, c->s, c->cflag,
+             pre ? c->preg : nullptr, pre ? c->pnew : nullptr, pre ? nbk : (size_t)0);
+  if (pre) {
     note_launch(c, 2);
-    cudaMemcpyAsync(c->pnew, c->preg, sizeof(int32_t) * nbk, cudaMemcpyDeviceToDevice, c->stream);
-    k_preempt_mark<<<g, 256, 0, c->stream>>>(c->dp, n, c->key, c->s, c->pnew);
+    launch_pdl(c->stream, k_preempt_mark, g, 256, 0, c->dp, n, c->key, c->s, c->pnew);
     launch_pdl(c->stream, k_preempt_apply, g, 256, 0, c->dp, n, c->key, c->pnew, c->s, c->cflag);
     int32_t* t = c->preg;
     c->preg = c->pnew;
