@@ -517,9 +517,14 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
     const int all_turn = mode == kModeGlobal || (mode == kModeSched && row <= min_sched);
     {
       PPhase ph(c, RTS_PHASE_ITERATE);
-      note_launch(c, 5);
+      note_launch(c, all_turn ? 4 : 5);
       // one chain of programmatically dependent launches (see launch_pdl)
       cudaStream_t st = c->stream;
+      // R_ob matters only to an iteration in which not every particle takes part: it is
+      // formed here, before the predict pass clears R_e, from the R_e of the previous
+      // iteration (cleared at the start of the minor step) and the regions
+      if (!all_turn)
+        launch_pdl(st, k_observed, fg, 256, 0, Q, c->filled, c->ctl, c->preg, c->in_re, c->ob);
       launch_pdl(st, k_predict, g, 256, 0, Q, n, c->s, c->xs, c->ctl, c->in_re, nbk);
       // every particle takes part (all_turn): kPLanes lanes each; else one
       if (all_turn)
@@ -529,7 +534,6 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
         launch_pdl(st, k_pdensity<1>, grid_lanes(n, 1), 256, 0, Q, n, j, row, mode, c->key, c->s,
                    c->in_se, c->ob, c->xs, c->xb, c->nbl);
       launch_pdl(st, k_se_reduce, g, 256, 0, Q, n, c->key, c->s, c->in_se, c->in_re, c->ctl);
-      launch_pdl(st, k_observed, fg, 256, 0, Q, c->filled, c->ctl, c->preg, c->in_re, c->ob);
       if (all_turn)
         launch_pdl(st, k_ppressure<kPLanes>, grid_lanes(n, kPLanes), 256, 0, Q, n, j, row, mode,
                    c->s, c->in_se, c->xs, c->xb, c->nbl);
@@ -797,9 +801,13 @@ void pcisph_minor_begin(rts_ctx* c) {
   } else {
     cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
   }
-  note_launch(c, 1);
-  launch_pdl(c->stream, k_observed, fg, 256, 0, c->dp, c->filled, c->ctl, c->preg, c->in_re,
-             c->ob);
+  // a single scene forms R_ob in the density correction, when an iteration needs it; the
+  // batched iterations read this one in their first iteration
+  if (c->batch) {
+    note_launch(c, 1);
+    launch_pdl(c->stream, k_observed, fg, 256, 0, c->dp, c->filled, c->ctl, c->preg, c->in_re,
+               c->ob);
+  }
 }
 
 // Integration, validity, pre-emption and the major-step bookkeeping after the density
