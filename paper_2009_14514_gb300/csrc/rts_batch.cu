@@ -272,16 +272,21 @@ __global__ void k_b_density(DevParams P, const BatchView* __restrict__ Vp, Batch
   }
 }
 
-// R_ob of the filled blocks of the iterating scenes.
+// R_ob of the filled blocks of the scenes whose iteration about to run does not give
+// every particle a turn (R_ob's only readers), from the R_e of their previous iteration
+// (cleared at the start of the minor step); runs before the predict pass clears R_e.
 __global__ void k_b_observed(DevParams P, const BatchView* __restrict__ Vp,
-                             const SceneIt* __restrict__ S) {
+                             const BatchCtl* __restrict__ B, const SceneIt* __restrict__ S) {
   const BatchView V = *Vp;
   const int nf = V.ctl->n_filled;
+  const int min_sched = B->min_sched;
   const uint32_t nxy = (uint32_t)P.nx * (uint32_t)P.ny;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
     const uint32_t b = V.filled[t];
     const int sc = scene_of_z(P.zbase, P.n_scenes, (int)(b / nxy));
-    if (!S[sc].active) continue;
+    const int mode = S[sc].mode;
+    if (!S[sc].active || mode == kModeGlobal || (mode == kModeSched && S[sc].row <= min_sched))
+      continue;
     V.ob[b] = observed_one(P, b, V.preg, V.in_re);
   }
 }
@@ -424,9 +429,9 @@ static void launch_body(rts_ctx* c, cudaStream_t st, cudaGraphConditionalHandle 
                         int in_graph) {
   BatchState* b = c->batch;
   const size_t sm = queue_smem(b);
+  k_b_observed<<<filled_grid_size(), 256, 0, st>>>(c->dp, b->d_view, b->bctl, b->sit);
   k_b_predict<<<b->grid[0], b->threads, sm, st>>>(c->dp, b->d_view, b->bctl, b->sit, b->tile);
   k_b_density<<<b->grid[1], b->threads, sm, st>>>(c->dp, b->d_view, b->bctl, b->sit, b->tile);
-  k_b_observed<<<filled_grid_size(), 256, 0, st>>>(c->dp, b->d_view, b->sit);
   k_b_pressure<<<b->grid[2], b->threads, sm, st>>>(c->dp, b->d_view, b->bctl, b->sit, b->tile);
   k_b_control<<<1, b->ctl_threads, 0, st>>>(b->ns, b->tile, c->p.eta, c->p.eta_T, c->p.max_iters,
                                            c->p.max_local_iters, b->bctl, b->sit, cond, in_graph);

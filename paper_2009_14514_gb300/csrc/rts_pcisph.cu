@@ -773,7 +773,6 @@ static rts_status pcisph_global(rts_ctx* c, int64_t max_mult) {
 void pcisph_minor_begin(rts_ctx* c) {
   const int n = c->n;
   const int g = grid_of(n > 0 ? n : 1);
-  const int fg = filled_grid_size();
   const size_t nbk = (size_t)c->dp.nblocks;
   if (c->n_minor_cur <= 0) c->n_minor_cur = c->p.n_minor;
   if (c->minor == 0) major_start(c);
@@ -801,13 +800,7 @@ void pcisph_minor_begin(rts_ctx* c) {
   } else {
     cudaMemsetAsync(c->in_re, 0, nbk, c->stream);
   }
-  // a single scene forms R_ob in the density correction, when an iteration needs it; the
-  // batched iterations read this one in their first iteration
-  if (c->batch) {
-    note_launch(c, 1);
-    launch_pdl(c->stream, k_observed, fg, 256, 0, c->dp, c->filled, c->ctl, c->preg, c->in_re,
-               c->ob);
-  }
+  // R_ob is formed in the density correction, before an iteration that reads it
 }
 
 // Integration, validity, pre-emption and the major-step bookkeeping after the density
