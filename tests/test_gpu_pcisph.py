@@ -128,6 +128,18 @@ def test_iteration_control_decisions_match_oracle(over):
     assert info["not_converged"] == S.stats["not_converged"]
 
 
+def test_state_after_local_iterations_matches_oracle():
+    # local iterations take S_e and R_ob only (R_ob formed just before each of them): the
+    # state after the minor step, not only the counts, follows the oracle
+    sc = scenes.pcisph_drop_small()
+    x = _compressed(sc)
+    ctx, S, P = _pair(sc, x=x, eta=0.002, eta_T=0.5)
+    rts.rts_pcisph_step(ctx, allow_not_converged=True)
+    S.step()
+    info = _compare_step(ctx, S, P)
+    assert info["local_iterations"] > 0
+
+
 def test_major_step_shortening_matches_oracle():
     sc = scenes.pcisph_drop_small()
     ctx, S, P = _pair(sc, max_global_iters=1, clean_majors=2)
