@@ -349,8 +349,9 @@ __global__ void k_canon_gather(int n, int nb, int max_per_block, const uint32_t*
 void scan_block_counts(uint32_t* count, int nb, uint32_t* tile_sums, uint32_t* cstart,
                        cudaStream_t stream) {
   int ntiles = (nb + kScanTile - 1) / kScanTile;
-  k_scan_reduce<<<ntiles, kScanThreads, 0, stream>>>(count, nb, tile_sums);
-  k_scan_apply<<<ntiles, kScanThreads, 0, stream>>>(count, nb, tile_sums, cstart, nullptr, nullptr);
+  launch_pdl(stream, k_scan_reduce, ntiles, kScanThreads, 0, count, nb, tile_sums);
+  launch_pdl(stream, k_scan_apply, ntiles, kScanThreads, 0, count, nb, tile_sums, cstart,
+             (uint32_t*)nullptr, (Ctl*)nullptr);
 }
 
 // Exclusive scan of the block counts into cstart (tile totals, then each tile adds the

@@ -107,6 +107,7 @@ __device__ __forceinline__ float tait_p(const DevParams& P, float B, float rho) 
 
 __global__ void kd_key(DevParams P, int n, const float4* __restrict__ x, uint32_t* __restrict__ key,
                        uint32_t* __restrict__ count, Ctl* ctl) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int bad = 0;
@@ -127,6 +128,7 @@ __global__ void kd_key(DevParams P, int n, const float4* __restrict__ x, uint32_
 
 __global__ void kd_place(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ cstart,
                          uint32_t* __restrict__ count, uint32_t* __restrict__ perm_tmp) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t b = key[i];
@@ -137,6 +139,7 @@ __global__ void kd_place(int n, const uint32_t* __restrict__ key, const uint32_t
 __global__ void kd_rank(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ cstart,
                         uint32_t* __restrict__ count, const uint32_t* __restrict__ perm_tmp,
                         uint32_t* __restrict__ perm) {
+  pdl_wait();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const uint32_t i = perm_tmp[q];
@@ -164,6 +167,7 @@ __global__ void kd_density(DevParams P, int n, float B, const float4* __restrict
                            const uint32_t* __restrict__ bcstart, int cap, float* __restrict__ rho,
                            float* __restrict__ prs, uint32_t* __restrict__ list,
                            int* __restrict__ nn, Ctl* ctl) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 xi = x[i];
@@ -222,6 +226,7 @@ __global__ void kd_force(DevParams P, int n, float K, const float4* __restrict__
                          const float* __restrict__ prs, const float4* __restrict__ xb,
                          const uint32_t* __restrict__ list, const int* __restrict__ nn, int cap,
                          float4* __restrict__ a) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 xi = x[i], vi = v[i];
@@ -266,6 +271,7 @@ __global__ void kd_predict(DevParams P, int n, float dt, const float4* __restric
                            const float4* __restrict__ v, const float4* __restrict__ a,
                            float4* __restrict__ xt, float4* __restrict__ vt,
                            uint8_t* __restrict__ mask) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 xi = x[i], vi = v[i], ai = a[i];
@@ -300,6 +306,7 @@ __global__ void kd_predict(DevParams P, int n, float dt, const float4* __restric
 __global__ void kd_correct(int n, float dt, const float4* __restrict__ xt, const float4* __restrict__ vt,
                            const float4* __restrict__ an, float4* __restrict__ x, float4* __restrict__ v,
                            float4* __restrict__ a) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 p = xt[i], q = vt[i], n1 = an[i], o = a[i];
@@ -403,6 +410,7 @@ __global__ void kd_adj_a(DevParams P, int n, float B, float K, float alpha, cons
                          const uint32_t* __restrict__ list, const int* __restrict__ nn, int cap,
                          const float4* __restrict__ abar, float* __restrict__ rhobar,
                          double* __restrict__ red) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double bB = 0.0, bA = 0.0;
   if (i < n) {
@@ -451,6 +459,7 @@ __global__ void kd_adj_b(DevParams P, int n, float K, const float4* __restrict__
                          const uint32_t* __restrict__ list, const int* __restrict__ nn, int cap,
                          const float4* __restrict__ abar, const float* __restrict__ rhobar,
                          float4* __restrict__ xbar, float4* __restrict__ vbar) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 xi = x[i], vi = v[i], ai = abar[i];
@@ -536,6 +545,7 @@ __global__ void kd_adj_density(DevParams P, int n, const float4* __restrict__ x,
 __global__ void kd_adj_correct(int n, float dt, const float4* __restrict__ xbar,
                                const float4* __restrict__ vbar, const float4* __restrict__ abar,
                                float4* __restrict__ anbar, float4* __restrict__ akbar) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float c1 = dt * dt / 6.f, c2 = 0.5f * dt;
@@ -550,6 +560,7 @@ __global__ void kd_adj_correct(int n, float dt, const float4* __restrict__ xbar,
 __global__ void kd_adj_predict(int n, float dt, const uint8_t* __restrict__ mask,
                                float4* __restrict__ xbar, float4* __restrict__ vbar,
                                const float4* __restrict__ akbar, float4* __restrict__ abar) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 xt = xbar[i], vt = vbar[i];
@@ -613,10 +624,11 @@ static rts_status dsync(rts_diff* d) {
 // Cell list of positions x (caller order).
 static void build_cells(rts_diff* d, const float4* x) {
   const int n = d->n, g = grid_of(n);
-  kd_key<<<g, kT, 0, d->stream>>>(d->dp, n, x, d->key, d->count, d->ctl);
+  // the kernels of a step are chained with programmatic dependencies (see launch_pdl)
+  launch_pdl(d->stream, kd_key, g, kT, 0, d->dp, n, x, d->key, d->count, d->ctl);
   scan_block_counts(d->count, d->dp.nblocks, d->tile_sums, d->cstart, d->stream);
-  kd_place<<<g, kT, 0, d->stream>>>(n, d->key, d->cstart, d->count, d->perm_tmp);
-  kd_rank<<<g, kT, 0, d->stream>>>(n, d->key, d->cstart, d->count, d->perm_tmp, d->perm);
+  launch_pdl(d->stream, kd_place, g, kT, 0, n, d->key, d->cstart, d->count, d->perm_tmp);
+  launch_pdl(d->stream, kd_rank, g, kT, 0, n, d->key, d->cstart, d->count, d->perm_tmp, d->perm);
 }
 
 // Density, lists and acceleration at (x, v) into rho/prs/list/nn and acc.
@@ -625,10 +637,11 @@ static void evaluate(rts_diff* d, const float4* x, const float4* v, float* rho, 
   const int n = d->n, g = grid_of(n);
   const float K = (float)(2.0 * d->alpha * 0.5 * d->p.support_r * d->p.c_s);
   build_cells(d, x);
-  kd_density<<<g, kT, 0, d->stream>>>(d->dp, n, d->B, x, d->key, d->cstart, d->perm, d->xb,
-                                      d->bcstart, d->cap, rho, prs, list, nn, d->ctl);
+  launch_pdl(d->stream, kd_density, g, kT, 0, d->dp, n, d->B, x, d->key, d->cstart, d->perm, d->xb,
+             d->bcstart, d->cap, rho, prs, list, nn, d->ctl);
   if (acc)
-    kd_force<<<g, kT, 0, d->stream>>>(d->dp, n, K, x, v, rho, prs, d->xb, list, nn, d->cap, acc);
+    launch_pdl(d->stream, kd_force, g, kT, 0, d->dp, n, K, x, v, rho, prs, d->xb, list, nn, d->cap,
+               acc);
 }
 
 // One step from (x, v, a); with rec >= 0 the evaluation point is recorded in slot rec.
@@ -639,13 +652,13 @@ static void step(rts_diff* d, int rec) {
   float4* xt = rec >= 0 ? d->rec_xt + off : d->xt;
   float4* vt = rec >= 0 ? d->rec_vt + off : d->vt;
   uint8_t* mk = rec >= 0 ? d->rec_mask + off : nullptr;
-  kd_predict<<<g, kT, 0, d->stream>>>(d->dp, n, dt, d->x, d->v, d->a, xt, vt, mk);
+  launch_pdl(d->stream, kd_predict, g, kT, 0, d->dp, n, dt, d->x, d->v, d->a, xt, vt, mk);
   float* rho = rec >= 0 ? d->rec_rho + off : d->rho;
   float* prs = rec >= 0 ? d->rec_prs + off : d->prs;
   uint32_t* list = rec >= 0 ? d->rec_list + off * d->cap : d->list;
   int* nn = rec >= 0 ? d->rec_nn + off : d->nn;
   evaluate(d, xt, vt, rho, prs, list, nn, d->an);
-  kd_correct<<<g, kT, 0, d->stream>>>(n, dt, xt, vt, d->an, d->x, d->v, d->a);
+  launch_pdl(d->stream, kd_correct, g, kT, 0, n, dt, xt, vt, d->an, d->x, d->v, d->a);
 }
 
 // Adjoint of A(x, v) at a recorded evaluation for the output adjoint abar_out; adds into
@@ -655,10 +668,10 @@ static void eval_adjoint(rts_diff* d, const float4* x, const float4* v, const fl
                          const float4* abar_out) {
   const int n = d->n, g = grid_of(n);
   const float K = (float)(2.0 * d->alpha * 0.5 * d->p.support_r * d->p.c_s);
-  kd_adj_a<<<g, kT, 0, d->stream>>>(d->dp, n, d->B, K, d->alpha, x, v, rho, prs, d->xb, list, nn,
-                                    d->cap, abar_out, d->rhobar, d->red);
-  kd_adj_b<<<g, kT, 0, d->stream>>>(d->dp, n, K, x, v, rho, prs, d->xb, list, nn, d->cap, abar_out,
-                                    d->rhobar, d->xbar, d->vbar);
+  launch_pdl(d->stream, kd_adj_a, g, kT, 0, d->dp, n, d->B, K, d->alpha, x, v, rho, prs, d->xb,
+             list, nn, d->cap, abar_out, d->rhobar, d->red);
+  launch_pdl(d->stream, kd_adj_b, g, kT, 0, d->dp, n, K, x, v, rho, prs, d->xb, list, nn, d->cap,
+             abar_out, d->rhobar, d->xbar, d->vbar);
 }
 
 extern "C" {
@@ -862,11 +875,12 @@ rts_status rts_diff_backward(rts_diff* d, const float* gx, const float* grho, fl
     for (int k = k0; k < k1; ++k) step(d, k - k0);     // recompute with records
     for (int k = k1 - 1; k >= k0; --k) {
       const size_t off = (size_t)(k - k0) * n;
-      kd_adj_correct<<<g, kT, 0, d->stream>>>(n, dt, d->xbar, d->vbar, d->abar, d->anbar, d->akbar);
+      launch_pdl(d->stream, kd_adj_correct, g, kT, 0, n, dt, d->xbar, d->vbar, d->abar, d->anbar,
+                 d->akbar);
       eval_adjoint(d, d->rec_xt + off, d->rec_vt + off, d->rec_rho + off, d->rec_prs + off,
                    d->rec_list + off * d->cap, d->rec_nn + off, d->anbar);
-      kd_adj_predict<<<g, kT, 0, d->stream>>>(n, dt, d->rec_mask + off, d->xbar, d->vbar, d->akbar,
-                                              d->abar);
+      launch_pdl(d->stream, kd_adj_predict, g, kT, 0, n, dt, d->rec_mask + off, d->xbar, d->vbar,
+                 d->akbar, d->abar);
     }
   }
   // priming evaluation a_0 = A(x_0, v_0): only its velocity (and parameter) adjoints matter
