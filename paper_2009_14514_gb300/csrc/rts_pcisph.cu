@@ -254,11 +254,15 @@ __global__ void k_nonpressure(DevParams P, int n, PState s, const float4* __rest
 
 // ------------------------------------------------------- Algorithm 3 ---
 
-// Predict v* = v + dt (a_np + a_p), x* = x + dt v* (every particle); the iteration's
-// error reductions and R_e flags (nbk blocks) start from zero (the previous ones were
-// read before).
+// Predict v* = v + dt (a_np + a_p), x* = x + dt v*; the iteration's error reductions and
+// R_e flags (nbk blocks) start from zero (the previous ones were read before).  With
+// prev_mode < 0 every particle is predicted; otherwise only those whose pressure
+// acceleration the previous iteration (prev_mode, prev_row of minor step j) updated —
+// a turn or S_e — since x* of every other particle is unchanged (its w lane, p / rho^2,
+// is refreshed by the density pass that changes its pressure).
 __global__ void k_predict(DevParams P, int n, PState s, float4* __restrict__ xs, Ctl* ctl,
-                          uint8_t* __restrict__ in_re, size_t nbk) {
+                          uint8_t* __restrict__ in_re, size_t nbk, int j, int prev_mode,
+                          int prev_row, const uint8_t* __restrict__ in_se) {
   pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
@@ -267,6 +271,7 @@ __global__ void k_predict(DevParams P, int n, PState s, float4* __restrict__ xs,
   }
   for (size_t b = (size_t)i; b < nbk; b += (size_t)gridDim.x * blockDim.x) in_re[b] = 0;
   if (i >= n) return;
+  if (prev_mode >= 0 && !has_turn(P, prev_mode, prev_row, j, s.level[i]) && !in_se[i]) return;
   xs[i] = predict_one(P, s, i);
 }
 
@@ -507,6 +512,7 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
   for (int r = 0; r < c->p.n_levels && r < 4; ++r)
     if (c->p.sched[r][j] < min_sched) min_sched = c->p.sched[r][j];
   int min_iter = 3, done = 0, row = 1, mode = kModeSched, local_run = 0, stay_global = 0;
+  int prev_mode = -1, prev_row = 0;   // the last iteration's pressure participants (-1: all)
   rts_status status = RTS_OK;
   if (plain) {
     mode = kModeGlobal;
@@ -525,7 +531,8 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
       // iteration (cleared at the start of the minor step) and the regions
       if (!all_turn)
         launch_pdl(st, k_observed, fg, 256, 0, Q, c->filled, c->ctl, c->preg, c->in_re, c->ob);
-      launch_pdl(st, k_predict, g, 256, 0, Q, n, c->s, c->xs, c->ctl, c->in_re, nbk);
+      launch_pdl(st, k_predict, g, 256, 0, Q, n, c->s, c->xs, c->ctl, c->in_re, nbk, j, prev_mode,
+                 prev_row, c->in_se);
       // every particle takes part (all_turn): kPLanes lanes each; else one
       if (all_turn)
         launch_pdl(st, k_pdensity<kPLanes>, grid_lanes(n, kPLanes), 256, 0, Q, n, j, row, mode,
@@ -540,6 +547,8 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
       else
         launch_pdl(st, k_ppressure<1>, grid_lanes(n, 1), 256, 0, Q, n, j, row, mode, c->s,
                    c->in_se, c->xs, c->xb, c->nbl);
+      prev_mode = mode;
+      prev_row = row;
     }
     ++done;
     if (all_turn) ++c->it_global;
@@ -586,6 +595,7 @@ static rts_status run_correction(rts_ctx* c, const DevParams& Q, int j, bool pla
       if (++local_run > c->p.max_local_iters) {
         cudaMemcpyAsync(c->s.prs, c->pbak, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice,
                         c->stream);
+        prev_mode = -1;   // every pressure changed: every x* (its w lane) is predicted anew
         ++c->it_reverts;
         mode = kModeGlobal;
         stay_global = 1;
