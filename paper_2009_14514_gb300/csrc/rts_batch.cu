@@ -47,8 +47,10 @@ struct SceneIt {
   int n;                           // fluid particles of the scene
   unsigned long long err_sum_fx;   // sum of latest errors, fixed point 2^-32
   float err_max;
-  int pad;
+  int prev_mode;     // mode and row of the iteration that ran last (-1: none this step)
   double err_avg;
+  int prev_row;
+  int pad;
 };
 
 struct BatchCtl {
@@ -150,6 +152,7 @@ __global__ void k_b_begin(int ns, const uint32_t* __restrict__ fbase, int tile, 
     t.active = t.n > 0;
     t.row = 1;
     t.mode = kModeSched;
+    t.prev_mode = -1;
     t.min_iter = 3;
     S[s] = t;
     tiles = t.active ? (t.n + tile - 1) / tile : 0;
@@ -195,24 +198,28 @@ __device__ __forceinline__ void load_queue(const BatchCtl* B, int ns, int* qpre)
   __syncthreads();
 }
 
-// Pending pressure backup / revert of the scene (Section 5.5), then x* of every particle
-// of the iterating scenes; R_e of their blocks is cleared for this iteration.
+// Pending pressure backup / revert of the scene (Section 5.5), then x* of the particles
+// of the iterating scenes whose pressure acceleration the scene's previous iteration
+// updated (a turn or S_e; every particle in a scene's first iteration or after a revert:
+// every other x* is unchanged); R_e of their blocks is cleared for this iteration.
 __global__ void k_b_predict(DevParams P, const BatchView* __restrict__ Vp, BatchCtl* B,
                             const SceneIt* __restrict__ S, int tile) {
   extern __shared__ int qpre[];
   const int ns = P.n_scenes;
   load_queue(B, ns, qpre);
   const BatchView V = *Vp;
-  const int qtot = B->qtot;
+  const int qtot = B->qtot, j = B->j;
   const int lane = threadIdx.x & 31;
   int sc;
   uint32_t i0, i1;
   if (tile_of(qtot, qpre, ns, P.fbase, tile, &sc, &i0, &i1)) {
     const int flags = S[sc].flags;
+    const int pm = (flags & kFlagRevert) ? -1 : S[sc].prev_mode, pr = S[sc].prev_row;
     for (uint32_t i = i0 + lane; i < i1; i += 32) {
       if (flags & kFlagBackup) V.pbak[i] = V.s.prs[i];
       if (flags & kFlagRevert) V.s.prs[i] = V.pbak[i];
-      V.xs[i] = predict_one(P, V.s, (int)i);
+      if (pm < 0 || has_turn(P, pm, pr, j, V.s.level[i]) || V.in_se[i])
+        V.xs[i] = predict_one(P, V.s, (int)i);
       V.in_re[V.key[i]] = 0;
     }
   }
@@ -334,6 +341,8 @@ __global__ void k_b_control(int ns, int tile, float eta, float eta_T, int max_it
     SceneIt t = S[s];
     if (t.active) {
       t.flags = 0;
+      t.prev_mode = t.mode;   // the iteration that just ran (its pressure participants)
+      t.prev_row = t.row;
       const bool all_turn = t.mode == kModeGlobal || (t.mode == kModeSched && t.row <= B->min_sched);
       ++t.done;
       if (all_turn) ++t.it_global;
