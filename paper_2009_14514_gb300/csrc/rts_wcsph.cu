@@ -349,49 +349,59 @@ __device__ __forceinline__ bool next_group(uint32_t base, uint32_t end,
   return true;
 }
 
-// Stage the candidates of the block's runs that lie within the support radius of the
-// box [lo, hi] bounding the group's evaluated particles (every neighbour of a particle
-// in the box passes), compacted into shared memory with their indices (boundary: top
-// bit).  Only kept candidates with kept index in [skip, skip + kCap) are stored; the
-// return value is the total number kept.  tab holds the 18 runs (start, length, offset).
+// Stage the candidates [c0, c0 + kCap) of the block's runs (tab: the 18 runs' start,
+// length and offset in the concatenation), then keep those within the support radius of
+// the box [lo, hi] bounding the group's evaluated particles (every neighbour of a particle
+// in the box passes), compacted in place in shared memory with their indices (boundary:
+// top bit).  The copies are asynchronous, so all of a lane's loads are in flight at once;
+// the cull reads shared memory.  Returns the number kept.
 __device__ __forceinline__ uint32_t stage_culled(const DevParams& P, const uint32_t* tab,
                                                  uint32_t total, float3 lo, float3 hi,
-                                                 uint32_t skip, const float4* __restrict__ xf,
+                                                 uint32_t c0, const float4* __restrict__ xf,
                                                  const float4* __restrict__ xbnd, float4* sx,
                                                  uint32_t* sidx, int lane, Ctl* ctl) {
   const float cut2 = P.r2_hi * 1.0001f;
   const unsigned below = (1u << lane) - 1u;
-  uint32_t kept = 0;
+  const uint32_t cnr = total - c0 < (uint32_t)kCap ? total - c0 : (uint32_t)kCap;
   int r = 0;
-#pragma unroll 2
-  for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+  for (uint32_t k = lane; k < cnr; k += 32) {
+    const uint32_t kk = c0 + k;
+    while (kk >= tab[3 * r + 2] + tab[3 * r + 1]) ++r;
+    const uint32_t g = tab[3 * r] + (kk - tab[3 * r + 2]);
+    if (r < 18 && g < (uint32_t)(r < 9 ? P.n_fluid : P.n_bound)) {
+      cp_async16(&sx[k], r < 9 ? &xf[g] : &xbnd[g]);
+      sidx[k] = r < 9 ? g : (g | kBoundaryBit);
+    } else {
+      check_failed(ctl, kChkRun, g);
+      sx[k] = make_float4(3e38f, 3e38f, 3e38f, 0.f);   // culled below
+      sidx[k] = 0u;
+    }
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  uint32_t kept = 0;
+  for (uint32_t k0 = 0; k0 < cnr; k0 += 32) {
     const uint32_t k = k0 + lane;
     bool keep = false;
     float4 xj = make_float4(0.f, 0.f, 0.f, 0.f);
     uint32_t tag = 0;
-    if (k < total) {
-      while (k >= tab[3 * r + 2] + tab[3 * r + 1]) ++r;
-      const uint32_t g = tab[3 * r] + (k - tab[3 * r + 2]);
-      if (r < 18 && g < (uint32_t)(r < 9 ? P.n_fluid : P.n_bound)) {
-        xj = r < 9 ? xf[g] : xbnd[g];
-        tag = r < 9 ? g : (g | kBoundaryBit);
-        const float ex = fmaxf(fmaxf(lo.x - xj.x, xj.x - hi.x), 0.f);
-        const float ey = fmaxf(fmaxf(lo.y - xj.y, xj.y - hi.y), 0.f);
-        const float ez = fmaxf(fmaxf(lo.z - xj.z, xj.z - hi.z), 0.f);
-        keep = ex * ex + ey * ey + ez * ez <= cut2;
-      } else {
-        check_failed(ctl, kChkRun, g);
-      }
+    if (k < cnr) {
+      xj = sx[k];
+      tag = sidx[k];
+      const float ex = fmaxf(fmaxf(lo.x - xj.x, xj.x - hi.x), 0.f);
+      const float ey = fmaxf(fmaxf(lo.y - xj.y, xj.y - hi.y), 0.f);
+      const float ez = fmaxf(fmaxf(lo.z - xj.z, xj.z - hi.z), 0.f);
+      keep = ex * ex + ey * ey + ez * ez <= cut2;
     }
-    const unsigned m = __ballot_sync(kFull, keep);
-    const uint32_t pos = kept + (uint32_t)__popc(m & below);
-    if (keep && pos >= skip && pos < skip + (uint32_t)kCap) {
-      sx[pos - skip] = xj;
-      sidx[pos - skip] = tag;
+    const unsigned m = __ballot_sync(kFull, keep);   // every read of the round precedes
+    const uint32_t pos = kept + (uint32_t)__popc(m & below);   // the writes (pos <= k)
+    if (keep) {
+      sx[pos] = xj;
+      sidx[pos] = tag;
     }
     kept += (uint32_t)__popc(m);
+    __syncwarp();
   }
-  __syncwarp();
   return kept;
 }
 
@@ -462,12 +472,10 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
       uint32_t* list = nbl + (size_t)(gvalid ? i : 0) * P.nbl_cap;
       float wsum = 0.f;
       int nn = 0;
-      uint32_t kept_total = 1;
-      for (uint32_t skip = 0; skip < kept_total; skip += kCap) {
+      for (uint32_t c0 = 0; c0 < R.total; c0 += kCap) {
         __syncwarp();
-        kept_total = stage_culled(P, tab, R.total, lo, hi, skip, s.x, xb, sx, sidx, lane, ctl);
-        if (kept_total <= skip) break;
-        const uint32_t cn = kept_total - skip < (uint32_t)kCap ? kept_total - skip : (uint32_t)kCap;
+        const uint32_t cn = stage_culled(P, tab, R.total, lo, hi, c0, s.x, xb, sx, sidx, lane, ctl);
+        if (cn == 0) continue;
         const uint32_t iters = (cn + lpp - 1) / lpp;  // uniform over the warp
         for (uint32_t r0 = 0; r0 < iters; r0 += 32) {
           const uint32_t rn = iters - r0 < 32u ? iters - r0 : 32u;
