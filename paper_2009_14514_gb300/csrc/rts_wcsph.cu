@@ -350,14 +350,15 @@ __device__ __forceinline__ bool next_group(uint32_t base, uint32_t end,
 }
 
 // Stage the candidates [c0, c0 + kCap) of the block's runs (tab: the 18 runs' start,
-// length and offset in the concatenation), then keep those within the support radius of
-// the box [lo, hi] bounding the group's evaluated particles (every neighbour of a particle
-// in the box passes), compacted in place in shared memory with their indices (boundary:
-// top bit).  The copies are asynchronous, so all of a lane's loads are in flight at once;
-// the cull reads shared memory.  Returns the number kept.
+// length and offset in the concatenation) in shared memory with their indices (boundary:
+// top bit); with cull, keep only those within the support radius of the box [lo, hi]
+// bounding the group's evaluated particles (every neighbour of a particle in the box
+// passes), compacted in place.  The copies are asynchronous, so all of a lane's loads are
+// in flight at once; the cull reads shared memory.  Returns the number kept.
 __device__ __forceinline__ uint32_t stage_culled(const DevParams& P, const uint32_t* tab,
                                                  uint32_t total, float3 lo, float3 hi,
-                                                 uint32_t c0, const float4* __restrict__ xf,
+                                                 uint32_t c0, bool cull,
+                                                 const float4* __restrict__ xf,
                                                  const float4* __restrict__ xbnd, float4* sx,
                                                  uint32_t* sidx, int lane, Ctl* ctl) {
   const float cut2 = P.r2_hi * 1.0001f;
@@ -379,6 +380,7 @@ __device__ __forceinline__ uint32_t stage_culled(const DevParams& P, const uint3
   }
   cp_async_wait_all();
   __syncwarp();
+  if (!cull) return cnr;
   uint32_t kept = 0;
   for (uint32_t k0 = 0; k0 < cnr; k0 += 32) {
     const uint32_t k = k0 + lane;
@@ -457,24 +459,30 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
       const bool gvalid = i >= 0;
       const uint32_t lpp = (uint32_t)G.lpp, sub = (uint32_t)G.sub;
       const float4 xi = gvalid ? s.x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-      // box of the group's evaluated particles
+      // box of the group's evaluated particles; a group of one or two (16 or 32 lanes per
+      // particle) tests every staged candidate instead: culling would cost it more than it
+      // saves (the kept candidates, and so the neighbours, are the same either way)
+      const bool cull = lpp < 16;
       float3 lo = gvalid ? make_float3(xi.x, xi.y, xi.z) : make_float3(3e38f, 3e38f, 3e38f);
       float3 hi = gvalid ? make_float3(xi.x, xi.y, xi.z) : make_float3(-3e38f, -3e38f, -3e38f);
+      if (cull) {
 #pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, o));
-        lo.y = fminf(lo.y, __shfl_xor_sync(kFull, lo.y, o));
-        lo.z = fminf(lo.z, __shfl_xor_sync(kFull, lo.z, o));
-        hi.x = fmaxf(hi.x, __shfl_xor_sync(kFull, hi.x, o));
-        hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, o));
-        hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
+        for (int o = 16; o; o >>= 1) {
+          lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, o));
+          lo.y = fminf(lo.y, __shfl_xor_sync(kFull, lo.y, o));
+          lo.z = fminf(lo.z, __shfl_xor_sync(kFull, lo.z, o));
+          hi.x = fmaxf(hi.x, __shfl_xor_sync(kFull, hi.x, o));
+          hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, o));
+          hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
+        }
       }
       uint32_t* list = nbl + (size_t)(gvalid ? i : 0) * P.nbl_cap;
       float wsum = 0.f;
       int nn = 0;
       for (uint32_t c0 = 0; c0 < R.total; c0 += kCap) {
         __syncwarp();
-        const uint32_t cn = stage_culled(P, tab, R.total, lo, hi, c0, s.x, xb, sx, sidx, lane, ctl);
+        const uint32_t cn =
+            stage_culled(P, tab, R.total, lo, hi, c0, cull, s.x, xb, sx, sidx, lane, ctl);
         if (cn == 0) continue;
         const uint32_t iters = (cn + lpp - 1) / lpp;  // uniform over the warp
         for (uint32_t r0 = 0; r0 < iters; r0 += 32) {
