@@ -49,7 +49,7 @@ FLOPS_PAIR_FORCE = 24
 # evaluated particles).  A launch of the 2 s rollout is not captured under ncu's size
 # rule, so its traffic is this figure times the launch's evaluations.  Valid for the
 # density kernel as captured; re-measure when k_density changes.
-DENSITY_DRAM_BYTES_PER_EVAL = 123.4
+DENSITY_DRAM_BYTES_PER_EVAL = 124.7
 
 
 def parse(argv=None):
