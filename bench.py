@@ -611,7 +611,9 @@ def reference_arm(args):
         "value": value, "unit": "particle-substeps/s", "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{sc.name} (FP64 CPU oracle; step = one regional substep from t=0)"},
+        "config": {"workload": workload_name(sc, args), "parallelism": "single",
+                   "sample": "FP64 CPU oracle; one step = one regional substep, from t=0 "
+                             "after a priming evaluation and the warm-up substeps"},
         "cpu_baseline": {"value": value, "unit": "particle-substeps/s", "cores": os.cpu_count(),
                          "kind": "oracle",
                          "sample": f"{args.steps} regional substeps after priming, from t=0"},
