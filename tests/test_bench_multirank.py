@@ -59,3 +59,26 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
     assert bench.job_value(1, 10, 20, 1000.0) == 200.0
+
+
+def test_reference_line_keeps_the_contract():
+    # the reference arm (the oracle, timed on the host) prints the CUDA arm's line: same
+    # metric, unit, direction and workload, an e2e equal to its value with no copies
+    sys.path.insert(0, ROOT)
+    import bench
+    args = bench.parse(["--impl", "reference", "--small", "--steps", "1", "--warmup", "0"])
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.reference_arm(args)
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["higher_is_better"] is True
+    assert line["unit"] == "particle-substeps/s" and line["value"] > 0
+    assert line["config"]["workload"] == bench.workload_name(bench.workload(True), args)
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle"
