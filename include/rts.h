@@ -18,6 +18,10 @@
  *    Vectors are n x 3 floats (x, y, z), contiguous, in the caller's particle order.
  *  - All work is enqueued on the CUDA stream given to rts_init (borrowed; 0 = legacy
  *    default stream).  Calls that return data to the caller synchronise that stream.
+ *    Dependent kernels of a call are launched with programmatic dependencies: each is
+ *    scheduled while the work before it drains but waits for that work to complete
+ *    before its first memory access, so stream order holds for the caller's own work on
+ *    the same stream as for any other launch.
  *  - Every call returns an rts_status and never throws or aborts.  Argument errors are
  *    returned at once.  Errors found on the device (particle outside the grid, block
  *    over capacity, PCISPH non-convergence) are recorded in a device status word and
