@@ -154,6 +154,10 @@ def _declare(L):
     L.orc_pcisph_step.argtypes = [vp, vp]
     L.orc_pcisph_plain_step.argtypes = [vp, vp]
     L.orc_pcisph_global_step.argtypes = [vp, vp, i32, vp]
+    L.orc_tait.restype = dbl
+    L.orc_tait.argtypes = [vp, dbl]
+    L.orc_pcisph_pressure_accel.argtypes = [vp, i32, vp, vp, vp, i32, vp, vp]
+    L.orc_pcisph_nonpressure_accel.argtypes = [vp, i32, vp, vp, i32, vp, vp]
 
 
 class OracleError(RuntimeError):
@@ -237,6 +241,10 @@ def accel(P, x, v, rho, prs, xb, mask=None):
     _check(lib().orc_wcsph_accel(C.byref(P), n, _p(x), _p(v), _p(rho), _p(prs), xb.shape[0],
                                  _p(xb), _p(m), _p(a)), "orc_wcsph_accel")
     return a
+
+
+def tait(P, rho):
+    return lib().orc_tait(C.byref(P), float(rho))
 
 
 def level_thresholds(P):
@@ -330,6 +338,26 @@ class PState(C.Structure):
         ("err_max", C.c_double), ("err_avg", C.c_double),
         ("total_iters", C.c_int64), ("total_local", C.c_int64), ("total_restarts", C.c_int64),
     ]
+
+
+def pcisph_pressure_accel(P, x, prs, rho, xb):
+    x, xb = d3(x), d3(xb)
+    n = x.shape[0]
+    prs = np.ascontiguousarray(prs, np.float64)
+    rho = np.ascontiguousarray(rho, np.float64)
+    a = np.zeros((n, 3))
+    _check(lib().orc_pcisph_pressure_accel(C.byref(P), n, _p(x), _p(prs), _p(rho), xb.shape[0],
+                                           _p(xb), _p(a)), "orc_pcisph_pressure_accel")
+    return a
+
+
+def pcisph_nonpressure_accel(P, x, v, xb):
+    x, v, xb = d3(x), d3(v), d3(xb)
+    n = x.shape[0]
+    a = np.zeros((n, 3))
+    _check(lib().orc_pcisph_nonpressure_accel(C.byref(P), n, _p(x), _p(v), xb.shape[0], _p(xb),
+                                              _p(a)), "orc_pcisph_nonpressure_accel")
+    return a
 
 
 def pcisph_delta(P):

@@ -234,6 +234,8 @@ static double tait(const orc_params* P, double rho) {
   return (p > 0.0 || P->tait_no_clamp) ? p : 0.0;
 }
 
+double orc_tait(const orc_params* P, double rho) { return tait(P, rho); }
+
 /* rho_i = m W(0) + sum_{j in N(i)} m W(|x_i - x_j|), fluid and boundary j. */
 static int density_one(const orc_params* P, const ogrid* G, int32_t n, const double* x,
                        const double* xb, int32_t i, int32_t* buf, double* rho, int32_t* nbr) {

@@ -110,6 +110,10 @@ int orc_wcsph_density(const orc_params* P, int32_t n, const double* x, int32_t n
 int orc_wcsph_accel(const orc_params* P, int32_t n, const double* x, const double* v,
                     const double* rho, const double* p, int32_t nb, const double* xb,
                     const uint8_t* mask, double* a_out);
+/* The Tait equation of state exactly as the density pass applies it (test entry).
+ * [pinned: p(rho0) = 0, dp/drho(rho0) = c_s^2, d2p/drho2(rho0) = (gamma - 1) c_s^2 / rho0,
+ * the clamp] */
+double orc_tait(const orc_params* P, double rho);
 
 /* Level thresholds of Eq. 1-3 per level [pinned: closed-form table]. */
 void orc_level_thresholds(const orc_params* P, double* vthr2, double* athr2, int32_t* eq1);
@@ -197,6 +201,17 @@ int orc_pcisph_plain_step(const orc_params* P, orc_pstate* S);
  * max_iters and retries it with half the multiplier.  [pinned: mode 2 is plain PCISPH] */
 int orc_pcisph_global_step(const orc_params* P, orc_pstate* S, int32_t max_mult,
                            int32_t* mult_used);
+
+/* Test entries: the pressure acceleration (given p and predicted densities rho) and the
+ * non-pressure acceleration (viscosity + gravity, given v) exactly as Algorithms 2-3
+ * apply them, for every fluid particle, over one-ring neighbourhoods searched at x.
+ * [pinned: linear-pressure lattice closed form, half-space closed forms, rigid motion] */
+int orc_pcisph_pressure_accel(const orc_params* P, int32_t n, const double* x,
+                              const double* p, const double* rho, int32_t nb,
+                              const double* xb, double* a_out);
+int orc_pcisph_nonpressure_accel(const orc_params* P, int32_t n, const double* x,
+                                 const double* v, int32_t nb, const double* xb,
+                                 double* a_out);
 
 #ifdef __cplusplus
 }

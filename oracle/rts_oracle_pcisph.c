@@ -232,6 +232,73 @@ static void pressure_accel(const orc_params* P, orc_pstate* S, const double* xs,
   memcpy(S->ap + 3 * (int64_t)i, a, sizeof a);
 }
 
+/* Test entries: a state holding only what pressure_accel / nonpressure read, with the
+ * one-ring neighbourhoods of every particle searched at x. */
+static int accel_state(const orc_params* P, int32_t n, const double* x, const double* v,
+                       const double* p, const double* rho, int32_t nb, const double* xb,
+                       orc_pstate* S, ogrid* G) {
+  memset(S, 0, sizeof(*S));
+  S->n = n;
+  S->nb = nb;
+  S->x = (double*)x;
+  S->v = (double*)v;
+  S->p = (double*)p;
+  S->rho = (double*)rho;
+  S->xb = xb;
+  S->cap = NBR_CAP;
+  S->nbr_cnt = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+  S->nbr_idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1) * NBR_CAP);
+  S->ap = (double*)calloc(3 * (size_t)(n > 0 ? n : 1), sizeof(double));
+  S->anp = (double*)calloc(3 * (size_t)(n > 0 ? n : 1), sizeof(double));
+  int st = orci_grid_build(P, n, x, nb, xb, G);
+  for (int32_t i = 0; i < n && !st; ++i) {
+    int c[3];
+    st = orci_block_coords(P, x + 3 * (int64_t)i, c);
+    if (st) break;
+    int cnt = orci_nbr_list(P, G, n, x, xb, i, c, 1, P->r * P->r,
+                            S->nbr_idx + (int64_t)i * NBR_CAP, NBR_CAP);
+    if (cnt < 0) st = ORC_ERR_CAPACITY;
+    else S->nbr_cnt[i] = cnt;
+  }
+  return st;
+}
+
+static void accel_state_free(orc_pstate* S, ogrid* G) {
+  free(S->nbr_cnt);
+  free(S->nbr_idx);
+  free(S->ap);
+  free(S->anp);
+  orci_grid_free(G);
+}
+
+int orc_pcisph_pressure_accel(const orc_params* P, int32_t n, const double* x,
+                              const double* p, const double* rho, int32_t nb,
+                              const double* xb, double* a_out) {
+  orc_pstate S;
+  ogrid G;
+  int st = accel_state(P, n, x, NULL, p, rho, nb, xb, &S, &G);
+  if (!st) {
+    for (int32_t i = 0; i < n; ++i) pressure_accel(P, &S, x, i);
+    memcpy(a_out, S.ap, sizeof(double) * 3 * (size_t)n);
+  }
+  accel_state_free(&S, &G);
+  return st;
+}
+
+int orc_pcisph_nonpressure_accel(const orc_params* P, int32_t n, const double* x,
+                                 const double* v, int32_t nb, const double* xb,
+                                 double* a_out) {
+  orc_pstate S;
+  ogrid G;
+  int st = accel_state(P, n, x, v, NULL, NULL, nb, xb, &S, &G);
+  if (!st) {
+    for (int32_t i = 0; i < n; ++i) nonpressure(P, &S, i);
+    memcpy(a_out, S.anp, sizeof(double) * 3 * (size_t)n);
+  }
+  accel_state_free(&S, &G);
+  return st;
+}
+
 /* ------------------------------------------------------ major-step start --- */
 
 static int major_start(const orc_params* P, orc_pstate* S) {

@@ -59,6 +59,11 @@ def test_kernel_derivative_matches_finite_difference():
 # -------------------------------------------------------------- rest lattice ---
 
 REST_SUM = (1.0 + 1.5 + 3.0 * (2.0 - math.sqrt(2.0)) ** 3 + 2.0 * (2.0 - math.sqrt(3.0)) ** 3) / math.pi
+# The SPH pressure gradient of a linear field p = p0 + G.x on the cubic lattice at h = s:
+# -(G / rho0) times this coefficient (cubic symmetry reduces sum_j (G.d_j) d_j W'/|d_j| to
+# G/3 sum_j |d_j| W'(|d_j|) over the shells 6 x s, 12 x sqrt2 s, 8 x sqrt3 s).
+LATTICE_GRADIENT_COEF = 0.25 / math.pi * (6.0 + 12.0 * math.sqrt(2.0) * (2.0 - math.sqrt(2.0)) ** 2
+                                          + 8.0 * math.sqrt(3.0) * (2.0 - math.sqrt(3.0)) ** 2)
 # Hand enumeration of a cubic lattice at h = s: the point itself (W = 1/pi s^-3),
 # 6 at distance s (q = 1), 12 at sqrt(2) s, 8 at sqrt(3) s; the 6 at 2 s are ties
 # that the predicate excludes and where W vanishes.  REST_SUM = 0.99997247...
@@ -450,6 +455,18 @@ def test_hydrostatic_column_holds_still():
     speed = np.linalg.norm(S.v, axis=1)
     assert np.sqrt(np.mean(speed ** 2)) < 0.05 * math.sqrt(9.81 * H)
     assert np.linalg.norm(S.x.mean(axis=0) - c0) < 0.1 * s
-    rho, _, _ = O.density(P, S.x, S.xb)
+    rho, prs, _ = O.density(P, S.x, S.xb)
     assert rho.max() < 1000.0 * 1.05
     assert S.x[:, 2].min() > 0.0                 # nothing leaks through the floor
+    # Force balance in the bulk: the pressure gradient that holds the fluid up is rho0 g
+    # divided by the lattice coefficient of the discrete gradient (1.02004 at h = s, the
+    # closed form of test_pressure_force_of_a_linear_field_on_the_lattice).  Least-squares
+    # slope of p(z) away from the walls and the free surface, band 5 %.  A factor-2 slip
+    # in the pressure term, or a dropped p_j / rho_j^2, moves it by 50-100 %.
+    x = S.x
+    bulk = ((x[:, 2] > 0.1) & (x[:, 2] < 0.3) & (x[:, 0] > 0.05) & (x[:, 0] < 0.15)
+            & (x[:, 1] > 0.05) & (x[:, 1] < 0.15))
+    assert bulk.sum() > 100
+    slope = np.polyfit(x[bulk, 2], prs[bulk], 1)[0]
+    expect = -1000.0 * 9.81 / LATTICE_GRADIENT_COEF
+    assert abs(slope / expect - 1.0) < 0.05, (slope, expect)
