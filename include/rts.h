@@ -122,6 +122,17 @@ typedef struct rts_params {
      paper searches two rings for region 1 only).                                      */
   int32_t serna_off;
   int32_t r2_search_rings;
+  /* Re-sorting with the level-aligned clock (level_clock = 1, WCSPH, regional).  S =
+     stale_bins > 1: a substep whose index is not a multiple of S keeps the particle
+     order of the last sort instead of sorting again.  Classification and activity use
+     every particle's current block as always; the density pass searches, around each
+     group of evaluated particles, the sorted blocks widened by the largest distance a
+     particle has left its sorted block since that sort, so the neighbour sets are
+     exactly those of a fresh sort (only the order of summation differs).  With S = 2
+     the kept substeps are those at which only the finest level is due.  0 or 1: sort
+     every substep.  A particle that moves a quarter of a block or more between sorts is
+     reported as RTS_ERR_INTERNAL.                                                       */
+  int32_t stale_bins;
 } rts_params;
 
 /* Counters accumulated over one rts_advance call. */
@@ -284,12 +295,19 @@ rts_status rts_sync(rts_ctx* ctx);
  *   n <= RTS_NOALLOC_MAX_PARTICLES and grid_dim[0]*grid_dim[1]*grid_dim[2] <=
  *   RTS_NOALLOC_MAX_BLOCKS, else RTS_ERR_ARG (nothing is launched).
  * Only the block grid fields of params are read.  The call synchronises the stream and
- * returns RTS_ERR_DOMAIN if a particle lies outside the grid.  The first call on a
+ * returns RTS_ERR_DOMAIN if a particle lies outside the grid (key, perm and cstart are
+ * then unspecified), RTS_ERR_CAPACITY if a block holds more than
+ * RTS_NOALLOC_MAX_PER_BLOCK particles (the in-block order by index is found by a scan of
+ * the block, quadratic in its occupancy, so the cap bounds a call's work), and
+ * RTS_ERR_CUDA, with nothing launched, if a CUDA error from earlier work was pending on
+ * the calling thread (it is cleared and named in rts_last_error(NULL)).  A failed call
+ * leaves nothing behind: the next call starts from cleared counters.  The first call on a
  * device looks up the array's device address (once per device); make that first call
  * before any stream capture.  Every call shares the one array: calls whose work can
  * overlap on the GPU (other streams, other host threads) race and must be serialised. */
 #define RTS_NOALLOC_MAX_PARTICLES 262144
 #define RTS_NOALLOC_MAX_BLOCKS 524288
+#define RTS_NOALLOC_MAX_PER_BLOCK 4096
 rts_status rts_bin_noalloc(const rts_params* params, int32_t n, const float* x, int32_t* key,
                            int32_t* perm, int32_t* cstart, void* cuda_stream);
 

@@ -88,6 +88,7 @@ const char* rts::validate_params(const rts_params* p, int32_t n, int32_t nb, int
   if (p->tait_no_clamp != 0 && p->tait_no_clamp != 1) return "tait_no_clamp must be 0 or 1";
   if (p->serna_off != 0 && p->serna_off != 1) return "serna_off must be 0 or 1";
   if (p->r2_search_rings < 0 || p->r2_search_rings > 3) return "r2_search_rings must be in [0, 3]";
+  if (p->stale_bins < 0 || p->stale_bins > 64) return "stale_bins must be in [0, 64]";
   if (p->r1_search_rings < 0 || p->r1_search_rings > 3) return "r1_search_rings must be in [0, 3]";
   if (p->wall_project)
     for (int k = 0; k < 3; ++k)
@@ -168,6 +169,9 @@ void rts::make_dev_params(const rts_params& p, DevParams& d) {
   for (int L = 0; L < kMaxLevels; ++L) {
     d.vthr2f[L] = (float)d.vthr2[L];
     d.athr2f[L] = (float)d.athr2[L];
+    // FP32 residuals: vthr2 = vthr2f + vthr2lo within 2^-48 (finite thresholds)
+    d.vthr2lo[L] = std::isfinite(d.vthr2[L]) ? (float)(d.vthr2[L] - (double)d.vthr2f[L]) : 0.f;
+    d.athr2lo[L] = std::isfinite(d.athr2[L]) ? (float)(d.athr2[L] - (double)d.athr2f[L]) : 0.f;
   }
   d.force_level = p.force_level;
   d.dt_b = p.dt_b;
@@ -403,11 +407,14 @@ static rts_status sync_status(rts_ctx* c) {
 
 // Density and forces of the evaluated particles; their Serna correction is deferred to
 // the next key pass (which reads the same flags and accelerations) or to finalize().
-static void run_physics(rts_ctx* c, int64_t k1, int prime) {
-  { Phase ph(c, RTS_PHASE_DENSITY); launch_density(c); }
+static void run_physics(rts_ctx* c, int64_t k1, int prime, bool stale = false) {
+  { Phase ph(c, RTS_PHASE_DENSITY); launch_density(c, stale); }
   { Phase ph(c, RTS_PHASE_FORCE); launch_force(c); }
   c->pend_mode = prime ? kPendPrime : kPendCorrect;
   c->pend_k1 = k1;
+  // the force pass cleared the filled list; the next classification outside the
+  // stepping loop bins the (corrected) positions afresh
+  c->bins_valid = 0;
 }
 
 // Apply a deferred correction now (before the state is read or classified directly).
@@ -421,23 +428,39 @@ rts_status rts::finalize(rts_ctx* c) {
 
 static rts_status wcsph_evaluate(rts_ctx* c) {
   { Phase ph(c, RTS_PHASE_BIN); launch_bin(c, 0.0f); }
-  { Phase ph(c, RTS_PHASE_CLASSIFY); launch_classify(c); }
-  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActAll, 0, 0, c->k); }
+  { Phase ph(c, RTS_PHASE_CLASSIFY); launch_classify(c, false); }
+  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActAll, 0, 0, c->k, false); }
   run_physics(c, c->k, 1);
   c->primed = 1;
-  c->bins_valid = 1;
   CK(cudaGetLastError());
   return RTS_OK;
 }
 
+// Substeps that keep the last sort (stale_bins = S > 1, level-aligned clock): on a
+// substep k1 that is not a multiple of S the particles are not re-sorted.  With
+// S = level_mult[1] those are the substeps at which only the finest level is due, so
+// their evaluations are few (the finest level and pre-emptions); the sort that the
+// others need is done then.  Classification and activity use the current blocks; the
+// density pass widens its search by how far particles have left their sorted blocks.
+static bool keeps_sort(const rts_ctx* c, int64_t k1) {
+  const rts_params& p = c->p;
+  return c->light_ok && p.stale_bins > 1 && p.level_clock && p.mode == RTS_MODE_REGIONAL &&
+         p.force_level < 0 && (k1 % p.stale_bins) != 0;
+}
+
 static rts_status wcsph_regional(rts_ctx* c) {
   int64_t k1 = c->k + 1;
-  { Phase ph(c, RTS_PHASE_BIN); launch_bin(c, c->p.dt_b); }
-  { Phase ph(c, RTS_PHASE_CLASSIFY); launch_classify(c); }
-  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActRegional, 0, 0, k1); }
-  run_physics(c, k1, 0);
+  const bool keep = keeps_sort(c, k1);
+  {
+    Phase ph(c, RTS_PHASE_BIN);
+    if (keep) launch_bin_light(c, c->p.dt_b);
+    else launch_bin(c, c->p.dt_b);
+  }
+  { Phase ph(c, RTS_PHASE_CLASSIFY); launch_classify(c, keep); }
+  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActRegional, 0, 0, k1, keep); }
+  run_physics(c, k1, 0, keep);
   c->k = k1;
-  c->bins_valid = 1;
+  if (keep) ++c->kept_sorts;
   CK(cudaGetLastError());
   return RTS_OK;
 }
@@ -496,11 +519,10 @@ static rts_status wcsph_global(rts_ctx* c, int64_t max_mult) {
   if (m < 1) m = 1;
   int64_t k1 = c->k + m;
   { Phase ph(c, RTS_PHASE_BIN); launch_bin(c, (float)m * c->p.dt_b); }
-  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActGlobal, L, (int)m, k1); }
+  { Phase ph(c, RTS_PHASE_ACTIVITY); launch_activity(c, kActGlobal, L, (int)m, k1, false); }
   c->last_global_level = L;
   run_physics(c, k1, 0);
   c->k = k1;
-  c->bins_valid = 1;
   CK(cudaGetLastError());
   return RTS_OK;
 }
@@ -587,6 +609,7 @@ static rts_status init_ctx(const rts_params* params, int32_t n_fluid, const floa
     ALLOC(c->anew, f4);
     ALLOC(c->cflag, (size_t)n1);
     ALLOC(c->key, u1);
+    ALLOC(c->key_cur, u1);
     ALLOC(c->key_tmp, u1);
     ALLOC(c->slot, u1);
     ALLOC(c->tmp_uid, u1);
@@ -715,7 +738,7 @@ rts_status rts_destroy(rts_ctx* c) {
     cudaFree(s->x); cudaFree(s->v); cudaFree(s->a); cudaFree(s->rho); cudaFree(s->prs);
     cudaFree(s->uid); cudaFree(s->klast); cudaFree(s->valid); cudaFree(s->level); cudaFree(s->nbr);
   }
-  cudaFree(c->anew); cudaFree(c->cflag); cudaFree(c->key); cudaFree(c->key_tmp); cudaFree(c->slot);
+  cudaFree(c->anew); cudaFree(c->cflag); cudaFree(c->key); cudaFree(c->key_cur); cudaFree(c->key_tmp); cudaFree(c->slot);
   cudaFree(c->tmp_uid); cudaFree(c->tmp_src); cudaFree(c->io); cudaFree(c->io_i);
   cudaFree(c->count); cudaFree(c->cstart); cudaFree(c->bcstart); cudaFree(c->tile_sums);
   cudaFree(c->raw); cudaFree(c->blevel); cudaFree(c->act); cudaFree(c->plist); cudaFree(c->actflag); cudaFree(c->ctl); cudaFree(c->xb);
@@ -769,11 +792,11 @@ rts_status rts_classify_blocks(rts_ctx* c) {
   c->bins_valid = 1;
   {
     Phase ph(c, RTS_PHASE_CLASSIFY);
-    launch_classify(c);
+    launch_classify(c, false);
   }
   {
     Phase ph(c, RTS_PHASE_ACTIVITY);
-    launch_activity(c, -1, 0, 0, c->k);
+    launch_activity(c, -1, 0, 0, c->k, false);
   }
   CK(cudaGetLastError());
   return RTS_OK;

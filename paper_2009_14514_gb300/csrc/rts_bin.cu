@@ -18,26 +18,19 @@ constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 // Deferred correction of the last step's evaluated particles (pend), then predict
-// (dt != 0: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt) and the container correction,
-// then key and slot.  Slots: particles arrive mostly in block order, so each run of
-// equal keys in lane order takes one atomic on its block's counter.
-__global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4* __restrict__ v,
-                              float4* __restrict__ a, float dt, uint32_t* __restrict__ key,
-                              uint32_t* __restrict__ slot, uint32_t* __restrict__ count, Ctl* ctl,
-                              int pend, int pend_k1, const uint8_t* __restrict__ cflag,
-                              const float4* __restrict__ anew, int32_t* __restrict__ klast,
-                              const uint32_t* __restrict__ uid) {
-  pdl_wait();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) {   // the scan that follows appends the filled blocks, the activity pass
-    ctl->n_filled = 0;   // the active blocks and the evaluated particles
-    ctl->n_act = 0;
-    ctl->n_plist = 0;
-  }
-  if (i >= n) return;
+// (dt != 0: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt) and the container correction.
+// Returns the particle's position; with vout / aout it also returns its (predicted)
+// velocity and held acceleration.  Shared by both key passes, so they give the same bits.
+__device__ __forceinline__ float4 predict_one(const DevParams& P, int i, float4* __restrict__ x,
+                                              float4* __restrict__ v, float4* __restrict__ a,
+                                              float dt, int pend, int pend_k1,
+                                              const uint8_t* __restrict__ cflag,
+                                              const float4* __restrict__ anew,
+                                              int32_t* __restrict__ klast, float4* vout,
+                                              float4* aout) {
   float4 xi = x[i];
   const bool corr = pend != kPendNone && cflag[i];
-  if (corr || dt != 0.0f) {
+  if (corr || dt != 0.0f || vout) {
     float4 vi = v[i], ai = a[i];
     bool moved = false;
     if (corr) {
@@ -67,7 +60,35 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
       x[i] = xi;
       v[i] = vi;
     }
+    if (vout) {
+      *vout = vi;
+      *aout = ai;
+    }
   }
+  return xi;
+}
+
+// Slots: particles arrive mostly in block order, so each run of equal keys in lane order
+// takes one atomic on its block's counter.
+__global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4* __restrict__ v,
+                              float4* __restrict__ a, float dt, uint32_t* __restrict__ key,
+                              uint32_t* __restrict__ slot, uint32_t* __restrict__ count, Ctl* ctl,
+                              int pend, int pend_k1, const uint8_t* __restrict__ cflag,
+                              const float4* __restrict__ anew, int32_t* __restrict__ klast,
+                              const uint32_t* __restrict__ uid) {
+  pdl_wait();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {   // the scan that follows appends the filled blocks, the activity pass
+    ctl->n_filled = 0;   // the active blocks and the evaluated particles
+    ctl->n_act = 0;
+    ctl->n_plist = 0;
+    // a following pass that keeps this sort counts into a clean slot
+    ctl->n_filled_light[0] = ctl->n_filled_light[1] = 0;
+    ctl->disp_bits[0] = ctl->disp_bits[1] = 0u;
+  }
+  if (i >= n) return;
+  const float4 xi = predict_one(P, i, x, v, a, dt, pend, pend_k1, cflag, anew, klast, nullptr,
+                                nullptr);
   int bad = 0;
   // a batch: each particle is binned in its own scene's grid (the fluid pass has v, the
   // boundary pass not; the caller index gives the scene)
@@ -100,6 +121,131 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
   if (head) base = atomicAdd(&count[b], (uint32_t)(next - lane));
   base = __shfl_sync(act, base, myhead);
   slot[i] = base + (uint32_t)(lane - myhead);
+}
+
+// Key pass of a substep that keeps the previous sort (stale bins): the same correction,
+// prediction and container as k_predict_key, then the particle's current block
+// (key_cur; the arrays stay in the order of the last sort, whose blocks are skey), the
+// block maxima of |v|^2 and |a|^2 merged by current block into the stamped records, and
+// the largest distance, per axis, by which a particle has left the block it was sorted
+// into (rounded up), which widens the density pass's search.  The particle that finds
+// a block's record from an older pass lists the block as filled.  The maximum and the
+// filled count live in slot stamp & 1, which the previous binning pass cleared (a sort
+// clears both, a pass like this one the slot of the next stamp; the kernels in between
+// never read it).  One atomic per CTA for the
+// list (entries gathered in shared memory) and, only when it raises it, for the
+// maximum, so neither counter is a point of contention.
+constexpr int kLightThreads = 256;
+constexpr int kLightItems = 4;
+
+__global__ void __launch_bounds__(kLightThreads) k_predict_light(
+    DevParams P, int n, float4* __restrict__ x, float4* __restrict__ v, float4* __restrict__ a,
+    float dt, const uint32_t* __restrict__ skey, uint32_t* __restrict__ key_cur, Ctl* ctl,
+    int pend, int pend_k1, const uint8_t* __restrict__ cflag, const float4* __restrict__ anew,
+    int32_t* __restrict__ klast, const uint32_t* __restrict__ uid, uint32_t stamp,
+    unsigned long long* __restrict__ bmax_v, unsigned long long* __restrict__ bmax_a,
+    uint32_t* __restrict__ filled) {
+  pdl_wait();
+  __shared__ float sdisp[kLightThreads / 32];
+  __shared__ uint32_t sfill[kLightThreads * kLightItems];
+  __shared__ uint32_t scount, sbase;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {   // the activity pass appends the work lists
+    ctl->n_act = 0;
+    ctl->n_plist = 0;
+    ctl->disp_bits[(stamp + 1) & 1] = 0u;
+    ctl->n_filled_light[(stamp + 1) & 1] = 0;
+  }
+  if (threadIdx.x == 0) scount = 0u;
+  __syncthreads();
+  float disp = 0.f;
+  const int base0 = blockIdx.x * (kLightThreads * kLightItems) + w * (32 * kLightItems) + lane;
+#pragma unroll 1
+  for (int it = 0; it < kLightItems; ++it) {
+    const int i = base0 + 32 * it;
+    const bool valid = i < n;
+    uint32_t b = 0xffffffffu;
+    float v2 = 0.f, a2 = 0.f;
+    if (valid) {
+      float4 vi, ai;
+      const float4 xi = predict_one(P, i, x, v, a, dt, pend, pend_k1, cflag, anew, klast, &vi, &ai);
+      int bad = 0;
+      b = block_key(P, xi, &bad);
+      if (bad) {
+        if (atomicCAS(&ctl->bad_set, 0, 1) == 0) {
+          ctl->bad_uid = uid[i];
+          ctl->bad_x = xi.x;
+          ctl->bad_y = xi.y;
+          ctl->bad_z = xi.z;
+        }
+        set_status(ctl, RTS_ERR_DOMAIN);
+        b = 0;
+      }
+      key_cur[i] = b;
+      v2 = vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+      a2 = ai.x * ai.x + ai.y * ai.y + ai.z * ai.z;
+      const uint32_t sb = skey[i];
+      if (sb != b && sb < (uint32_t)P.nblocks) {   // outside its sorted block: how far
+        const int cx = (int)(sb % (uint32_t)P.nx), rr = (int)(sb / (uint32_t)P.nx);
+        const int cy = rr % P.ny, cz = rr / P.ny;
+        const float lx = P.ox + (float)cx * P.edge, ly = P.oy + (float)cy * P.edge,
+                    lz = P.oz + (float)cz * P.edge;
+        const float dx = fmaxf(fmaxf(lx - xi.x, xi.x - (lx + P.edge)), 0.f);
+        const float dy = fmaxf(fmaxf(ly - xi.y, xi.y - (ly + P.edge)), 0.f);
+        const float dz = fmaxf(fmaxf(lz - xi.z, xi.z - (lz + P.edge)), 0.f);
+        // rounded up by more than the FP32 errors of the box corners and differences
+        disp = fmaxf(disp, fmaxf(fmaxf(dx, dy), dz) * 1.0001f + 1e-5f * P.edge);
+      }
+    }
+    // segmented maxima over lanes of the same block (every lane reaches the shuffles)
+    unsigned long long mv = valid ? (((unsigned long long)stamp << 32) | __float_as_uint(v2)) : 0ull;
+    unsigned long long ma = valid ? (((unsigned long long)stamp << 32) | __float_as_uint(a2)) : 0ull;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long ov = __shfl_down_sync(0xffffffffu, mv, d);
+      const unsigned long long oa = __shfl_down_sync(0xffffffffu, ma, d);
+      const uint32_t ob = __shfl_down_sync(0xffffffffu, b, d);
+      if (lane + d < 32 && ob == b) {
+        mv = ov > mv ? ov : mv;
+        ma = oa > ma ? oa : ma;
+      }
+    }
+    const uint32_t prevb = __shfl_up_sync(0xffffffffu, b, 1);
+    bool claim = false;
+    if (valid && (lane == 0 || prevb != b)) {
+      const unsigned long long old = atomicMax(bmax_v + b, mv);
+      atomicMax(bmax_a + b, ma);
+      claim = (uint32_t)(old >> 32) != stamp;   // the block's first particle this pass
+    }
+    const unsigned cm = __ballot_sync(0xffffffffu, claim);
+    uint32_t off = 0;
+    if (lane == 0 && cm) off = atomicAdd(&scount, (uint32_t)__popc(cm));
+    off = __shfl_sync(0xffffffffu, off, 0);
+    if (claim) sfill[off + __popc(cm & ((1u << lane) - 1u))] = b;
+  }
+#pragma unroll
+  for (int d = 16; d; d >>= 1) disp = fmaxf(disp, __shfl_xor_sync(0xffffffffu, disp, d));
+  if (lane == 0) sdisp[w] = disp;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    sbase = scount ? (uint32_t)atomicAdd(&ctl->n_filled_light[stamp & 1], (int)scount) : 0u;
+  __syncthreads();
+  if (sbase + scount > (uint32_t)P.nblocks) {   // a block listed twice: a broken invariant
+    if (threadIdx.x == 0) check_failed(ctl, kChkGather, sbase + scount);
+  } else {
+    for (uint32_t k = threadIdx.x; k < scount; k += blockDim.x) filled[sbase + k] = sfill[k];
+  }
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int k = 0; k < kLightThreads / 32; ++k) m = fmaxf(m, sdisp[k]);
+    unsigned int* slot = &ctl->disp_bits[stamp & 1];
+    if (m > 0.f && __float_as_uint(m) > *(volatile unsigned int*)slot) {
+      atomicMax(slot, __float_as_uint(m));
+      // the density pass searches at most 5 blocks per axis around a group, enough
+      // while every particle stays within a quarter block of its sorted block
+      if (m >= 0.25f * P.edge) check_failed(ctl, kChkDisp, __float_as_uint(m));
+    }
+  }
 }
 
 // ---- exclusive scan of the per-block counts (reduce, scan tile sums, apply) ----
@@ -374,11 +520,28 @@ static void next_stamp(rts_ctx* c) {
     cudaMemsetAsync(c->raw, 0, sizeof(uint32_t) * nb, c->stream);
     cudaMemsetAsync(c->blevel, 0, sizeof(uint32_t) * nb, c->stream);
     cudaMemsetAsync(c->actflag, 0, sizeof(uint32_t) * nb, c->stream);
+    // two passes in a row now share a parity: clear the slots of the kept-sort passes
+    cudaMemsetAsync(c->ctl->n_filled_light, 0, sizeof(c->ctl->n_filled_light), c->stream);
+    cudaMemsetAsync(c->ctl->disp_bits, 0, sizeof(c->ctl->disp_bits), c->stream);
     c->stamp = 1;
   }
 }
 
+// A substep that keeps the previous sort (see k_predict_light).
+rts_status launch_bin_light(rts_ctx* c, float dt) {
+  int n = c->n;
+  const int g = (n + kLightThreads * kLightItems - 1) / (kLightThreads * kLightItems);
+  note_launch(c, 1);
+  next_stamp(c);
+  launch_pdl(c->stream, k_predict_light, g, kLightThreads, 0, c->dp, n, c->s.x, c->s.v, c->s.a,
+             dt, c->key, c->key_cur, c->ctl, c->pend_mode, (int)c->pend_k1, c->cflag, c->anew,
+             c->s.klast, c->s.uid, c->stamp, c->bmax_v, c->bmax_a, c->filled);
+  c->pend_mode = kPendNone;
+  return RTS_OK;
+}
+
 rts_status launch_bin(rts_ctx* c, float dt) {
+  c->light_ok = 1;   // the arrays are block-sorted by c->key from here on
   int n = c->n;
   if (n == 0) {
     next_stamp(c);

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -159,13 +160,20 @@ __global__ void k_place(int n, const int32_t* __restrict__ key, const int32_t* _
   S->tuid[q] = (uint32_t)i;
 }
 
-// Within each block, order by particle index: rank among the block's entries.
+// Within each block, order by particle index: rank among the block's entries.  The rank
+// scans the block, so a block's cost grows with the square of its occupancy; a block
+// holding more than RTS_NOALLOC_MAX_PER_BLOCK particles is not ranked and the call
+// returns RTS_ERR_CAPACITY (at most n x RTS_NOALLOC_MAX_PER_BLOCK comparisons a call).
 __global__ void k_rank(int n, const int32_t* __restrict__ cstart, int32_t* __restrict__ perm,
                        Scratch* S) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   uint32_t b = S->tkey[q];
   uint32_t beg = (uint32_t)cstart[b], end = (uint32_t)cstart[b + 1];
+  if (end - beg > (uint32_t)RTS_NOALLOC_MAX_PER_BLOCK) {
+    if (q == (int)beg) atomicCAS(&S->status, 0, (int)RTS_ERR_CAPACITY);
+    return;
+  }
   uint32_t u = S->tuid[q];
   uint32_t rank = 0;
   for (uint32_t r = beg; r < end; ++r) rank += S->tuid[r] < u ? 1u : 0u;
@@ -193,6 +201,17 @@ static rts_status reject(rts_status st, const char* msg) {
   return st;
 }
 
+// A launch error of this call (read and cleared), reported with the kernel's name.
+static bool launch_failed(const char* kernel) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return false;
+  char msg[256];
+  snprintf(msg, sizeof msg, "rts_bin_noalloc: launching %s failed: %s", kernel,
+           cudaGetErrorString(e));
+  rts_set_global_error(msg);
+  return true;
+}
+
 extern "C" rts_status rts_bin_noalloc(const rts_params* p, int32_t n, const float* x,
                                       int32_t* key, int32_t* perm, int32_t* cstart,
                                       void* cuda_stream) {
@@ -207,6 +226,16 @@ extern "C" rts_status rts_bin_noalloc(const rts_params* p, int32_t n, const floa
     return reject(RTS_ERR_ARG,
                   "rts_bin_noalloc: more than RTS_NOALLOC_MAX_PARTICLES (262144) particles or "
                   "RTS_NOALLOC_MAX_BLOCKS (524288) blocks; its fixed working memory holds no more");
+  {  // an error left by earlier work on this thread is not this call's: report it as such
+    cudaError_t pre = cudaGetLastError();
+    if (pre != cudaSuccess) {
+      char msg[256];
+      snprintf(msg, sizeof msg,
+               "rts_bin_noalloc: a CUDA error from earlier work was pending (now cleared): %s; "
+               "nothing was launched", cudaGetErrorString(pre));
+      return reject(RTS_ERR_CUDA, msg);
+    }
+  }
   Scratch* S = nullptr;
   rts_status st = scratch_on_current_device(&S);
   if (st != RTS_OK) return reject(st, "rts_bin_noalloc: cudaGetSymbolAddress of the working memory failed");
@@ -230,18 +259,36 @@ extern "C" rts_status rts_bin_noalloc(const rts_params* p, int32_t n, const floa
     return reject(RTS_ERR_CUDA, "rts_bin_noalloc: clearing the working memory failed");
   int g = (n + kThreads - 1) / kThreads;
   int ntiles = (G.nblocks + kTile - 1) / kTile;
-  if (n > 0) k_key<<<g, kThreads, 0, s>>>(G, n, x, key, S);
+  // each launch is checked before the next one is queued
+  if (n > 0) {
+    k_key<<<g, kThreads, 0, s>>>(G, n, x, key, S);
+    if (launch_failed("k_key")) return RTS_ERR_CUDA;
+  }
   k_tile_sums<<<ntiles, kThreads, 0, s>>>(G.nblocks, S);
+  if (launch_failed("k_tile_sums")) return RTS_ERR_CUDA;
   k_scan_tile_sums<<<1, 1024, 0, s>>>(ntiles, S);
+  if (launch_failed("k_scan_tile_sums")) return RTS_ERR_CUDA;
   k_starts<<<ntiles, kThreads, 0, s>>>(G.nblocks, cstart, S);
+  if (launch_failed("k_starts")) return RTS_ERR_CUDA;
   if (n > 0) {
     k_place<<<g, kThreads, 0, s>>>(n, key, cstart, S);
+    if (launch_failed("k_place")) return RTS_ERR_CUDA;
     k_rank<<<g, kThreads, 0, s>>>(n, cstart, perm, S);
+    if (launch_failed("k_rank")) return RTS_ERR_CUDA;
   }
   int status = 0;
-  if (cudaMemcpyAsync(&status, &S->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
-    return reject(RTS_ERR_CUDA, "rts_bin_noalloc: a CUDA call failed");
-  if (status) return reject((rts_status)status, "rts_bin_noalloc: a particle lies outside the grid");
+  cudaError_t e = cudaMemcpyAsync(&status, &S->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    char msg[256];
+    snprintf(msg, sizeof msg, "rts_bin_noalloc: reading the status failed: %s", cudaGetErrorString(e));
+    return reject(RTS_ERR_CUDA, msg);
+  }
+  if (status == RTS_ERR_DOMAIN)
+    return reject(RTS_ERR_DOMAIN, "rts_bin_noalloc: a particle lies outside the grid");
+  if (status == RTS_ERR_CAPACITY)
+    return reject(RTS_ERR_CAPACITY,
+                  "rts_bin_noalloc: a block holds more than RTS_NOALLOC_MAX_PER_BLOCK particles");
+  if (status) return reject(RTS_ERR_INTERNAL, "rts_bin_noalloc: unexpected device status");
   return RTS_OK;
 }

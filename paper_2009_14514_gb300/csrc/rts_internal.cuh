@@ -54,6 +54,7 @@ struct DevParams {
   int mult[kMaxLevels];
   double vthr2[kMaxLevels], athr2[kMaxLevels];
   float vthr2f[kMaxLevels], athr2f[kMaxLevels];   // the same thresholds rounded to FP32
+  float vthr2lo[kMaxLevels], athr2lo[kMaxLevels]; // and their FP32 residuals
   int eq1[kMaxLevels];
   int force_level;
   int level_clock;   // 0: validity = multiplier (Algorithm 1); 1: aligned to multiples
@@ -93,13 +94,19 @@ struct Ctl {
   int bad_set;                    // a particle left the grid: its caller index and position
   unsigned int bad_uid;
   float bad_x, bad_y, bad_z;
+  // Substeps that keep the previous sort: the largest per-axis distance (FP32 bits,
+  // rounded up) by which a particle has left the block it was sorted into, in slot
+  // stamp & 1 of the pass that computed it.
+  unsigned int disp_bits[2];
+  int n_filled_light[2];          // filled-list length of such a pass, slot stamp & 1
 };
 
 // Device-side consistency checks: an index read from memory is tested before it is
 // used; a failure records its code and value, sets RTS_ERR_INTERNAL and skips the access.
 enum CheckCode {
   kChkNone = 0, kChkNeighbour = 1, kChkRun = 2, kChkGather = 3, kChkScatter = 4,
-  kChkLevel = 5, kChkUid = 6, kChkActive = 7
+  kChkLevel = 5, kChkUid = 6, kChkActive = 7,
+  kChkDisp = 8   // a particle moved a quarter block or more since the last sort
 };
 
 // Particle state in block-sorted order.  x.w = p / rho^2 and v.w = rho of the last
@@ -308,7 +315,10 @@ struct rts_ctx {
   rts::PState s, s2;
   float4* anew;
   uint8_t* cflag;
-  uint32_t* key;      // block of each sorted particle
+  uint32_t* key;      // block of each sorted particle (at the last sort)
+  uint32_t* key_cur;  // current block of each particle on a substep that kept the sort
+  int light_ok;       // a sort has ordered the arrays by key, so a substep may keep it
+  int64_t kept_sorts; // substeps that kept the last sort
   uint32_t* key_tmp;
   uint32_t* slot;
   uint32_t* tmp_uid;
@@ -411,9 +421,12 @@ inline void launch_pdl(cudaStream_t st, void (*k)(KArgs...), int grid, int block
 // Host helpers implemented in rts_api.cu / kernels implemented in the .cu files.
 namespace rts {
 rts_status launch_bin(rts_ctx* c, float dt_predict);
+rts_status launch_bin_light(rts_ctx* c, float dt_predict);
 rts_status launch_bin_boundary(rts_ctx* c, const float4* xb_unsorted, int nb);
-rts_status launch_classify(rts_ctx* c);
-rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1);
+// stale: the substep kept the last sort (the light key pass's filled list, current blocks)
+rts_status launch_classify(rts_ctx* c, bool stale);
+rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1,
+                           bool stale);
 void scan_block_counts(uint32_t* count, int nb, uint32_t* tile_sums, uint32_t* cstart,
                        cudaStream_t stream);
 const char* validate_params(const rts_params* p, int32_t n, int32_t nb,
@@ -422,7 +435,7 @@ void make_dev_params(const rts_params& p, DevParams& d);
 // Level of the global adaptive comparator from the FP32 maxima (as from the FP64 maxima);
 // -1 when a maximum lies within 1e-5 of a threshold and the FP64 maxima must decide.
 int pick_level_from_f32_max(const DevParams& d, float v2, float a2);
-rts_status launch_density(rts_ctx* c);
+rts_status launch_density(rts_ctx* c, bool stale = false);
 rts_status launch_force(rts_ctx* c);
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime);
 rts_status finalize(rts_ctx* c);

@@ -472,8 +472,8 @@ static rts_status major_start(rts_ctx* c) {
     launch_bin(c, 0.0f);
   }
   PPhase ph(c, RTS_PHASE_CLASSIFY);
-  launch_classify(c);             // Eq. 2-3 from the block maxima (thresholds for PCISPH)
-  launch_activity(c, -1, 0, 0, 0);   // R_min (or the forced region)
+  launch_classify(c, false);      // Eq. 2-3 from the block maxima (thresholds for PCISPH)
+  launch_activity(c, -1, 0, 0, 0, false);   // R_min (or the forced region)
   int fg = filled_grid_size();
   const int gg = (int)((nbk + 255) / 256 < (size_t)(fg * 4) ? (nbk + 255) / 256 : (size_t)(fg * 4));
   note_launch(c, 1);

@@ -42,38 +42,93 @@ __device__ __forceinline__ int pick_level_f(const DevParams& P, float v2, float 
   return L;
 }
 
+// |u|^2 <= thr as the FP64 definition decides it, ((ux ux + uy uy) + uz uz) <= thr in
+// double precision from FP32 components, without FP64 in the common case (FP64 runs at a
+// small fraction of the FP32 rate here and a chain of dependent FP64 operations is slow):
+// the squares are split exactly (FMA TwoProduct), summed with TwoSum, and compared with
+// thr = th + tl (th = thr rounded to FP32, tl the FP32 residual, within 2^-48 thr).  The
+// FP32 form is known within about 2^-42 of the larger side and the FP64 one within
+// 2^-51 of the exact sum, so outside +-2^-38 thr both agree; inside, FP64 decides.
+__device__ __forceinline__ bool norm2_le(float x, float y, float z, float th, float tl, double thd) {
+  if (!isfinite(th)) return true;   // no bound (level 0 of Eq. 3)
+  const float px = __fmul_rn(x, x), py = __fmul_rn(y, y), pz = __fmul_rn(z, z);
+  if (!isfinite(px + py + pz)) return norm2d(x, y, z) <= thd;
+  const float ex = __fmaf_rn(x, x, -px), ey = __fmaf_rn(y, y, -py), ez = __fmaf_rn(z, z, -pz);
+  float s1, t1, s2, t2;
+  two_sum(px, py, s1, t1);
+  two_sum(s1, pz, s2, t2);
+  const float small = __fadd_rn(__fadd_rn(__fadd_rn(ex, ey), ez), __fadd_rn(t1, t2));
+  const float diff = __fadd_rn(__fsub_rn(s2, th), __fsub_rn(small, tl));
+  const float win = 3.637978807091713e-12f * th;   // 2^-38 thr
+  if (diff < -win) return true;
+  if (diff > win) return false;
+  return norm2d(x, y, z) <= thd;
+}
+
+// Level of a block from its particles when its FP32 maxima are undecided (Section 3.1,
+// exact): a level passes iff every particle passes its tests; the block takes the
+// largest passing level.  The block's particles are those whose current block (key_cur)
+// is b: after a sort, block b's range; on a substep that kept the last sort, also in b's
+// 26 sorted neighbours (particles move less than a quarter block between sorts).
+static __device__ __noinline__ int level_exact(const DevParams& P, uint32_t b, int stale,
+                                               const uint32_t* __restrict__ cstart,
+                                               const uint32_t* __restrict__ key_cur,
+                                               const float4* __restrict__ v,
+                                               const float4* __restrict__ a,
+                                               const float4* __restrict__ ap) {
+  unsigned pass = (1u << P.n_levels) - 1u;
+  const int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
+  const int R = stale ? 1 : 0;
+  for (int dz = -R; dz <= R; ++dz)
+    for (int dy = -R; dy <= R; ++dy)
+      for (int dx = -R; dx <= R; ++dx) {
+        const int cx = bx + dx, cy = by + dy, cz = bz + dz;
+        if (cx < 0 || cy < 0 || cz < 0 || cx >= P.nx || cy >= P.ny || cz >= P.nz) continue;
+        const uint32_t cb = ((uint32_t)cz * P.ny + cy) * P.nx + cx;
+        for (uint32_t i = cstart[cb]; i < cstart[cb + 1]; ++i) {
+          if (stale && key_cur[i] != b) continue;
+          const float4 vi = v[i];
+          float4 ai = a[i];
+          if (ap) {  // PCISPH: total acceleration
+            const float4 pa = ap[i];
+            ai.x += pa.x;
+            ai.y += pa.y;
+            ai.z += pa.z;
+          }
+          for (int l = 0; l < P.n_levels; ++l)
+            if (((pass >> l) & 1u) &&
+                !(norm2_le(vi.x, vi.y, vi.z, P.vthr2f[l], P.vthr2lo[l], P.vthr2[l]) &&
+                  norm2_le(ai.x, ai.y, ai.z, P.athr2f[l], P.athr2lo[l], P.athr2[l])))
+              pass &= ~(1u << l);
+        }
+      }
+  int L = 0;
+  for (int l = 0; l < P.n_levels; ++l)
+    if (P.eq1[l] && ((pass >> l) & 1u)) L = l;
+  return L;
+}
+
 // Raw level of every filled block (Section 3.1 steps 1-2) from the stamped FP32 block
-// maxima written by the sort; in the rare undecided case the exact FP64 maxima of the
-// block's particles decide, as the double-precision definition does.
-__global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled, const Ctl* ctl,
-                              const uint32_t* __restrict__ cstart, const float4* __restrict__ v,
-                              const float4* __restrict__ a, const float4* __restrict__ ap,
+// maxima; in the rare undecided case the exact decision of the double-precision
+// definition is taken from the block's particles (level_exact).  nfilled: the length of
+// the filled list (the sort's, or that of a key pass that kept the last sort).
+__global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled,
+                              const int* __restrict__ nfilled, const uint32_t* __restrict__ cstart,
+                              const uint32_t* __restrict__ key_cur, int stale,
+                              const float4* __restrict__ v, const float4* __restrict__ a,
+                              const float4* __restrict__ ap,
                               const unsigned long long* __restrict__ bmax_v,
                               const unsigned long long* __restrict__ bmax_a, uint32_t stamp,
                               uint32_t* __restrict__ raw) {
   pdl_wait();
-  const int nf = ctl->n_filled;
+  const int nf = *nfilled;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
     uint32_t b = filled[t];
     float vm = __uint_as_float((uint32_t)bmax_v[b]);
     float am = __uint_as_float((uint32_t)bmax_a[b]);
     bool undecided = false;
     int L = pick_level_f(P, vm, am, &undecided);
-    if (undecided) {
-      double vmd = 0.0, amd = 0.0;
-      for (uint32_t i = cstart[b]; i < cstart[b + 1]; ++i) {
-        float4 vi = v[i], ai = a[i];
-        if (ap) {  // PCISPH: total acceleration
-          float4 pa = ap[i];
-          ai.x += pa.x;
-          ai.y += pa.y;
-          ai.z += pa.z;
-        }
-        vmd = fmax(vmd, norm2d(vi.x, vi.y, vi.z));
-        amd = fmax(amd, norm2d(ai.x, ai.y, ai.z));
-      }
-      L = pick_level(P, vmd, amd);
-    }
+    if (undecided) L = level_exact(P, b, stale, cstart, key_cur, v, a, ap);
     raw[b] = (stamp << 8) | (uint32_t)L;
   }
 }
@@ -81,11 +136,11 @@ __global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled, 
 // R_min (Section 4.2: a filled block takes the smallest level among itself and its
 // filled 26 neighbours, one Jacobi pass), or the forced / global level.
 __global__ void k_block_rmin(DevParams P, int mode, int level_g,
-                             const uint32_t* __restrict__ filled, const Ctl* ctl,
+                             const uint32_t* __restrict__ filled, const int* __restrict__ nfilled,
                              const uint32_t* __restrict__ raw, uint32_t* __restrict__ blevel,
                              uint32_t stamp) {
   pdl_wait();
-  const int nf = ctl->n_filled;
+  const int nf = *nfilled;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
     const uint32_t b = filled[t];
     int L;
@@ -134,7 +189,8 @@ struct LevelPhase {
 
 __global__ void __launch_bounds__(kActThreads) k_particle_activity(
     DevParams P, int mode, int mult_g, LevelPhase kmod, int n, const uint32_t* __restrict__ key,
-    const uint32_t* __restrict__ blevel, uint32_t stamp, PState s, uint8_t* __restrict__ cflag,
+    const uint32_t* __restrict__ key_cur, const uint32_t* __restrict__ blevel, uint32_t stamp,
+    PState s, uint8_t* __restrict__ cflag,
     uint32_t* __restrict__ actflag, uint32_t* __restrict__ act, uint32_t* __restrict__ plist,
     Ctl* ctl) {
   pdl_wait();
@@ -154,18 +210,21 @@ __global__ void __launch_bounds__(kActThreads) k_particle_activity(
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned below = (1u << lane) - 1u;
   const int base0 = blockIdx.x * (kActThreads * kActItems) + w * (32 * kActItems) + lane;
-  // loads of every item first (the block record depends on the key)
-  uint32_t bk[kActItems], rec[kActItems];
+  // loads of every item first (the block record depends on the key).  bk: the block the
+  // particle is sorted in (its work-list entry); its level is that of its current block.
+  uint32_t bk[kActItems], rec[kActItems], ck[kActItems];
   int vold[kActItems], lold[kActItems];
 #pragma unroll
   for (int it = 0; it < kActItems; ++it) {
     const int i = base0 + 32 * it;
     bk[it] = i < n ? key[i] : 0xffffffffu;
+    ck[it] = i < n ? key_cur[i] : 0xffffffffu;
     vold[it] = (i < n && mode == kActRegional) ? s.valid[i] : 0;
     lold[it] = (i < n && mode == kActRegional) ? s.level[i] : 0;
   }
 #pragma unroll
-  for (int it = 0; it < kActItems; ++it) rec[it] = bk[it] != 0xffffffffu ? blevel[bk[it]] : 0u;
+  for (int it = 0; it < kActItems; ++it)
+    rec[it] = ck[it] < (uint32_t)P.nblocks ? blevel[ck[it]] : 0u;
 #pragma unroll
   for (int it = 0; it < kActItems; ++it) {
     const int i = base0 + 32 * it;
@@ -355,9 +414,10 @@ __device__ __forceinline__ bool next_group(uint32_t base, uint32_t end,
 // bounding the group's evaluated particles (every neighbour of a particle in the box
 // passes), compacted in place.  The copies are asynchronous, so all of a lane's loads are
 // in flight at once; the cull reads shared memory.  Returns the number kept.
+// nfr: fluid runs (runs 0 .. nfr - 1), nr: all runs; tab[3 nr ..] is a sentinel run.
 __device__ __forceinline__ uint32_t stage_culled(const DevParams& P, const uint32_t* tab,
-                                                 uint32_t total, float3 lo, float3 hi,
-                                                 uint32_t c0, bool cull,
+                                                 int nfr, int nr, uint32_t total, float3 lo,
+                                                 float3 hi, uint32_t c0, bool cull,
                                                  const float4* __restrict__ xf,
                                                  const float4* __restrict__ xbnd, float4* sx,
                                                  uint32_t* sidx, int lane, Ctl* ctl) {
@@ -369,9 +429,9 @@ __device__ __forceinline__ uint32_t stage_culled(const DevParams& P, const uint3
     const uint32_t kk = c0 + k;
     while (kk >= tab[3 * r + 2] + tab[3 * r + 1]) ++r;
     const uint32_t g = tab[3 * r] + (kk - tab[3 * r + 2]);
-    if (r < 18 && g < (uint32_t)(r < 9 ? P.n_fluid : P.n_bound)) {
-      cp_async16(&sx[k], r < 9 ? &xf[g] : &xbnd[g]);
-      sidx[k] = r < 9 ? g : (g | kBoundaryBit);
+    if (r < nr && g < (uint32_t)(r < nfr ? P.n_fluid : P.n_bound)) {
+      cp_async16(&sx[k], r < nfr ? &xf[g] : &xbnd[g]);
+      sidx[k] = r < nfr ? g : (g | kBoundaryBit);
     } else {
       check_failed(ctl, kChkRun, g);
       sx[k] = make_float4(3e38f, 3e38f, 3e38f, 0.f);   // culled below
@@ -407,29 +467,113 @@ __device__ __forceinline__ uint32_t stage_culled(const DevParams& P, const uint3
   return kept;
 }
 
+// Runs of the sorted blocks that can hold a neighbour of a group of evaluated particles
+// on a substep that kept the last sort (stale bins): every particle is at most dlt (per
+// axis) outside the block it was sorted into, so a neighbour of a particle in the box
+// [lo, hi] was sorted into a block meeting [lo - r - dlt, hi + r + dlt] (rounded outward
+// here).  Up to 5 x 5 rows of contiguous x runs, of the fluid (runs 0 .. nrow - 1) and
+// of the static boundary (nrow .. 2 nrow - 1), written to tab with the sentinel; the
+// candidates are a superset of the neighbours, which the exact predicate then selects,
+// so the neighbour sets are those of a fresh sort.  Returns the candidate count.
+constexpr int kStaleAxis = 5;
+constexpr int kTabFresh = 64, kTabStale = 160;   // u32 per warp: 3 x (runs + sentinel)
+
+__device__ __forceinline__ void axis_range(float l, float h, float ext, float o, float inv_e,
+                                           int n, int* c0, int* c1, bool* clipped) {
+  int a = (int)floorf((l - ext - o) * inv_e - 1e-3f);
+  int b = (int)floorf((h + ext - o) * inv_e + 1e-3f);
+  a = a < 0 ? 0 : a;
+  b = b > n - 1 ? n - 1 : b;
+  if (b - a + 1 > kStaleAxis) {
+    *clipped = true;
+    b = a + kStaleAxis - 1;
+  }
+  *c0 = a;
+  *c1 = b;
+}
+
+__device__ __forceinline__ uint32_t stale_runs(const DevParams& P, float3 lo, float3 hi, float dlt,
+                                               const uint32_t* __restrict__ cstart,
+                                               const uint32_t* __restrict__ bcstart, uint32_t* tab,
+                                               int lane, Ctl* ctl, int* nfr, int* nr) {
+  const float ext = P.r + dlt;
+  int x0, x1, y0, y1, z0, z1;
+  bool clipped = false;
+  axis_range(lo.x, hi.x, ext, P.ox, P.inv_edge, P.nx, &x0, &x1, &clipped);
+  axis_range(lo.y, hi.y, ext, P.oy, P.inv_edge, P.ny, &y0, &y1, &clipped);
+  axis_range(lo.z, hi.z, ext, P.oz, P.inv_edge, P.nz, &z0, &z1, &clipped);
+  if (clipped && lane == 0) check_failed(ctl, kChkDisp, 0u);
+  const int nyr = y1 - y0 + 1, nrow = nyr * (z1 - z0 + 1), nrun = 2 * nrow;
+  uint32_t st[2], ln[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = lane + 32 * h;
+    st[h] = 0;
+    ln[h] = 0;
+    if (e < nrun) {
+      const bool fl = e < nrow;
+      const int ri = fl ? e : e - nrow;
+      const int cy = y0 + ri % nyr, cz = z0 + ri / nyr;
+      const uint32_t rb = ((uint32_t)cz * P.ny + cy) * P.nx;
+      const uint32_t* cs = fl ? cstart : bcstart;
+      st[h] = __ldg(&cs[rb + x0]);
+      ln[h] = __ldg(&cs[rb + x1 + 1]) - st[h];
+    }
+  }
+  const uint32_t inc0 = warp_incl_sum(ln[0], lane);
+  const uint32_t tot0 = __shfl_sync(kFull, inc0, 31);
+  const uint32_t inc1 = warp_incl_sum(ln[1], lane) + tot0;
+  const uint32_t total = __shfl_sync(kFull, inc1, 31);
+  __syncwarp();   // the previous chunk's readers of tab are done
+  if (lane < nrun) {
+    tab[3 * lane] = st[0];
+    tab[3 * lane + 1] = ln[0];
+    tab[3 * lane + 2] = inc0 - ln[0];
+  }
+  if (lane + 32 < nrun) {
+    tab[3 * (lane + 32)] = st[1];
+    tab[3 * (lane + 32) + 1] = ln[1];
+    tab[3 * (lane + 32) + 2] = inc1 - ln[1];
+  }
+  if (lane == 0) {  // sentinel run: never exhausted
+    tab[3 * nrun] = 0;
+    tab[3 * nrun + 1] = 0xffffffffu;
+    tab[3 * nrun + 2] = 0;
+  }
+  __syncwarp();
+  *nfr = nrow;
+  *nr = nrun;
+  return total;
+}
+
 // Density pass (Algorithm 1, "find neighborhoods" and "update rho, p"): every evaluated
 // particle tests the candidates kept for its group with the exact predicate, sums m W
 // over its neighbours (itself included), applies the Tait equation and records its
 // neighbour list for the force pass.  Each round of up to 32 candidates per lane first
 // tests distances only (a bit per candidate inside the guard band), then evaluates the
-// kernel for those, then appends the neighbours in a fixed order.
+// kernel for those, then appends the neighbours in a fixed order.  kStale: a substep
+// that kept the last sort; the candidates of each group come from stale_runs instead of
+// the 27 blocks around the active block.
+template <bool kStale>
 __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const uint32_t* __restrict__ act,
                                                         Ctl* ctl, const uint32_t* __restrict__ cstart,
                                                         const uint32_t* __restrict__ bcstart, PState s,
                                                         const float4* __restrict__ xb,
                                                         const uint8_t* __restrict__ cflag,
-                                                        uint32_t* __restrict__ nbl) {
+                                                        uint32_t* __restrict__ nbl, uint32_t stamp) {
   pdl_wait();
+  constexpr int kTab = kStale ? kTabStale : kTabFresh;
   extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float4* sx = smem + wib * kCap;
   uint32_t* sidx = reinterpret_cast<uint32_t*>(smem + (kNbThreads / 32) * kCap) + wib * kCap;
   uint32_t* tab = reinterpret_cast<uint32_t*>(smem + (kNbThreads / 32) * kCap) +
-                  (kNbThreads / 32) * kCap + wib * 64;
+                  (kNbThreads / 32) * kCap + wib * kTab;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n_act = *(volatile int*)&ctl->n_act;
+  const float dlt = kStale ? __uint_as_float(*(volatile unsigned int*)&ctl->disp_bits[stamp & 1]) : 0.f;
   unsigned long long pairs = 0, tests = 0, kept_tests = 0;
   for (int t = warp; t < n_act; t += nwarps) {
     const uint32_t b = act[t];
@@ -437,21 +581,26 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
       if (lane == 0) check_failed(ctl, kChkActive, b);
       continue;
     }
-    const int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
     const uint32_t beg = cstart[b], end = cstart[b + 1];
-    const Runs R = block_runs(P, bx, by, bz, cstart, bcstart, lane);
-    __syncwarp();
-    if (lane < 18) {
-      tab[3 * lane] = R.start;
-      tab[3 * lane + 1] = R.len;
-      tab[3 * lane + 2] = R.off;
+    uint32_t total = 0;
+    int nfr = 9, nr = 18;
+    if (!kStale) {
+      const int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
+      const Runs R = block_runs(P, bx, by, bz, cstart, bcstart, lane);
+      total = R.total;
+      __syncwarp();
+      if (lane < 18) {
+        tab[3 * lane] = R.start;
+        tab[3 * lane + 1] = R.len;
+        tab[3 * lane + 2] = R.off;
+      }
+      if (lane == 18) {  // sentinel run: never exhausted
+        tab[3 * 18] = 0;
+        tab[3 * 18 + 1] = 0xffffffffu;
+        tab[3 * 18 + 2] = 0;
+      }
+      __syncwarp();
     }
-    if (lane == 18) {  // sentinel run: never exhausted
-      tab[3 * 18] = 0;
-      tab[3 * 18 + 1] = 0xffffffffu;
-      tab[3 * 18 + 2] = 0;
-    }
-    __syncwarp();
     for (uint32_t base = beg; base < end; base += 32) {
       Group G;
       if (!next_group(base, end, cflag, lane, G)) continue;
@@ -465,7 +614,7 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
       const bool cull = lpp < 16;
       float3 lo = gvalid ? make_float3(xi.x, xi.y, xi.z) : make_float3(3e38f, 3e38f, 3e38f);
       float3 hi = gvalid ? make_float3(xi.x, xi.y, xi.z) : make_float3(-3e38f, -3e38f, -3e38f);
-      if (cull) {
+      if (cull || kStale) {
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
           lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, o));
@@ -476,13 +625,14 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
           hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
         }
       }
+      if (kStale) total = stale_runs(P, lo, hi, dlt, cstart, bcstart, tab, lane, ctl, &nfr, &nr);
       uint32_t* list = nbl + (size_t)(gvalid ? i : 0) * P.nbl_cap;
       float wsum = 0.f;
       int nn = 0;
-      for (uint32_t c0 = 0; c0 < R.total; c0 += kCap) {
+      for (uint32_t c0 = 0; c0 < total; c0 += kCap) {
         __syncwarp();
-        const uint32_t cn =
-            stage_culled(P, tab, R.total, lo, hi, c0, cull, s.x, xb, sx, sidx, lane, ctl);
+        const uint32_t cn = stage_culled(P, tab, nfr, nr, total, lo, hi, c0, cull, s.x, xb, sx,
+                                         sidx, lane, ctl);
         if (cn == 0) continue;
         const uint32_t iters = (cn + lpp - 1) / lpp;  // uniform over the warp
         for (uint32_t r0 = 0; r0 < iters; r0 += 32) {
@@ -534,7 +684,7 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
         }
         if (gvalid && sub == 0) kept_tests += cn;
       }
-      if (gvalid && sub == 0) tests += R.total;
+      if (gvalid && sub == 0) tests += total;
       for (uint32_t o = lpp >> 1; o; o >>= 1) wsum += __shfl_down_sync(kFull, wsum, o, lpp);
       if (sub == 0 && gvalid) {
         if (nn > P.nbl_cap) set_status(ctl, RTS_ERR_CAPACITY);
@@ -580,24 +730,22 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
 // neighbour list of the density pass.  Pressure: -m (p_i/rho_i^2 + p_j/rho_j^2) grad W;
 // boundary neighbours: -m p_i/rho_i^2 grad W.  Artificial viscosity for approaching
 // pairs with nu = 2 alpha h c / (rho_i + rho_j) (boundary: rho_j = rho_i, v_j = 0).
-// Particle-parallel over the evaluated-particle list: kForceLanes lanes per particle,
-// so the cost per particle does not depend on how many particles of a block evaluate.
 constexpr int kForceLanes = 4;
 
-__global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_t* __restrict__ plist,
-                                                      Ctl* ctl, PState s, const float4* __restrict__ xb,
-                                                      const uint32_t* __restrict__ nbl,
-                                                      float4* __restrict__ anew) {
-  pdl_wait();
+// One round of the force pass: slot's particle (t = r * nslots + slot) walked by LANES
+// lanes.  Every lane of a warp runs the same rounds (the shuffles).
+template <int LANES>
+__device__ __forceinline__ void force_rounds(const DevParams& P, const uint32_t* __restrict__ plist,
+                                             Ctl* ctl, const PState& s,
+                                             const float4* __restrict__ xb,
+                                             const uint32_t* __restrict__ nbl,
+                                             float4* __restrict__ anew, int np) {
   const int lane = threadIdx.x & 31;
-  const int sub = lane & (kForceLanes - 1);
-  const int slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / kForceLanes) +
-                   lane / kForceLanes;
-  const int nslots = ((gridDim.x * blockDim.x) >> 5) * (32 / kForceLanes);
-  const int np = *(volatile int*)&ctl->n_plist;
+  const int sub = lane & (LANES - 1);
+  const int slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LANES) + lane / LANES;
+  const int nslots = ((gridDim.x * blockDim.x) >> 5) * (32 / LANES);
   const float4* __restrict__ xf = s.x;
   const float4* __restrict__ vf = s.v;
-  // every lane of a warp runs the same number of rounds (the shuffles below)
   const int rounds = (np + nslots - 1) / nslots;
   for (int r = 0; r < rounds; ++r) {
     const int t = r * nslots + slot;
@@ -615,7 +763,7 @@ __global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_
       int nn = s.nbr[i];
       if (nn > P.nbl_cap) nn = P.nbl_cap;
       const uint32_t* list = nbl + (size_t)i * P.nbl_cap;
-      for (int e = sub; e < nn; e += kForceLanes) {
+      for (int e = sub; e < nn; e += LANES) {
         const uint32_t jg = __ldg(&list[e]);
         float4 xj, vj;
         float pcj;
@@ -649,13 +797,29 @@ __global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_
       }
     }
 #pragma unroll
-    for (int o = kForceLanes >> 1; o; o >>= 1) {
-      ax += __shfl_down_sync(kFull, ax, o, kForceLanes);
-      ay += __shfl_down_sync(kFull, ay, o, kForceLanes);
-      az += __shfl_down_sync(kFull, az, o, kForceLanes);
+    for (int o = LANES >> 1; o; o >>= 1) {
+      ax += __shfl_down_sync(kFull, ax, o, LANES);
+      ay += __shfl_down_sync(kFull, ay, o, LANES);
+      az += __shfl_down_sync(kFull, az, o, LANES);
     }
     if (sub == 0 && i >= 0) anew[i] = make_float4(P.gx + ax, P.gy + ay, P.gz + az, 0.f);
   }
+}
+
+// Particle-parallel over the evaluated-particle list: kForceLanes lanes per particle, so
+// the cost per particle does not depend on how many particles of a block evaluate; when
+// the list is short enough for one warp per particle (substeps where few particles are
+// due), 32 lanes walk each list, which shortens the chain of dependent loads per
+// particle.  The lane count only changes the summation order.
+__global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_t* __restrict__ plist,
+                                                      Ctl* ctl, PState s, const float4* __restrict__ xb,
+                                                      const uint32_t* __restrict__ nbl,
+                                                      float4* __restrict__ anew) {
+  pdl_wait();
+  const int np = *(volatile int*)&ctl->n_plist;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  if (np <= warps) force_rounds<32>(P, plist, ctl, s, xb, nbl, anew, np);
+  else force_rounds<kForceLanes>(P, plist, ctl, s, xb, nbl, anew, np);
 }
 
 // Section 4.1 correction of the evaluated particles: x += (a_new - a_old) dt^2 / 6,
@@ -776,20 +940,24 @@ static int sm_count() {
   return g_sms;
 }
 
-static size_t density_smem() {
-  return (size_t)(kNbThreads / 32) * (kCap * (sizeof(float4) + sizeof(uint32_t)) + 64 * sizeof(uint32_t));
+static size_t density_smem(bool stale) {
+  return (size_t)(kNbThreads / 32) * (kCap * (sizeof(float4) + sizeof(uint32_t)) +
+                                      (stale ? kTabStale : kTabFresh) * sizeof(uint32_t));
 }
 
 // Persistent grids: every resident slot of every SM, per kernel (the force and
 // correction passes hold fewer registers and no shared memory, so more warps fit).
-static int g_grid_force = 0;
+static int g_grid_force = 0, g_grid_stale = 0;
 int neighbor_grid_size() {
-  int occ0 = 1, occ1 = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_density, kNbThreads, density_smem());
+  int occ0 = 1, occ1 = 1, occ2 = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_density<false>, kNbThreads, density_smem(false));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_force, kNbThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_density<true>, kNbThreads, density_smem(true));
   if (occ0 < 1) occ0 = 1;
   if (occ1 < 1) occ1 = 1;
+  if (occ2 < 1) occ2 = 1;
   g_grid_force = sm_count() * occ1;
+  g_grid_stale = sm_count() * occ2;
   return sm_count() * occ0;
 }
 static int force_grid(const rts_ctx* c) { return g_grid_force > 0 ? g_grid_force : c->grid_persistent; }
@@ -797,21 +965,26 @@ static int force_grid(const rts_ctx* c) { return g_grid_force > 0 ? g_grid_force
 static int filled_grid() { return sm_count() * 8; }
 int filled_grid_size() { return filled_grid(); }
 
-rts_status launch_classify(rts_ctx* c) {
+// The filled list and its length: the sort's, or (stale) the light key pass's.
+static const int* filled_count(rts_ctx* c, bool stale) {
+  return stale ? &c->ctl->n_filled_light[c->stamp & 1] : &c->ctl->n_filled;
+}
+
+rts_status launch_classify(rts_ctx* c, bool stale) {
   note_launch(c, 1);
-  launch_pdl(c->stream, k_block_level, filled_grid(), 256, 0, c->dp, c->filled, c->ctl, c->cstart,
-             c->s.v, c->s.a, c->s.ap, c->bmax_v, c->bmax_a, c->stamp, c->raw);
+  launch_pdl(c->stream, k_block_level, filled_grid(), 256, 0, c->dp, c->filled,
+             filled_count(c, stale), c->cstart, (const uint32_t*)(stale ? c->key_cur : c->key),
+             stale ? 1 : 0, c->s.v, c->s.a, c->s.ap, c->bmax_v, c->bmax_a, c->stamp, c->raw);
   return RTS_OK;
 }
 
 // mode < 0: smoothing only (public classification); otherwise smoothing + activity.
-
 // The work-list counters n_act and n_plist were reset by the key pass of this step's
 // binning (every step bins before its activity pass).
-rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1) {
+rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1, bool stale) {
   note_launch(c, 1);
   launch_pdl(c->stream, k_block_rmin, filled_grid(), 256, 0, c->dp, mode, level_g, c->filled,
-             c->ctl, c->raw, c->blevel, c->stamp);
+             filled_count(c, stale), c->raw, c->blevel, c->stamp);
   if (mode >= 0 && c->n > 0) {
     note_launch(c, 1);
     const int g = (c->n + kActThreads * kActItems - 1) / (kActThreads * kActItems);
@@ -819,16 +992,22 @@ rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_
     for (int L = 0; L < kMaxLevels; ++L)
       kmod.v[L] = L < c->p.n_levels ? (int)(k1 % (int64_t)c->p.level_mult[L]) : 0;
     launch_pdl(c->stream, k_particle_activity, g, kActThreads, 0, c->dp, mode, mult_g, kmod, c->n,
-               c->key, c->blevel, c->stamp, c->s, c->cflag, c->actflag, c->act, c->plist,
-               c->ctl);
+               c->key, (const uint32_t*)(stale ? c->key_cur : c->key), c->blevel, c->stamp,
+               c->s, c->cflag, c->actflag, c->act, c->plist, c->ctl);
   }
   return RTS_OK;
 }
 
-rts_status launch_density(rts_ctx* c) {
+rts_status launch_density(rts_ctx* c, bool stale) {
   note_launch(c, 1);
-  launch_pdl(c->stream, k_density, c->grid_persistent, kNbThreads, density_smem(), c->dp, c->act,
-             c->ctl, c->cstart, c->bcstart, c->s, c->xb, c->cflag, c->nbl);
+  if (stale)
+    launch_pdl(c->stream, k_density<true>, g_grid_stale > 0 ? g_grid_stale : c->grid_persistent,
+               kNbThreads, density_smem(true), c->dp, c->act, c->ctl, c->cstart, c->bcstart, c->s,
+               c->xb, c->cflag, c->nbl, c->stamp);
+  else
+    launch_pdl(c->stream, k_density<false>, c->grid_persistent, kNbThreads, density_smem(false),
+               c->dp, c->act, c->ctl, c->cstart, c->bcstart, c->s, c->xb, c->cflag, c->nbl,
+               c->stamp);
   return RTS_OK;
 }
 

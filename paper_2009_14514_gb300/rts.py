@@ -15,6 +15,8 @@ import numpy as np
 from . import build as _build
 
 RTS_OK = 0
+RTS_ERR_ARG, RTS_ERR_DOMAIN, RTS_ERR_CUDA, RTS_ERR_OOM, RTS_ERR_CAPACITY = 1, 2, 3, 4, 5
+RTS_ERR_NOT_CONVERGED, RTS_ERR_TIMEOUT, RTS_ERR_STATE, RTS_ERR_INTERNAL = 6, 7, 8, 9
 STATUS_NAMES = {
     0: "RTS_OK", 1: "RTS_ERR_ARG", 2: "RTS_ERR_DOMAIN", 3: "RTS_ERR_CUDA", 4: "RTS_ERR_OOM",
     5: "RTS_ERR_CAPACITY", 6: "RTS_ERR_NOT_CONVERGED", 7: "RTS_ERR_TIMEOUT", 8: "RTS_ERR_STATE", 9: "RTS_ERR_INTERNAL",
@@ -62,6 +64,7 @@ class RtsParams(C.Structure):
         ("tait_no_clamp", C.c_int32),
         ("serna_off", C.c_int32),
         ("r2_search_rings", C.c_int32),
+        ("stale_bins", C.c_int32),
     ]
 
 
@@ -148,6 +151,7 @@ def make_params(d: dict) -> RtsParams:
     P.tait_no_clamp = int(d.get("tait_no_clamp", 0))
     P.serna_off = int(d.get("serna_off", 0))
     P.r2_search_rings = int(d.get("r2_search_rings", 1))
+    P.stale_bins = int(d.get("stale_bins", 0))
     return P
 
 
@@ -426,11 +430,43 @@ def rts_last_error(ctx=None) -> str:
     return lib().rts_last_error(h).decode()
 
 
-def rts_bin_noalloc(params, x, key, perm, cstart, stream=None):
-    """Binning without device allocation (see rts.h): x, key, perm, cstart are CUDA
-    tensors the caller owns.  For callers that cannot allocate device memory."""
-    P = params if isinstance(params, RtsParams) else make_params(params)
+def _noalloc_args(P, x, key, perm, cstart):
+    """Validate rts_bin_noalloc's arguments before any pointer reaches the library: the
+    library writes n entries of key and perm and nblocks + 1 of cstart into device memory
+    of the current device, so a short or host buffer would be written out of bounds."""
+    import torch
+    named = (("x", x), ("key", key), ("perm", perm), ("cstart", cstart))
+    for name, t in named:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"rts_bin_noalloc: {name} must be a torch tensor, not {type(t).__name__}")
+        if not t.is_contiguous():
+            raise ValueError(f"rts_bin_noalloc: {name} must be contiguous")
+    if x.dtype != torch.float32 or x.dim() != 2 or x.shape[1] != 3:
+        raise ValueError(f"rts_bin_noalloc: x must be float32 of shape (n, 3), not "
+                         f"{x.dtype} {tuple(x.shape)}")
     n = int(x.shape[0])
+    nblocks = int(P.grid_dim[0]) * int(P.grid_dim[1]) * int(P.grid_dim[2])
+    for name, t, need in (("key", key, n), ("perm", perm, n), ("cstart", cstart, nblocks + 1)):
+        if t.dtype != torch.int32:
+            raise ValueError(f"rts_bin_noalloc: {name} must be int32, not {t.dtype}")
+        if t.numel() < need:
+            raise ValueError(f"rts_bin_noalloc: {name} holds {t.numel()} entries, needs {need}")
+    for name, t in named:
+        if not t.is_cuda:
+            raise ValueError(f"rts_bin_noalloc: {name} must be in device memory (a CUDA tensor)")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"rts_bin_noalloc: {name} is on cuda:{t.device.index}, the current "
+                             f"device is cuda:{torch.cuda.current_device()}")
+    return n
+
+
+def rts_bin_noalloc(params, x, key, perm, cstart, stream=None):
+    """Binning without device allocation (see rts.h): x (n x 3 float32), key and perm
+    (int32, >= n entries) and cstart (int32, >= nblocks + 1 entries) are contiguous CUDA
+    tensors on the current device that the caller owns.  For callers that cannot
+    allocate device memory.  Raises ValueError on any other argument, before the call."""
+    P = params if isinstance(params, RtsParams) else make_params(params)
+    n = _noalloc_args(P, x, key, perm, cstart)
     st = lib().rts_bin_noalloc(C.byref(P), n, _ptr(x), _ptr(key), _ptr(perm), _ptr(cstart),
                                _stream(stream))
     return _check(st, "rts_bin_noalloc")

@@ -63,6 +63,43 @@ def test_block_levels_are_bit_exact(force_level):
         assert len(set(oraw[oraw >= 0].tolist())) == 4        # every level occurs
 
 
+def test_block_levels_at_the_thresholds_are_decided_exactly():
+    # one particle per block set to the two FP32 neighbours of an FP64 threshold (|v|^2
+    # just below and just above it, the FP32 maximum undecided), the rest at rest: the
+    # level must be the double-precision definition's, as the oracle's
+    sc = scenes.wcsph_dam_break_8k()
+    d = params(sc)
+    P = O.make_params(d)
+    vthr2, athr2, _ = O.level_thresholds(P)
+    key, perm, cstart = O.bin_particles(P, sc.x)
+    v = np.zeros((sc.n, 3), np.float32)
+    a = np.zeros((sc.n, 3), np.float32)
+    a[:, 2] = -9.81
+    filled = np.nonzero(np.diff(cstart))[0]
+    rng = np.random.default_rng(8)
+    for j, b in enumerate(filled):
+        i = perm[cstart[b]]
+        L = 1 + j % (len(vthr2) - 1)
+        if j % 3 == 2:                          # an acceleration threshold instead
+            t = np.sqrt(athr2[L])
+            c = np.float32(t)
+            c = np.nextafter(c, np.float32(np.inf)) if j % 2 else np.nextafter(c, np.float32(0))
+            a[i] = [0.0, 0.0, c]
+        else:
+            t = np.sqrt(vthr2[L])
+            c = np.float32(t)
+            c = np.nextafter(c, np.float32(np.inf)) if j % 2 else c
+            v[i] = [c, 0.0, 0.0]
+        assert rng is not None
+    ctx = gpu_ctx(sc, d)
+    rts.rts_set_state(ctx, sc.x, v, a=a)
+    rts.rts_classify_blocks(ctx)
+    raw, _ = rts.rts_get_blocks(ctx)
+    oraw, _ = O.classify_wcsph(P, sc.x, v, a)
+    assert np.array_equal(raw, oraw)
+    assert len(set(oraw[filled].tolist())) >= 3
+
+
 # ----------------------------------------------------------------- evaluation ---
 
 def _near_tie(i, xp, xb, r, rel=1e-5):
