@@ -32,7 +32,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-N_SM = 152
+METRIC = "particle-substeps/s (regional time stepping, WCSPH, 1M particles)"
+# The headline arm: regional time stepping with the level-aligned activity clock (every
+# particle of level L computes at the multiples of its multiplier; the substeps between
+# keep the last sort, stale_bins of the scene).  Algorithm 1's clock as stated is the
+# second RTS arm.
+HEADLINE = {"level_clock": 1}
 FP32_LANES_PER_SM = 128
 # Algorithmic FP32 flops of the neighbour passes (FMA = 2), per unit of work that the
 # standard cell-list formulation does, independent of this implementation's culling:
@@ -44,12 +49,14 @@ FP32_LANES_PER_SM = 128
 FLOPS_TEST = 8
 FLOPS_PAIR_DENSITY = 8
 FLOPS_PAIR_FORCE = 24
-# DRAM bytes (read + write) per evaluated particle of the density pass, from one ncu
-# capture of k_density on the profiling case (--profile-case; 23.49 MB for 191,176
-# evaluated particles).  A launch of the 2 s rollout is not captured under ncu's size
-# rule, so its traffic is this figure times the launch's evaluations.  Valid for the
-# density kernel as captured; re-measure when k_density changes.
-DENSITY_DRAM_BYTES_PER_EVAL = 124.7
+# DRAM bytes (read + write) per evaluated particle of the density pass, from one-pass ncu
+# counters of every density launch in a window of the rollout itself (16 substeps from the
+# warm state at t = 1 s, --profile-warm); the traffic per launch of the benchmark is this
+# figure times the launch's evaluations.  Re-measure when k_density changes.
+DENSITY_DRAM_BYTES_PER_EVAL = 192.6
+DENSITY_TRAFFIC_SOURCE = ("ncu dram__bytes of every k_density launch of 16 substeps from the "
+                          "warm state at t = 1 s (profiles/k_density_warm_window_1m.md), "
+                          "192.6 B per evaluation, times this run's evaluations per launch")
 
 
 def parse(argv=None):
@@ -62,8 +69,8 @@ def parse(argv=None):
     ap.add_argument("--constant-steps", type=int, default=5,
                     help="steps of the constant-dt_b arm (compared with the same steps of RTS)")
     ap.add_argument("--no-global", action="store_true", help="skip the global comparators")
-    ap.add_argument("--no-aligned", action="store_true",
-                    help="skip the level-aligned activity clock variant")
+    ap.add_argument("--no-alg1", action="store_true",
+                    help="skip the arm with Algorithm 1's activity clock as stated")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="8k-particle dam break (quick check)")
@@ -88,6 +95,12 @@ def parse(argv=None):
                     help="--profile-case: also print the evaluations of every density launch")
     ap.add_argument("--profile-pcisph", action="store_true",
                     help="short run for ncu: the 1M pool drop from t=0 for --steps minor steps")
+    ap.add_argument("--profile-warm-save", metavar="PATH",
+                    help="simulate the headline arm to t = 1 s and save its state to PATH "
+                         "(.npz) for --profile-warm")
+    ap.add_argument("--profile-warm", metavar="PATH",
+                    help="short run for ncu: load the state saved by --profile-warm-save and "
+                         "advance the headline arm --steps substeps in one call")
     ap.add_argument("--profile-case", action="store_true",
                     help="short run for ncu: 1M jittered lattice with a seeded dynamic state, "
                          "primed, then --steps windows (few launches, nothing printed but a line)")
@@ -118,6 +131,31 @@ def profile_case(args):
         per[1] -= sc.n
         out["evals_per_density_launch"] = per
     print(json.dumps(out), flush=True)
+
+
+def profile_warm(args):
+    """A bounded case at the rollout's own regime: the headline arm's state at t = 1 s
+    (saved by a plain run), advanced --steps substeps in one rts_advance call, so the
+    density launches are those of the rollout (light and heavy substeps mixed)."""
+    import numpy as np
+    from paper_2009_14514_gb300 import rts, scenes
+    sc = scenes.wcsph_dam_break_1m()
+    d = dict(sc.params)
+    d.update(HEADLINE)
+    ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
+    if args.profile_warm_save:
+        rts.rts_advance(ctx, 1.0)
+        g = rts.rts_get_state(ctx)
+        np.savez(args.profile_warm_save, k=ctx.substep_index, **g)
+        print(json.dumps({"saved": args.profile_warm_save, "k": int(ctx.substep_index)}))
+        return
+    w = np.load(args.profile_warm)
+    rts.rts_set_state(ctx, w["x"], w["v"], a=w["a"], rho=w["rho"], p=w["p"], level=w["level"],
+                      validity=w["validity"], klast=w["klast"], k=int(w["k"]), primed=True)
+    st = rts.rts_advance(ctx, (int(w["k"]) + args.steps) * d["dt_b"])
+    print(json.dumps({"profile_warm": sc.name, "k0": int(w["k"]), "substeps": st["substeps"],
+                      "particle_evals": st["particle_evals"],
+                      "pair_interactions": st["pair_interactions"]}), flush=True)
 
 
 def profile_batch(args):
@@ -177,8 +215,9 @@ def workload(small):
 def workload_name(sc, args):
     sim = args.steps * args.step_sim
     return (f"{sc.name}: {sc.n} fluid + {sc.nb} boundary particles, WCSPH regional time "
-            f"stepping, levels dt_b*{sc.params['level_mult']}, dt_b={sc.params['dt_b']}, "
-            f"{sim:g} s simulated from t=0 in steps of {args.step_sim:g} s")
+            f"stepping (level-aligned clock), levels dt_b*{sc.params['level_mult']}, "
+            f"dt_b={sc.params['dt_b']}, {sim:g} s simulated from t=0 in steps of "
+            f"{args.step_sim:g} s")
 
 
 class ClockSampler:
@@ -535,12 +574,13 @@ def run_diff(args, torch):
             "grad_B": float(B.grad), "grad_alpha": float(a.grad)}
 
 
-def run_e2e(sc, args, torch, rts):
+def run_e2e(sc, args, torch, rts, over):
     """End to end through the C ABI: every step uploads the full state from pinned host
     memory (rts_set_state), advances one step, and copies the full state back to pinned
     host memory (rts_get_state); host clock around the three calls."""
     n = sc.n
     d = dict(sc.params)
+    d.update(over)
     ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
     dtb = d["dt_b"]
     per = int(round(args.step_sim / dtb))
@@ -569,11 +609,19 @@ def run_e2e(sc, args, torch, rts):
             "ms_per_step": 1e3 * total / len(times), "steps": len(times)}
 
 
-def cpu_oracle(sc, budget_s=12.0, max_substeps=64):
-    """The FP64 oracle as it stands, on the host cores: priming evaluation (untimed), then
-    regional substeps from t = 0 until the time budget is spent."""
+def oracle_cores():
     import oracle as O
-    P = O.make_params(sc.params)
+    return O.num_threads()
+
+
+def cpu_oracle(sc, over, budget_s=15.0, max_substeps=200):
+    """The FP64 oracle as it stands, on the host cores, on the headline workload: priming
+    evaluation (untimed), then regional substeps from t = 0 (the first 0.01 s = 200
+    substeps of the 1M dam break) until the window or the time budget ends."""
+    import oracle as O
+    d = dict(sc.params)
+    d.update(over)
+    P = O.make_params(d)
     S = O.WCSPH(P, sc.x, sc.v, sc.xb)
     S.evaluate()
     t0 = time.perf_counter()
@@ -584,10 +632,88 @@ def cpu_oracle(sc, budget_s=12.0, max_substeps=64):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": sc.n * k / dt, "unit": "particle-substeps/s", "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": f"{sc.name}: priming evaluation then {k} regional substeps from t=0 "
-                      f"({dt:.1f} s, FP64, OpenMP over all host cores)"}
+    return {"value": sc.n * k / dt, "unit": "particle-substeps/s", "cores": oracle_cores(),
+            "kind": "oracle", "substeps": k, "seconds": dt,
+            "sample": f"{sc.name}: priming evaluation, then the first {k} regional substeps "
+                      f"({k * d['dt_b']:g} s simulated) from t=0, level-aligned clock "
+                      f"(FP64, OpenMP over {oracle_cores()} host threads)"}
+
+
+def gpu_window(torch, rts, d, sc, t_end):
+    """Device seconds of advancing a fresh context from t = 0 to t_end (one rts_advance)."""
+    stream = torch.cuda.current_stream()
+    ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = rts.rts_advance(ctx, t_end)
+    e1.record(stream)
+    e1.synchronize()
+    ctx.close()
+    return e0.elapsed_time(e1) / 1e3, st
+
+
+def config_baselines(torch, rts, head_over):
+    """The oracle beside the GPU on the paper-scale windows: the 8k dam break with global
+    adaptive steps run in full (200 steps), the first 0.01 s (200 substeps) of the 1M WCSPH
+    dam break, and the first 8 PCISPH major steps (32 minor steps) of the 1M pool drop.
+    Values: fluid particles x base substeps per second (the same on both sides)."""
+    import oracle as O
+    from paper_2009_14514_gb300 import scenes
+    out = {"cores": oracle_cores()}
+    # config 1: 8k, global adaptive, 200 steps, both in full
+    sc = scenes.wcsph_dam_break_8k()
+    d = dict(sc.params, mode=1)
+    P = O.make_params(d)
+    S = O.WCSPH(P, sc.x, sc.v, sc.xb)
+    t0 = time.perf_counter()
+    subs = sum(S.global_step() for _ in range(200))
+    osec = time.perf_counter() - t0
+    ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    gsubs = 0
+    for _ in range(200):
+        k0 = ctx.substep_index
+        rts.rts_wcsph_substep(ctx)
+        gsubs += ctx.substep_index - k0
+    e1.record(stream)
+    e1.synchronize()
+    gsec = e0.elapsed_time(e1) / 1e3
+    ctx.close()
+    out["config1_8k_global_200_steps"] = {
+        "oracle": {"seconds": osec, "substeps": int(subs), "value": sc.n * subs / osec},
+        "gpu": {"seconds": gsec, "substeps": int(gsubs), "value": sc.n * gsubs / gsec,
+                "note": "one rts_wcsph_substep call (one global step) at a time"}}
+    # config 2 window: the first 0.01 s of the 1M dam break, headline arm's parameters
+    sc = scenes.wcsph_dam_break_1m()
+    d = dict(sc.params)
+    d.update(head_over)
+    orc = cpu_oracle(sc, head_over, budget_s=40.0, max_substeps=200)
+    gsec, st = gpu_window(torch, rts, d, sc, 200 * d["dt_b"])
+    out["config2_1m_wcsph_first_0.01s"] = {
+        "oracle": {"seconds": orc["seconds"], "substeps": orc["substeps"], "value": orc["value"]},
+        "gpu": {"seconds": gsec, "substeps": int(st["substeps"]),
+                "value": sc.n * st["substeps"] / gsec}}
+    # config 3 window: 8 major steps of the 1M pool drop (RTS-PCISPH)
+    sc = scenes.pcisph_drop_1m()
+    P = O.make_params(sc.params)
+    S = O.PCISPH(P, sc.x, sc.v, sc.xb)
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(32):
+        S.step()
+        its += S.S.iters
+    osec = time.perf_counter() - t0
+    gsec, st = gpu_window(torch, rts, sc.params, sc, 32 * sc.params["dt_b"])
+    out["config3_1m_pcisph_8_major_steps"] = {
+        "oracle": {"seconds": osec, "substeps": 32, "iterations": its, "value": sc.n * 32 / osec},
+        "gpu": {"seconds": gsec, "substeps": int(st["substeps"]),
+                "iterations": int(st["pcisph_iterations"]), "value": sc.n * st["substeps"] / gsec}}
+    return out
 
 
 def reference_arm(args):
@@ -596,7 +722,9 @@ def reference_arm(args):
         return
     sc = workload(args.small)
     import oracle as O
-    P = O.make_params(sc.params)
+    d = dict(sc.params)
+    d.update(HEADLINE)
+    P = O.make_params(d)
     S = O.WCSPH(P, sc.x, sc.v, sc.xb)
     S.evaluate()
     for _ in range(args.warmup):
@@ -606,17 +734,18 @@ def reference_arm(args):
         S.substep()
     dt = time.perf_counter() - t0
     value = sc.n * args.steps / dt
+    sample = (f"{sc.name}: priming evaluation and {args.warmup} warm-up substeps, then "
+              f"{args.steps} timed regional substeps (level-aligned clock) from t=0")
     line = {
-        "impl": "reference", "metric": "particle-substeps/s (regional time stepping, WCSPH, 1M particles)",
+        "impl": "reference", "metric": METRIC,
         "value": value, "unit": "particle-substeps/s", "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(sc, args), "parallelism": "single",
-                   "sample": "FP64 CPU oracle; one step = one regional substep, from t=0 "
-                             "after a priming evaluation and the warm-up substeps"},
-        "cpu_baseline": {"value": value, "unit": "particle-substeps/s", "cores": os.cpu_count(),
-                         "kind": "oracle",
-                         "sample": f"{args.steps} regional substeps after priming, from t=0"},
+        "config": {"workload": f"{sc.name}: {sc.n} fluid + {sc.nb} boundary particles, WCSPH "
+                               f"regional time stepping, FP64 CPU oracle; one step = one "
+                               f"regional substep from t=0", "parallelism": "single"},
+        "cpu_baseline": {"value": value, "unit": "particle-substeps/s", "cores": oracle_cores(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "particle-substeps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -630,6 +759,9 @@ def main():
         return
     if args.profile_batch:
         profile_batch(args)
+        return
+    if args.profile_warm or args.profile_warm_save:
+        profile_warm(args)
         return
     if args.profile_pcisph:
         profile_pcisph(args)
@@ -655,20 +787,20 @@ def main():
         torch.cuda.synchronize()
 
     if args.warmup > 0:   # untimed: the first steps of the same rollout on a throwaway context
-        run_rollout(sc, {}, args.warmup, args, torch, rts, flush=flush, name="warmup")
+        run_rollout(sc, HEADLINE, args.warmup, args, torch, rts, flush=flush, name="warmup")
     barrier()
     with ClockSampler(local) as clk:
-        ours = run_rollout(sc, {}, args.steps, args, torch, rts, profile=True, flush=flush,
+        ours = run_rollout(sc, HEADLINE, args.steps, args, torch, rts, profile=True, flush=flush,
                            name="timed_rts")
     barrier()
     total_ms = max_over_ranks(sum(ours["ms"]), world, "cuda")
     subs = ours["tot"]["substeps"]
     value = job_value(world, sc.n, subs, total_ms)
 
-    aligned = None
-    if not args.no_aligned:
-        aligned = run_rollout(sc, {"level_clock": 1}, args.steps, args, torch, rts, profile=True,
-                              flush=flush, name="timed_rts_aligned")
+    alg1 = None
+    if not args.no_alg1:
+        alg1 = run_rollout(sc, {"level_clock": 0}, args.steps, args, torch, rts, profile=True,
+                           flush=flush, name="timed_rts_alg1")
     glob = const = None
     if not args.no_global:
         glob = run_rollout(sc, {"mode": 1}, args.steps, args, torch, rts, profile=True,
@@ -676,7 +808,7 @@ def main():
         nc = min(args.constant_steps, args.steps)
         const = run_rollout(sc, {"mode": 2}, nc, args, torch, rts, flush=flush,
                             name="timed_constant")
-    e2e = None if args.no_e2e else run_e2e(sc, args, torch, rts)
+    e2e = None if args.no_e2e else run_e2e(sc, args, torch, rts, HEADLINE)
     pcisph = None if (args.no_pcisph or args.small) else run_pcisph(args, torch, rts, flush)
     dres = None if (args.no_diff or args.small) else run_diff(args, torch)
     bres = None if (args.no_batch or args.small) else run_batch(args, torch, rts, flush)
@@ -686,7 +818,8 @@ def main():
     prof = ours["prof"]
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     tests, pairs = ours["tot"]["candidate_tests"], ours["tot"]["pair_interactions"]
     kern = max(("density", "force"), key=lambda k: phase_total_ms(prof, k))
     launches = max(1, prof["launches"][kern])
@@ -701,14 +834,16 @@ def main():
                 "frac": achieved / peak_tflops,
                 "traffic": (DENSITY_DRAM_BYTES_PER_EVAL * ours["tot"]["particle_evals"] / launches
                             if kern == "density" else None),
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived)",
+                "traffic_source": DENSITY_TRAFFIC_SOURCE if kern == "density" else None,
+                "peak_source": f"{n_sm} SMs (queried) x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                               f"(derived; the measured peaks cover HBM copy and bf16 GEMM only)",
                 "avg_launch_us": dur_s * 1e6, "launches": launches,
                 "launches_timed": int(prof["timed"][kern])}
 
     sim = ours["sim_s"]
     tot = ours["tot"]
     line = {
-        "metric": "particle-substeps/s (regional time stepping, WCSPH, 1M particles)",
+        "metric": METRIC,
         "value": value, "unit": "particle-substeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -729,19 +864,20 @@ def main():
         "ms_per_step_list": [round(m, 1) for m in ours["ms"]],
         "roofline": roofline, "clocks": clk.summary(),
     }
-    if aligned is not None:
-        line["rts_level_aligned"] = arm_summary(sc, aligned, dtb)
-        line["rts_level_aligned"]["evals_per_active_block"] = (
-            aligned["tot"]["particle_evals"] / max(1, aligned["tot"]["active_blocks"]))
+    if alg1 is not None:
+        line["rts_algorithm1_clock"] = arm_summary(sc, alg1, dtb)
+        line["rts_algorithm1_clock"]["evals_per_active_block"] = (
+            alg1["tot"]["particle_evals"] / max(1, alg1["tot"]["active_blocks"]))
     if glob is not None:
         line["global_adaptive"] = arm_summary(sc, glob, dtb)
         line["rts_vs_global"] = (value / world) / line["global_adaptive"]["value"]
-        if aligned is not None:
-            line["rts_level_aligned_vs_global"] = (line["rts_level_aligned"]["value"] /
-                                                   line["global_adaptive"]["value"])
+        if alg1 is not None:
+            line["rts_algorithm1_clock_vs_global"] = (line["rts_algorithm1_clock"]["value"] /
+                                                      line["global_adaptive"]["value"])
         line["global_constant_dt_b"] = arm_summary(sc, const, dtb)
         nc = len(const["ms"])
         line["rts_vs_constant_same_span"] = sum(const["ms"]) / sum(ours["ms"][:nc])
+        line["equal_error"] = equal_error(line, ours, alg1, glob, value / world)
     if e2e is not None:
         line["e2e"] = e2e
     if pcisph is not None:
@@ -753,11 +889,37 @@ def main():
     if ares is not None:
         line["ablations"] = ares
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_oracle(sc)
+        line["cpu_baseline"] = cpu_oracle(sc, HEADLINE)
+        if not args.small:
+            line["cpu_baseline_configs"] = config_baselines(torch, rts, HEADLINE)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def equal_error(line, ours, alg1, glob, rts_value):
+    """The acceptance at an equal density-error bound: an RTS arm passes when its
+    time-averaged bulk density error is at most 1.1 x the global adaptive arm's.  The ratio
+    at equal error is that of the fastest passing arm (None when none passes)."""
+    eg = glob["err_time_avg"].get("bulk_mean", 0.0)
+    arms = {"rts_level_aligned (headline)": (ours, rts_value)}
+    if alg1 is not None:
+        arms["rts_algorithm1_clock"] = (alg1, line["rts_algorithm1_clock"]["value"])
+    gv = line["global_adaptive"]["value"]
+    out = {"acceptance": "RTS bulk density error (time average) <= 1.1 x global adaptive's",
+           "global_bulk_error": eg, "arms": {}}
+    best = None
+    for name, (r, v) in arms.items():
+        e = r["err_time_avg"].get("bulk_mean", 0.0)
+        ok = e <= 1.1 * eg
+        out["arms"][name] = {"bulk_error": e, "error_vs_global": e / eg if eg > 0 else None,
+                             "pass": bool(ok), "speed_vs_global": v / gv}
+        if ok and (best is None or v / gv > best[1]):
+            best = (name, v / gv)
+    out["rts_vs_global_at_equal_error"] = best[1] if best else None
+    out["arm_at_equal_error"] = best[0] if best else None
+    return out
 
 
 if __name__ == "__main__":

@@ -154,6 +154,8 @@ def _declare(L):
     L.orc_pcisph_step.argtypes = [vp, vp]
     L.orc_pcisph_plain_step.argtypes = [vp, vp]
     L.orc_pcisph_global_step.argtypes = [vp, vp, i32, vp]
+    L.orc_num_threads.restype = C.c_int
+    L.orc_num_threads.argtypes = []
     L.orc_tait.restype = dbl
     L.orc_tait.argtypes = [vp, dbl]
     L.orc_pcisph_pressure_accel.argtypes = [vp, i32, vp, vp, vp, i32, vp, vp]
@@ -241,6 +243,11 @@ def accel(P, x, v, rho, prs, xb, mask=None):
     _check(lib().orc_wcsph_accel(C.byref(P), n, _p(x), _p(v), _p(rho), _p(prs), xb.shape[0],
                                  _p(xb), _p(m), _p(a)), "orc_wcsph_accel")
     return a
+
+
+def num_threads():
+    """OpenMP threads of the oracle's parallel loops (omp_get_max_threads)."""
+    return int(lib().orc_num_threads())
 
 
 def tait(P, rho):

@@ -85,6 +85,9 @@ typedef struct orc_wstate {
   int32_t primed;
 } orc_wstate;
 
+/* Threads used by the OpenMP loops (omp_get_max_threads). */
+int orc_num_threads(void);
+
 /* Cubic-spline (M4) kernel in 3D, support 2h [pinned: normalisation, symmetry]. */
 double orc_kernel_W(double d, double h);
 double orc_kernel_dW(double d, double h);   /* dW/dd */

@@ -18,51 +18,57 @@ constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 // Deferred correction of the last step's evaluated particles (pend), then predict
-// (dt != 0: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt) and the container correction.
-// Returns the particle's position; with vout / aout it also returns its (predicted)
-// velocity and held acceleration.  Shared by both key passes, so they give the same bits.
+// (dt != 0: x~ = x + v dt + a dt^2 / 2, v~ = v + a dt) and the container correction, on
+// loaded values: corr = the particle's correction is pending, an its new acceleration,
+// dtc the length of its completed true step.  Returns whether x and v changed.  Both key
+// passes use it, so they give the same bits.
+__device__ __forceinline__ bool predict_math(const DevParams& P, float4& xi, float4& vi,
+                                             float4& ai, bool corr, int pend, float4 an,
+                                             float dtc, float dt) {
+  bool moved = false;
+  if (corr) {
+    if (pend == kPendCorrect && !P.serna_off) {
+      serna_correct(xi, vi, ai, an, dtc);
+      moved = true;
+    }
+    ai = an;
+  }
+  if (dt != 0.0f) {
+    const float hdt2 = 0.5f * dt * dt;
+    xi.x = xi.x + vi.x * dt + ai.x * hdt2;
+    xi.y = xi.y + vi.y * dt + ai.y * hdt2;
+    xi.z = xi.z + vi.z * dt + ai.z * hdt2;
+    vi.x = vi.x + ai.x * dt;
+    vi.y = vi.y + ai.y * dt;
+    vi.z = vi.z + ai.z * dt;
+    if (P.wall_project) wall_project(P, xi, vi);
+    moved = true;
+  }
+  return moved;
+}
+
+// predict_math on particle i, loads and stores included; returns its position.
 __device__ __forceinline__ float4 predict_one(const DevParams& P, int i, float4* __restrict__ x,
                                               float4* __restrict__ v, float4* __restrict__ a,
                                               float dt, int pend, int pend_k1,
                                               const uint8_t* __restrict__ cflag,
                                               const float4* __restrict__ anew,
-                                              int32_t* __restrict__ klast, float4* vout,
-                                              float4* aout) {
+                                              int32_t* __restrict__ klast) {
   float4 xi = x[i];
   const bool corr = pend != kPendNone && cflag[i];
-  if (corr || dt != 0.0f || vout) {
+  if (corr || dt != 0.0f) {
     float4 vi = v[i], ai = a[i];
-    bool moved = false;
+    float4 an = make_float4(0.f, 0.f, 0.f, 0.f);
+    float dtc = 0.f;
     if (corr) {
-      const float4 an = anew[i];
-      if (pend == kPendCorrect) {
-        if (!P.serna_off) {
-          serna_correct(xi, vi, ai, an, (float)(pend_k1 - klast[i]) * P.dt_b);
-          moved = true;
-        }
-      }
-      ai = an;
+      an = anew[i];
+      dtc = (float)(pend_k1 - klast[i]) * P.dt_b;
       a[i] = an;
       klast[i] = pend_k1;
     }
-    if (dt != 0.0f) {
-      const float hdt2 = 0.5f * dt * dt;
-      xi.x = xi.x + vi.x * dt + ai.x * hdt2;
-      xi.y = xi.y + vi.y * dt + ai.y * hdt2;
-      xi.z = xi.z + vi.z * dt + ai.z * hdt2;
-      vi.x = vi.x + ai.x * dt;
-      vi.y = vi.y + ai.y * dt;
-      vi.z = vi.z + ai.z * dt;
-      if (P.wall_project) wall_project(P, xi, vi);
-      moved = true;
-    }
-    if (moved) {
+    if (predict_math(P, xi, vi, ai, corr, pend, an, dtc, dt)) {
       x[i] = xi;
       v[i] = vi;
-    }
-    if (vout) {
-      *vout = vi;
-      *aout = ai;
     }
   }
   return xi;
@@ -87,8 +93,7 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
     ctl->disp_bits[0] = ctl->disp_bits[1] = 0u;
   }
   if (i >= n) return;
-  const float4 xi = predict_one(P, i, x, v, a, dt, pend, pend_k1, cflag, anew, klast, nullptr,
-                                nullptr);
+  const float4 xi = predict_one(P, i, x, v, a, dt, pend, pend_k1, cflag, anew, klast);
   int bad = 0;
   // a batch: each particle is binned in its own scene's grid (the fluid pass has v, the
   // boundary pass not; the caller index gives the scene)
@@ -136,7 +141,7 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
 // list (entries gathered in shared memory) and, only when it raises it, for the
 // maximum, so neither counter is a point of contention.
 constexpr int kLightThreads = 256;
-constexpr int kLightItems = 4;
+constexpr int kLightItems = 1;
 
 __global__ void __launch_bounds__(kLightThreads) k_predict_light(
     DevParams P, int n, float4* __restrict__ x, float4* __restrict__ v, float4* __restrict__ a,
@@ -160,15 +165,40 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
   __syncthreads();
   float disp = 0.f;
   const int base0 = blockIdx.x * (kLightThreads * kLightItems) + w * (32 * kLightItems) + lane;
-#pragma unroll 1
+  // every item's loads first, so they are in flight together
+  float4 xs[kLightItems], vs[kLightItems], as[kLightItems];
+  uint32_t sk[kLightItems];
+  bool cr[kLightItems];
+#pragma unroll
+  for (int it = 0; it < kLightItems; ++it) {
+    const int i = base0 + 32 * it;
+    const bool valid = i < n;
+    xs[it] = valid ? x[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    vs[it] = valid ? v[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    as[it] = valid ? a[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    sk[it] = valid ? skey[i] : 0xffffffffu;
+    cr[it] = valid && pend != kPendNone && cflag[i];
+  }
+#pragma unroll
   for (int it = 0; it < kLightItems; ++it) {
     const int i = base0 + 32 * it;
     const bool valid = i < n;
     uint32_t b = 0xffffffffu;
     float v2 = 0.f, a2 = 0.f;
     if (valid) {
-      float4 vi, ai;
-      const float4 xi = predict_one(P, i, x, v, a, dt, pend, pend_k1, cflag, anew, klast, &vi, &ai);
+      float4 xi = xs[it], vi = vs[it], ai = as[it];
+      float4 an = make_float4(0.f, 0.f, 0.f, 0.f);
+      float dtc = 0.f;
+      if (cr[it]) {
+        an = anew[i];
+        dtc = (float)(pend_k1 - klast[i]) * P.dt_b;
+        a[i] = an;
+        klast[i] = pend_k1;
+      }
+      if (predict_math(P, xi, vi, ai, cr[it], pend, an, dtc, dt)) {
+        x[i] = xi;
+        v[i] = vi;
+      }
       int bad = 0;
       b = block_key(P, xi, &bad);
       if (bad) {
@@ -184,7 +214,7 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
       key_cur[i] = b;
       v2 = vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
       a2 = ai.x * ai.x + ai.y * ai.y + ai.z * ai.z;
-      const uint32_t sb = skey[i];
+      const uint32_t sb = sk[it];
       if (sb != b && sb < (uint32_t)P.nblocks) {   // outside its sorted block: how far
         const int cx = (int)(sb % (uint32_t)P.nx), rr = (int)(sb / (uint32_t)P.nx);
         const int cy = rr % P.ny, cz = rr / P.ny;
@@ -197,13 +227,13 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
         disp = fmaxf(disp, fmaxf(fmaxf(dx, dy), dz) * 1.0001f + 1e-5f * P.edge);
       }
     }
-    // segmented maxima over lanes of the same block (every lane reaches the shuffles)
-    unsigned long long mv = valid ? (((unsigned long long)stamp << 32) | __float_as_uint(v2)) : 0ull;
-    unsigned long long ma = valid ? (((unsigned long long)stamp << 32) | __float_as_uint(a2)) : 0ull;
+    // segmented maxima over lanes of the same block on the FP32 bits (non-negative, so
+    // ordered as integers); every lane reaches the shuffles
+    uint32_t mv = __float_as_uint(v2), ma = __float_as_uint(a2);
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const unsigned long long ov = __shfl_down_sync(0xffffffffu, mv, d);
-      const unsigned long long oa = __shfl_down_sync(0xffffffffu, ma, d);
+      const uint32_t ov = __shfl_down_sync(0xffffffffu, mv, d);
+      const uint32_t oa = __shfl_down_sync(0xffffffffu, ma, d);
       const uint32_t ob = __shfl_down_sync(0xffffffffu, b, d);
       if (lane + d < 32 && ob == b) {
         mv = ov > mv ? ov : mv;
@@ -213,8 +243,9 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
     const uint32_t prevb = __shfl_up_sync(0xffffffffu, b, 1);
     bool claim = false;
     if (valid && (lane == 0 || prevb != b)) {
-      const unsigned long long old = atomicMax(bmax_v + b, mv);
-      atomicMax(bmax_a + b, ma);
+      const unsigned long long tag = (unsigned long long)stamp << 32;
+      const unsigned long long old = atomicMax(bmax_v + b, tag | mv);
+      atomicMax(bmax_a + b, tag | ma);
       claim = (uint32_t)(old >> 32) != stamp;   // the block's first particle this pass
     }
     const unsigned cm = __ballot_sync(0xffffffffu, claim);

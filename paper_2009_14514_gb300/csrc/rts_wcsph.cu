@@ -16,6 +16,15 @@ namespace rts {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+__device__ __forceinline__ uint32_t warp_incl_sum(uint32_t v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t t = __shfl_up_sync(kFull, v, d);
+    if (lane >= d) v += t;
+  }
+  return v;
+}
+
 __device__ __forceinline__ double norm2d(float x, float y, float z) {
   double dx = x, dy = y, dz = z;
   return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
@@ -69,39 +78,64 @@ __device__ __forceinline__ bool norm2_le(float x, float y, float z, float th, fl
 // exact): a level passes iff every particle passes its tests; the block takes the
 // largest passing level.  The block's particles are those whose current block (key_cur)
 // is b: after a sort, block b's range; on a substep that kept the last sort, also in b's
-// 26 sorted neighbours (particles move less than a quarter block between sorts).
-static __device__ __noinline__ int level_exact(const DevParams& P, uint32_t b, int stale,
-                                               const uint32_t* __restrict__ cstart,
-                                               const uint32_t* __restrict__ key_cur,
-                                               const float4* __restrict__ v,
-                                               const float4* __restrict__ a,
-                                               const float4* __restrict__ ap) {
-  unsigned pass = (1u << P.n_levels) - 1u;
+// 26 sorted neighbours (particles move less than a quarter block between sorts).  The
+// whole warp takes part (every lane calls it with the same b): the lanes share out the
+// candidate particles, so the loads of one round are in flight together.
+static __device__ __noinline__ int level_exact_warp(const DevParams& P, uint32_t b, int stale,
+                                                    const uint32_t* __restrict__ cstart,
+                                                    const uint32_t* __restrict__ key_cur,
+                                                    const float4* __restrict__ v,
+                                                    const float4* __restrict__ a,
+                                                    const float4* __restrict__ ap, int lane) {
   const int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
-  const int R = stale ? 1 : 0;
-  for (int dz = -R; dz <= R; ++dz)
-    for (int dy = -R; dy <= R; ++dy)
-      for (int dx = -R; dx <= R; ++dx) {
-        const int cx = bx + dx, cy = by + dy, cz = bz + dz;
-        if (cx < 0 || cy < 0 || cz < 0 || cx >= P.nx || cy >= P.ny || cz >= P.nz) continue;
-        const uint32_t cb = ((uint32_t)cz * P.ny + cy) * P.nx + cx;
-        for (uint32_t i = cstart[cb]; i < cstart[cb + 1]; ++i) {
-          if (stale && key_cur[i] != b) continue;
-          const float4 vi = v[i];
-          float4 ai = a[i];
-          if (ap) {  // PCISPH: total acceleration
-            const float4 pa = ap[i];
-            ai.x += pa.x;
-            ai.y += pa.y;
-            ai.z += pa.z;
-          }
-          for (int l = 0; l < P.n_levels; ++l)
-            if (((pass >> l) & 1u) &&
-                !(norm2_le(vi.x, vi.y, vi.z, P.vthr2f[l], P.vthr2lo[l], P.vthr2[l]) &&
-                  norm2_le(ai.x, ai.y, ai.z, P.athr2f[l], P.athr2lo[l], P.athr2[l])))
-              pass &= ~(1u << l);
-        }
-      }
+  // lane c < ncells: cell c's range (the 27 cells around b, or b alone)
+  const int ncells = stale ? 27 : 1;
+  uint32_t st = 0, ln = 0;
+  if (lane < ncells) {
+    const int cx = bx + (stale ? lane % 3 - 1 : 0), cy = by + (stale ? (lane / 3) % 3 - 1 : 0),
+              cz = bz + (stale ? lane / 9 - 1 : 0);
+    if (cx >= 0 && cy >= 0 && cz >= 0 && cx < P.nx && cy < P.ny && cz < P.nz) {
+      const uint32_t cb = ((uint32_t)cz * P.ny + cy) * P.nx + cx;
+      st = cstart[cb];
+      ln = cstart[cb + 1] - st;
+    }
+  }
+  const uint32_t inc = warp_incl_sum(ln, lane);
+  const uint32_t off = inc - ln;
+  const uint32_t total = __shfl_sync(kFull, inc, 31);
+  unsigned pass = (1u << P.n_levels) - 1u;
+  for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+    const uint32_t k = k0 + lane;
+    // the candidate's cell: the last with off <= k
+    uint32_t i = 0xffffffffu;
+    for (int c = 0; c < ncells; ++c) {
+      const uint32_t oc = __shfl_sync(kFull, off, c), sc = __shfl_sync(kFull, st, c),
+                     lc = __shfl_sync(kFull, ln, c);
+      if (k < total && k >= oc && k < oc + lc) i = sc + (k - oc);
+    }
+    if (i == 0xffffffffu || (stale && key_cur[i] != b)) continue;
+    const float4 vi = v[i];
+    float4 ai = a[i];
+    if (ap) {  // PCISPH: total acceleration
+      const float4 pa = ap[i];
+      ai.x += pa.x;
+      ai.y += pa.y;
+      ai.z += pa.z;
+    }
+    // outside 2e-5 of a threshold the FP32 norm decides (its error is below 3e-7)
+    const float v2 = vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+    const float a2 = ai.x * ai.x + ai.y * ai.y + ai.z * ai.z;
+    for (int l = 0; l < P.n_levels; ++l) {
+      const float tv = P.vthr2f[l], ta = P.athr2f[l];
+      bool ok_v = v2 <= tv, ok_a = a2 <= ta;
+      if (isfinite(tv) && fabsf(v2 - tv) <= 2e-5f * tv)
+        ok_v = norm2_le(vi.x, vi.y, vi.z, tv, P.vthr2lo[l], P.vthr2[l]);
+      if (isfinite(ta) && fabsf(a2 - ta) <= 2e-5f * ta)
+        ok_a = norm2_le(ai.x, ai.y, ai.z, ta, P.athr2lo[l], P.athr2[l]);
+      if (!(ok_v && ok_a)) pass &= ~(1u << l);
+    }
+  }
+  pass = __reduce_and_sync(kFull, pass);
   int L = 0;
   for (int l = 0; l < P.n_levels; ++l)
     if (P.eq1[l] && ((pass >> l) & 1u)) L = l;
@@ -110,8 +144,9 @@ static __device__ __noinline__ int level_exact(const DevParams& P, uint32_t b, i
 
 // Raw level of every filled block (Section 3.1 steps 1-2) from the stamped FP32 block
 // maxima; in the rare undecided case the exact decision of the double-precision
-// definition is taken from the block's particles (level_exact).  nfilled: the length of
-// the filled list (the sort's, or that of a key pass that kept the last sort).
+// definition is taken from the block's particles (level_exact_warp, the warp working on
+// one such block at a time).  nfilled: the length of the filled list (the sort's, or that
+// of a key pass that kept the last sort).
 __global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled,
                               const int* __restrict__ nfilled, const uint32_t* __restrict__ cstart,
                               const uint32_t* __restrict__ key_cur, int stale,
@@ -122,14 +157,27 @@ __global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled,
                               uint32_t* __restrict__ raw) {
   pdl_wait();
   const int nf = *nfilled;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
-    uint32_t b = filled[t];
-    float vm = __uint_as_float((uint32_t)bmax_v[b]);
-    float am = __uint_as_float((uint32_t)bmax_a[b]);
+  const int lane = threadIdx.x & 31;
+  const int wstride = gridDim.x * blockDim.x;
+  // warp-uniform trip count (the fallback needs every lane)
+  for (int t0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; t0 < nf; t0 += wstride) {
+    const int t = t0 + lane;
+    uint32_t b = 0;
+    int L = 0;
     bool undecided = false;
-    int L = pick_level_f(P, vm, am, &undecided);
-    if (undecided) L = level_exact(P, b, stale, cstart, key_cur, v, a, ap);
-    raw[b] = (stamp << 8) | (uint32_t)L;
+    if (t < nf) {
+      b = filled[t];
+      const float vm = __uint_as_float((uint32_t)bmax_v[b]);
+      const float am = __uint_as_float((uint32_t)bmax_a[b]);
+      L = pick_level_f(P, vm, am, &undecided);
+    }
+    for (unsigned m = __ballot_sync(kFull, undecided); m; m &= m - 1u) {
+      const int src = __ffs(m) - 1;
+      const uint32_t bu = __shfl_sync(kFull, b, src);
+      const int Lu = level_exact_warp(P, bu, stale, cstart, key_cur, v, a, ap, lane);
+      if (lane == src) L = Lu;
+    }
+    if (t < nf) raw[b] = (stamp << 8) | (uint32_t)L;
   }
 }
 
@@ -149,23 +197,21 @@ __global__ void k_block_rmin(DevParams P, int mode, int level_g,
     } else if (P.force_level >= 0) {
       L = P.force_level;
     } else {
-      L = (int)(raw[b] & 0xffu);
+      // the 27 records are loaded independently (an offset outside the grid reads the
+      // block's own record instead, which leaves the minimum unchanged)
       const int bx = b % P.nx, r = b / P.nx, by = r % P.ny, bz = r / P.ny;
-      for (int dz = -1; dz <= 1; ++dz) {
-        const int cz = bz + dz;
-        if (cz < 0 || cz >= P.nz) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-          const int cy = by + dy;
-          if (cy < 0 || cy >= P.ny) continue;
-          const uint32_t row = ((uint32_t)cz * P.ny + cy) * P.nx;
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int cx = bx + dx;
-            if (cx < 0 || cx >= P.nx) continue;
-            const uint32_t rc = raw[row + cx];
-            if ((rc >> 8) == stamp && (int)(rc & 0xffu) < L) L = (int)(rc & 0xffu);
-          }
-        }
-      }
+      const int xm = bx > 0 ? -1 : 0, xp = bx + 1 < P.nx ? 1 : 0;
+      const int ym = by > 0 ? -(int)P.nx : 0, yp = by + 1 < P.ny ? (int)P.nx : 0;
+      const int pl = P.nx * P.ny;
+      const int zm = bz > 0 ? -pl : 0, zp = bz + 1 < P.nz ? pl : 0;
+      const int ox[3] = {xm, 0, xp}, oy[3] = {ym, 0, yp}, oz[3] = {zm, 0, zp};
+      uint32_t rc[27];
+#pragma unroll
+      for (int k = 0; k < 27; ++k) rc[k] = raw[(int)b + ox[k % 3] + oy[(k / 3) % 3] + oz[k / 9]];
+      L = (int)(rc[13] & 0xffu);
+#pragma unroll
+      for (int k = 0; k < 27; ++k)
+        if ((rc[k] >> 8) == stamp && (int)(rc[k] & 0xffu) < L) L = (int)(rc[k] & 0xffu);
     }
     blevel[b] = (stamp << 8) | (uint32_t)L;
   }
@@ -338,14 +384,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-__device__ __forceinline__ uint32_t warp_incl_sum(uint32_t v, int lane) {
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    uint32_t t = __shfl_up_sync(kFull, v, d);
-    if (lane >= d) v += t;
-  }
-  return v;
-}
 
 // The candidates of block b are 18 contiguous runs: for each of the 9 (dz, dy) rows the
 // x range [bx - 1, bx + 1] of the fluid array (runs 0-8) and of the boundary array

@@ -107,7 +107,7 @@ def wcsph_params(s, box, dt_b, *, support_factor=2.0):
         sched=[[3, 3, 3, 3], [2, 1, 2, 1], [2, 1, 1, 1], [2, 1, 1, 1]],
         refresh=[1, 2, 4, 4], max_neighbors=96,
         wall_project=1, wall_lo=[0.0, 0.0, 0.0], wall_hi=[float(L) for L in box],
-        stale_bins=2,
+        stale_bins=4,
     )
 
 

@@ -63,7 +63,7 @@ def test_single_rank_needs_no_process_group():
 
 def test_reference_line_keeps_the_contract():
     # the reference arm (the oracle, timed on the host) prints the CUDA arm's line: same
-    # metric, unit, direction and workload, an e2e equal to its value with no copies
+    # metric, unit, direction and scene, an e2e equal to its value with no copies
     sys.path.insert(0, ROOT)
     import bench
     args = bench.parse(["--impl", "reference", "--small", "--steps", "1", "--warmup", "0"])
@@ -77,7 +77,13 @@ def test_reference_line_keeps_the_contract():
         assert k in line, k
     assert line["impl"] == "reference" and line["higher_is_better"] is True
     assert line["unit"] == "particle-substeps/s" and line["value"] > 0
-    assert line["config"]["workload"] == bench.workload_name(bench.workload(True), args)
+    # the same scene and metric as the CUDA arm; the workload says what the oracle ran
+    sc = bench.workload(True)
+    assert line["metric"] == bench.METRIC
+    assert line["config"]["workload"].startswith(f"{sc.name}: {sc.n} fluid + {sc.nb} boundary")
+    assert "one step = one regional substep" in line["config"]["workload"]
+    assert "1 timed regional substeps" in line["cpu_baseline"]["sample"]
+    assert line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["cpu_baseline"]["value"] == line["value"]
