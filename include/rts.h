@@ -130,8 +130,8 @@ typedef struct rts_params {
      particle has left its sorted block since that sort, so the neighbour sets are
      exactly those of a fresh sort (only the order of summation differs).  With S = 2
      the kept substeps are those at which only the finest level is due.  0 or 1: sort
-     every substep.  A particle that moves a quarter of a block or more between sorts is
-     reported as RTS_ERR_INTERNAL.                                                       */
+     every substep.  A particle that moves half a block or more between sorts is
+     reported as RTS_ERR_INTERNAL (check 8): lower stale_bins for such flows.             */
   int32_t stale_bins;
 } rts_params;
 

@@ -625,6 +625,8 @@ static rts_status init_ctx(const rts_params* params, int32_t n_fluid, const floa
     ALLOC(c->bmax_v, sizeof(unsigned long long) * nbk);
     ALLOC(c->bmax_a, sizeof(unsigned long long) * nbk);
     ALLOC(c->filled, sizeof(uint32_t) * nbk);
+    ALLOC(c->filled_new, sizeof(uint32_t) * nbk);
+    ALLOC(c->near_list, sizeof(uint32_t) * kNearCap);
     c->nbl_cap = c->dp.nbl_cap;
     ALLOC(c->nbl, sizeof(uint32_t) * (size_t)n1 * (size_t)c->nbl_cap);
     ALLOC(c->buid, sizeof(uint32_t) * (size_t)(n_boundary > 0 ? n_boundary : 1));
@@ -742,7 +744,7 @@ rts_status rts_destroy(rts_ctx* c) {
   cudaFree(c->tmp_uid); cudaFree(c->tmp_src); cudaFree(c->io); cudaFree(c->io_i);
   cudaFree(c->count); cudaFree(c->cstart); cudaFree(c->bcstart); cudaFree(c->tile_sums);
   cudaFree(c->raw); cudaFree(c->blevel); cudaFree(c->act); cudaFree(c->plist); cudaFree(c->actflag); cudaFree(c->ctl); cudaFree(c->xb);
-  cudaFree(c->bmax_v); cudaFree(c->bmax_a); cudaFree(c->filled); cudaFree(c->nbl);
+  cudaFree(c->bmax_v); cudaFree(c->bmax_a); cudaFree(c->filled); cudaFree(c->filled_new); cudaFree(c->near_list); cudaFree(c->nbl);
   cudaFree(c->buid); cudaFree(c->s.ap); cudaFree(c->s2.ap); cudaFree(c->s.err); cudaFree(c->s2.err);
   cudaFree(c->xs); cudaFree(c->pbak); cudaFree(c->in_se); cudaFree(c->in_re); cudaFree(c->ob);
   cudaFree(c->preg); cudaFree(c->pnew);

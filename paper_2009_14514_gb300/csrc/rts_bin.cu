@@ -90,6 +90,7 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
     ctl->n_plist = 0;
     // a following pass that keeps this sort counts into a clean slot
     ctl->n_filled_light[0] = ctl->n_filled_light[1] = 0;
+    ctl->n_near[0] = ctl->n_near[1] = 0;
     ctl->disp_bits[0] = ctl->disp_bits[1] = 0u;
   }
   if (i >= n) return;
@@ -133,8 +134,10 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
 // (key_cur; the arrays stay in the order of the last sort, whose blocks are skey), the
 // block maxima of |v|^2 and |a|^2 merged by current block into the stamped records, and
 // the largest distance, per axis, by which a particle has left the block it was sorted
-// into (rounded up), which widens the density pass's search.  The particle that finds
-// a block's record from an older pass lists the block as filled.  The maximum and the
+// into (rounded up), which widens the density pass's search.  The blocks holding fluid
+// are the sort's filled list (some may have emptied: their records keep an older stamp)
+// plus the blocks the sort found empty that particles have moved into, listed here in
+// filled_new by the first such particle to reach the block's record.  The maximum and the
 // filled count live in slot stamp & 1, which the previous binning pass cleared (a sort
 // clears both, a pass like this one the slot of the next stamp; the kernels in between
 // never read it).  One atomic per CTA for the
@@ -149,7 +152,8 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
     int pend, int pend_k1, const uint8_t* __restrict__ cflag, const float4* __restrict__ anew,
     int32_t* __restrict__ klast, const uint32_t* __restrict__ uid, uint32_t stamp,
     unsigned long long* __restrict__ bmax_v, unsigned long long* __restrict__ bmax_a,
-    uint32_t* __restrict__ filled) {
+    const uint32_t* __restrict__ cstart, uint32_t* __restrict__ filled,
+    uint32_t* __restrict__ near_list) {
   pdl_wait();
   __shared__ float sdisp[kLightThreads / 32];
   __shared__ uint32_t sfill[kLightThreads * kLightItems];
@@ -160,6 +164,7 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
     ctl->n_plist = 0;
     ctl->disp_bits[(stamp + 1) & 1] = 0u;
     ctl->n_filled_light[(stamp + 1) & 1] = 0;
+    ctl->n_near[(stamp + 1) & 1] = 0;
   }
   if (threadIdx.x == 0) scount = 0u;
   __syncthreads();
@@ -185,6 +190,7 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
     const bool valid = i < n;
     uint32_t b = 0xffffffffu;
     float v2 = 0.f, a2 = 0.f;
+    bool near = false;
     if (valid) {
       float4 xi = xs[it], vi = vs[it], ai = as[it];
       float4 an = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -214,6 +220,12 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
       key_cur[i] = b;
       v2 = vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
       a2 = ai.x * ai.x + ai.y * ai.y + ai.z * ai.z;
+      for (int l = 0; l < P.n_levels; ++l) {   // near a threshold: listed for the exact level
+        const float tv = P.vthr2f[l], ta = P.athr2f[l];
+        if ((isfinite(tv) && fabsf(v2 - tv) <= 2e-5f * tv) ||
+            (isfinite(ta) && fabsf(a2 - ta) <= 2e-5f * ta))
+          near = true;
+      }
       const uint32_t sb = sk[it];
       if (sb != b && sb < (uint32_t)P.nblocks) {   // outside its sorted block: how far
         const int cx = (int)(sb % (uint32_t)P.nx), rr = (int)(sb / (uint32_t)P.nx);
@@ -228,25 +240,41 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
       }
     }
     // segmented maxima over lanes of the same block on the FP32 bits (non-negative, so
-    // ordered as integers); every lane reaches the shuffles
+    // ordered as integers), and whether the run holds a particle still in its sorted
+    // block; every lane reaches the shuffles
     uint32_t mv = __float_as_uint(v2), ma = __float_as_uint(a2);
+    uint32_t stay = (valid && sk[it] == b) ? 1u : 0u;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const uint32_t ov = __shfl_down_sync(0xffffffffu, mv, d);
       const uint32_t oa = __shfl_down_sync(0xffffffffu, ma, d);
+      const uint32_t os = __shfl_down_sync(0xffffffffu, stay, d);
       const uint32_t ob = __shfl_down_sync(0xffffffffu, b, d);
       if (lane + d < 32 && ob == b) {
         mv = ov > mv ? ov : mv;
         ma = oa > ma ? oa : ma;
+        stay |= os;
       }
     }
     const uint32_t prevb = __shfl_up_sync(0xffffffffu, b, 1);
     bool claim = false;
     if (valid && (lane == 0 || prevb != b)) {
       const unsigned long long tag = (unsigned long long)stamp << 32;
-      const unsigned long long old = atomicMax(bmax_v + b, tag | mv);
-      atomicMax(bmax_a + b, tag | ma);
-      claim = (uint32_t)(old >> 32) != stamp;   // the block's first particle this pass
+      if (stay) {   // b held this particle at the sort: it is on the sort's filled list
+        atomicMax(bmax_v + b, tag | mv);
+        atomicMax(bmax_a + b, tag | ma);
+      } else {      // only particles that moved in: list b if the sort found it empty
+        const unsigned long long old = atomicMax(bmax_v + b, tag | mv);
+        atomicMax(bmax_a + b, tag | ma);
+        claim = (uint32_t)(old >> 32) != stamp && cstart[b + 1] == cstart[b];
+      }
+    }
+    const unsigned nm = __ballot_sync(0xffffffffu, near);   // rare: one atomic per such warp
+    if (nm) {
+      uint32_t nb = 0;
+      if (lane == 0) nb = (uint32_t)atomicAdd(&ctl->n_near[stamp & 1], __popc(nm));
+      nb = __shfl_sync(0xffffffffu, nb, 0) + (uint32_t)__popc(nm & ((1u << lane) - 1u));
+      if (near && nb < (uint32_t)kNearCap) near_list[nb] = (uint32_t)i;
     }
     const unsigned cm = __ballot_sync(0xffffffffu, claim);
     uint32_t off = 0;
@@ -272,9 +300,9 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
     unsigned int* slot = &ctl->disp_bits[stamp & 1];
     if (m > 0.f && __float_as_uint(m) > *(volatile unsigned int*)slot) {
       atomicMax(slot, __float_as_uint(m));
-      // the density pass searches at most 5 blocks per axis around a group, enough
-      // while every particle stays within a quarter block of its sorted block
-      if (m >= 0.25f * P.edge) check_failed(ctl, kChkDisp, __float_as_uint(m));
+      // the density pass searches at most 7 blocks per axis around a group, enough
+      // while every particle stays within half a block of its sorted block
+      if (m >= 0.5f * P.edge) check_failed(ctl, kChkDisp, __float_as_uint(m));
     }
   }
 }
@@ -553,6 +581,7 @@ static void next_stamp(rts_ctx* c) {
     cudaMemsetAsync(c->actflag, 0, sizeof(uint32_t) * nb, c->stream);
     // two passes in a row now share a parity: clear the slots of the kept-sort passes
     cudaMemsetAsync(c->ctl->n_filled_light, 0, sizeof(c->ctl->n_filled_light), c->stream);
+    cudaMemsetAsync(c->ctl->n_near, 0, sizeof(c->ctl->n_near), c->stream);
     cudaMemsetAsync(c->ctl->disp_bits, 0, sizeof(c->ctl->disp_bits), c->stream);
     c->stamp = 1;
   }
@@ -566,7 +595,8 @@ rts_status launch_bin_light(rts_ctx* c, float dt) {
   next_stamp(c);
   launch_pdl(c->stream, k_predict_light, g, kLightThreads, 0, c->dp, n, c->s.x, c->s.v, c->s.a,
              dt, c->key, c->key_cur, c->ctl, c->pend_mode, (int)c->pend_k1, c->cflag, c->anew,
-             c->s.klast, c->s.uid, c->stamp, c->bmax_v, c->bmax_a, c->filled);
+             c->s.klast, c->s.uid, c->stamp, c->bmax_v, c->bmax_a, c->cstart, c->filled_new,
+             c->near_list);
   c->pend_mode = kPendNone;
   return RTS_OK;
 }

@@ -99,14 +99,18 @@ struct Ctl {
   // stamp & 1 of the pass that computed it.
   unsigned int disp_bits[2];
   int n_filled_light[2];          // filled-list length of such a pass, slot stamp & 1
+  int n_near[2];                  // its list of particles near a level threshold, slot stamp & 1
 };
+
+// Capacity of that list; beyond it the level fallback scans the sorted cells instead.
+constexpr int kNearCap = 1 << 16;
 
 // Device-side consistency checks: an index read from memory is tested before it is
 // used; a failure records its code and value, sets RTS_ERR_INTERNAL and skips the access.
 enum CheckCode {
   kChkNone = 0, kChkNeighbour = 1, kChkRun = 2, kChkGather = 3, kChkScatter = 4,
   kChkLevel = 5, kChkUid = 6, kChkActive = 7,
-  kChkDisp = 8   // a particle moved a quarter block or more since the last sort
+  kChkDisp = 8   // a particle moved half a block or more since the last sort
 };
 
 // Particle state in block-sorted order.  x.w = p / rho^2 and v.w = rho of the last
@@ -334,7 +338,9 @@ struct rts_ctx {
   unsigned long long* bmax_a;     // (stamp << 32) | FP32 bits of the block max |a|^2
   uint32_t* raw;                  // (stamp << 8) | level from Eq. 1-3
   uint32_t* blevel;               // (stamp << 8) | level after smoothing
-  uint32_t* filled;               // list of filled blocks of the current pass
+  uint32_t* filled;               // list of filled blocks of the current pass (the sort's)
+  uint32_t* filled_new;           // blocks filled since the sort (a pass that kept it)
+  uint32_t* near_list;            // its particles with a norm near a level threshold
   uint32_t* act;      // active block list
   uint32_t* plist;    // evaluated particles (sorted-order indices), any order
   uint32_t* actflag;  // per block: stamp of the pass that listed it as active

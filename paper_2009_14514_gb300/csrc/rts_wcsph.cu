@@ -78,7 +78,7 @@ __device__ __forceinline__ bool norm2_le(float x, float y, float z, float th, fl
 // exact): a level passes iff every particle passes its tests; the block takes the
 // largest passing level.  The block's particles are those whose current block (key_cur)
 // is b: after a sort, block b's range; on a substep that kept the last sort, also in b's
-// 26 sorted neighbours (particles move less than a quarter block between sorts).  The
+// 26 sorted neighbours (particles move less than half a block between sorts).  The
 // whole warp takes part (every lane calls it with the same b): the lanes share out the
 // candidate particles, so the loads of one round are in flight together.
 static __device__ __noinline__ int level_exact_warp(const DevParams& P, uint32_t b, int stale,
@@ -142,21 +142,69 @@ static __device__ __noinline__ int level_exact_warp(const DevParams& P, uint32_t
   return L;
 }
 
+// The same decision on a substep that kept the sort, from the particles the key pass
+// listed as near a threshold (within 2e-5 of one in FP32): a threshold that the block's
+// FP32 maximum (vm, am) decides keeps that decision; an undecided one (the maximum within
+// 1e-5 of it) can only be failed by listed particles, since every other particle of the
+// block lies below it by more than the FP32 error, so the listed particles of block b
+// decide it exactly.  The whole warp takes part (every lane calls it with the same b).
+static __device__ __noinline__ int level_from_near(const DevParams& P, uint32_t b, float vm,
+                                                   float am, const uint32_t* __restrict__ near,
+                                                   int nn, const uint32_t* __restrict__ key_cur,
+                                                   const float4* __restrict__ v,
+                                                   const float4* __restrict__ a, int lane) {
+  unsigned pv = (1u << P.n_levels) - 1u, pa = pv;
+  for (int k0 = 0; k0 < nn; k0 += 32) {
+    const int k = k0 + lane;
+    if (k >= nn) continue;
+    const uint32_t i = near[k];
+    if (i >= (uint32_t)P.n_fluid || key_cur[i] != b) continue;
+    const float4 vi = v[i], ai = a[i];
+    const float v2 = vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
+    const float a2 = ai.x * ai.x + ai.y * ai.y + ai.z * ai.z;
+    for (int l = 0; l < P.n_levels; ++l) {
+      const float tv = P.vthr2f[l], ta = P.athr2f[l];
+      bool ok_v = v2 <= tv, ok_a = a2 <= ta;
+      if (isfinite(tv) && fabsf(v2 - tv) <= 2e-5f * tv)
+        ok_v = norm2_le(vi.x, vi.y, vi.z, tv, P.vthr2lo[l], P.vthr2[l]);
+      if (isfinite(ta) && fabsf(a2 - ta) <= 2e-5f * ta)
+        ok_a = norm2_le(ai.x, ai.y, ai.z, ta, P.athr2lo[l], P.athr2[l]);
+      if (!ok_v) pv &= ~(1u << l);
+      if (!ok_a) pa &= ~(1u << l);
+    }
+  }
+  pv = __reduce_and_sync(kFull, pv);
+  pa = __reduce_and_sync(kFull, pa);
+  int L = 0;
+  for (int l = 0; l < P.n_levels; ++l) {
+    const float tv = P.vthr2f[l], ta = P.athr2f[l];
+    const bool ok_v = (isfinite(tv) && fabsf(vm - tv) <= 1e-5f * tv) ? ((pv >> l) & 1u) : vm <= tv;
+    const bool ok_a = (isfinite(ta) && fabsf(am - ta) <= 1e-5f * ta) ? ((pa >> l) & 1u) : am <= ta;
+    if (P.eq1[l] && ok_v && ok_a) L = l;
+  }
+  return L;
+}
+
 // Raw level of every filled block (Section 3.1 steps 1-2) from the stamped FP32 block
 // maxima; in the rare undecided case the exact decision of the double-precision
 // definition is taken from the block's particles (level_exact_warp, the warp working on
-// one such block at a time).  nfilled: the length of the filled list (the sort's, or that
-// of a key pass that kept the last sort).
+// one such block at a time).  The blocks: the sort's filled list, and with stale (a pass
+// that kept the sort) also filled2, the blocks filled since; a block whose maxima carry
+// an older stamp has emptied since the sort and gets no level.
 __global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled,
-                              const int* __restrict__ nfilled, const uint32_t* __restrict__ cstart,
+                              const int* __restrict__ nfilled, const uint32_t* __restrict__ filled2,
+                              const int* __restrict__ nfilled2, const uint32_t* __restrict__ cstart,
                               const uint32_t* __restrict__ key_cur, int stale,
+                              const uint32_t* __restrict__ near, const int* __restrict__ n_near,
                               const float4* __restrict__ v, const float4* __restrict__ a,
                               const float4* __restrict__ ap,
                               const unsigned long long* __restrict__ bmax_v,
                               const unsigned long long* __restrict__ bmax_a, uint32_t stamp,
                               uint32_t* __restrict__ raw) {
   pdl_wait();
-  const int nf = *nfilled;
+  const int nf1 = *nfilled;
+  const int nf = nf1 + (stale ? *nfilled2 : 0);
+  const int nn = stale ? *n_near : 0;   // beyond kNearCap the sorted cells are scanned
   const int lane = threadIdx.x & 31;
   const int wstride = gridDim.x * blockDim.x;
   // warp-uniform trip count (the fallback needs every lane)
@@ -164,33 +212,44 @@ __global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled,
     const int t = t0 + lane;
     uint32_t b = 0;
     int L = 0;
-    bool undecided = false;
+    bool undecided = false, live = false;
+    float vm = 0.f, am = 0.f;
     if (t < nf) {
-      b = filled[t];
-      const float vm = __uint_as_float((uint32_t)bmax_v[b]);
-      const float am = __uint_as_float((uint32_t)bmax_a[b]);
-      L = pick_level_f(P, vm, am, &undecided);
+      b = t < nf1 ? filled[t] : filled2[t - nf1];
+      const unsigned long long rv = bmax_v[b], ra = bmax_a[b];
+      live = (uint32_t)(rv >> 32) == stamp;
+      vm = __uint_as_float((uint32_t)rv);
+      am = __uint_as_float((uint32_t)ra);
+      if (live) L = pick_level_f(P, vm, am, &undecided);
     }
     for (unsigned m = __ballot_sync(kFull, undecided); m; m &= m - 1u) {
       const int src = __ffs(m) - 1;
       const uint32_t bu = __shfl_sync(kFull, b, src);
-      const int Lu = level_exact_warp(P, bu, stale, cstart, key_cur, v, a, ap, lane);
+      const float vmu = __shfl_sync(kFull, vm, src), amu = __shfl_sync(kFull, am, src);
+      const int Lu = (stale && nn <= kNearCap)
+                         ? level_from_near(P, bu, vmu, amu, near, nn, key_cur, v, a, lane)
+                         : level_exact_warp(P, bu, stale, cstart, key_cur, v, a, ap, lane);
       if (lane == src) L = Lu;
     }
-    if (t < nf) raw[b] = (stamp << 8) | (uint32_t)L;
+    if (live) raw[b] = (stamp << 8) | (uint32_t)L;
   }
 }
 
 // R_min (Section 4.2: a filled block takes the smallest level among itself and its
 // filled 26 neighbours, one Jacobi pass), or the forced / global level.
+// stale: the sort's list and filled2 (a pass that kept the sort); a block without a raw
+// level of this pass has emptied since the sort and is skipped.
 __global__ void k_block_rmin(DevParams P, int mode, int level_g,
                              const uint32_t* __restrict__ filled, const int* __restrict__ nfilled,
-                             const uint32_t* __restrict__ raw, uint32_t* __restrict__ blevel,
-                             uint32_t stamp) {
+                             const uint32_t* __restrict__ filled2, const int* __restrict__ nfilled2,
+                             int stale, const uint32_t* __restrict__ raw,
+                             uint32_t* __restrict__ blevel, uint32_t stamp) {
   pdl_wait();
-  const int nf = *nfilled;
+  const int nf1 = *nfilled;
+  const int nf = nf1 + (stale ? *nfilled2 : 0);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
-    const uint32_t b = filled[t];
+    const uint32_t b = t < nf1 ? filled[t] : filled2[t - nf1];
+    if (stale && (raw[b] >> 8) != stamp) continue;
     int L;
     if (mode == kActGlobal) {
       L = level_g;
@@ -509,12 +568,14 @@ __device__ __forceinline__ uint32_t stage_culled(const DevParams& P, const uint3
 // on a substep that kept the last sort (stale bins): every particle is at most dlt (per
 // axis) outside the block it was sorted into, so a neighbour of a particle in the box
 // [lo, hi] was sorted into a block meeting [lo - r - dlt, hi + r + dlt] (rounded outward
-// here).  Up to 5 x 5 rows of contiguous x runs, of the fluid (runs 0 .. nrow - 1) and
-// of the static boundary (nrow .. 2 nrow - 1), written to tab with the sentinel; the
-// candidates are a superset of the neighbours, which the exact predicate then selects,
-// so the neighbour sets are those of a fresh sort.  Returns the candidate count.
-constexpr int kStaleAxis = 5;
-constexpr int kTabFresh = 64, kTabStale = 160;   // u32 per warp: 3 x (runs + sentinel)
+// here).  Up to 7 x 7 rows of contiguous x runs (enough while particles stay within half
+// a block of their sorted blocks), of the fluid (runs 0 .. nrow - 1) and of the static
+// boundary (nrow .. 2 nrow - 1), written to tab with the sentinel; the candidates are a
+// superset of the neighbours, which the exact predicate then selects, so the neighbour
+// sets are those of a fresh sort.  Returns the candidate count.
+constexpr int kStaleAxis = 7;
+constexpr int kStaleRuns = 2 * kStaleAxis * kStaleAxis;   // 98
+constexpr int kTabFresh = 64, kTabStale = 300;   // u32 per warp: 3 x (runs + sentinel)
 
 __device__ __forceinline__ void axis_range(float l, float h, float ext, float o, float inv_e,
                                            int n, int* c0, int* c1, bool* clipped) {
@@ -542,9 +603,10 @@ __device__ __forceinline__ uint32_t stale_runs(const DevParams& P, float3 lo, fl
   axis_range(lo.z, hi.z, ext, P.oz, P.inv_edge, P.nz, &z0, &z1, &clipped);
   if (clipped && lane == 0) check_failed(ctl, kChkDisp, 0u);
   const int nyr = y1 - y0 + 1, nrow = nyr * (z1 - z0 + 1), nrun = 2 * nrow;
-  uint32_t st[2], ln[2];
+  constexpr int kH = (kStaleRuns + 31) / 32;
+  uint32_t st[kH], ln[kH];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < kH; ++h) {
     const int e = lane + 32 * h;
     st[h] = 0;
     ln[h] = 0;
@@ -558,21 +620,20 @@ __device__ __forceinline__ uint32_t stale_runs(const DevParams& P, float3 lo, fl
       ln[h] = __ldg(&cs[rb + x1 + 1]) - st[h];
     }
   }
-  const uint32_t inc0 = warp_incl_sum(ln[0], lane);
-  const uint32_t tot0 = __shfl_sync(kFull, inc0, 31);
-  const uint32_t inc1 = warp_incl_sum(ln[1], lane) + tot0;
-  const uint32_t total = __shfl_sync(kFull, inc1, 31);
   __syncwarp();   // the previous chunk's readers of tab are done
-  if (lane < nrun) {
-    tab[3 * lane] = st[0];
-    tab[3 * lane + 1] = ln[0];
-    tab[3 * lane + 2] = inc0 - ln[0];
+  uint32_t carry = 0;
+#pragma unroll
+  for (int h = 0; h < kH; ++h) {
+    const uint32_t inc = warp_incl_sum(ln[h], lane) + carry;
+    const int e = lane + 32 * h;
+    if (e < nrun) {
+      tab[3 * e] = st[h];
+      tab[3 * e + 1] = ln[h];
+      tab[3 * e + 2] = inc - ln[h];
+    }
+    carry = __shfl_sync(kFull, inc, 31);
   }
-  if (lane + 32 < nrun) {
-    tab[3 * (lane + 32)] = st[1];
-    tab[3 * (lane + 32) + 1] = ln[1];
-    tab[3 * (lane + 32) + 2] = inc1 - ln[1];
-  }
+  const uint32_t total = carry;
   if (lane == 0) {  // sentinel run: never exhausted
     tab[3 * nrun] = 0;
     tab[3 * nrun + 1] = 0xffffffffu;
@@ -1003,16 +1064,16 @@ static int force_grid(const rts_ctx* c) { return g_grid_force > 0 ? g_grid_force
 static int filled_grid() { return sm_count() * 8; }
 int filled_grid_size() { return filled_grid(); }
 
-// The filled list and its length: the sort's, or (stale) the light key pass's.
-static const int* filled_count(rts_ctx* c, bool stale) {
-  return stale ? &c->ctl->n_filled_light[c->stamp & 1] : &c->ctl->n_filled;
-}
+// The blocks filled since the sort, and their count (a pass that kept the sort).
+static const int* new_count(rts_ctx* c) { return &c->ctl->n_filled_light[c->stamp & 1]; }
 
 rts_status launch_classify(rts_ctx* c, bool stale) {
   note_launch(c, 1);
-  launch_pdl(c->stream, k_block_level, filled_grid(), 256, 0, c->dp, c->filled,
-             filled_count(c, stale), c->cstart, (const uint32_t*)(stale ? c->key_cur : c->key),
-             stale ? 1 : 0, c->s.v, c->s.a, c->s.ap, c->bmax_v, c->bmax_a, c->stamp, c->raw);
+  launch_pdl(c->stream, k_block_level, filled_grid(), 256, 0, c->dp, (const uint32_t*)c->filled,
+             (const int*)&c->ctl->n_filled, (const uint32_t*)c->filled_new, new_count(c),
+             (const uint32_t*)c->cstart, (const uint32_t*)(stale ? c->key_cur : c->key),
+             stale ? 1 : 0, (const uint32_t*)c->near_list, (const int*)&c->ctl->n_near[c->stamp & 1],
+             c->s.v, c->s.a, c->s.ap, c->bmax_v, c->bmax_a, c->stamp, c->raw);
   return RTS_OK;
 }
 
@@ -1021,8 +1082,10 @@ rts_status launch_classify(rts_ctx* c, bool stale) {
 // binning (every step bins before its activity pass).
 rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1, bool stale) {
   note_launch(c, 1);
-  launch_pdl(c->stream, k_block_rmin, filled_grid(), 256, 0, c->dp, mode, level_g, c->filled,
-             filled_count(c, stale), c->raw, c->blevel, c->stamp);
+  launch_pdl(c->stream, k_block_rmin, filled_grid(), 256, 0, c->dp, mode, level_g,
+             (const uint32_t*)c->filled, (const int*)&c->ctl->n_filled,
+             (const uint32_t*)c->filled_new, new_count(c), stale ? 1 : 0,
+             (const uint32_t*)c->raw, c->blevel, c->stamp);
   if (mode >= 0 && c->n > 0) {
     note_launch(c, 1);
     const int g = (c->n + kActThreads * kActItems - 1) / (kActThreads * kActItems);

@@ -117,3 +117,50 @@ def test_rollout_with_kept_sorts_matches_sorted_rollout_statistics():
     assert abs(e1 - e0) < 0.1 * e0 + 1e-4
     assert abs(n1 / n0 - 1.0) < 0.02
     assert np.all(np.isfinite(x1)) and len(x1) == sc.n
+
+
+def test_kept_sort_levels_at_the_thresholds_are_decided_exactly():
+    # A calm lattice (v = 0, held a = 0: nothing moves) with one particle in every third
+    # block at the largest FP32 speeds whose FP64 square is at most the level-3 threshold:
+    # the FP32 block maxima are undecided, on substeps that keep the sort as well, and
+    # the block levels must be the double-precision definition's (level 3), as the
+    # oracle's and as a context that sorts every substep
+    sc = scenes.wcsph_dam_break_8k()
+    base = params(sc, level_clock=1)
+    P = O.make_params(base)
+    vthr2, _, _ = O.level_thresholds(P)
+    t = float(vthr2[3])
+    c = np.float32(np.sqrt(t))
+    while float(c) ** 2 > t:
+        c = np.nextafter(c, np.float32(0))
+    cands = [c, np.nextafter(c, np.float32(0)), np.nextafter(np.nextafter(c, np.float32(0)),
+                                                              np.float32(0))]
+    assert all(abs(float(x) ** 2 / float(np.float32(t)) - 1) < 1e-5 for x in cands)
+    n = sc.n
+    v = np.zeros((n, 3), np.float32)
+    a = np.zeros((n, 3), np.float32)
+    _, perm, cstart = O.bin_particles(P, sc.x)
+    filled = np.nonzero(np.diff(cstart))[0]
+    for j, b in enumerate(filled[::3]):
+        v[perm[cstart[b]], j % 3] = cands[j % 3]
+    st = dict(x=sc.x, v=v, a=a, rho=np.full(n, 1000.0, np.float32), p=np.zeros(n, np.float32),
+              level=np.full(n, 3, np.int32), validity=np.full(n, 7, np.int32),
+              klast=np.zeros(n, np.int32))
+    levels = {}
+    for stale in (0, 4):
+        d = dict(base, stale_bins=stale)
+        ctx = gpu_ctx(sc, d)
+        rts.rts_set_state(ctx, st["x"], st["v"], a=st["a"], rho=st["rho"], p=st["p"],
+                          level=st["level"], validity=st["validity"], klast=st["klast"], k=1,
+                          primed=True)
+        rts.rts_advance(ctx, 3 * d["dt_b"])          # substeps 2 and 3 (both keep the sort)
+        levels[stale] = rts.rts_get_blocks(ctx)
+        rts.rts_sync(ctx)
+        ctx.close()
+    o = oracle_state(sc, base, st, k=1, primed=True)
+    o.substep()
+    o.substep()
+    assert np.array_equal(levels[4][0], levels[0][0])
+    assert np.array_equal(levels[4][1], levels[0][1])
+    assert np.array_equal(levels[4][1], o.block_level)
+    assert np.all(levels[4][1][filled] == 3)
