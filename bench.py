@@ -98,6 +98,8 @@ def parse(argv=None):
     ap.add_argument("--profile-warm-save", metavar="PATH",
                     help="simulate the headline arm to t = 1 s and save its state to PATH "
                          "(.npz) for --profile-warm")
+    ap.add_argument("--profile-warm-time", type=float, default=1.0,
+                    help="--profile-warm-save: simulated seconds before the state is saved")
     ap.add_argument("--profile-warm", metavar="PATH",
                     help="short run for ncu: load the state saved by --profile-warm-save and "
                          "advance the headline arm --steps substeps in one call")
@@ -134,8 +136,8 @@ def profile_case(args):
 
 
 def profile_warm(args):
-    """A bounded case at the rollout's own regime: the headline arm's state at t = 1 s
-    (saved by a plain run), advanced --steps substeps in one rts_advance call, so the
+    """A bounded case at the rollout's own regime: the headline arm's state at t = 1 s (or
+    --profile-warm-time; saved by a plain run), advanced --steps substeps in one call, so the
     density launches are those of the rollout (light and heavy substeps mixed)."""
     import numpy as np
     from paper_2009_14514_gb300 import rts, scenes
@@ -144,7 +146,7 @@ def profile_warm(args):
     d.update(HEADLINE)
     ctx = rts.rts_init(d, sc.x, sc.v, sc.xb)
     if args.profile_warm_save:
-        rts.rts_advance(ctx, 1.0)
+        rts.rts_advance(ctx, args.profile_warm_time)
         g = rts.rts_get_state(ctx)
         np.savez(args.profile_warm_save, k=ctx.substep_index, **g)
         print(json.dumps({"saved": args.profile_warm_save, "k": int(ctx.substep_index)}))
@@ -353,7 +355,8 @@ def arm_summary(sc, r, dt_norm):
            "wall_s_per_sim_s": sec / r["sim_s"], "steps_advanced": r["tot"]["steps"],
            "particle_evals": r["tot"]["particle_evals"],
            "evals_per_s": r["tot"]["particle_evals"] / sec,
-           "density_error_time_avg": r["err_time_avg"], "density_error_final": r["err_final"]}
+           "density_error_time_avg": r["err_time_avg"], "density_error_final": r["err_final"],
+           "ms_per_step_list": [round(m, 1) for m in r["ms"]]}
     if r["prof"] is not None:
         out["phases_ms"] = phase_split(r["prof"], sum(r["ms"]))
     return out

@@ -408,8 +408,12 @@ static rts_status sync_status(rts_ctx* c) {
 // Density and forces of the evaluated particles; their Serna correction is deferred to
 // the next key pass (which reads the same flags and accelerations) or to finalize().
 static void run_physics(rts_ctx* c, int64_t k1, int prime, bool stale = false) {
+  // global adaptive stepping: the force pass also forms the maxima that choose the next
+  // step (of the state the deferred correction will give)
+  const int gmode = c->p.mode == RTS_MODE_GLOBAL_ADAPTIVE ? (prime ? 2 : 1) : 0;
   { Phase ph(c, RTS_PHASE_DENSITY); launch_density(c, stale); }
-  { Phase ph(c, RTS_PHASE_FORCE); launch_force(c); }
+  { Phase ph(c, RTS_PHASE_FORCE); launch_force(c, gmode, k1); }
+  c->gmax_ok = gmode != 0;
   c->pend_mode = prime ? kPendPrime : kPendCorrect;
   c->pend_k1 = k1;
   // the force pass cleared the filled list; the next classification outside the
@@ -488,8 +492,11 @@ int rts::pick_level_from_f32_max(const DevParams& d, float v2, float a2) {
 static rts_status wcsph_global(rts_ctx* c, int64_t max_mult) {
   int L = 0;
   if (c->p.mode == RTS_MODE_GLOBAL_ADAPTIVE) {
-    finalize(c);  // the step size is chosen from the corrected state
-    {
+    // the step size is chosen from the corrected state: its FP32 maxima were formed by the
+    // last force pass (the correction itself stays deferred to the next key pass), else
+    // by a pass over the corrected state
+    if (!c->gmax_ok) {
+      finalize(c);
       Phase ph(c, RTS_PHASE_CLASSIFY);
       launch_global_max(c, 0);
     }
@@ -501,6 +508,7 @@ static rts_status wcsph_global(rts_ctx* c, int64_t max_mult) {
     memcpy(&a2f, &c->h_ctl->amax2f_bits, sizeof a2f);
     L = pick_level_from_f32_max(c->dp, v2f, a2f);
     if (L < 0) {   // a maximum at a threshold: the FP64 maxima decide
+      finalize(c);
       {
         Phase ph(c, RTS_PHASE_CLASSIFY);
         launch_global_max(c, 1);

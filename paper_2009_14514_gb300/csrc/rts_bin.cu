@@ -92,6 +92,7 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
     ctl->n_filled_light[0] = ctl->n_filled_light[1] = 0;
     ctl->n_near[0] = ctl->n_near[1] = 0;
     ctl->disp_bits[0] = ctl->disp_bits[1] = 0u;
+    ctl->vmax2f_bits = ctl->amax2f_bits = 0u;   // formed again by this step's force pass
   }
   if (i >= n) return;
   const float4 xi = predict_one(P, i, x, v, a, dt, pend, pend_k1, cflag, anew, klast);
@@ -603,6 +604,7 @@ rts_status launch_bin_light(rts_ctx* c, float dt) {
 
 rts_status launch_bin(rts_ctx* c, float dt) {
   c->light_ok = 1;   // the arrays are block-sorted by c->key from here on
+  c->gmax_ok = 0;    // the key pass clears the maxima of the global step size
   int n = c->n;
   if (n == 0) {
     next_stamp(c);

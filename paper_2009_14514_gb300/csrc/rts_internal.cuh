@@ -322,6 +322,8 @@ struct rts_ctx {
   uint32_t* key;      // block of each sorted particle (at the last sort)
   uint32_t* key_cur;  // current block of each particle on a substep that kept the sort
   int light_ok;       // a sort has ordered the arrays by key, so a substep may keep it
+  int gmax_ok;        // ctl's FP32 maxima are those of the (corrected) state: the last
+                      // force pass formed them and no key pass has cleared them since
   int64_t kept_sorts; // substeps that kept the last sort
   uint32_t* key_tmp;
   uint32_t* slot;
@@ -442,7 +444,9 @@ void make_dev_params(const rts_params& p, DevParams& d);
 // -1 when a maximum lies within 1e-5 of a threshold and the FP64 maxima must decide.
 int pick_level_from_f32_max(const DevParams& d, float v2, float a2);
 rts_status launch_density(rts_ctx* c, bool stale = false);
-rts_status launch_force(rts_ctx* c);
+// gmode: 0; 1 the force pass also forms the maxima of the corrected state (global
+// adaptive stepping, step ending at k1); 2 the same for a priming evaluation.
+rts_status launch_force(rts_ctx* c, int gmode = 0, int64_t k1 = 0);
 rts_status launch_correct(rts_ctx* c, int64_t k1, int prime);
 rts_status finalize(rts_ctx* c);
 rts_status launch_global_max(rts_ctx* c, int fp64);

@@ -831,14 +831,24 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
 // pairs with nu = 2 alpha h c / (rho_i + rho_j) (boundary: rho_j = rho_i, v_j = 0).
 constexpr int kForceLanes = 4;
 
+// FP32 squared norm without contraction (3 products, 2 sums, each rounded).
+__device__ __forceinline__ float norm2f(float x, float y, float z) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
+}
+
 // One round of the force pass: slot's particle (t = r * nslots + slot) walked by LANES
 // lanes.  Every lane of a warp runs the same rounds (the shuffles).
+// gmode != 0 (global adaptive stepping): also the maxima over the evaluated particles of
+// |v|^2 and |a_new|^2 of the state the Section 4.1 correction of this step (ending at
+// substep k1) will give (gmode 1; gmode 2: a priming evaluation, no correction), the
+// inputs of the next step size; *vm, *am collect this thread's (FP32 bits).
 template <int LANES>
 __device__ __forceinline__ void force_rounds(const DevParams& P, const uint32_t* __restrict__ plist,
                                              Ctl* ctl, const PState& s,
                                              const float4* __restrict__ xb,
                                              const uint32_t* __restrict__ nbl,
-                                             float4* __restrict__ anew, int np) {
+                                             float4* __restrict__ anew, int np, int gmode, int k1,
+                                             unsigned* vm, unsigned* am) {
   const int lane = threadIdx.x & 31;
   const int sub = lane & (LANES - 1);
   const int slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LANES) + lane / LANES;
@@ -901,7 +911,17 @@ __device__ __forceinline__ void force_rounds(const DevParams& P, const uint32_t*
       ay += __shfl_down_sync(kFull, ay, o, LANES);
       az += __shfl_down_sync(kFull, az, o, LANES);
     }
-    if (sub == 0 && i >= 0) anew[i] = make_float4(P.gx + ax, P.gy + ay, P.gz + az, 0.f);
+    if (sub == 0 && i >= 0) {
+      const float4 an = make_float4(P.gx + ax, P.gy + ay, P.gz + az, 0.f);
+      anew[i] = an;
+      if (gmode) {   // the corrected velocity, with the correction's own arithmetic
+        float4 xc = make_float4(0.f, 0.f, 0.f, 0.f), vc = vf[i];
+        if (gmode == 1 && !P.serna_off)
+          serna_correct(xc, vc, s.a[i], an, (float)(k1 - s.klast[i]) * P.dt_b);
+        *vm = max(*vm, __float_as_uint(norm2f(vc.x, vc.y, vc.z)));
+        *am = max(*am, __float_as_uint(norm2f(an.x, an.y, an.z)));
+      }
+    }
   }
 }
 
@@ -913,12 +933,34 @@ __device__ __forceinline__ void force_rounds(const DevParams& P, const uint32_t*
 __global__ void __launch_bounds__(kNbThreads) k_force(DevParams P, const uint32_t* __restrict__ plist,
                                                       Ctl* ctl, PState s, const float4* __restrict__ xb,
                                                       const uint32_t* __restrict__ nbl,
-                                                      float4* __restrict__ anew) {
+                                                      float4* __restrict__ anew, int gmode, int k1) {
   pdl_wait();
   const int np = *(volatile int*)&ctl->n_plist;
   const int warps = (gridDim.x * blockDim.x) >> 5;
-  if (np <= warps) force_rounds<32>(P, plist, ctl, s, xb, nbl, anew, np);
-  else force_rounds<kForceLanes>(P, plist, ctl, s, xb, nbl, anew, np);
+  unsigned vm = 0u, am = 0u;
+  if (np <= warps) force_rounds<32>(P, plist, ctl, s, xb, nbl, anew, np, gmode, k1, &vm, &am);
+  else force_rounds<kForceLanes>(P, plist, ctl, s, xb, nbl, anew, np, gmode, k1, &vm, &am);
+  if (gmode) {   // one atomic per CTA (the key pass of this step cleared the maxima)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      vm = max(vm, __shfl_xor_sync(kFull, vm, o));
+      am = max(am, __shfl_xor_sync(kFull, am, o));
+    }
+    __shared__ unsigned svm[kNbThreads / 32], sam[kNbThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+      svm[threadIdx.x >> 5] = vm;
+      sam[threadIdx.x >> 5] = am;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < kNbThreads / 32; ++k) {
+        vm = max(vm, svm[k]);
+        am = max(am, sam[k]);
+      }
+      if (vm) atomicMax(&ctl->vmax2f_bits, vm);
+      if (am) atomicMax(&ctl->amax2f_bits, am);
+    }
+  }
 }
 
 // Section 4.1 correction of the evaluated particles: x += (a_new - a_old) dt^2 / 6,
@@ -946,10 +988,6 @@ __global__ void k_correct(DevParams P, const uint32_t* __restrict__ plist, Ctl* 
   }
 }
 
-// FP32 squared norm without contraction (3 products, 2 sums, each rounded).
-__device__ __forceinline__ float norm2f(float x, float y, float z) {
-  return __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
-}
 
 // Global maxima of |v|^2 and |a|^2 over the fluid (global adaptive comparator): of the
 // FP32 norms (fp64 = 0, exact maximum on FP32 bits), or of the FP64 norms (fp64 = 1),
@@ -1112,10 +1150,10 @@ rts_status launch_density(rts_ctx* c, bool stale) {
   return RTS_OK;
 }
 
-rts_status launch_force(rts_ctx* c) {
+rts_status launch_force(rts_ctx* c, int gmode, int64_t k1) {
   note_launch(c, 1);
   launch_pdl(c->stream, k_force, force_grid(c), kNbThreads, 0, c->dp, c->plist, c->ctl, c->s,
-             c->xb, c->nbl, c->anew);
+             c->xb, c->nbl, c->anew, gmode, (int)k1);
   return RTS_OK;
 }
 

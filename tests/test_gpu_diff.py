@@ -11,7 +11,9 @@ match central differences of the oracle's forward.  With the pressure clamped at
 only piecewise smooth: FP32 and FP64 trajectories cross the clamp at slightly different
 times for the free-surface particles, so single entries of dL/dv0 may differ by up to
 ~15 % of the largest one; the comparison is then on the whole gradient (relative L2), on
-the two scalar gradients, and on central finite differences of the oracle's forward.
+the two scalar gradients, and on central finite differences of the oracle's forward,
+and entry by entry on the entries that the FP64 reference shows to be insensitive to
+small perturbations of the initial velocities (where the branch is stable).
 """
 import numpy as np
 import pytest
@@ -86,6 +88,34 @@ def test_clamped_rollout_gradients_match_the_reference_in_aggregate(clamped):
     assert np.median(np.abs(gv - ref)) <= 1e-3 * np.abs(ref).max()
     assert abs(gB - clamped["gB"]) <= 0.02 * abs(clamped["gB"])
     assert abs(ga - clamped["ga"]) <= 0.02 * abs(clamped["ga"])
+
+
+def test_clamped_rollout_gradients_match_entry_by_entry_where_the_branch_is_stable(clamped):
+    # The clamp makes some entries of dL/dv0 depend on exactly when a particle's density
+    # crosses rho0, which FP32 and FP64 trajectories decide at different steps.  The FP64
+    # reference itself tells which entries are insensitive: rerun it from initial
+    # velocities perturbed by 1e-4 relative (three seeds); the entries that move by at most
+    # 1e-3 of the largest in every rerun are stable, and there the GPU gradient must match
+    # the reference entry by entry: 99 % of them within 2e-3 of the largest entry, every
+    # one within 1e-2 (the FP32 trajectory departs from the FP64 one by more than the
+    # perturbation, so a few stable entries still see a different crossing).
+    R, v0 = clamped["R"], clamped["v0"].astype(np.float64)
+    ref = clamped["gv"]
+    mx = np.abs(ref).max()
+    rng = np.random.default_rng(2024)
+    dev = np.zeros(len(ref))
+    for _ in range(3):
+        vp = v0 * (1.0 + 1e-4 * rng.standard_normal(v0.shape))
+        xT, rhoT, recs = R.forward(vp, B0, A0, STEPS)
+        _, xbar, rhobar = centroid_density_loss(xT, rhoT, TARGET, 1000.0)
+        gp = R.backward(recs, B0, A0, xT, xbar, rhobar)[0]
+        dev = np.maximum(dev, np.abs(gp - ref).max(axis=1))
+    stable = dev <= 1e-3 * mx
+    assert stable.mean() > 0.8
+    _, _, _, gv, _, _ = _gpu_grads(clamped)
+    err = np.abs(gv[stable] - ref[stable]).max(axis=1)
+    assert np.mean(err <= 2e-3 * mx) >= 0.99, np.quantile(err / mx, [0.5, 0.99, 1.0])
+    assert err.max() <= 1e-2 * mx
 
 
 @pytest.mark.parametrize("which", ["smooth", "clamped"])
