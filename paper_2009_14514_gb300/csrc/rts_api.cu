@@ -119,6 +119,8 @@ void rts::make_dev_params(const rts_params& p, DevParams& d) {
   d.ny = p.grid_dim[1];
   d.nz = p.grid_dim[2];
   d.nblocks = d.nx * d.ny * d.nz;
+  d.div_nx = (1ull << 40) / (unsigned long long)d.nx + 1ull;
+  d.div_ny = (1ull << 40) / (unsigned long long)d.ny + 1ull;
   {
     // the FP32 block coordinate of a point up to one block outside the grid carries at
     // most 3 * 2^-24 relative error; 8 * 2^-24 * (largest dim + 2) bounds it with margin
@@ -449,7 +451,7 @@ static rts_status wcsph_evaluate(rts_ctx* c) {
 static bool keeps_sort(const rts_ctx* c, int64_t k1) {
   const rts_params& p = c->p;
   return c->light_ok && p.stale_bins > 1 && p.level_clock && p.mode == RTS_MODE_REGIONAL &&
-         p.force_level < 0 && (k1 % p.stale_bins) != 0;
+         p.force_level < 0 && (k1 % p.stale_bins) != 0 && c->dp.nblocks < (1 << 24);
 }
 
 static rts_status wcsph_regional(rts_ctx* c) {

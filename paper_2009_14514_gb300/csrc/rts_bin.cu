@@ -229,8 +229,9 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
       }
       const uint32_t sb = sk[it];
       if (sb != b && sb < (uint32_t)P.nblocks) {   // outside its sorted block: how far
-        const int cx = (int)(sb % (uint32_t)P.nx), rr = (int)(sb / (uint32_t)P.nx);
-        const int cy = rr % P.ny, cz = rr / P.ny;
+        const uint32_t rr = div_by(sb, P.div_nx), rz = div_by(rr, P.div_ny);
+        const int cx = (int)(sb - rr * (uint32_t)P.nx), cy = (int)(rr - rz * (uint32_t)P.ny);
+        const int cz = (int)rz;
         const float lx = P.ox + (float)cx * P.edge, ly = P.oy + (float)cy * P.edge,
                     lz = P.oz + (float)cz * P.edge;
         const float dx = fmaxf(fmaxf(lx - xi.x, xi.x - (lx + P.edge)), 0.f);

@@ -28,6 +28,10 @@ struct DevParams {
   double oxd, oyd, ozd, edged;
   int nx, ny, nz;
   int nblocks;
+  // floor(u / nx) = (u * div_nx) >> 40 for every u < 2^24 (exact for divisors < 2^16:
+  // div = floor(2^40 / d) + 1 overshoots 1/d by less than 2^-40, too little to reach the
+  // next integer); the same for ny.
+  unsigned long long div_nx, div_ny;
   int max_per_block;
   float key_band;    // FP32 block-coordinate band that defers to FP64 (see block_coord)
   // cubic spline kernel, h = r / 2, support r
@@ -238,6 +242,10 @@ __device__ __forceinline__ uint32_t block_key(const DevParams& P, float4 p, int*
   int cy = block_coord(p.y, P.oy, P.oyd, P.inv_edge, P.edged, P.ny, P.key_band, bad);
   int cz = block_coord(p.z, P.oz, P.ozd, P.inv_edge, P.edged, P.nz, P.key_band, bad);
   return ((uint32_t)cz * P.ny + cy) * P.nx + cx;
+}
+
+__device__ __forceinline__ uint32_t div_by(uint32_t u, unsigned long long m) {
+  return (uint32_t)(((unsigned long long)u * m) >> 40);
 }
 
 // Non-penetration of the container box: a particle beyond a face is put back on it and
