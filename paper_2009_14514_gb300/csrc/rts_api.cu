@@ -175,6 +175,9 @@ void rts::make_dev_params(const rts_params& p, DevParams& d) {
     d.vthr2lo[L] = std::isfinite(d.vthr2[L]) ? (float)(d.vthr2[L] - (double)d.vthr2f[L]) : 0.f;
     d.athr2lo[L] = std::isfinite(d.athr2[L]) ? (float)(d.athr2[L] - (double)d.athr2f[L]) : 0.f;
   }
+  d.levels_monotone = 1;
+  for (int L = 1; L < p.n_levels; ++L)
+    if (!(d.vthr2[L] <= d.vthr2[L - 1]) || !(d.athr2[L] <= d.athr2[L - 1])) d.levels_monotone = 0;
   d.force_level = p.force_level;
   d.dt_b = p.dt_b;
   d.nbl_cap = p.max_neighbors > 0 ? p.max_neighbors : 96;

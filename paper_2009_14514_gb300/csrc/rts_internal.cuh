@@ -60,6 +60,7 @@ struct DevParams {
   float vthr2f[kMaxLevels], athr2f[kMaxLevels];   // the same thresholds rounded to FP32
   float vthr2lo[kMaxLevels], athr2lo[kMaxLevels]; // and their FP32 residuals
   int eq1[kMaxLevels];
+  int levels_monotone;   // both thresholds non-increasing in the level (see k_block_levels)
   int force_level;
   int level_clock;   // 0: validity = multiplier (Algorithm 1); 1: aligned to multiples
   int no_clamp;      // 1: negative Tait pressure kept

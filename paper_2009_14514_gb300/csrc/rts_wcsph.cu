@@ -185,95 +185,175 @@ static __device__ __noinline__ int level_from_near(const DevParams& P, uint32_t 
   return L;
 }
 
-// Raw level of every filled block (Section 3.1 steps 1-2) from the stamped FP32 block
-// maxima; in the rare undecided case the exact decision of the double-precision
-// definition is taken from the block's particles (level_exact_warp, the warp working on
-// one such block at a time).  The blocks: the sort's filled list, and with stale (a pass
-// that kept the sort) also filled2, the blocks filled since; a block whose maxima carry
-// an older stamp has emptied since the sort and gets no level.
-__global__ void k_block_level(DevParams P, const uint32_t* __restrict__ filled,
-                              const int* __restrict__ nfilled, const uint32_t* __restrict__ filled2,
-                              const int* __restrict__ nfilled2, const uint32_t* __restrict__ cstart,
-                              const uint32_t* __restrict__ key_cur, int stale,
-                              const uint32_t* __restrict__ near, const int* __restrict__ n_near,
-                              const float4* __restrict__ v, const float4* __restrict__ a,
-                              const float4* __restrict__ ap,
-                              const unsigned long long* __restrict__ bmax_v,
-                              const unsigned long long* __restrict__ bmax_a, uint32_t stamp,
-                              uint32_t* __restrict__ raw) {
+// Raw levels (Section 3.1 steps 1-2) and R_min (Section 4.2) of every filled block in one
+// pass, so that no pass over the grid has to finish between the raw levels and their
+// minimum.  The thread of a filled block reads the stamped FP32 maxima of the block and
+// its 26 neighbours (a neighbour whose maxima carry an older stamp holds no particle now
+// and takes no part; an offset outside the grid stands for the block itself, which
+// leaves the minimum unchanged).
+//
+// When both thresholds are non-increasing in the level (levels_monotone: a coarser level
+// never admits a larger speed or acceleration), the levels a block passes on speed alone
+// form a prefix 0..Lv of the levels, likewise on acceleration, and its raw level is the
+// largest Eq. 1-admissible level up to min(Lv, La), a non-decreasing function of that
+// minimum; the smallest raw level over the 27 blocks is therefore the raw level of the
+// union of their particles, decided from the largest of their maxima.  Only when that
+// decision is undecided (a maximum within 1e-5 of a threshold) does the thread decide
+// each neighbour's raw level on its own and take the minimum, as it always does without
+// the monotone thresholds.  An undecided raw level is taken from the block's particles
+// with the exact decision of the double-precision definition (level_from_near /
+// level_exact_warp) by the whole warp, one (lane, neighbour) at a time.
+// The blocks: the sort's filled list, and with stale (a pass that kept the sort) also
+// filled2, the blocks filled since; a block whose maxima carry an older stamp has emptied
+// since the sort and gets no level.  Writes the raw level (raw) and R_min, or the forced
+// level (blevel), both stamped.
+// A lower bound of the exact level from FP32 maxima: every threshold within 1e-5 of them
+// counts as failed (the exact decision can only pass it).
+__device__ __forceinline__ int pick_level_lo(const DevParams& P, float v2, float a2) {
+  int L = 0;
+  for (int l = 0; l < P.n_levels; ++l) {
+    const float tv = P.vthr2f[l], ta = P.athr2f[l];
+    const bool ok_v = isfinite(tv) ? v2 < tv - 1e-5f * tv : true;
+    const bool ok_a = isfinite(ta) ? a2 < ta - 1e-5f * ta : true;
+    if (P.eq1[l] && ok_v && ok_a) L = l;
+  }
+  return L;
+}
+
+// Neighbour k (9 (dz + 1) + 3 (dy + 1) + dx + 1) of block (bx, by, bz); an axis that
+// leaves the grid keeps the block's own coordinate.
+__device__ __forceinline__ uint32_t nbr_block(const DevParams& P, int bx, int by, int bz, int k) {
+  const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+  const int cx = (bx + dx >= 0 && bx + dx < P.nx) ? bx + dx : bx;
+  const int cy = (by + dy >= 0 && by + dy < P.ny) ? by + dy : by;
+  const int cz = (bz + dz >= 0 && bz + dz < P.nz) ? bz + dz : bz;
+  return ((uint32_t)cz * P.ny + cy) * P.nx + cx;
+}
+
+__global__ void k_block_levels(DevParams P, const uint32_t* __restrict__ filled,
+                               const int* __restrict__ nfilled, const uint32_t* __restrict__ filled2,
+                               const int* __restrict__ nfilled2, const uint32_t* __restrict__ cstart,
+                               const uint32_t* __restrict__ key_cur, int stale,
+                               const uint32_t* __restrict__ near, const int* __restrict__ n_near,
+                               const float4* __restrict__ v, const float4* __restrict__ a,
+                               const float4* __restrict__ ap,
+                               const unsigned long long* __restrict__ bmax_v,
+                               const unsigned long long* __restrict__ bmax_a, uint32_t stamp,
+                               uint32_t* __restrict__ raw, uint32_t* __restrict__ blevel) {
   pdl_wait();
   const int nf1 = *nfilled;
   const int nf = nf1 + (stale ? *nfilled2 : 0);
   const int nn = stale ? *n_near : 0;   // beyond kNearCap the sorted cells are scanned
   const int lane = threadIdx.x & 31;
   const int wstride = gridDim.x * blockDim.x;
-  // warp-uniform trip count (the fallback needs every lane)
+  const int pl = P.nx * P.ny;
+  // warp-uniform trip count (the exact decision needs every lane)
   for (int t0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; t0 < nf; t0 += wstride) {
     const int t = t0 + lane;
     uint32_t b = 0;
-    int L = 0;
-    bool undecided = false, live = false;
-    float vm = 0.f, am = 0.f;
+    bool live = false;
+    int bx = 0, by = 0, bz = 0, own = 0, lmin = P.n_levels;
+    uint32_t undec = 0;   // blocks (bit 9 (dz + 1) + 3 (dy + 1) + dx + 1) still to decide
     if (t < nf) {
       b = t < nf1 ? filled[t] : filled2[t - nf1];
-      const unsigned long long rv = bmax_v[b], ra = bmax_a[b];
-      live = (uint32_t)(rv >> 32) == stamp;
-      vm = __uint_as_float((uint32_t)rv);
-      am = __uint_as_float((uint32_t)ra);
-      if (live) L = pick_level_f(P, vm, am, &undecided);
+      bx = (int)(b % (uint32_t)P.nx);
+      const int rr = (int)(b / (uint32_t)P.nx);
+      by = rr % P.ny;
+      bz = rr / P.ny;
+      const int ox[3] = {bx > 0 ? -1 : 0, 0, bx + 1 < P.nx ? 1 : 0};
+      const int oy[3] = {by > 0 ? -P.nx : 0, 0, by + 1 < P.ny ? P.nx : 0};
+      const int oz[3] = {bz > 0 ? -pl : 0, 0, bz + 1 < P.nz ? pl : 0};
+      // the block's own maxima and those of the union (FP32 bits of non-negative values:
+      // ordered as integers); the block's own stamp is checked after the loads
+      uint32_t uv = 0, ua = 0, cv = 0, ca = 0;
+#pragma unroll
+      for (int zl = 0; zl < 3; ++zl) {
+        unsigned long long rv[9], ra[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {   // one layer's 18 loads in flight together
+          const int nb = (int)b + ox[q % 3] + oy[q / 3] + oz[zl];
+          rv[q] = bmax_v[nb];
+          ra[q] = bmax_a[nb];
+        }
+        if (zl == 1) {
+          live = (uint32_t)(rv[4] >> 32) == stamp;
+          cv = (uint32_t)rv[4];
+          ca = (uint32_t)ra[4];
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          if ((uint32_t)(rv[q] >> 32) != stamp) continue;
+          uv = (uint32_t)rv[q] > uv ? (uint32_t)rv[q] : uv;
+          ua = (uint32_t)ra[q] > ua ? (uint32_t)ra[q] : ua;
+        }
+      }
+      if (live) {
+        bool u_own = false, u_all = !P.levels_monotone;
+        own = pick_level_f(P, __uint_as_float(cv), __uint_as_float(ca), &u_own);
+        if (u_own) undec |= 1u << 13;
+        if (!u_all) lmin = pick_level_f(P, __uint_as_float(uv), __uint_as_float(ua), &u_all);
+        if (u_all) {   // every block on its own: decided ones now, undecided ones below
+          lmin = P.n_levels;
+          for (int k = 0; k < 27; ++k) {
+            const uint32_t nb = nbr_block(P, bx, by, bz, k);
+            const unsigned long long rv = bmax_v[nb];
+            if ((uint32_t)(rv >> 32) != stamp) continue;
+            bool u = false;
+            const int lk = pick_level_f(P, __uint_as_float((uint32_t)rv),
+                                        __uint_as_float((uint32_t)bmax_a[nb]), &u);
+            if (u) undec |= 1u << k;
+            else lmin = lk < lmin ? lk : lmin;
+          }
+          // an undecided neighbour whose level cannot fall below the decided minimum
+          // (every threshold near its maxima taken as failed) need not be decided
+          for (uint32_t mm = undec & ~(1u << 13); mm; mm &= mm - 1u) {
+            const int k = __ffs(mm) - 1;
+            const uint32_t nb = nbr_block(P, bx, by, bz, k);
+            if (pick_level_lo(P, __uint_as_float((uint32_t)bmax_v[nb]),
+                              __uint_as_float((uint32_t)bmax_a[nb])) >= lmin)
+              undec &= ~(1u << k);
+          }
+        }
+      }
     }
-    for (unsigned m = __ballot_sync(kFull, undecided); m; m &= m - 1u) {
+    // undecided raw levels: the exact decision, warp-wide, one (lane, block) at a time
+    for (;;) {
+      const int k = undec ? __ffs(undec) - 1 : -1;
+      const unsigned m = __ballot_sync(kFull, k >= 0);
+      if (!m) break;
       const int src = __ffs(m) - 1;
-      const uint32_t bu = __shfl_sync(kFull, b, src);
-      const float vmu = __shfl_sync(kFull, vm, src), amu = __shfl_sync(kFull, am, src);
-      const int Lu = (stale && nn <= kNearCap)
+      const uint32_t nbk = k >= 0 ? nbr_block(P, bx, by, bz, k) : 0u;
+      const uint32_t bu = __shfl_sync(kFull, nbk, src);
+      const float vmu = __uint_as_float((uint32_t)bmax_v[bu]);
+      const float amu = __uint_as_float((uint32_t)bmax_a[bu]);
+      const int lu = (stale && nn <= kNearCap)
                          ? level_from_near(P, bu, vmu, amu, near, nn, key_cur, v, a, lane)
                          : level_exact_warp(P, bu, stale, cstart, key_cur, v, a, ap, lane);
-      if (lane == src) L = Lu;
+      // every lane takes it for each of its blocks that is bu (after the union's decision
+      // a block's own level is never below it: the minimum keeps that decision)
+      for (uint32_t mm = undec; mm; mm &= mm - 1u) {
+        const int kk = __ffs(mm) - 1;
+        if (nbr_block(P, bx, by, bz, kk) != bu) continue;
+        if (kk == 13) own = lu;
+        lmin = lu < lmin ? lu : lmin;
+        undec &= ~(1u << kk);
+      }
     }
-    if (live) raw[b] = (stamp << 8) | (uint32_t)L;
+    if (live) {
+      raw[b] = (stamp << 8) | (uint32_t)own;
+      blevel[b] = (stamp << 8) | (uint32_t)(P.force_level >= 0 ? P.force_level : lmin);
+    }
   }
 }
 
-// R_min (Section 4.2: a filled block takes the smallest level among itself and its
-// filled 26 neighbours, one Jacobi pass), or the forced / global level.
-// stale: the sort's list and filled2 (a pass that kept the sort); a block without a raw
-// level of this pass has emptied since the sort and is skipped.
-__global__ void k_block_rmin(DevParams P, int mode, int level_g,
-                             const uint32_t* __restrict__ filled, const int* __restrict__ nfilled,
-                             const uint32_t* __restrict__ filled2, const int* __restrict__ nfilled2,
-                             int stale, const uint32_t* __restrict__ raw,
-                             uint32_t* __restrict__ blevel, uint32_t stamp) {
+// Global adaptive stepping: every filled block takes the step's level.
+__global__ void k_block_set_level(int level_g, const uint32_t* __restrict__ filled,
+                                  const int* __restrict__ nfilled, uint32_t* __restrict__ blevel,
+                                  uint32_t stamp) {
   pdl_wait();
-  const int nf1 = *nfilled;
-  const int nf = nf1 + (stale ? *nfilled2 : 0);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
-    const uint32_t b = t < nf1 ? filled[t] : filled2[t - nf1];
-    if (stale && (raw[b] >> 8) != stamp) continue;
-    int L;
-    if (mode == kActGlobal) {
-      L = level_g;
-    } else if (P.force_level >= 0) {
-      L = P.force_level;
-    } else {
-      // the 27 records are loaded independently (an offset outside the grid reads the
-      // block's own record instead, which leaves the minimum unchanged)
-      const int bx = b % P.nx, r = b / P.nx, by = r % P.ny, bz = r / P.ny;
-      const int xm = bx > 0 ? -1 : 0, xp = bx + 1 < P.nx ? 1 : 0;
-      const int ym = by > 0 ? -(int)P.nx : 0, yp = by + 1 < P.ny ? (int)P.nx : 0;
-      const int pl = P.nx * P.ny;
-      const int zm = bz > 0 ? -pl : 0, zp = bz + 1 < P.nz ? pl : 0;
-      const int ox[3] = {xm, 0, xp}, oy[3] = {ym, 0, yp}, oz[3] = {zm, 0, zp};
-      uint32_t rc[27];
-#pragma unroll
-      for (int k = 0; k < 27; ++k) rc[k] = raw[(int)b + ox[k % 3] + oy[(k / 3) % 3] + oz[k / 9]];
-      L = (int)(rc[13] & 0xffu);
-#pragma unroll
-      for (int k = 0; k < 27; ++k)
-        if ((rc[k] >> 8) == stamp && (int)(rc[k] & 0xffu) < L) L = (int)(rc[k] & 0xffu);
-    }
-    blevel[b] = (stamp << 8) | (uint32_t)L;
-  }
+  const int nf = *nfilled;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x)
+    blevel[filled[t]] = (stamp << 8) | (uint32_t)level_g;
 }
 
 // Algorithm 1's per-particle bookkeeping, in block order: validity -= 1; compute iff
@@ -292,7 +372,7 @@ struct LevelPhase {
   int v[kMaxLevels];
 };
 
-__global__ void __launch_bounds__(kActThreads) k_particle_activity(
+__global__ void __launch_bounds__(kActThreads, 8) k_particle_activity(
     DevParams P, int mode, int mult_g, LevelPhase kmod, int n, const uint32_t* __restrict__ key,
     const uint32_t* __restrict__ key_cur, const uint32_t* __restrict__ blevel, uint32_t stamp,
     PState s, uint8_t* __restrict__ cflag,
@@ -310,96 +390,100 @@ __global__ void __launch_bounds__(kActThreads) k_particle_activity(
       if ((int)threadIdx.x == l) val = kmod.v[l];
     s_kmod[threadIdx.x] = val;
   }
-  if (threadIdx.x < 2) scount[threadIdx.x] = 0u;
-  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned below = (1u << lane) - 1u;
-  const int base0 = blockIdx.x * (kActThreads * kActItems) + w * (32 * kActItems) + lane;
-  // loads of every item first (the block record depends on the key).  bk: the block the
-  // particle is sorted in (its work-list entry); its level is that of its current block.
-  uint32_t bk[kActItems], rec[kActItems], ck[kActItems];
-  int vold[kActItems], lold[kActItems];
-#pragma unroll
-  for (int it = 0; it < kActItems; ++it) {
-    const int i = base0 + 32 * it;
-    bk[it] = i < n ? key[i] : 0xffffffffu;
-    ck[it] = i < n ? key_cur[i] : 0xffffffffu;
-    vold[it] = (i < n && mode == kActRegional) ? s.valid[i] : 0;
-    lold[it] = (i < n && mode == kActRegional) ? s.level[i] : 0;
-  }
-#pragma unroll
-  for (int it = 0; it < kActItems; ++it)
-    rec[it] = ck[it] < (uint32_t)P.nblocks ? blevel[ck[it]] : 0u;
-#pragma unroll
-  for (int it = 0; it < kActItems; ++it) {
-    const int i = base0 + 32 * it;
-    const bool valid = i < n;
-    bool c = false;
-    const uint32_t b = bk[it];
-    if (valid) {
-      int L = (int)(rec[it] & 0xffu);
-      if ((rec[it] >> 8) != stamp || L >= P.n_levels) {
-        check_failed(ctl, kChkLevel, rec[it]);
-        L = 0;
-      }
-      const int mb = mode == kActGlobal ? mult_g : P.mult[L];
-      // validity of a particle that starts a true step now (level-aligned variant: up
-      // to the next multiple of the multiplier)
-      const int vnew = (mode != kActGlobal && P.level_clock) ? mb - s_kmod[L] : mb;
-      if (mode == kActRegional) {
-        int val = vold[it] - 1;
-        int li = lold[it];
-        if (li >= P.n_levels) {
-          check_failed(ctl, kChkLevel, (unsigned)li);
-          li = -1;
+  // a grid of resident CTAs, each taking chunks of kActThreads x kActItems particles
+  for (int chunk = blockIdx.x; chunk * (kActThreads * kActItems) < n; chunk += gridDim.x) {
+    if (threadIdx.x < 2) scount[threadIdx.x] = 0u;
+    __syncthreads();   // (also: the previous chunk's lists are written out)
+    const int base0 = chunk * (kActThreads * kActItems) + w * (32 * kActItems) + lane;
+    // loads of every item first (the block record depends on the key).  bk: the block the
+    // particle is sorted in (its work-list entry); its level is that of its current block.
+    uint32_t bk[kActItems], rec[kActItems], ck[kActItems];
+    int vold[kActItems], lold[kActItems];
+  #pragma unroll
+    for (int it = 0; it < kActItems; ++it) {
+      const int i = base0 + 32 * it;
+      bk[it] = i < n ? key[i] : 0xffffffffu;
+      ck[it] = i < n ? key_cur[i] : 0xffffffffu;
+      vold[it] = (i < n && mode == kActRegional) ? s.valid[i] : 0;
+      lold[it] = (i < n && mode == kActRegional) ? s.level[i] : 0;
+    }
+  #pragma unroll
+    for (int it = 0; it < kActItems; ++it)
+      rec[it] = ck[it] < (uint32_t)P.nblocks ? blevel[ck[it]] : 0u;
+  #pragma unroll
+    for (int it = 0; it < kActItems; ++it) {
+      const int i = base0 + 32 * it;
+      const bool valid = i < n;
+      bool c = false;
+      const uint32_t b = bk[it];
+      if (valid) {
+        int L = (int)(rec[it] & 0xffu);
+        if ((rec[it] >> 8) != stamp || L >= P.n_levels) {
+          check_failed(ctl, kChkLevel, rec[it]);
+          L = 0;
         }
-        if (val <= 0 || li < 0 || P.mult[li] != mb) {
+        const int mb = mode == kActGlobal ? mult_g : P.mult[L];
+        // validity of a particle that starts a true step now (level-aligned variant: up
+        // to the next multiple of the multiplier)
+        const int vnew = (mode != kActGlobal && P.level_clock) ? mb - s_kmod[L] : mb;
+        if (mode == kActRegional) {
+          int val = vold[it] - 1;
+          int li = lold[it];
+          if (li >= P.n_levels) {
+            check_failed(ctl, kChkLevel, (unsigned)li);
+            li = -1;
+          }
+          if (val <= 0 || li < 0 || P.mult[li] != mb) {
+            c = true;
+            s.level[i] = L;
+            val = vnew;
+          }
+          s.valid[i] = val;
+        } else {
           c = true;
           s.level[i] = L;
-          val = vnew;
+          s.valid[i] = vnew;
         }
-        s.valid[i] = val;
-      } else {
-        c = true;
-        s.level[i] = L;
-        s.valid[i] = vnew;
+        cflag[i] = c ? 1 : 0;
       }
-      cflag[i] = c ? 1 : 0;
+      const unsigned m = __ballot_sync(kFull, c);
+      // runs of equal blocks in lane order; a run with an evaluated particle claims its block
+      const uint32_t prevb = __shfl_up_sync(kFull, b, 1);
+      const bool head = valid && (lane == 0 || prevb != b);
+      const unsigned heads = __ballot_sync(kFull, head);
+      const unsigned after = heads & ~(below | (1u << lane));
+      const int next = after ? __ffs(after) - 1 : 32;
+      const unsigned span = (next - lane >= 32) ? (kFull << lane) : (((1u << (next - lane)) - 1u) << lane);
+      bool claim = false;
+      if (head && (m & span)) claim = atomicExch(&actflag[b], stamp) != stamp;
+      const unsigned cm = __ballot_sync(kFull, claim);
+      uint32_t op = 0, oa = 0;
+      if (lane == 0) {
+        if (m) op = atomicAdd(&scount[0], (uint32_t)__popc(m));
+        if (cm) oa = atomicAdd(&scount[1], (uint32_t)__popc(cm));
+      }
+      op = __shfl_sync(kFull, op, 0);
+      oa = __shfl_sync(kFull, oa, 0);
+      if (c) sp[op + __popc(m & below)] = (uint32_t)i;
+      if (claim) sa[oa + __popc(cm & below)] = b;
     }
-    const unsigned m = __ballot_sync(kFull, c);
-    // runs of equal blocks in lane order; a run with an evaluated particle claims its block
-    const uint32_t prevb = __shfl_up_sync(kFull, b, 1);
-    const bool head = valid && (lane == 0 || prevb != b);
-    const unsigned heads = __ballot_sync(kFull, head);
-    const unsigned after = heads & ~(below | (1u << lane));
-    const int next = after ? __ffs(after) - 1 : 32;
-    const unsigned span = (next - lane >= 32) ? (kFull << lane) : (((1u << (next - lane)) - 1u) << lane);
-    bool claim = false;
-    if (head && (m & span)) claim = atomicExch(&actflag[b], stamp) != stamp;
-    const unsigned cm = __ballot_sync(kFull, claim);
-    uint32_t op = 0, oa = 0;
-    if (lane == 0) {
-      if (m) op = atomicAdd(&scount[0], (uint32_t)__popc(m));
-      if (cm) oa = atomicAdd(&scount[1], (uint32_t)__popc(cm));
+    __syncthreads();
+    if (threadIdx.x == 0) {   // one atomic per list and counter
+      const uint32_t tp = scount[0], ta = scount[1];
+      sbase[0] = tp ? (uint32_t)atomicAdd(&ctl->n_plist, (int)tp) : 0u;
+      sbase[1] = ta ? (uint32_t)atomicAdd(&ctl->n_act, (int)ta) : 0u;
+      if (tp) {
+        atomicAdd(&ctl->evals, (unsigned long long)tp);
+        atomicAdd(&ctl->act_blocks, (unsigned long long)ta);
+      }
     }
-    op = __shfl_sync(kFull, op, 0);
-    oa = __shfl_sync(kFull, oa, 0);
-    if (c) sp[op + __popc(m & below)] = (uint32_t)i;
-    if (claim) sa[oa + __popc(cm & below)] = b;
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < scount[0]; k += blockDim.x) plist[sbase[0] + k] = sp[k];
+    for (uint32_t k = threadIdx.x; k < scount[1]; k += blockDim.x) act[sbase[1] + k] = sa[k];
+    __syncthreads();
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {   // one atomic per list and counter
-    const uint32_t tp = scount[0], ta = scount[1];
-    sbase[0] = tp ? (uint32_t)atomicAdd(&ctl->n_plist, (int)tp) : 0u;
-    sbase[1] = ta ? (uint32_t)atomicAdd(&ctl->n_act, (int)ta) : 0u;
-    if (tp) {
-      atomicAdd(&ctl->evals, (unsigned long long)tp);
-      atomicAdd(&ctl->act_blocks, (unsigned long long)ta);
-    }
-  }
-  __syncthreads();
-  for (uint32_t k = threadIdx.x; k < scount[0]; k += blockDim.x) plist[sbase[0] + k] = sp[k];
-  for (uint32_t k = threadIdx.x; k < scount[1]; k += blockDim.x) act[sbase[1] + k] = sa[k];
 }
 
 // ---------------------------------------------------------------- kernel W ---
@@ -645,6 +729,141 @@ __device__ __forceinline__ uint32_t stale_runs(const DevParams& P, float3 lo, fl
   return total;
 }
 
+// The density pass with one lane per particle, for a pass that sorted and evaluates at
+// least half of the particles: each warp takes 32 consecutive sorted positions, and each
+// lane whose particle is evaluated walks the 18 runs of its block's stencil (the fluid
+// and boundary particles of the x range [bx - 1, bx + 1] of each of the 9 (dy, dz) rows)
+// straight from the sorted arrays, which the warp's lanes share through L1 (they lie in a
+// few neighbouring blocks).  Runs are taken 32 candidates at a time: distance tests only
+// (a bit per candidate inside the guard band), then the exact predicate, kernel sum and
+// list entry for those.  The neighbour list of a particle is in stencil order: fluid rows
+// then boundary rows, each in sorted order.
+__device__ __forceinline__ bool dense_pass(const DevParams& P, int np) {
+  return np > 0 && 2 * (long long)np >= (long long)P.n_fluid;
+}
+
+constexpr int kDenseThreads = 256;
+
+__global__ void __launch_bounds__(kDenseThreads) k_density_dense(
+    DevParams P, const uint32_t* __restrict__ key, Ctl* ctl, const uint32_t* __restrict__ cstart,
+    const uint32_t* __restrict__ bcstart, PState s, const float4* __restrict__ xb,
+    const uint8_t* __restrict__ cflag, uint32_t* __restrict__ nbl) {
+  pdl_wait();
+  if (!dense_pass(P, *(volatile int*)&ctl->n_plist)) return;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int n = P.n_fluid;
+  const int pl = P.nx * P.ny;
+  const float4 far = make_float4(3e38f, 3e38f, 3e38f, 0.f);
+  unsigned long long pairs = 0, tests = 0;
+  for (int base = warp * 32; base < n; base += nwarps * 32) {
+    const int i = base + lane;
+    if (i >= n || !cflag[i]) continue;
+    const float4 xi = s.x[i];
+    const uint32_t b = key[i];
+    if (b >= (uint32_t)P.nblocks) {
+      check_failed(ctl, kChkActive, b);
+      continue;
+    }
+    const int bx = (int)(b % (uint32_t)P.nx), rr = (int)(b / (uint32_t)P.nx);
+    const int by = rr % P.ny, bz = rr / P.ny;
+    const int xlo = bx > 0 ? bx - 1 : 0, xhi = bx + 1 < P.nx ? bx + 1 : P.nx - 1;
+    uint32_t* list = nbl + (size_t)i * P.nbl_cap;
+    float wsum = 0.f;
+    int nn = 0;
+    uint32_t ncand = 0;
+    for (int r = 0; r < 18; ++r) {   // runs 0-8 fluid, 9-17 boundary
+      const int row = r < 9 ? r : r - 9;
+      const int cz = bz + row / 3 - 1, cy = by + row % 3 - 1;
+      if (cz < 0 || cz >= P.nz || cy < 0 || cy >= P.ny) continue;
+      const uint32_t rb = (uint32_t)cz * (uint32_t)pl + (uint32_t)cy * (uint32_t)P.nx;
+      const uint32_t* cs = r < 9 ? cstart : bcstart;
+      const float4* X = r < 9 ? s.x : xb;
+      const uint32_t tag = r < 9 ? 0u : kBoundaryBit;
+      const uint32_t lim = (uint32_t)(r < 9 ? P.n_fluid : P.n_bound);
+      const uint32_t js = __ldg(&cs[rb + xlo]);
+      uint32_t je = __ldg(&cs[rb + xhi + 1]);
+      if (je > lim || js > je) {
+        check_failed(ctl, kChkRun, je);
+        je = js > lim ? js : lim;
+        if (js >= je) continue;
+      }
+      ncand += je - js;
+      for (uint32_t j0 = js; j0 < je; j0 += 32) {
+        const uint32_t cnt = je - j0 < 32u ? je - j0 : 32u;
+        // distance tests only, four candidates' loads in flight at a time (past the end
+        // of the run a far point, never near)
+        uint32_t near = 0;
+        for (uint32_t t0 = 0; t0 < cnt; t0 += 4) {
+          float4 xj[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) xj[u] = t0 + u < cnt ? X[j0 + t0 + u] : far;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float dx = xi.x - xj[u].x, dy = xi.y - xj[u].y, dz = xi.z - xj[u].z;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            near |= d2 < P.r2_hi ? (1u << (t0 + u)) : 0u;
+          }
+        }
+        // the exact predicate, kernel sum and list entry of the near ones
+        for (uint32_t m = near; m; m &= m - 1u) {
+          const uint32_t j = j0 + (uint32_t)(__ffs(m) - 1);
+          const float4 xj = X[j];
+          const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+          const float d2 = dx * dx + dy * dy + dz * dz;
+          if (!(d2 < P.r2_lo || nbr_exact(P, xi, xj))) continue;
+          bool put = true;
+          if (d2 > 0.f) {
+            wsum += spline_W(P, d2 * rsqrtf(d2) * P.inv_h);
+          } else {
+            wsum += P.sigma;   // the particle itself, or a coincident neighbour
+            put = tag != 0u || j != (uint32_t)i;
+          }
+          if (put) {
+            if (nn < P.nbl_cap) list[nn] = j | tag;
+            ++nn;
+          }
+        }
+      }
+    }
+    if (nn > P.nbl_cap) set_status(ctl, RTS_ERR_CAPACITY);
+    const float rho = P.m * wsum;
+    const float p = tait(P, rho);
+    s.rho[i] = rho;
+    s.prs[i] = p;
+    s.nbr[i] = nn;
+    s.x[i].w = p / (rho * rho);
+    s.v[i].w = rho;
+    pairs += (unsigned long long)nn;
+    tests += ncand;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    pairs += __shfl_down_sync(kFull, pairs, o);
+    tests += __shfl_down_sync(kFull, tests, o);
+  }
+  // one atomic per counter and CTA (every candidate is tested: no cull)
+  __shared__ unsigned long long red[2][kDenseThreads / 32];
+  if (lane == 0) {
+    red[0][wib] = pairs;
+    red[1][wib] = tests;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, t = 0;
+    for (int k = 0; k < kDenseThreads / 32; ++k) {
+      a += red[0][k];
+      t += red[1][k];
+    }
+    if (a) atomicAdd(&ctl->pairs, a);
+    if (t) {
+      atomicAdd(&ctl->cands, t);
+      atomicAdd(&ctl->kept, t);
+    }
+  }
+}
+
 // Density pass (Algorithm 1, "find neighborhoods" and "update rho, p"): every evaluated
 // particle tests the candidates kept for its group with the exact predicate, sums m W
 // over its neighbours (itself included), applies the Tait equation and records its
@@ -655,6 +874,7 @@ __device__ __forceinline__ uint32_t stale_runs(const DevParams& P, float3 lo, fl
 // the 27 blocks around the active block.
 template <bool kStale>
 __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const uint32_t* __restrict__ act,
+                                                        const uint32_t* __restrict__ plist,
                                                         Ctl* ctl, const uint32_t* __restrict__ cstart,
                                                         const uint32_t* __restrict__ bcstart, PState s,
                                                         const float4* __restrict__ xb,
@@ -673,17 +893,36 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n_act = *(volatile int*)&ctl->n_act;
   const float dlt = kStale ? __uint_as_float(*(volatile unsigned int*)&ctl->disp_bits[stamp & 1]) : 0.f;
+  // kStale with at most one evaluated particle per warp of the grid (the substeps where
+  // only the finest levels are due): one warp per particle (all 32 lanes on its
+  // candidates) instead of one per active block, so that no warp walks a block with many
+  // evaluated particles while the others idle
+  const int np = *(volatile int*)&ctl->n_plist;
+  // a sorted pass that evaluates at least half of the particles runs k_density_dense
+  if (!kStale && dense_pass(P, np)) return;
+  const bool by_particle = kStale && np <= nwarps;
+  const int n_items = by_particle ? np : n_act;
   unsigned long long pairs = 0, tests = 0, kept_tests = 0;
-  for (int t = warp; t < n_act; t += nwarps) {
-    const uint32_t b = act[t];
-    if (b >= (uint32_t)P.nblocks) {
-      if (lane == 0) check_failed(ctl, kChkActive, b);
-      continue;
+  for (int t = warp; t < n_items; t += nwarps) {
+    uint32_t beg = 0, end = 1;   // by_particle: one group, the particle plist[t]
+    if (by_particle) {
+      if (plist[t] >= (uint32_t)P.n_fluid) {
+        if (lane == 0) check_failed(ctl, kChkActive, plist[t]);
+        continue;
+      }
+    } else {
+      const uint32_t b = act[t];
+      if (b >= (uint32_t)P.nblocks) {
+        if (lane == 0) check_failed(ctl, kChkActive, b);
+        continue;
+      }
+      beg = cstart[b];
+      end = cstart[b + 1];
     }
-    const uint32_t beg = cstart[b], end = cstart[b + 1];
     uint32_t total = 0;
     int nfr = 9, nr = 18;
     if (!kStale) {
+      const uint32_t b = act[t];
       const int bx = b % P.nx, rr = b / P.nx, by = rr % P.ny, bz = rr / P.ny;
       const Runs R = block_runs(P, bx, by, bz, cstart, bcstart, lane);
       total = R.total;
@@ -702,7 +941,15 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
     }
     for (uint32_t base = beg; base < end; base += 32) {
       Group G;
-      if (!next_group(base, end, cflag, lane, G)) continue;
+      if (by_particle) {
+        G.i = (int)plist[t];
+        G.lpp = 32;
+        G.pid = 0;
+        G.sub = lane;
+        G.gmask = kFull;
+      } else if (!next_group(base, end, cflag, lane, G)) {
+        continue;
+      }
       const int i = G.i;
       const bool gvalid = i >= 0;
       const uint32_t lpp = (uint32_t)G.lpp, sub = (uint32_t)G.sub;
@@ -1084,7 +1331,7 @@ static size_t density_smem(bool stale) {
 
 // Persistent grids: every resident slot of every SM, per kernel (the force and
 // correction passes hold fewer registers and no shared memory, so more warps fit).
-static int g_grid_force = 0, g_grid_stale = 0;
+static int g_grid_force = 0, g_grid_stale = 0, g_grid_levels = 0, g_grid_act = 0, g_grid_dense = 0;
 int neighbor_grid_size() {
   int occ0 = 1, occ1 = 1, occ2 = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_density<false>, kNbThreads, density_smem(false));
@@ -1093,8 +1340,18 @@ int neighbor_grid_size() {
   if (occ0 < 1) occ0 = 1;
   if (occ1 < 1) occ1 = 1;
   if (occ2 < 1) occ2 = 1;
+  int occ3 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_block_levels, 256, 0);
+  if (occ3 < 1) occ3 = 1;
   g_grid_force = sm_count() * occ1;
   g_grid_stale = sm_count() * occ2;
+  g_grid_levels = sm_count() * occ3;   // one resident wave; threads loop over the blocks
+  int occ5 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ5, k_density_dense, kDenseThreads, 0);
+  g_grid_dense = sm_count() * (occ5 < 1 ? 1 : occ5);
+  int occ4 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ4, k_particle_activity, kActThreads, 0);
+  g_grid_act = sm_count() * (occ4 < 1 ? 1 : occ4);
   return sm_count() * occ0;
 }
 static int force_grid(const rts_ctx* c) { return g_grid_force > 0 ? g_grid_force : c->grid_persistent; }
@@ -1107,26 +1364,30 @@ static const int* new_count(rts_ctx* c) { return &c->ctl->n_filled_light[c->stam
 
 rts_status launch_classify(rts_ctx* c, bool stale) {
   note_launch(c, 1);
-  launch_pdl(c->stream, k_block_level, filled_grid(), 256, 0, c->dp, (const uint32_t*)c->filled,
+  launch_pdl(c->stream, k_block_levels, g_grid_levels > 0 ? g_grid_levels : filled_grid(), 256, 0,
+             c->dp, (const uint32_t*)c->filled,
              (const int*)&c->ctl->n_filled, (const uint32_t*)c->filled_new, new_count(c),
              (const uint32_t*)c->cstart, (const uint32_t*)(stale ? c->key_cur : c->key),
              stale ? 1 : 0, (const uint32_t*)c->near_list, (const int*)&c->ctl->n_near[c->stamp & 1],
-             c->s.v, c->s.a, c->s.ap, c->bmax_v, c->bmax_a, c->stamp, c->raw);
+             c->s.v, c->s.a, c->s.ap, c->bmax_v, c->bmax_a, c->stamp, c->raw, c->blevel);
   return RTS_OK;
 }
 
-// mode < 0: smoothing only (public classification); otherwise smoothing + activity.
-// The work-list counters n_act and n_plist were reset by the key pass of this step's
-// binning (every step bins before its activity pass).
+// The block levels of this step: R_min from launch_classify, which every step of the
+// regional modes launches first, or (global adaptive) the step's level.  mode < 0: the
+// block levels only (public classification); otherwise also the activity pass.  The
+// work-list counters n_act and n_plist were reset by the key pass of this step's binning
+// (every step bins before its activity pass).
 rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_t k1, bool stale) {
-  note_launch(c, 1);
-  launch_pdl(c->stream, k_block_rmin, filled_grid(), 256, 0, c->dp, mode, level_g,
-             (const uint32_t*)c->filled, (const int*)&c->ctl->n_filled,
-             (const uint32_t*)c->filled_new, new_count(c), stale ? 1 : 0,
-             (const uint32_t*)c->raw, c->blevel, c->stamp);
+  if (mode == kActGlobal) {
+    note_launch(c, 1);
+    launch_pdl(c->stream, k_block_set_level, filled_grid(), 256, 0, level_g,
+               (const uint32_t*)c->filled, (const int*)&c->ctl->n_filled, c->blevel, c->stamp);
+  }
   if (mode >= 0 && c->n > 0) {
     note_launch(c, 1);
-    const int g = (c->n + kActThreads * kActItems - 1) / (kActThreads * kActItems);
+    int g = (c->n + kActThreads * kActItems - 1) / (kActThreads * kActItems);
+    if (g_grid_act > 0 && g > g_grid_act) g = g_grid_act;
     LevelPhase kmod;
     for (int L = 0; L < kMaxLevels; ++L)
       kmod.v[L] = L < c->p.n_levels ? (int)(k1 % (int64_t)c->p.level_mult[L]) : 0;
@@ -1141,12 +1402,19 @@ rts_status launch_density(rts_ctx* c, bool stale) {
   note_launch(c, 1);
   if (stale)
     launch_pdl(c->stream, k_density<true>, g_grid_stale > 0 ? g_grid_stale : c->grid_persistent,
-               kNbThreads, density_smem(true), c->dp, c->act, c->ctl, c->cstart, c->bcstart, c->s,
-               c->xb, c->cflag, c->nbl, c->stamp);
-  else
+               kNbThreads, density_smem(true), c->dp, c->act, (const uint32_t*)c->plist, c->ctl,
+               c->cstart, c->bcstart, c->s, c->xb, c->cflag, c->nbl, c->stamp);
+  else {
+    // the two forms of a sorted pass: each finds from the evaluated-particle count
+    // whether it is the one to run, and the other returns at once
+    note_launch(c, 1);
+    launch_pdl(c->stream, k_density_dense, g_grid_dense > 0 ? g_grid_dense : c->grid_persistent,
+               kDenseThreads, 0, c->dp, (const uint32_t*)c->key, c->ctl, c->cstart, c->bcstart,
+               c->s, c->xb, c->cflag, c->nbl);
     launch_pdl(c->stream, k_density<false>, c->grid_persistent, kNbThreads, density_smem(false),
-               c->dp, c->act, c->ctl, c->cstart, c->bcstart, c->s, c->xb, c->cflag, c->nbl,
-               c->stamp);
+               c->dp, c->act, (const uint32_t*)c->plist, c->ctl, c->cstart, c->bcstart, c->s, c->xb,
+               c->cflag, c->nbl, c->stamp);
+  }
   return RTS_OK;
 }
 

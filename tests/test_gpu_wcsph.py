@@ -5,6 +5,8 @@ input state.  Bins, neighbour counts, block levels, activity flags: bit-exact.  
 1e-4 relative.  Accelerations: 1e-3 of the max-norm.  Positions and velocities after a
 substep: the consequences of those bounds (plus FP32 rounding of the predictor).
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -46,11 +48,17 @@ def test_bins_are_bit_exact(which):
 
 # ------------------------------------------------------------ classification ---
 
-@pytest.mark.parametrize("force_level", [-1, 2])
-def test_block_levels_are_bit_exact(force_level):
+# the third case: speed thresholds that rise from level 1 to level 2 (beta_3 / 4 >
+# beta_2 / 2), so the levels a block passes are not a prefix and R_min cannot be taken
+# from the union's maxima: every block is decided on its own
+@pytest.mark.parametrize("force_level,beta", [(-1, None), (2, None),
+                                              (-1, [math.inf, 0.4, 1.6, 0.016])])
+def test_block_levels_are_bit_exact(force_level, beta):
     sc = scenes.wcsph_dam_break_8k()
     st = dynamic_state(sc, seed=21)
     d = params(sc, force_level=force_level)
+    if beta is not None:
+        d["beta"] = beta
     P = O.make_params(d)
     ctx = gpu_ctx(sc, d)
     rts.rts_set_state(ctx, st["x"], st["v"], a=st["a"])
@@ -59,7 +67,7 @@ def test_block_levels_are_bit_exact(force_level):
     oraw, olev = O.classify_wcsph(P, st["x"], st["v"], st["a"])
     assert np.array_equal(raw, oraw)
     assert np.array_equal(lev, olev)
-    if force_level < 0:
+    if force_level < 0 and beta is None:
         assert len(set(oraw[oraw >= 0].tolist())) == 4        # every level occurs
 
 
