@@ -50,13 +50,15 @@ FLOPS_TEST = 8
 FLOPS_PAIR_DENSITY = 8
 FLOPS_PAIR_FORCE = 24
 # DRAM bytes (read + write) per evaluated particle of the density pass, from one-pass ncu
-# counters of every density launch in a window of the rollout itself (16 substeps from the
-# warm state at t = 1 s, --profile-warm); the traffic per launch of the benchmark is this
-# figure times the launch's evaluations.  Re-measure when k_density changes.
-DENSITY_DRAM_BYTES_PER_EVAL = 192.6
-DENSITY_TRAFFIC_SOURCE = ("ncu dram__bytes of every k_density launch of 16 substeps from the "
-                          "warm state at t = 1 s (profiles/k_density_warm_window_1m.md), "
-                          "192.6 B per evaluation, times this run's evaluations per launch")
+# counters of every density launch (k_density_dense and k_density) in a window of the
+# rollout itself (16 substeps from the warm state at t = 1 s, --profile-warm); the traffic
+# per pass of the benchmark is this figure times the pass's evaluations.  Re-measure when
+# a density kernel changes.
+DENSITY_DRAM_BYTES_PER_EVAL = 257.8
+DENSITY_TRAFFIC_SOURCE = ("ncu dram__bytes of every density launch (k_density_dense, k_density) "
+                          "of 16 substeps from the warm state at t = 1 s "
+                          "(profiles/k_density_warm_window_1m.md), 257.8 B per evaluation, "
+                          "times this run's evaluations per pass")
 
 
 def parse(argv=None):
@@ -364,9 +366,9 @@ def arm_summary(sc, r, dt_norm):
 
 def phase_total_ms(prof, ph):
     """Device time of a phase over the run: the sampled instances' mean times the
-    number of instances (every phase instance launches one kernel for these phases)."""
+    number of instances."""
     timed = max(1, prof["timed"][ph])
-    return prof["ms"][ph] / timed * prof["launches"][ph]
+    return prof["ms"][ph] / timed * prof["passes"][ph]
 
 
 def phase_split(prof, total_ms):
@@ -825,14 +827,18 @@ def main():
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     tests, pairs = ours["tot"]["candidate_tests"], ours["tot"]["pair_interactions"]
     kern = max(("density", "force"), key=lambda k: phase_total_ms(prof, k))
-    launches = max(1, prof["launches"][kern])
+    # per pass: a sorted density pass launches k_density_dense and k_density, of which the
+    # one that does not fit the pass returns at once; a pass that kept the sort launches
+    # k_density alone
+    launches = max(1, prof["passes"][kern])
     if kern == "density":   # the neighbour search and the density sum
         flops_per_launch = (tests * FLOPS_TEST + pairs * FLOPS_PAIR_DENSITY) / launches
     else:                   # the force pass walks the pair list of the density pass
         flops_per_launch = pairs * FLOPS_PAIR_FORCE / launches
     dur_s = prof["ms"][kern] / 1e3 / max(1, prof["timed"][kern])   # mean sampled launch
     achieved = flops_per_launch / dur_s / 1e12 if dur_s > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "k_force" if kern == "force" else "k_density",
+    roofline = {"bound": "alu",
+                "kernel": "k_force" if kern == "force" else "k_density_dense + k_density (one pass)",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops,
                 "traffic": (DENSITY_DRAM_BYTES_PER_EVAL * ours["tot"]["particle_evals"] / launches
@@ -841,6 +847,7 @@ def main():
                 "peak_source": f"{n_sm} SMs (queried) x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                f"(derived; the measured peaks cover HBM copy and bf16 GEMM only)",
                 "avg_launch_us": dur_s * 1e6, "launches": launches,
+                "kernel_launches": int(prof["launches"][kern]),
                 "launches_timed": int(prof["timed"][kern])}
 
     sim = ours["sim_s"]

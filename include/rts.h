@@ -241,6 +241,8 @@ typedef struct rts_profile {
   int64_t launches[RTS_NUM_PHASES];  /* kernel launches per phase                          */
   int64_t kernels;                   /* all kernel launches of this library                */
   int64_t timed[RTS_NUM_PHASES];     /* phase instances that were timed                    */
+  int64_t passes[RTS_NUM_PHASES];    /* phase instances (a sorted density pass launches
+                                        two kernels, of which one returns at once)         */
 } rts_profile;
 
 /* Per-phase event timing: 0 off; 1 every phase instance; 2 every 7th instance of the

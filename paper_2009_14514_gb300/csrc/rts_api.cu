@@ -174,6 +174,9 @@ void rts::make_dev_params(const rts_params& p, DevParams& d) {
     // FP32 residuals: vthr2 = vthr2f + vthr2lo within 2^-48 (finite thresholds)
     d.vthr2lo[L] = std::isfinite(d.vthr2[L]) ? (float)(d.vthr2[L] - (double)d.vthr2f[L]) : 0.f;
     d.athr2lo[L] = std::isfinite(d.athr2[L]) ? (float)(d.athr2[L] - (double)d.athr2f[L]) : 0.f;
+    // the key pass's near-threshold band, as the device forms it (one FP32 product)
+    d.vnear[L] = std::isfinite(d.vthr2f[L]) ? 2e-5f * d.vthr2f[L] : -1.f;
+    d.anear[L] = std::isfinite(d.athr2f[L]) ? 2e-5f * d.athr2f[L] : -1.f;
   }
   d.levels_monotone = 1;
   for (int L = 1; L < p.n_levels; ++L)
@@ -255,6 +258,7 @@ struct Phase {
   int prev, slot;
   Phase(rts_ctx* c_, int ph) : c(c_), prev(c_->cur_phase), slot(-1) {
     c->cur_phase = ph;
+    c->passes[ph] += 1;
     bool timed = c->prof == 1;
     if (c->prof == 2 && (ph == RTS_PHASE_DENSITY || ph == RTS_PHASE_FORCE))
       timed = (c->prof_seen[ph]++ % 7) == 0;
@@ -1011,6 +1015,7 @@ rts_status rts_profile_read(rts_ctx* c, rts_profile* out, int32_t reset) {
     out->ms[k] = c->prof_ms[k];
     out->launches[k] = c->launches[k];
     out->timed[k] = c->prof_timed[k];
+    out->passes[k] = c->passes[k];
   }
   out->kernels = c->kernels;
   if (reset) {
@@ -1018,6 +1023,7 @@ rts_status rts_profile_read(rts_ctx* c, rts_profile* out, int32_t reset) {
     memset(c->launches, 0, sizeof c->launches);
     memset(c->prof_timed, 0, sizeof c->prof_timed);
     memset(c->prof_seen, 0, sizeof c->prof_seen);
+    memset(c->passes, 0, sizeof c->passes);
     c->kernels = 0;
   }
   return RTS_OK;

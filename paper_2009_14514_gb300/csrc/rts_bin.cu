@@ -221,12 +221,8 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
       key_cur[i] = b;
       v2 = vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
       a2 = ai.x * ai.x + ai.y * ai.y + ai.z * ai.z;
-      for (int l = 0; l < P.n_levels; ++l) {   // near a threshold: listed for the exact level
-        const float tv = P.vthr2f[l], ta = P.athr2f[l];
-        if ((isfinite(tv) && fabsf(v2 - tv) <= 2e-5f * tv) ||
-            (isfinite(ta) && fabsf(a2 - ta) <= 2e-5f * ta))
-          near = true;
-      }
+      for (int l = 0; l < P.n_levels; ++l)   // near a threshold: listed for the exact level
+        near |= fabsf(v2 - P.vthr2f[l]) <= P.vnear[l] || fabsf(a2 - P.athr2f[l]) <= P.anear[l];
       const uint32_t sb = sk[it];
       if (sb != b && sb < (uint32_t)P.nblocks) {   // outside its sorted block: how far
         const uint32_t rr = div_by(sb, P.div_nx), rz = div_by(rr, P.div_ny);

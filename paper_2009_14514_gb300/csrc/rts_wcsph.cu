@@ -738,8 +738,10 @@ __device__ __forceinline__ uint32_t stale_runs(const DevParams& P, float3 lo, fl
 // (a bit per candidate inside the guard band), then the exact predicate, kernel sum and
 // list entry for those.  The neighbour list of a particle is in stencil order: fluid rows
 // then boundary rows, each in sorted order.
-__device__ __forceinline__ bool dense_pass(const DevParams& P, int np) {
-  return np > 0 && 2 * (long long)np >= (long long)P.n_fluid;
+// A sorted pass runs k_density_dense when it evaluates at least half of the particles and
+// enough of them to fill the GPU with lanes (lanes_min); otherwise k_density.
+__device__ __forceinline__ bool dense_pass(const DevParams& P, int np, int lanes_min) {
+  return np > 0 && np >= lanes_min && 2 * (long long)np >= (long long)P.n_fluid;
 }
 
 constexpr int kDenseThreads = 256;
@@ -747,9 +749,9 @@ constexpr int kDenseThreads = 256;
 __global__ void __launch_bounds__(kDenseThreads) k_density_dense(
     DevParams P, const uint32_t* __restrict__ key, Ctl* ctl, const uint32_t* __restrict__ cstart,
     const uint32_t* __restrict__ bcstart, PState s, const float4* __restrict__ xb,
-    const uint8_t* __restrict__ cflag, uint32_t* __restrict__ nbl) {
+    const uint8_t* __restrict__ cflag, uint32_t* __restrict__ nbl, int lanes_min) {
   pdl_wait();
-  if (!dense_pass(P, *(volatile int*)&ctl->n_plist)) return;
+  if (!dense_pass(P, *(volatile int*)&ctl->n_plist, lanes_min)) return;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -879,7 +881,8 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
                                                         const uint32_t* __restrict__ bcstart, PState s,
                                                         const float4* __restrict__ xb,
                                                         const uint8_t* __restrict__ cflag,
-                                                        uint32_t* __restrict__ nbl, uint32_t stamp) {
+                                                        uint32_t* __restrict__ nbl, uint32_t stamp,
+                                                        int lanes_min) {
   pdl_wait();
   constexpr int kTab = kStale ? kTabStale : kTabFresh;
   extern __shared__ float4 smem[];
@@ -898,8 +901,7 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
   // candidates) instead of one per active block, so that no warp walks a block with many
   // evaluated particles while the others idle
   const int np = *(volatile int*)&ctl->n_plist;
-  // a sorted pass that evaluates at least half of the particles runs k_density_dense
-  if (!kStale && dense_pass(P, np)) return;
+  if (!kStale && dense_pass(P, np, lanes_min)) return;   // k_density_dense runs this pass
   const bool by_particle = kStale && np <= nwarps;
   const int n_items = by_particle ? np : n_act;
   unsigned long long pairs = 0, tests = 0, kept_tests = 0;
@@ -1399,21 +1401,22 @@ rts_status launch_activity(rts_ctx* c, int mode, int level_g, int mult_g, int64_
 }
 
 rts_status launch_density(rts_ctx* c, bool stale) {
-  note_launch(c, 1);
-  if (stale)
+  const int lanes_min = 8 * 32 * sm_count();   // eight warps of lanes per SM
+  if (stale) {
+    note_launch(c, 1);
     launch_pdl(c->stream, k_density<true>, g_grid_stale > 0 ? g_grid_stale : c->grid_persistent,
                kNbThreads, density_smem(true), c->dp, c->act, (const uint32_t*)c->plist, c->ctl,
-               c->cstart, c->bcstart, c->s, c->xb, c->cflag, c->nbl, c->stamp);
-  else {
+               c->cstart, c->bcstart, c->s, c->xb, c->cflag, c->nbl, c->stamp, lanes_min);
+  } else {
     // the two forms of a sorted pass: each finds from the evaluated-particle count
-    // whether it is the one to run, and the other returns at once
-    note_launch(c, 1);
+    // whether it is the one to run (dense_pass), and the other returns at once
+    note_launch(c, 2);
     launch_pdl(c->stream, k_density_dense, g_grid_dense > 0 ? g_grid_dense : c->grid_persistent,
                kDenseThreads, 0, c->dp, (const uint32_t*)c->key, c->ctl, c->cstart, c->bcstart,
-               c->s, c->xb, c->cflag, c->nbl);
+               c->s, c->xb, c->cflag, c->nbl, lanes_min);
     launch_pdl(c->stream, k_density<false>, c->grid_persistent, kNbThreads, density_smem(false),
                c->dp, c->act, (const uint32_t*)c->plist, c->ctl, c->cstart, c->bcstart, c->s, c->xb,
-               c->cflag, c->nbl, c->stamp);
+               c->cflag, c->nbl, c->stamp, lanes_min);
   }
   return RTS_OK;
 }

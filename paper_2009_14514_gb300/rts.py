@@ -107,12 +107,13 @@ class RtsPcisphInfo(C.Structure):
 
 class RtsProfile(C.Structure):
     _fields_ = [("ms", C.c_double * 8), ("launches", C.c_int64 * 8), ("kernels", C.c_int64),
-                ("timed", C.c_int64 * 8)]
+                ("timed", C.c_int64 * 8), ("passes", C.c_int64 * 8)]
 
     def as_dict(self):
         return {"ms": dict(zip(PHASES, list(self.ms))),
                 "launches": dict(zip(PHASES, list(self.launches))), "kernels": self.kernels,
-                "timed": dict(zip(PHASES, list(self.timed)))}
+                "timed": dict(zip(PHASES, list(self.timed))),
+                "passes": dict(zip(PHASES, list(self.passes)))}
 
 
 def make_params(d: dict) -> RtsParams:

@@ -152,6 +152,46 @@ def test_evaluate_density_neighbours_forces_match_oracle(wide):
     assert np.array_equal(g["x"], st["x"]) and np.array_equal(g["v"], st["v"])
 
 
+def _dam_break_64k():
+    # 40^3 = 64,000 particles: more evaluated particles than eight warps of lanes per SM
+    # of a GB300 (38,912), so a pass that evaluates most of them runs one lane per
+    # particle (k_density_dense); the 8k scenes of the other tests run the warp-per-block
+    # pass
+    return scenes.dam_break((40, 40, 40), 0.01, (1.6, 0.8, 0.8), 5e-5, jitter=2e-4, seed=99,
+                            name="wcsph_dam_break_64k")
+
+
+def test_lane_per_particle_density_pass_matches_oracle():
+    sc = _dam_break_64k()
+    st = dynamic_state(sc, seed=13)
+    ctx = gpu_ctx(sc)
+    rts.rts_set_state(ctx, st["x"], st["v"], a=st["a"], rho=st["rho"], p=st["p"])
+    rts.rts_evaluate(ctx)
+    g = rts.rts_get_state(ctx)
+    o = oracle_state(sc, sc.params, st)
+    o.evaluate()
+    _check_eval(g, o)
+    lists = rts.rts_get_neighbors(ctx)
+    off, idx = O.neighbors_grid(O.make_params(sc.params), st["x"], sc.xb)
+    for i in range(sc.n):
+        assert sorted(lists[i].tolist()) == sorted(idx[off[i]:off[i + 1]].tolist()), i
+
+
+def test_lane_per_particle_density_pass_in_global_steps_matches_oracle():
+    sc = _dam_break_64k()
+    d = params(sc, mode=1)
+    ctx = gpu_ctx(sc, d)
+    o = oracle_state(sc, d, {"x": sc.x, "v": sc.v})
+    for _ in range(3):
+        o.global_step()                            # every particle evaluated each step
+    st = rts.rts_advance(ctx, o.k * d["dt_b"])     # the same steps (the level is exact)
+    assert ctx.substep_index == o.k and st["steps"] == 3
+    assert st["candidate_tests"] == st["tests_performed"]   # no cull: the lane-per-particle pass
+    g = rts.rts_get_state(ctx)
+    np.testing.assert_allclose(g["x"], o.x, atol=2e-5)
+    np.testing.assert_allclose(g["rho"], o.rho, rtol=RHO_RTOL)
+
+
 def test_rest_lattice_density_on_gpu():
     # fluid filling the tank: every particle has a complete lattice (dyadic spacing)
     s = 1.0 / 64
