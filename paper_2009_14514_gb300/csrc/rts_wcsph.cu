@@ -757,7 +757,6 @@ __global__ void __launch_bounds__(kDenseThreads) k_density_dense(
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n = P.n_fluid;
   const int pl = P.nx * P.ny;
-  const float4 far = make_float4(3e38f, 3e38f, 3e38f, 0.f);
   unsigned long long pairs = 0, tests = 0;
   for (int base = warp * 32; base < n; base += nwarps * 32) {
     const int i = base + lane;
@@ -794,19 +793,25 @@ __global__ void __launch_bounds__(kDenseThreads) k_density_dense(
       ncand += je - js;
       for (uint32_t j0 = js; j0 < je; j0 += 32) {
         const uint32_t cnt = je - j0 < 32u ? je - j0 : 32u;
-        // distance tests only, four candidates' loads in flight at a time (past the end
-        // of the run a far point, never near)
+        // distance tests only, four candidates' loads in flight at a time
         uint32_t near = 0;
-        for (uint32_t t0 = 0; t0 < cnt; t0 += 4) {
+        uint32_t t0 = 0;
+        for (; t0 + 4 <= cnt; t0 += 4) {   // whole groups of four, then the rest one by one
           float4 xj[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) xj[u] = t0 + u < cnt ? X[j0 + t0 + u] : far;
+          for (int u = 0; u < 4; ++u) xj[u] = X[j0 + t0 + u];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const float dx = xi.x - xj[u].x, dy = xi.y - xj[u].y, dz = xi.z - xj[u].z;
             const float d2 = dx * dx + dy * dy + dz * dz;
             near |= d2 < P.r2_hi ? (1u << (t0 + u)) : 0u;
           }
+        }
+        for (; t0 < cnt; ++t0) {
+          const float4 xj = X[j0 + t0];
+          const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+          const float d2 = dx * dx + dy * dy + dz * dz;
+          near |= d2 < P.r2_hi ? (1u << t0) : 0u;
         }
         // the exact predicate, kernel sum and list entry of the near ones
         for (uint32_t m = near; m; m &= m - 1u) {
