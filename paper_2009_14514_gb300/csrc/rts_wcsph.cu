@@ -871,6 +871,13 @@ __global__ void __launch_bounds__(kDenseThreads) k_density_dense(
   }
 }
 
+// The next work item of a warp after its first: nwarps + a shared counter (every lane calls).
+__device__ __forceinline__ int next_item(Ctl* ctl, int lane, int nwarps) {
+  int v = 0;
+  if (lane == 0) v = atomicAdd(&ctl->dens_next, 1);
+  return nwarps + __shfl_sync(kFull, v, 0);
+}
+
 // Density pass (Algorithm 1, "find neighborhoods" and "update rho, p"): every evaluated
 // particle tests the candidates kept for its group with the exact predicate, sums m W
 // over its neighbours (itself included), applies the Tait equation and records its
@@ -910,7 +917,9 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
   const bool by_particle = kStale && np <= nwarps;
   const int n_items = by_particle ? np : n_act;
   unsigned long long pairs = 0, tests = 0, kept_tests = 0;
-  for (int t = warp; t < n_items; t += nwarps) {
+  // each warp's first item by its index, every further one from a shared counter, so that
+  // warps that drew cheap blocks take more of them (the blocks' costs differ widely)
+  for (int t = warp; t < n_items; t = next_item(ctl, lane, nwarps)) {
     uint32_t beg = 0, end = 1;   // by_particle: one group, the particle plist[t]
     if (by_particle) {
       if (plist[t] >= (uint32_t)P.n_fluid) {
