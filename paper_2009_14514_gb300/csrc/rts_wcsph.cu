@@ -744,6 +744,13 @@ __device__ __forceinline__ bool dense_pass(const DevParams& P, int np, int lanes
   return np > 0 && np >= lanes_min && 2 * (long long)np >= (long long)P.n_fluid;
 }
 
+// The next work item of a warp after its first: nwarps + a shared counter (every lane calls).
+__device__ __forceinline__ int next_item(int* counter, int lane, int nwarps) {
+  int v = 0;
+  if (lane == 0) v = atomicAdd(counter, 1);
+  return nwarps + __shfl_sync(kFull, v, 0);
+}
+
 constexpr int kDenseThreads = 256;
 
 __global__ void __launch_bounds__(kDenseThreads) k_density_dense(
@@ -758,92 +765,95 @@ __global__ void __launch_bounds__(kDenseThreads) k_density_dense(
   const int n = P.n_fluid;
   const int pl = P.nx * P.ny;
   unsigned long long pairs = 0, tests = 0;
-  for (int base = warp * 32; base < n; base += nwarps * 32) {
-    const int i = base + lane;
-    if (i >= n || !cflag[i]) continue;
-    const float4 xi = s.x[i];
-    const uint32_t b = key[i];
-    if (b >= (uint32_t)P.nblocks) {
-      check_failed(ctl, kChkActive, b);
-      continue;
-    }
-    const int bx = (int)(b % (uint32_t)P.nx), rr = (int)(b / (uint32_t)P.nx);
-    const int by = rr % P.ny, bz = rr / P.ny;
-    const int xlo = bx > 0 ? bx - 1 : 0, xhi = bx + 1 < P.nx ? bx + 1 : P.nx - 1;
-    uint32_t* list = nbl + (size_t)i * P.nbl_cap;
-    float wsum = 0.f;
-    int nn = 0;
-    uint32_t ncand = 0;
-    for (int r = 0; r < 18; ++r) {   // runs 0-8 fluid, 9-17 boundary
-      const int row = r < 9 ? r : r - 9;
-      const int cz = bz + row / 3 - 1, cy = by + row % 3 - 1;
-      if (cz < 0 || cz >= P.nz || cy < 0 || cy >= P.ny) continue;
-      const uint32_t rb = (uint32_t)cz * (uint32_t)pl + (uint32_t)cy * (uint32_t)P.nx;
-      const uint32_t* cs = r < 9 ? cstart : bcstart;
-      const float4* X = r < 9 ? s.x : xb;
-      const uint32_t tag = r < 9 ? 0u : kBoundaryBit;
-      const uint32_t lim = (uint32_t)(r < 9 ? P.n_fluid : P.n_bound);
-      const uint32_t js = __ldg(&cs[rb + xlo]);
-      uint32_t je = __ldg(&cs[rb + xhi + 1]);
-      if (je > lim || js > je) {
-        check_failed(ctl, kChkRun, je);
-        je = js > lim ? js : lim;
-        if (js >= je) continue;
+  // each warp's first 32 positions by its index, every further 32 from a shared counter
+  for (int base = warp * 32; base < n; base = 32 * next_item(&ctl->dens_next, lane, nwarps)) {
+    do {   // this lane's particle (break: nothing to do)
+      const int i = base + lane;
+      if (i >= n || !cflag[i]) break;
+      const float4 xi = s.x[i];
+      const uint32_t b = key[i];
+      if (b >= (uint32_t)P.nblocks) {
+        check_failed(ctl, kChkActive, b);
+        break;
       }
-      ncand += je - js;
-      for (uint32_t j0 = js; j0 < je; j0 += 32) {
-        const uint32_t cnt = je - j0 < 32u ? je - j0 : 32u;
-        // distance tests only, four candidates' loads in flight at a time
-        uint32_t near = 0;
-        uint32_t t0 = 0;
-        for (; t0 + 4 <= cnt; t0 += 4) {   // whole groups of four, then the rest one by one
-          float4 xj[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) xj[u] = X[j0 + t0 + u];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float dx = xi.x - xj[u].x, dy = xi.y - xj[u].y, dz = xi.z - xj[u].z;
+      const int bx = (int)(b % (uint32_t)P.nx), rr = (int)(b / (uint32_t)P.nx);
+      const int by = rr % P.ny, bz = rr / P.ny;
+      const int xlo = bx > 0 ? bx - 1 : 0, xhi = bx + 1 < P.nx ? bx + 1 : P.nx - 1;
+      uint32_t* list = nbl + (size_t)i * P.nbl_cap;
+      float wsum = 0.f;
+      int nn = 0;
+      uint32_t ncand = 0;
+      for (int r = 0; r < 18; ++r) {   // runs 0-8 fluid, 9-17 boundary
+        const int row = r < 9 ? r : r - 9;
+        const int cz = bz + row / 3 - 1, cy = by + row % 3 - 1;
+        if (cz < 0 || cz >= P.nz || cy < 0 || cy >= P.ny) continue;
+        const uint32_t rb = (uint32_t)cz * (uint32_t)pl + (uint32_t)cy * (uint32_t)P.nx;
+        const uint32_t* cs = r < 9 ? cstart : bcstart;
+        const float4* X = r < 9 ? s.x : xb;
+        const uint32_t tag = r < 9 ? 0u : kBoundaryBit;
+        const uint32_t lim = (uint32_t)(r < 9 ? P.n_fluid : P.n_bound);
+        const uint32_t js = __ldg(&cs[rb + xlo]);
+        uint32_t je = __ldg(&cs[rb + xhi + 1]);
+        if (je > lim || js > je) {
+          check_failed(ctl, kChkRun, je);
+          je = js > lim ? js : lim;
+          if (js >= je) continue;
+        }
+        ncand += je - js;
+        for (uint32_t j0 = js; j0 < je; j0 += 32) {
+          const uint32_t cnt = je - j0 < 32u ? je - j0 : 32u;
+          // distance tests only, four candidates' loads in flight at a time
+          uint32_t near = 0;
+          uint32_t t0 = 0;
+          for (; t0 + 4 <= cnt; t0 += 4) {   // whole groups of four, then the rest one by one
+            float4 xj[4];
+  #pragma unroll
+            for (int u = 0; u < 4; ++u) xj[u] = X[j0 + t0 + u];
+  #pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float dx = xi.x - xj[u].x, dy = xi.y - xj[u].y, dz = xi.z - xj[u].z;
+              const float d2 = dx * dx + dy * dy + dz * dz;
+              near |= d2 < P.r2_hi ? (1u << (t0 + u)) : 0u;
+            }
+          }
+          for (; t0 < cnt; ++t0) {
+            const float4 xj = X[j0 + t0];
+            const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
             const float d2 = dx * dx + dy * dy + dz * dz;
-            near |= d2 < P.r2_hi ? (1u << (t0 + u)) : 0u;
+            near |= d2 < P.r2_hi ? (1u << t0) : 0u;
           }
-        }
-        for (; t0 < cnt; ++t0) {
-          const float4 xj = X[j0 + t0];
-          const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-          const float d2 = dx * dx + dy * dy + dz * dz;
-          near |= d2 < P.r2_hi ? (1u << t0) : 0u;
-        }
-        // the exact predicate, kernel sum and list entry of the near ones
-        for (uint32_t m = near; m; m &= m - 1u) {
-          const uint32_t j = j0 + (uint32_t)(__ffs(m) - 1);
-          const float4 xj = X[j];
-          const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-          const float d2 = dx * dx + dy * dy + dz * dz;
-          if (!(d2 < P.r2_lo || nbr_exact(P, xi, xj))) continue;
-          bool put = true;
-          if (d2 > 0.f) {
-            wsum += spline_W(P, d2 * rsqrtf(d2) * P.inv_h);
-          } else {
-            wsum += P.sigma;   // the particle itself, or a coincident neighbour
-            put = tag != 0u || j != (uint32_t)i;
-          }
-          if (put) {
-            if (nn < P.nbl_cap) list[nn] = j | tag;
-            ++nn;
+          // the exact predicate, kernel sum and list entry of the near ones
+          for (uint32_t m = near; m; m &= m - 1u) {
+            const uint32_t j = j0 + (uint32_t)(__ffs(m) - 1);
+            const float4 xj = X[j];
+            const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            if (!(d2 < P.r2_lo || nbr_exact(P, xi, xj))) continue;
+            bool put = true;
+            if (d2 > 0.f) {
+              wsum += spline_W(P, d2 * rsqrtf(d2) * P.inv_h);
+            } else {
+              wsum += P.sigma;   // the particle itself, or a coincident neighbour
+              put = tag != 0u || j != (uint32_t)i;
+            }
+            if (put) {
+              if (nn < P.nbl_cap) list[nn] = j | tag;
+              ++nn;
+            }
           }
         }
       }
-    }
-    if (nn > P.nbl_cap) set_status(ctl, RTS_ERR_CAPACITY);
-    const float rho = P.m * wsum;
-    const float p = tait(P, rho);
-    s.rho[i] = rho;
-    s.prs[i] = p;
-    s.nbr[i] = nn;
-    s.x[i].w = p / (rho * rho);
-    s.v[i].w = rho;
-    pairs += (unsigned long long)nn;
-    tests += ncand;
+      if (nn > P.nbl_cap) set_status(ctl, RTS_ERR_CAPACITY);
+      const float rho = P.m * wsum;
+      const float p = tait(P, rho);
+      s.rho[i] = rho;
+      s.prs[i] = p;
+      s.nbr[i] = nn;
+      s.x[i].w = p / (rho * rho);
+      s.v[i].w = rho;
+      pairs += (unsigned long long)nn;
+      tests += ncand;
+    } while (false);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -871,12 +881,6 @@ __global__ void __launch_bounds__(kDenseThreads) k_density_dense(
   }
 }
 
-// The next work item of a warp after its first: nwarps + a shared counter (every lane calls).
-__device__ __forceinline__ int next_item(Ctl* ctl, int lane, int nwarps) {
-  int v = 0;
-  if (lane == 0) v = atomicAdd(&ctl->dens_next, 1);
-  return nwarps + __shfl_sync(kFull, v, 0);
-}
 
 // Density pass (Algorithm 1, "find neighborhoods" and "update rho, p"): every evaluated
 // particle tests the candidates kept for its group with the exact predicate, sums m W
@@ -919,7 +923,7 @@ __global__ void __launch_bounds__(kNbThreads, 6) k_density(DevParams P, const ui
   unsigned long long pairs = 0, tests = 0, kept_tests = 0;
   // each warp's first item by its index, every further one from a shared counter, so that
   // warps that drew cheap blocks take more of them (the blocks' costs differ widely)
-  for (int t = warp; t < n_items; t = next_item(ctl, lane, nwarps)) {
+  for (int t = warp; t < n_items; t = next_item(&ctl->dens_next, lane, nwarps)) {
     uint32_t beg = 0, end = 1;   // by_particle: one group, the particle plist[t]
     if (by_particle) {
       if (plist[t] >= (uint32_t)P.n_fluid) {
