@@ -54,10 +54,10 @@ FLOPS_PAIR_FORCE = 24
 # rollout itself (16 substeps from the warm state at t = 1 s, --profile-warm); the traffic
 # per pass of the benchmark is this figure times the pass's evaluations.  Re-measure when
 # a density kernel changes.
-DENSITY_DRAM_BYTES_PER_EVAL = 264.6
+DENSITY_DRAM_BYTES_PER_EVAL = 259.3
 DENSITY_TRAFFIC_SOURCE = ("ncu dram__bytes of every density launch (k_density_dense, k_density) "
                           "of 16 substeps from the warm state at t = 1 s "
-                          "(profiles/k_density_warm_window_1m.md), 264.6 B per evaluation, "
+                          "(profiles/k_density_warm_window_1m.md), 259.3 B per evaluation, "
                           "times this run's evaluations per pass")
 
 
