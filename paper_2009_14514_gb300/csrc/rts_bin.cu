@@ -89,7 +89,6 @@ __global__ void k_predict_key(DevParams P, int n, float4* __restrict__ x, float4
     ctl->n_act = 0;
     ctl->n_plist = 0;
     ctl->dens_next = 0;
-    ctl->force_next = 0;
     // a following pass that keeps this sort counts into a clean slot
     ctl->n_filled_light[0] = ctl->n_filled_light[1] = 0;
     ctl->n_near[0] = ctl->n_near[1] = 0;
@@ -166,7 +165,6 @@ __global__ void __launch_bounds__(kLightThreads) k_predict_light(
     ctl->n_act = 0;
     ctl->n_plist = 0;
     ctl->dens_next = 0;
-    ctl->force_next = 0;
     ctl->disp_bits[(stamp + 1) & 1] = 0u;
     ctl->n_filled_light[(stamp + 1) & 1] = 0;
     ctl->n_near[(stamp + 1) & 1] = 0;

@@ -83,7 +83,6 @@ struct Ctl {
   int n_act;                     // active blocks in the work list
   int n_plist;                   // evaluated particles in the particle work list
   int dens_next;                 // density pass: work items handed out after the first round
-  int force_next;                // force pass: the same
   unsigned long long evals;      // evaluated particles
   unsigned long long pairs;      // neighbour pairs of evaluated particles
   unsigned long long act_blocks; // active blocks summed over steps

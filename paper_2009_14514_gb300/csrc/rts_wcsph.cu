@@ -1118,18 +1118,13 @@ __device__ __forceinline__ void force_rounds(const DevParams& P, const uint32_t*
                                              unsigned* vm, unsigned* am) {
   const int lane = threadIdx.x & 31;
   const int sub = lane & (LANES - 1);
-  constexpr int kPer = 32 / LANES;          // list entries per warp round
-  constexpr int kRounds = LANES >= 4 ? 4 : 1;   // rounds per work item
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int items = (np + kPer * kRounds - 1) / (kPer * kRounds);
+  const int slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LANES) + lane / LANES;
+  const int nslots = ((gridDim.x * blockDim.x) >> 5) * (32 / LANES);
   const float4* __restrict__ xf = s.x;
   const float4* __restrict__ vf = s.v;
-  // each warp's first item by its index, every further one from a shared counter (an
-  // item of several rounds, so that the counter is not contended)
-  for (int it = warp; it < items; it = next_item(&ctl->force_next, lane, nwarps))
-  for (int rr = 0; rr < kRounds; ++rr) {
-    const int t = (it * kRounds + rr) * kPer + lane / LANES;
+  const int rounds = (np + nslots - 1) / nslots;
+  for (int r = 0; r < rounds; ++r) {
+    const int t = r * nslots + slot;
     float ax = 0.f, ay = 0.f, az = 0.f;
     int i = -1;
     if (t < np) {
