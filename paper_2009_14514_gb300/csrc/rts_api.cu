@@ -175,8 +175,8 @@ void rts::make_dev_params(const rts_params& p, DevParams& d) {
     d.vthr2lo[L] = std::isfinite(d.vthr2[L]) ? (float)(d.vthr2[L] - (double)d.vthr2f[L]) : 0.f;
     d.athr2lo[L] = std::isfinite(d.athr2[L]) ? (float)(d.athr2[L] - (double)d.athr2f[L]) : 0.f;
     // the key pass's near-threshold band, as the device forms it (one FP32 product)
-    d.vnear[L] = std::isfinite(d.vthr2f[L]) ? 2e-5f * d.vthr2f[L] : -1.f;
-    d.anear[L] = std::isfinite(d.athr2f[L]) ? 2e-5f * d.athr2f[L] : -1.f;
+    d.vnear[L] = std::isfinite(d.vthr2f[L]) ? 2e-6f * d.vthr2f[L] : -1.f;
+    d.anear[L] = std::isfinite(d.athr2f[L]) ? 2e-6f * d.athr2f[L] : -1.f;
   }
   d.levels_monotone = 1;
   for (int L = 1; L < p.n_levels; ++L)

@@ -59,7 +59,7 @@ struct DevParams {
   double vthr2[kMaxLevels], athr2[kMaxLevels];
   float vthr2f[kMaxLevels], athr2f[kMaxLevels];   // the same thresholds rounded to FP32
   float vthr2lo[kMaxLevels], athr2lo[kMaxLevels]; // and their FP32 residuals
-  float vnear[kMaxLevels], anear[kMaxLevels];     // 2e-5 of each finite FP32 threshold, else -1
+  float vnear[kMaxLevels], anear[kMaxLevels];     // 2e-6 of each finite FP32 threshold, else -1
   int eq1[kMaxLevels];
   int levels_monotone;   // both thresholds non-increasing in the level (see k_block_levels)
   int force_level;

@@ -38,14 +38,17 @@ __device__ __forceinline__ int pick_level(const DevParams& P, double v2, double 
   return L;
 }
 
-// Section 3.1 in FP32: thresholds rounded to FP32; a maximum within 1e-5 of a finite
-// threshold is undecided in FP32 (its error is below 3e-7 relative).
+// Section 3.1 in FP32: thresholds rounded to FP32; a maximum within 1e-6 of a finite
+// threshold is undecided in FP32.  The FP32 square norm is within 3e-7 relative of the
+// FP64 one of the same FP32 components (at most five roundings of half an ulp each, all
+// terms non-negative) and the FP32 threshold within 6e-8 of the FP64 one, so outside the band
+// both decide alike, with a margin of more than twice those errors.
 __device__ __forceinline__ int pick_level_f(const DevParams& P, float v2, float a2, bool* undecided) {
   int L = 0;
   for (int l = 0; l < P.n_levels; ++l) {
     const float tv = P.vthr2f[l], ta = P.athr2f[l];
-    if (isfinite(tv) && fabsf(v2 - tv) <= 1e-5f * tv) *undecided = true;
-    if (isfinite(ta) && fabsf(a2 - ta) <= 1e-5f * ta) *undecided = true;
+    if (isfinite(tv) && fabsf(v2 - tv) <= 1e-6f * tv) *undecided = true;
+    if (isfinite(ta) && fabsf(a2 - ta) <= 1e-6f * ta) *undecided = true;
     if (P.eq1[l] && v2 <= tv && a2 <= ta) L = l;
   }
   return L;
@@ -122,15 +125,15 @@ static __device__ __noinline__ int level_exact_warp(const DevParams& P, uint32_t
       ai.y += pa.y;
       ai.z += pa.z;
     }
-    // outside 2e-5 of a threshold the FP32 norm decides (its error is below 3e-7)
+    // outside 2e-6 of a threshold the FP32 norm decides (its error is below 3e-7)
     const float v2 = vi.x * vi.x + vi.y * vi.y + vi.z * vi.z;
     const float a2 = ai.x * ai.x + ai.y * ai.y + ai.z * ai.z;
     for (int l = 0; l < P.n_levels; ++l) {
       const float tv = P.vthr2f[l], ta = P.athr2f[l];
       bool ok_v = v2 <= tv, ok_a = a2 <= ta;
-      if (isfinite(tv) && fabsf(v2 - tv) <= 2e-5f * tv)
+      if (isfinite(tv) && fabsf(v2 - tv) <= 2e-6f * tv)
         ok_v = norm2_le(vi.x, vi.y, vi.z, tv, P.vthr2lo[l], P.vthr2[l]);
-      if (isfinite(ta) && fabsf(a2 - ta) <= 2e-5f * ta)
+      if (isfinite(ta) && fabsf(a2 - ta) <= 2e-6f * ta)
         ok_a = norm2_le(ai.x, ai.y, ai.z, ta, P.athr2lo[l], P.athr2[l]);
       if (!(ok_v && ok_a)) pass &= ~(1u << l);
     }
@@ -143,9 +146,9 @@ static __device__ __noinline__ int level_exact_warp(const DevParams& P, uint32_t
 }
 
 // The same decision on a substep that kept the sort, from the particles the key pass
-// listed as near a threshold (within 2e-5 of one in FP32): a threshold that the block's
+// listed as near a threshold (within 2e-6 of one in FP32): a threshold that the block's
 // FP32 maximum (vm, am) decides keeps that decision; an undecided one (the maximum within
-// 1e-5 of it) can only be failed by listed particles, since every other particle of the
+// 1e-6 of it) can only be failed by listed particles, since every other particle of the
 // block lies below it by more than the FP32 error, so the listed particles of block b
 // decide it exactly.  The whole warp takes part (every lane calls it with the same b).
 static __device__ __noinline__ int level_from_near(const DevParams& P, uint32_t b, float vm,
@@ -165,9 +168,9 @@ static __device__ __noinline__ int level_from_near(const DevParams& P, uint32_t 
     for (int l = 0; l < P.n_levels; ++l) {
       const float tv = P.vthr2f[l], ta = P.athr2f[l];
       bool ok_v = v2 <= tv, ok_a = a2 <= ta;
-      if (isfinite(tv) && fabsf(v2 - tv) <= 2e-5f * tv)
+      if (isfinite(tv) && fabsf(v2 - tv) <= 2e-6f * tv)
         ok_v = norm2_le(vi.x, vi.y, vi.z, tv, P.vthr2lo[l], P.vthr2[l]);
-      if (isfinite(ta) && fabsf(a2 - ta) <= 2e-5f * ta)
+      if (isfinite(ta) && fabsf(a2 - ta) <= 2e-6f * ta)
         ok_a = norm2_le(ai.x, ai.y, ai.z, ta, P.athr2lo[l], P.athr2[l]);
       if (!ok_v) pv &= ~(1u << l);
       if (!ok_a) pa &= ~(1u << l);
@@ -178,8 +181,8 @@ static __device__ __noinline__ int level_from_near(const DevParams& P, uint32_t 
   int L = 0;
   for (int l = 0; l < P.n_levels; ++l) {
     const float tv = P.vthr2f[l], ta = P.athr2f[l];
-    const bool ok_v = (isfinite(tv) && fabsf(vm - tv) <= 1e-5f * tv) ? ((pv >> l) & 1u) : vm <= tv;
-    const bool ok_a = (isfinite(ta) && fabsf(am - ta) <= 1e-5f * ta) ? ((pa >> l) & 1u) : am <= ta;
+    const bool ok_v = (isfinite(tv) && fabsf(vm - tv) <= 1e-6f * tv) ? ((pv >> l) & 1u) : vm <= tv;
+    const bool ok_a = (isfinite(ta) && fabsf(am - ta) <= 1e-6f * ta) ? ((pa >> l) & 1u) : am <= ta;
     if (P.eq1[l] && ok_v && ok_a) L = l;
   }
   return L;
@@ -198,7 +201,7 @@ static __device__ __noinline__ int level_from_near(const DevParams& P, uint32_t 
 // largest Eq. 1-admissible level up to min(Lv, La), a non-decreasing function of that
 // minimum; the smallest raw level over the 27 blocks is therefore the raw level of the
 // union of their particles, decided from the largest of their maxima.  Only when that
-// decision is undecided (a maximum within 1e-5 of a threshold) does the thread decide
+// decision is undecided (a maximum within 1e-6 of a threshold) does the thread decide
 // each neighbour's raw level on its own and take the minimum, as it always does without
 // the monotone thresholds.  An undecided raw level is taken from the block's particles
 // with the exact decision of the double-precision definition (level_from_near /
@@ -207,14 +210,14 @@ static __device__ __noinline__ int level_from_near(const DevParams& P, uint32_t 
 // filled2, the blocks filled since; a block whose maxima carry an older stamp has emptied
 // since the sort and gets no level.  Writes the raw level (raw) and R_min, or the forced
 // level (blevel), both stamped.
-// A lower bound of the exact level from FP32 maxima: every threshold within 1e-5 of them
+// A lower bound of the exact level from FP32 maxima: every threshold within 1e-6 of them
 // counts as failed (the exact decision can only pass it).
 __device__ __forceinline__ int pick_level_lo(const DevParams& P, float v2, float a2) {
   int L = 0;
   for (int l = 0; l < P.n_levels; ++l) {
     const float tv = P.vthr2f[l], ta = P.athr2f[l];
-    const bool ok_v = isfinite(tv) ? v2 < tv - 1e-5f * tv : true;
-    const bool ok_a = isfinite(ta) ? a2 < ta - 1e-5f * ta : true;
+    const bool ok_v = isfinite(tv) ? v2 < tv - 1e-6f * tv : true;
+    const bool ok_a = isfinite(ta) ? a2 < ta - 1e-6f * ta : true;
     if (P.eq1[l] && ok_v && ok_a) L = l;
   }
   return L;
